@@ -1,0 +1,81 @@
+"""The oracle's pins must catch plausible mistakes.
+
+Each case copies the oracle source, plants one mistake in the copy (a dropped
+term, a wrong comparison, a wrong index, a wrong tie rule), compiles it on the
+CPU and runs the pins of test_oracle_pins.py against it: at least one pin must
+fail. The real oracle is restored afterwards.
+"""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import pytest
+
+import oracle
+import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "scan_oracle.cpp")
+LSH = os.path.join(os.path.dirname(oracle.__file__), "lsh_oracle.cpp")
+
+MUTANTS = {
+    "cosine without the closed +1": ("const int64_t prod = (du + 1) * (dv + 1);",
+                                     "const int64_t prod = du * dv;"),
+    "jaccard union without -c": ("return (double)c / (double)(du + 1 + dv + 1 - c);",
+                                 "return (double)c / (double)(du + 1 + dv + 1);"),
+    "count misses v itself": ("int64_t c = mark[v];  // v itself is in N̄(v)",
+                              "int64_t c = 0;"),
+    "strict eps in the core test": ("ne += sim[i] >= eps;", "ne += sim[i] > eps;"),
+    "core order membership off by one": ("if (deg_of(off, v) + 1 >= mu) row.emplace_back",
+                                         "if (deg_of(off, v) >= mu) row.emplace_back"),
+    "border takes the least similar core": (
+        "if (core[no_id[i]]) { labels[v] = dsu.find(no_id[i]); break; }",
+        "if (core[no_id[i]]) { labels[v] = dsu.find(no_id[i]); }"),
+    "union hooks to the larger root": ("if (a < b) p[b] = a; else p[a] = b;",
+                                       "if (a > b) p[b] = a; else p[a] = b;"),
+    "hub with a single neighbouring cluster": ("else if (l != first) { hub = true; break; }",
+                                               "else { hub = true; break; }"),
+    "neighbour order ascending": (
+        "return a.first > b.first;\n                     });\n    for (size_t j",
+        "return a.first < b.first;\n                     });\n    for (size_t j"),
+}
+
+PINS = [
+    lambda: pins.test_counts_equal_dense_square(25, 0.2, 2),
+    pins.test_triangle_identity,
+    pins.test_clique_all_one,
+    lambda: pins.test_star(7),
+    pins.test_bridged_cliques_hub,
+    pins.test_sigma_exactly_eps_counts,
+    pins.test_isolated_vertices_are_outliers,
+    pins.test_vertex_next_to_one_cluster_is_outlier,
+    pins.test_worked_example_sigma,
+    pins.test_figure_captions,
+    lambda: pins.test_order_invariants(oracle.COSINE),
+    pins.test_exhaustive_five_vertices,
+]
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name, tmp_path):
+    old, new = MUTANTS[name]
+    text = open(SRC).read()
+    assert text.count(old) == 1, name
+    mutated = tmp_path / "scan_oracle.cpp"
+    mutated.write_text(text.replace(old, new))
+    shutil.copy(LSH, tmp_path / "lsh_oracle.cpp")
+    so = tmp_path / "libmutant.so"
+    subprocess.run(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", str(mutated),
+                    str(tmp_path / "lsh_oracle.cpp"), "-o", str(so)], check=True)
+    saved = oracle._load()
+    oracle._lib = oracle.bind(ctypes.CDLL(str(so)))
+    caught = []
+    try:
+        for pin in PINS:
+            try:
+                pin()
+            except (AssertionError, RuntimeError, ValueError, IndexError):
+                caught.append(pin)
+    finally:
+        oracle._lib = saved
+    assert caught, f"no pin caught the mutant '{name}'"
