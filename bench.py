@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Benchmark: exact SCAN index build on R-MAT scale 24 (edge factor 16), one GB300.
+
+One step = one exact cosine index build through the C ABI (orientation,
+closed counts, similarities, neighbour order, core order) over the resident
+CSR of the R-MAT scale-24 graph, then the release of the index. The headline
+`value` is undirected edges per second of that build; `e2e` is the same build
+from pinned host buffers (CSR upload inside the timed region) followed by one
+(mu=5, eps=0.5) query whose labels are read back to pinned host memory.
+
+`roofline` reports the dominant kernel (closed-count enumeration) against the
+measured HBM copy bandwidth; `cpu_baseline` times the CPU oracle on a bounded
+sample. `--impl reference` times the CPU oracle itself as the reference arm.
+
+Launch: python bench.py [--gpus 1] [--steps K] [--warmup W]; for N > 1 under
+torchrun each rank builds its own replica (the build is not sharded).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gscan", choices=["gscan", "reference"])
+    p.add_argument("--scale", type=int, default=24)
+    p.add_argument("--edgefactor", type=int, default=16)
+    p.add_argument("--seed", type=int, default=1)
+    p.add_argument("--kind", default="cosine", choices=["cosine", "jaccard"])
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash() -> str:
+    src = os.path.join(ROOT, "paper_2012_11188_gb300", "csrc", "triangles.cu")
+    return hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+
+
+def profiled_traffic(arcs: int):
+    """DRAM bytes per counting launch from the committed ncu summary, scaled to
+    this graph by arcs, or None when the kernel source changed since capture."""
+    path = os.path.join(ROOT, "profiles", "counting_kernel_rmat.txt")
+    try:
+        kv = {}
+        for line in open(path):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("source_sha1") != kernel_source_hash():
+            return None
+        per_arc = float(kv["dram_bytes_per_launch"]) / float(kv["arcs"])
+        return per_arc * arcs if int(kv["arcs"]) != arcs else float(kv["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def algorithmic_bytes(off_t, adj_t):
+    """Bytes the paper's oriented merge reads (4 * sum over oriented u->v of
+    d+_u + d+_v = 4 * sum_u d_u d+_u), plus the CSR and output bytes of a build."""
+    import torch
+    n = off_t.shape[0] - 1
+    deg = (off_t[1:] - off_t[:-1])
+    src = torch.repeat_interleave(torch.arange(n, device=off_t.device), deg)
+    dsrc, ddst = deg[src], deg[adj_t.long()]
+    up = (dsrc < ddst) | ((dsrc == ddst) & (src < adj_t.long()))
+    dplus = torch.bincount(src[up], minlength=n)
+    del src, dsrc, ddst, up
+    touch = 4 * int((deg * dplus).sum().item())
+    hash_probe = 4 * int((dplus * dplus).sum().item())
+    A = int(adj_t.shape[0])
+    csr = 8 * (n + 1) + 4 * A
+    out = 60 * A + 4 * n
+    return {"touch": touch, "csr": csr, "out": out, "hash_probe": hash_probe,
+            "max_out_degree": int(dplus.max().item()) if n else 0}
+
+
+def cpu_baseline(edgefactor: int, seed: int, kind: int, repeats: int = 2):
+    import graphgen
+    import oracle
+    g = graphgen.rmat(18, edgefactor, seed=seed)
+    ts = []
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        oracle.Index(g, kind)
+        ts.append(time.perf_counter() - t0)
+    t = statistics.median(ts)
+    return {"value": g.edges / t, "unit": "edges/s", "cores": 1, "kind": "oracle",
+            "sample": f"full oracle index build (counts, similarities, NO, CO) of R-MAT scale 18 "
+                      f"edge factor {edgefactor} ({g.edges} edges), median of {repeats}, single thread"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import graphgen
+    import oracle
+    kind = oracle.COSINE if args.kind == "cosine" else oracle.JACCARD
+    g = graphgen.rmat(18, args.edgefactor, seed=args.seed)
+    for _ in range(args.warmup):
+        oracle.Index(g, kind)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.Index(g, kind)
+    dt = time.perf_counter() - t0
+    value = g.edges * args.steps / dt
+    sample = (f"full oracle index build of R-MAT scale 18 edge factor {args.edgefactor} "
+              f"({g.edges} edges) per step, single thread")
+    print(json.dumps({
+        "impl": "reference", "metric": f"index-build edges/s (R-MAT s{args.scale})",
+        "value": value, "unit": "edges/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"exact {args.kind} SCAN index build, R-MAT scale {args.scale} "
+                               f"edge factor {args.edgefactor} (oracle runs a scale-18 sample)"},
+        "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    ws, rank, local = dist_env()
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import graphgen
+    import paper_2012_11188_gb300 as gs
+
+    kind = gs.COSINE if args.kind == "cosine" else gs.JACCARD
+    t_gen = time.perf_counter()
+    g = graphgen.rmat(args.scale, args.edgefactor, seed=args.seed)
+    t_gen = time.perf_counter() - t_gen
+    off_d = torch.from_numpy(g.off).cuda()
+    adj_d = torch.from_numpy(g.adj).cuda()
+    stream = torch.cuda.current_stream()
+    alg = algorithmic_bytes(off_d, adj_d)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    # warm-up
+    for _ in range(args.warmup):
+        ix = gs.ScanIndex.build((off_d, adj_d), kind, stream=stream)
+        ix.free()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    count_ms, step_ms, phases = [], [], []
+    barrier()
+    torch.cuda.synchronize()
+    launches0 = gs.kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        e_a = torch.cuda.Event(enable_timing=True)
+        e_b = torch.cuda.Event(enable_timing=True)
+        e_a.record(stream)
+        ix = gs.ScanIndex.build((off_d, adj_d), kind, stream=stream)
+        e_b.record(stream)
+        tm = gs.last_build_timings()
+        count_ms.append(tm.count_ms)
+        phases.append(tm)
+        ix.free()
+        e_b.synchronize()
+        step_ms.append(e_a.elapsed_time(e_b))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = gs.kernel_launches() - launches0
+    clocks = sampler.stop()
+    total_ms = ev0.elapsed_time(ev1)
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = g.edges * args.steps * ws / (total_ms / 1000.0)
+
+    # end to end through the public API from pinned host buffers
+    off_h = torch.from_numpy(g.off).pin_memory()
+    adj_h = torch.from_numpy(g.adj).pin_memory()
+    lab_h = torch.empty(g.n, dtype=torch.int32).pin_memory()
+    ix = gs.ScanIndex.build((off_h, adj_h), kind, stream=stream)
+    ix.query(5, 0.5, out=lab_h, stream=stream)
+    ix.free()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        ix = gs.ScanIndex.build((off_h, adj_h), kind, stream=stream)
+        ix.query(5, 0.5, out=lab_h, stream=stream)
+        ix.free()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    e2e = {"value": g.edges / e2e_s, "unit": "edges/s",
+           "h2d_bytes_per_step": int(g.off.nbytes + g.adj.nbytes),
+           "d2h_bytes_per_step": int(lab_h.numel() * 4)}
+
+    # queries on the resident index
+    ix = gs.ScanIndex.build((off_d, adj_d), kind, stream=stream)
+    lab_d = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    qres = {}
+    for eps in (0.3, 0.5, 0.7):
+        ix.query(5, eps, out=lab_d, stream=stream)
+        ts = []
+        for _ in range(5):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ix.query(5, eps, out=lab_d, stream=stream)
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        qres[f"mu5_eps{eps}_ms"] = round(statistics.median(ts), 3)
+    nq = 16
+    mus = np.array([2, 4, 8, 16, 32, 5, 5, 5] * 2, dtype=np.int32)[:nq]
+    epss = np.array([0.1, 0.3, 0.5, 0.7, 0.9, 0.3, 0.5, 0.7] * 2)[:nq]
+    labq = torch.empty((nq, g.n), dtype=torch.int32, device="cuda")
+    ix.query_batch(mus, epss, out=labq, stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ix.query_batch(mus, epss, out=labq, stream=stream)
+    torch.cuda.synchronize()
+    qres["batch16_queries_per_s"] = round(nq / (time.perf_counter() - t0), 1)
+    ix.free()
+
+    peak, peak_src = measured_peak()
+    cnt_ms = statistics.mean(count_ms)
+    achieved = alg["touch"] / (cnt_ms / 1000.0) / 1e9
+    traffic = profiled_traffic(g.arcs)
+    out = {
+        "metric": f"index-build edges/s (R-MAT s{args.scale})",
+        "value": value, "unit": "edges/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {
+            "workload": f"exact {args.kind} SCAN index build, R-MAT scale {args.scale} edge factor "
+                        f"{args.edgefactor} (a,b,c,d = .57,.19,.19,.05), seed {args.seed}",
+            "n": g.n, "edges": g.edges, "arcs": g.arcs, "max_degree": int(np.diff(g.off).max()),
+            "max_out_degree": alg["max_out_degree"],
+            "l2": "inputs larger than L2 (CSR %.2f GB; index %.1f GB)" % (
+                (g.off.nbytes + g.adj.nbytes) / 1e9, 28 * g.arcs / 1e9),
+            "parallelism": "replicas" if ws > 1 else "single GPU",
+        },
+        "phases_ms": {k: round(statistics.mean(getattr(p, k) for p in phases), 3)
+                      for k in ("orient_ms", "count_ms", "sims_ms", "neighbor_order_ms",
+                                "core_order_ms", "total_ms")},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "k_triangles (closed counts by oriented triangle enumeration)",
+                     "algorithmic_bytes_per_launch": alg["touch"],
+                     "hash_probe_bytes_per_launch": alg["hash_probe"],
+                     "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"},
+        "build_roofline": {"bytes": alg["touch"] + alg["csr"] + alg["out"],
+                           "achieved_gbs": (alg["touch"] + alg["csr"] + alg["out"])
+                           / (statistics.mean(step_ms) / 1000.0) / 1e9},
+        "query": qres,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "graph_generation_s": round(t_gen, 1),
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.edgefactor, args.seed,
+                                           0 if args.kind == "cosine" else 1)
+    if rank == 0:
+        print(json.dumps(out))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

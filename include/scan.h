@@ -1,0 +1,162 @@
+/*
+ * scan.h -- C ABI of the GB300 index-based SCAN library (libscan.so).
+ *
+ * The library builds the SCAN index of Tseng, Dhulipala and Shun, "Parallel
+ * Index-Based Structural Graph Clustering and Its Approximation" (SIGMOD
+ * 2021), on one NVIDIA GPU, and answers (mu, eps) clustering queries from it.
+ *
+ *   index = per-edge similarity sigma over closed neighbourhoods (Section 3.1),
+ *           the neighbour order NO and the core order CO (Section 3.2,
+ *           Algorithm 2), optionally with LSH-approximated similarities
+ *           (Sections 5 and 6.3);
+ *   query = GetCores / Cluster / AssignNonCores (Algorithms 3-5), with the
+ *           union-find of Section 6.2 and the hub/outlier pass of Section 4.3.
+ *
+ * Conventions shared by every entry point
+ *  - Every function returns a scan_status (0 = SCAN_OK, negative = error) and
+ *    never aborts the process. scan_strerror() names a status.
+ *  - Graphs are simple and undirected (Section 2.2): CSR with ascending
+ *    adjacency lists, no self-loops, no duplicates, every arc u->v matched by
+ *    v->u. Vertex ids are 0-based int32 (the paper numbers them 1..n).
+ *  - Pointers passed in are borrowed for the duration of the call only, unless
+ *    stated otherwise. Output buffers belong to the caller. "host or device"
+ *    buffers are classified with cudaPointerGetAttributes: device (or managed)
+ *    memory is written by kernels, anything else is treated as host memory and
+ *    filled by a copy.
+ *  - `stream` is a cudaStream_t cast to uintptr_t (0 = the legacy default
+ *    stream). Work is enqueued on it; functions that return data to host
+ *    memory synchronise it before returning.
+ *  - Device memory is obtained from the allocator installed with
+ *    scan_set_allocator (default: cudaMallocAsync/cudaFreeAsync on the
+ *    stream). An allocation failure returns SCAN_ENOMEM and leaves no partial
+ *    index behind.
+ *  - Similarities are IEEE double. Cosine is c / sqrt((d_u+1)(d_v+1)) with
+ *    one correctly rounded square root of the exact integer product and one
+ *    correctly rounded division; Jaccard is c / (d_u + d_v + 2 - c); c is
+ *    |N̄(u) ∩ N̄(v)|. The results are therefore bit-reproducible.
+ */
+#ifndef GB300_SCAN_H
+#define GB300_SCAN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SCAN_OK = 0,
+  SCAN_EINVAL = -1,    /* bad argument (mu < 2, eps outside [0,1] or NaN, ...) */
+  SCAN_ENOMEM = -2,    /* the allocator returned NULL */
+  SCAN_EBADGRAPH = -3, /* CSR is not a simple undirected graph (Section 2.2) */
+  SCAN_ECUDA = -4,     /* a CUDA runtime call failed */
+  SCAN_ETIMEOUT = -5,  /* a bounded wait expired */
+  SCAN_EBUSY = -6      /* serving: admission refused (memory or slots) */
+} scan_status;
+
+typedef enum { SCAN_COSINE = 0, SCAN_JACCARD = 1 } scan_sim_kind;
+
+/* Query flags. */
+enum { SCAN_Q_HUBS = 1 /* label unclustered vertices -2 (hub) or -1 (outlier), Section 4.3 */ };
+
+/* Compressed sparse rows of a simple undirected graph (Section 2.2).
+ * offsets: n+1 entries, int32 (offsets_64 = 0) or int64 (offsets_64 = 1);
+ * adj: num_arcs int32 vertex ids, each list strictly ascending.
+ * on_device = 1: both arrays are in device memory; 0: host memory (copied in). */
+typedef struct scan_csr {
+  int64_t n;
+  int64_t num_arcs;
+  const void* offsets;
+  int offsets_64;
+  const int32_t* adj;
+  int on_device;
+} scan_csr;
+
+/* LSH index mode (Sections 5 and 6.3). With enabled = 0 the index is exact.
+ * An edge is approximated iff both endpoints have degree > degree_threshold;
+ * every other edge keeps its exact similarity.
+ *  cosine  -> SimHash with simhash_bits (a multiple of 64, <= 4096) Rademacher
+ *             hyperplanes; estimate max(0, cos(pi * hamming / bits)).
+ *  Jaccard -> MinHash with minhash_k (power of two when minhash_kpartition = 1,
+ *             <= 1024); k-partition (one-permutation) by default, estimate =
+ *             equal non-empty bins / (k - bins empty in both); standard
+ *             k-hash MinHash when minhash_kpartition = 0, estimate = equal / k.
+ * Random signs and hashes are SplitMix64 outputs of `seed`. */
+typedef struct scan_lsh_params {
+  int enabled;
+  int simhash_bits;
+  int minhash_k;
+  int minhash_kpartition;
+  int degree_threshold;
+  uint64_t seed;
+} scan_lsh_params;
+
+typedef struct scan_index scan_index; /* opaque, owned by the library */
+
+/* Device memory hooks. alloc returns NULL on failure. Passing NULL for both
+ * restores the default (cudaMallocAsync / cudaFreeAsync on the stream). The
+ * hooks are process-wide; install them before any other call. */
+typedef void* (*scan_alloc_fn)(size_t bytes, uintptr_t stream, void* ctx);
+typedef void (*scan_free_fn)(void* ptr, size_t bytes, uintptr_t stream, void* ctx);
+int scan_set_allocator(scan_alloc_fn alloc, scan_free_fn release, void* ctx);
+
+/* Build the index (Algorithms 1-2; Section 6.1 for the oriented counting).
+ * csr: borrowed; kind: similarity; lsh: NULL or enabled = 0 for the exact
+ * index; *out receives a new handle (NULL on error). The CSR is checked: a
+ * graph that is not simple and undirected returns SCAN_EBADGRAPH. Returns
+ * after the build has completed on the stream. */
+int scan_index_build(const scan_csr* csr, scan_sim_kind kind, const scan_lsh_params* lsh,
+                     uintptr_t stream, scan_index** out);
+
+/* Build `count` independent indexes (one per graph) in one batched pass:
+ * the graphs are packed into one device arena and every step runs once over
+ * all of them; each handle then behaves exactly like one from
+ * scan_index_build. out: array of `count` handles. */
+int scan_index_build_batch(const scan_csr* graphs, int count, scan_sim_kind kind,
+                           const scan_lsh_params* lsh, uintptr_t stream, scan_index** out);
+
+/* Answer one (mu, eps) query (Algorithms 3-5). labels: n int32, host or
+ * device. Label = smallest core id of the vertex's cluster; -1 unclustered;
+ * with SCAN_Q_HUBS, -2 marks hubs. Borders join the most similar adjacent
+ * eps-similar core, the smallest id on ties (Section 7.3.4). mu < 2 or eps
+ * outside [0,1] returns SCAN_EINVAL; mu > maxdeg+1 gives no cores. */
+int scan_query(scan_index* index, int mu, double eps, int32_t* labels, int flags,
+               uintptr_t stream);
+
+/* Answer q queries in one batched pass over the index. mu, eps: q entries
+ * (host memory). labels: q*n int32 (row i = query i), host or device. */
+int scan_query_batch(scan_index* index, int q, const int* mu, const double* eps,
+                     int32_t* labels, int flags, uintptr_t stream);
+
+/* Copy the index out (test hook; any pointer may be NULL, each host or
+ * device): sim[num_arcs] in CSR arc order, no_id/no_sim[num_arcs] (NO[v]
+ * occupies the slots of v's CSR row), co_off[max_deg+1], co_id/co_thr
+ * [num_arcs] (CO[mu] = entries co_off[mu-2] .. co_off[mu-1]). */
+int scan_index_export(scan_index* index, double* sim, int32_t* no_id, double* no_sim,
+                      int64_t* co_off, int32_t* co_id, double* co_thr);
+
+/* Sizes of an index; any pointer may be NULL. */
+int scan_index_info(scan_index* index, int64_t* n, int64_t* num_arcs, int32_t* max_deg,
+                    size_t* device_bytes);
+
+/* Release an index (NULL is ignored). */
+void scan_index_free(scan_index* index);
+
+/* Human-readable name of a status. */
+const char* scan_strerror(int status);
+
+/* Timings of the last build on this thread, milliseconds per phase measured
+ * with CUDA events: [0] orientation, [1] counting, [2] similarity/keys,
+ * [3] neighbour order, [4] core order, [5] LSH sketch+estimate, [6] total.
+ * Also the duration of the dominant (counting) kernel. */
+int scan_last_build_timings(double* ms7);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (all threads); a benchmark reads it before and after a timed region. */
+int scan_kernel_launches(uint64_t* count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GB300_SCAN_H */

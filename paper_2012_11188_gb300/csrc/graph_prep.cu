@@ -1,0 +1,245 @@
+// Graph preparation: device-wide scans, degrees with CSR checks, and the
+// degree orientation of Section 6.1 (every edge directed towards its endpoint
+// of larger (degree, id)).
+#include "scan_internal.cuh"
+
+namespace gscan {
+
+namespace {
+
+constexpr int SCAN_T = 256;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_T * SCAN_ITEMS;
+
+template <class T>
+__device__ __forceinline__ int64_t load_val(const T* in, int64_t i, int64_t n) {
+  return i < n ? (int64_t)in[i] : 0;
+}
+
+// Block-wide exclusive scan of one int64 per thread; returns the block total.
+__device__ int64_t block_exclusive_scan(int64_t v, int64_t* out_excl) {
+  __shared__ int64_t warp_tot[SCAN_T / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int64_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int64_t w = lane < SCAN_T / 32 ? warp_tot[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < SCAN_T / 32) warp_tot[lane] = w;  // inclusive
+  }
+  __syncthreads();
+  const int64_t before_warp = wid ? warp_tot[wid - 1] : 0;
+  const int64_t total = warp_tot[SCAN_T / 32 - 1];
+  *out_excl = before_warp + x - v;
+  __syncthreads();
+  return total;
+}
+
+template <class T>
+__global__ void k_tile_sums(const T* in, int64_t n, int64_t* sums) {
+  const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+  int64_t s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) s += load_val(in, base + k, n);
+  int64_t ex;
+  int64_t tot = block_exclusive_scan(s, &ex);
+  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+// out has n+1 entries; tile_base[b] is the exclusive prefix of tile b.
+template <class T>
+__global__ void k_tile_scan(const T* in, int64_t n, const int64_t* tile_base, int64_t* out) {
+  const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+  int64_t v[SCAN_ITEMS];
+  int64_t s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) { v[k] = load_val(in, base + k, n); s += v[k]; }
+  int64_t ex;
+  block_exclusive_scan(s, &ex);
+  int64_t run = ex + (tile_base ? tile_base[blockIdx.x] : 0);
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    const int64_t i = base + k;
+    if (i <= n) out[i] = run;
+    run += v[k];
+  }
+}
+
+template <class T>
+int scan_impl(const T* in, int64_t* out, int64_t n, Pool& pool, cudaStream_t s) {
+  // tiles cover indices 0..n (n+1 outputs)
+  const int64_t tiles = (n + 1 + SCAN_TILE - 1) / SCAN_TILE;
+  if (tiles == 1) {
+    k_tile_scan<T><<<1, SCAN_T, 0, s>>>(in, n, nullptr, out);
+    GS_LAUNCH();
+    return SCAN_OK;
+  }
+  int64_t* sums = pool.get<int64_t>(tiles);
+  int64_t* base = pool.get<int64_t>(tiles + 1);
+  if (!sums || !base) return SCAN_ENOMEM;
+  k_tile_sums<T><<<(unsigned)tiles, SCAN_T, 0, s>>>(in, n, sums);
+  GS_LAUNCH();
+  GS_TRY(scan_impl<int64_t>(sums, base, tiles, pool, s));
+  k_tile_scan<T><<<(unsigned)tiles, SCAN_T, 0, s>>>(in, n, base, out);
+  GS_LAUNCH();
+  pool.put(sums);
+  pool.put(base);
+  return SCAN_OK;
+}
+
+// deg[v], per-row checks, max degree. One warp per vertex row.
+__global__ void k_degrees(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+                          int64_t n, int64_t arcs, int32_t* __restrict__ deg, int32_t* maxdeg,
+                          unsigned* status) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  int32_t local_max = 0;
+  unsigned bad = 0;
+  for (int64_t v = warp; v < n; v += nwarps) {
+    const int64_t b = off[v], e = off[v + 1];
+    const int64_t d = e - b;
+    // rows must lie inside [0, arcs] before adj is touched
+    if (b < 0 || e > arcs || d < 0 || d > 0x7fffffff) {
+      bad = 1;
+      if (lane == 0) deg[v] = 0;
+      continue;
+    }
+    if (lane == 0) deg[v] = (int32_t)d;
+    local_max = max(local_max, (int32_t)d);
+    for (int64_t i = b + lane; i < e; i += 32) {
+      const int32_t x = adj[i];
+      if (x < 0 || x >= n || x == v) bad = 1;
+      if (i > b && adj[i - 1] >= x) bad = 1;  // strictly ascending: sorted, no duplicates
+    }
+  }
+  for (int o = 16; o; o >>= 1) local_max = max(local_max, __shfl_xor_sync(0xffffffffu, local_max, o));
+  bad = __any_sync(0xffffffffu, bad);
+  if (lane == 0) {
+    if (local_max) atomicMax(maxdeg, local_max);
+    if (bad) atomicOr(status, (unsigned)DEV_BADGRAPH);
+  }
+}
+
+__device__ __forceinline__ bool lower(int32_t du, int32_t u, int32_t dv, int32_t v) {
+  return du < dv || (du == dv && u < v);
+}
+
+// Out-degree of each vertex: neighbours of larger (degree, id). Warp per row.
+__global__ void k_outdeg(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+                         const int32_t* __restrict__ deg, int64_t n, int32_t* __restrict__ od,
+                         int32_t* max_od) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = warp; v < n; v += nwarps) {
+    const int64_t b = off[v], e = off[v + 1];
+    const int32_t dv = deg[v];
+    int c = 0;
+    for (int64_t i = b + lane; i < e; i += 32) {
+      const int32_t x = adj[i];
+      c += lower(dv, (int32_t)v, deg[x], x);
+    }
+    for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) {
+      od[v] = c;
+      if (c) atomicMax(max_od, c);
+    }
+  }
+}
+
+// Compact each row to its out-arcs, keeping id order; opos = index in the row.
+__global__ void k_orient(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+                         const int32_t* __restrict__ deg, int64_t n,
+                         const int64_t* __restrict__ oo, int32_t* __restrict__ oadj,
+                         int32_t* __restrict__ opos) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = warp; v < n; v += nwarps) {
+    const int64_t b = off[v], e = off[v + 1];
+    const int32_t dv = deg[v];
+    int64_t w = oo[v];
+    for (int64_t i0 = b; i0 < e; i0 += 32) {
+      const int64_t i = i0 + lane;
+      bool up = false;
+      int32_t x = 0;
+      if (i < e) { x = adj[i]; up = lower(dv, (int32_t)v, deg[x], x); }
+      const unsigned m = __ballot_sync(0xffffffffu, up);
+      if (up) {
+        const int64_t dst = w + __popc(m & ((1u << lane) - 1u));
+        oadj[dst] = x;
+        opos[dst] = (int32_t)(i - b);
+      }
+      w += __popc(m);
+    }
+  }
+}
+
+inline unsigned grid_for(int64_t work, int per_block, int cap = 152 * 32) {
+  int64_t g = (work + per_block - 1) / per_block;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (unsigned)g;
+}
+
+}  // namespace
+
+int exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, Pool& pool, cudaStream_t s) {
+  return scan_impl<int64_t>(in, out, n, pool, s);
+}
+
+int exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, Pool& pool,
+                              cudaStream_t s) {
+  return scan_impl<int32_t>(in, out, n, pool, s);
+}
+
+int launch_degrees(const int64_t* off, const int32_t* adj, int64_t n, int64_t arcs, int32_t* deg,
+                   int32_t* maxdeg_dev, unsigned* status, cudaStream_t s) {
+  if (n == 0) return SCAN_OK;
+  k_degrees<<<grid_for(n, 8), 256, 0, s>>>(off, adj, n, arcs, deg, maxdeg_dev, status);
+  GS_LAUNCH();
+  return SCAN_OK;
+}
+
+int launch_orient(const int64_t* off, const int32_t* adj, const int32_t* deg, int64_t n,
+                  int64_t arcs, Pool& pool, int64_t** oo_out, int32_t** oadj_out,
+                  int32_t** opos_out, int32_t* max_od_dev, cudaStream_t s) {
+  int32_t* od = pool.get<int32_t>(n);
+  int64_t* oo = pool.get<int64_t>(n + 1);
+  int32_t* oadj = pool.get<int32_t>(arcs / 2 + 1);
+  int32_t* opos = pool.get<int32_t>(arcs / 2 + 1);
+  if (!od || !oo || !oadj || !opos) return SCAN_ENOMEM;
+  if (n > 0) {
+    k_outdeg<<<grid_for(n, 8), 256, 0, s>>>(off, adj, deg, n, od, max_od_dev);
+    GS_LAUNCH();
+  }
+  GS_TRY(exclusive_scan_i32_to_i64(od, oo, n, pool, s));
+  // a symmetric graph orients exactly arcs/2 edges; anything else would not
+  // fit the out-list arrays, so it is rejected before they are written
+  int64_t m_or = -1;
+  GS_CUDA(cudaMemcpyAsync(&m_or, oo + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  GS_CUDA(cudaStreamSynchronize(s));
+  if (m_or != arcs / 2) return SCAN_EBADGRAPH;
+  if (n > 0) {
+    k_orient<<<grid_for(n, 8), 256, 0, s>>>(off, adj, deg, n, oo, oadj, opos);
+    GS_LAUNCH();
+  }
+  pool.put(od);
+  *oo_out = oo;
+  *oadj_out = oadj;
+  *opos_out = opos;
+  return SCAN_OK;
+}
+
+}  // namespace gscan

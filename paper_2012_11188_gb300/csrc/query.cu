@@ -1,0 +1,222 @@
+// (mu, eps) queries on the index (Algorithms 3-5, Section 6.2, Section 4.3).
+//
+// For a batch of Q queries every phase is one launch over all of them
+// (blockIdx.y = query), so CO/NO reads are shared in L2 across the batch:
+//  1. GetCores (Algorithm 3): the cores are the prefix of CO[mu] whose
+//     threshold is >= eps; its length comes from one binary search (CO[mu] is
+//     sorted by non-increasing threshold). The prefix marks parent[v] = v.
+//  2. Cluster (Algorithm 5, union-find of Section 6.2): every core u takes the
+//     eps-prefix of NO[u] (binary search) and unions with each core neighbour
+//     of larger id. The union-find is lock-free: find() halves paths, unite()
+//     CASes the larger root under the smaller one, so every root is the
+//     smallest id of its component and labels are canonical.
+//  3. AssignNonCores (Algorithm 4) with the deterministic rule of Section
+//     7.3.4: a non-core takes the label of the first core in its own
+//     eps-prefix of NO -- the most similar eps-similar core, smallest id among
+//     equal similarities (NO breaks ties by id).
+//  4. With SCAN_Q_HUBS (Section 4.3): an unclustered vertex whose neighbours
+//     carry two distinct labels becomes -2.
+#include "scan_internal.cuh"
+
+namespace gscan {
+
+namespace {
+
+constexpr int UNITE_LIMIT = 1 << 22;
+
+__device__ __forceinline__ int32_t ld_volatile(const int32_t* p) {
+  return *(const volatile int32_t*)p;
+}
+
+__device__ __forceinline__ int32_t uf_find(int32_t* parent, int32_t x) {
+  for (int it = 0; it < UNITE_LIMIT; ++it) {
+    const int32_t p = ld_volatile(parent + x);
+    if (p == x) return x;
+    const int32_t gp = ld_volatile(parent + p);
+    if (gp != p) atomicCAS(parent + x, p, gp);  // path halving; only moves towards the root
+    x = gp;
+  }
+  return x;
+}
+
+__device__ __forceinline__ bool uf_unite(int32_t* parent, int32_t a, int32_t b) {
+  for (int it = 0; it < UNITE_LIMIT; ++it) {
+    a = uf_find(parent, a);
+    b = uf_find(parent, b);
+    if (a == b) return true;
+    if (a > b) { const int32_t t = a; a = b; b = t; }
+    if (atomicCAS(parent + b, b, a) == b) return true;  // hook larger root under smaller
+  }
+  return false;
+}
+
+// number of leading entries of the non-increasing array x[0..len) that are >= eps
+__device__ __forceinline__ int64_t prefix_ge(const double* x, int64_t len, double eps) {
+  int64_t lo = 0, hi = len;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (x[mid] >= eps) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+struct QArgs {
+  const int64_t* off;
+  const int32_t* deg;
+  const int32_t* adj;
+  const int32_t* no_id;
+  const double* no_sim;
+  const int64_t* co_off;
+  const int32_t* co_id;
+  const double* co_thr;
+  int64_t n;
+  int32_t maxdeg;
+  const int* mu;       // Q
+  const double* eps;   // Q
+  int64_t* ncores;     // Q
+  int32_t* parent;     // Q * n (-1 = not a core)
+  int32_t* labels;     // Q * n
+  unsigned* status;
+};
+
+__global__ void k_get_cores(QArgs a, int Q) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= Q) return;
+  const int mu = a.mu[q];
+  int64_t nc = 0;
+  if (mu >= 2 && mu <= a.maxdeg + 1) {
+    const int64_t b = a.co_off[mu - 2], e = a.co_off[mu - 1];
+    nc = prefix_ge(a.co_thr + b, e - b, a.eps[q]);
+  }
+  a.ncores[q] = nc;
+}
+
+__global__ void k_mark_cores(QArgs a) {
+  const int q = blockIdx.y;
+  const int64_t nc = a.ncores[q];
+  if (nc == 0) return;
+  const int64_t b = a.co_off[a.mu[q] - 2];
+  int32_t* parent = a.parent + (int64_t)q * a.n;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nc;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = a.co_id[b + i];
+    parent[v] = v;
+  }
+}
+
+// warp per core
+__global__ void k_union(QArgs a) {
+  const int q = blockIdx.y;
+  const int64_t nc = a.ncores[q];
+  if (nc == 0) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t cb = a.co_off[a.mu[q] - 2];
+  const double eps = a.eps[q];
+  int32_t* parent = a.parent + (int64_t)q * a.n;
+  bool fail = false;
+  for (int64_t i = w0; i < nc; i += nw) {
+    const int32_t u = a.co_id[cb + i];
+    const int64_t rb = a.off[u];
+    const int64_t pu = prefix_ge(a.no_sim + rb, a.deg[u], eps);
+    for (int64_t j = lane; j < pu; j += 32) {
+      const int32_t x = a.no_id[rb + j];
+      if (x > u && ld_volatile(parent + x) >= 0) fail |= !uf_unite(parent, u, x);
+    }
+  }
+  if (__any_sync(0xffffffffu, fail) && lane == 0) atomicOr(a.status, (unsigned)DEV_LIMIT);
+}
+
+// thread per vertex: cores take their root, non-cores the first core of their eps-prefix
+__global__ void k_finalize(QArgs a) {
+  const int q = blockIdx.y;
+  const double eps = a.eps[q];
+  const bool any = a.ncores[q] > 0;
+  int32_t* parent = a.parent + (int64_t)q * a.n;
+  int32_t* lab = a.labels + (int64_t)q * a.n;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < a.n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    int32_t l = -1;
+    if (any) {
+      if (ld_volatile(parent + v) >= 0) {
+        l = uf_find(parent, (int32_t)v);
+      } else {
+        const int64_t rb = a.off[v], re = rb + a.deg[v];
+        for (int64_t j = rb; j < re; ++j) {
+          if (a.no_sim[j] < eps) break;
+          const int32_t x = a.no_id[j];
+          if (ld_volatile(parent + x) >= 0) { l = uf_find(parent, x); break; }
+        }
+      }
+    }
+    lab[v] = l;
+  }
+}
+
+// warp per unclustered vertex
+__global__ void k_hubs(QArgs a) {
+  const int q = blockIdx.y;
+  int32_t* lab = a.labels + (int64_t)q * a.n;
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = w0; v < a.n; v += nw) {
+    if (lab[v] != -1) continue;
+    const int64_t rb = a.off[v], re = rb + a.deg[v];
+    int32_t first = -1;
+    bool hub = false;
+    for (int64_t j0 = rb; j0 < re && !hub; j0 += 32) {
+      const int64_t j = j0 + lane;
+      int32_t l = -1;
+      if (j < re) l = lab[a.adj[j]];
+      if (l == -2) l = -1;  // hub marks are written in this pass; they are not clusters
+      // first clustered label in this chunk
+      const unsigned m = __ballot_sync(0xffffffffu, l >= 0);
+      if (!m) continue;
+      if (first < 0) first = __shfl_sync(0xffffffffu, l, __ffs(m) - 1);
+      hub = __any_sync(0xffffffffu, l >= 0 && l != first);
+    }
+    if (hub && lane == 0) lab[v] = -2;
+  }
+}
+
+}  // namespace
+
+int run_queries(const IndexData& ix, int Q, const int* mu_host, const double* eps_host,
+                int32_t* labels_dev, int flags, Pool& pool, cudaStream_t s) {
+  if (Q <= 0) return SCAN_OK;
+  const int64_t n = ix.n;
+  int* mu = pool.get<int>(Q);
+  double* eps = pool.get<double>(Q);
+  int64_t* nc = pool.get<int64_t>(Q);
+  int32_t* parent = pool.get<int32_t>((size_t)Q * (size_t)(n > 0 ? n : 1));
+  if (!mu || !eps || !nc || !parent) return SCAN_ENOMEM;
+  GS_CUDA(cudaMemcpyAsync(mu, mu_host, sizeof(int) * Q, cudaMemcpyHostToDevice, s));
+  GS_CUDA(cudaMemcpyAsync(eps, eps_host, sizeof(double) * Q, cudaMemcpyHostToDevice, s));
+  if (n == 0) return SCAN_OK;
+  GS_CUDA(cudaMemsetAsync(parent, 0xff, sizeof(int32_t) * (size_t)Q * n, s));
+  QArgs a{ix.off, ix.deg, ix.adj, ix.no_id, ix.no_sim, ix.co_off, ix.co_id, ix.co_thr,
+          n, ix.maxdeg, mu, eps, nc, parent, labels_dev, ix.status};
+  k_get_cores<<<(Q + 127) / 128, 128, 0, s>>>(a, Q);
+  GS_LAUNCH();
+  const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8 / std::min(Q, 8) + 1));
+  k_mark_cores<<<dim3(gx, Q), 256, 0, s>>>(a);
+  GS_LAUNCH();
+  const unsigned gw = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 7) / 8, 152 * 16 / std::min(Q, 16) + 1));
+  k_union<<<dim3(gw, Q), 256, 0, s>>>(a);
+  GS_LAUNCH();
+  k_finalize<<<dim3(gx, Q), 256, 0, s>>>(a);
+  GS_LAUNCH();
+  if (flags & SCAN_Q_HUBS) {
+    k_hubs<<<dim3(gw, Q), 256, 0, s>>>(a);
+    GS_LAUNCH();
+  }
+  pool.put(mu);
+  pool.put(eps);
+  pool.put(nc);
+  pool.put(parent);
+  return SCAN_OK;
+}
+
+}  // namespace gscan

@@ -1,0 +1,163 @@
+// Internal declarations shared by the translation units of libscan.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <vector>
+
+#include "../../include/scan.h"
+
+namespace gscan {
+
+// Kernels launched by this library (every launch site is followed by GS_LAUNCH).
+extern std::atomic<unsigned long long> g_kernel_launches;
+
+// ------------------------------------------------------------ error plumbing
+struct Err {
+  int code = SCAN_OK;
+  bool ok() const { return code == SCAN_OK; }
+};
+
+#define GS_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return (int)SCAN_ECUDA;      \
+  } while (0)
+
+#define GS_LAUNCH()                                     \
+  do {                                                  \
+    ::gscan::g_kernel_launches.fetch_add(1, std::memory_order_relaxed); \
+    cudaError_t e_ = cudaGetLastError();                \
+    if (e_ != cudaSuccess) return (int)SCAN_ECUDA;      \
+  } while (0)
+
+#define GS_TRY(expr)                                    \
+  do {                                                  \
+    int r_ = (expr);                                    \
+    if (r_ != SCAN_OK) return r_;                       \
+  } while (0)
+
+// Device status word bits (written by kernels, read by the host).
+enum : unsigned {
+  DEV_BADGRAPH = 1u,   // unsorted / duplicate / self-loop / out-of-range / asymmetric
+  DEV_LIMIT = 2u,      // a bounded loop gave up
+  DEV_OVERFLOW = 4u,   // a fixed-capacity structure would overflow
+};
+
+// ------------------------------------------------------------ device memory
+// All device allocations go through the installed hooks (or the stream-ordered
+// CUDA allocator). A Pool remembers what it handed out so a failed build can
+// release everything.
+void* dev_alloc(size_t bytes, cudaStream_t s);
+void dev_free(void* p, size_t bytes, cudaStream_t s);
+
+struct Pool {
+  cudaStream_t s;
+  struct Blk { void* p; size_t b; };
+  std::vector<Blk> blocks;
+  explicit Pool(cudaStream_t st) : s(st) {}
+  ~Pool() { release_all(); }
+  template <class T>
+  T* get(size_t count) {
+    size_t b = count * sizeof(T);
+    if (b == 0) b = 16;
+    void* p = dev_alloc(b, s);
+    if (p) blocks.push_back({p, b});
+    return (T*)p;
+  }
+  void put(void* p) {
+    for (size_t i = 0; i < blocks.size(); ++i)
+      if (blocks[i].p == p) {
+        dev_free(p, blocks[i].b, s);
+        blocks[i] = blocks.back();
+        blocks.pop_back();
+        return;
+      }
+  }
+  void release_all() {
+    for (auto& b : blocks) dev_free(b.p, b.b, s);
+    blocks.clear();
+  }
+  // hand ownership of every block to the caller (the index)
+  std::vector<Blk> detach() {
+    std::vector<Blk> out;
+    out.swap(blocks);
+    return out;
+  }
+};
+
+// ------------------------------------------------------------ the index
+struct IndexData {
+  int64_t n = 0, arcs = 0;
+  int32_t maxdeg = 0;
+  int kind = SCAN_COSINE;
+  int lsh = 0;
+  // device arrays
+  int64_t* off = nullptr;    // n+1
+  int32_t* deg = nullptr;    // n
+  int32_t* adj = nullptr;    // arcs (id-sorted lists)
+  int32_t* no_id = nullptr;  // arcs
+  double* no_sim = nullptr;  // arcs
+  int64_t* co_off = nullptr; // maxdeg+1
+  int32_t* co_id = nullptr;  // arcs
+  double* co_thr = nullptr;  // arcs
+  unsigned* status = nullptr;  // one device status word
+  std::vector<Pool::Blk> blocks;
+  size_t bytes = 0;
+  cudaStream_t home = 0;
+};
+
+// ------------------------------------------------------------ kernels' host launchers
+// Each returns a scan_status; all work is enqueued on `s`.
+
+// Degrees, CSR checks (sorted, in range, no self-loops), max degree.
+int launch_degrees(const int64_t* off, const int32_t* adj, int64_t n, int64_t arcs, int32_t* deg,
+                   int32_t* maxdeg_dev, unsigned* status, cudaStream_t s);
+
+// Orientation by (degree, id): out-degree, out offsets, out lists and the
+// position of each out-arc inside its source's CSR row.
+int launch_orient(const int64_t* off, const int32_t* adj, const int32_t* deg, int64_t n,
+                  int64_t arcs, Pool& pool, int64_t** oo, int32_t** oadj, int32_t** opos,
+                  int32_t* max_od_dev, cudaStream_t s);
+
+// Closed counts of every edge by oriented triangle enumeration, then the
+// similarity of every CSR arc written to sim_csr (the unsorted NO). With
+// lsh_T >= 0, edges whose endpoints both have degree > lsh_T are left for the
+// LSH estimate (their sim_csr entries are overwritten later).
+int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* adj,
+                                  const int32_t* deg, int64_t n, int64_t arcs, const int64_t* oo,
+                                  const int32_t* oadj, const int32_t* opos, int32_t max_od,
+                                  int lsh_T, double* sim_csr, unsigned* status, Pool& pool,
+                                  cudaStream_t s, float* count_ms);
+
+// Sort every segment [seg_off[i], seg_off[i+1]) of (key, val) pairs by key
+// descending, then val ascending. Keys are non-negative doubles viewed as
+// uint64. max_len bounds every segment length.
+int segmented_sort_desc(uint64_t* key, int32_t* val, const int64_t* seg_off, int64_t nseg,
+                        int64_t total, int64_t max_len, Pool& pool, cudaStream_t s);
+
+// Core order from the neighbour order (Algorithm 2, MakeCoreOrder).
+int build_core_order(IndexData& ix, Pool& pool, cudaStream_t s);
+
+// Queries (Algorithms 3-5).
+int run_queries(const IndexData& ix, int q, const int* mu, const double* eps, int32_t* labels_dev,
+                int flags, Pool& pool, cudaStream_t s);
+
+// LSH mode: overwrite the similarities of approximated arcs.
+int lsh_apply(const scan_lsh_params& p, int kind, const int64_t* off, const int32_t* adj,
+              const int32_t* deg, int64_t n, int64_t arcs, const int32_t* row, int64_t nH,
+              double* no_sim, Pool& pool, cudaStream_t s);
+int lsh_select(const int64_t* off, const int32_t* adj, const int32_t* deg, int64_t n,
+               int threshold, int32_t* row, int64_t* nH_host, Pool& pool, cudaStream_t s);
+
+// Device-wide exclusive scan of int64 counts (n entries -> n+1 offsets).
+int exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, Pool& pool, cudaStream_t s);
+int exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, Pool& pool,
+                              cudaStream_t s);
+
+// Per-thread record of the last build's phase timings.
+void record_timings(const double* ms7);
+
+}  // namespace gscan

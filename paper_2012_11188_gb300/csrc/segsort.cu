@@ -1,0 +1,390 @@
+// Segmented sort of (key, val) pairs: key descending, then val ascending.
+//
+// Used for the neighbour order (each CSR row sorted by similarity, Algorithm
+// 2 MakeNeighborOrder) and the core order (each CO[mu] sorted by threshold,
+// Algorithm 2 MakeCoreOrder). Keys are the bit patterns of non-negative IEEE
+// doubles, which order like the doubles. Within a segment the vals (vertex
+// ids) are distinct, so (key, val) is a strict total order and the result
+// does not depend on stability: equal similarities come out in ascending id,
+// the tie rule of the paper's deterministic experiments.
+//
+// Segments are bucketed by length: <= 32 (one warp, registers and shuffles),
+// <= 256 / 1024 / 4096 (one CTA, bitonic network in shared memory), longer
+// (4096-element tiles sorted by CTAs, then merge-path passes that double the
+// run length, ping-ponging between the data and a scratch buffer).
+#include "scan_internal.cuh"
+
+namespace gscan {
+
+namespace {
+
+constexpr int TILE = 4096;
+constexpr int NCLASS = 5;  // <=32, <=256, <=1024, <=4096, >4096
+
+struct KV {
+  uint64_t k;
+  int32_t v;
+};
+
+// true iff a must come before b
+__device__ __forceinline__ bool before(uint64_t ka, int32_t va, uint64_t kb, int32_t vb) {
+  return ka > kb || (ka == kb && va < vb);
+}
+
+constexpr int32_t SENT_V = 0x7fffffff;  // sorts after every real element (key 0, val max)
+
+__device__ __forceinline__ int seg_class(int64_t len) {
+  return len <= 32 ? 0 : len <= 256 ? 1 : len <= 1024 ? 2 : len <= TILE ? 3 : 4;
+}
+
+// Count segments per class and number of tiles of long segments.
+__global__ void k_classify_count(const int64_t* __restrict__ seg_off, int64_t nseg,
+                                 unsigned long long* counts /* NCLASS + 1 (tiles) */) {
+  __shared__ unsigned long long c[NCLASS + 1];
+  if (threadIdx.x < NCLASS + 1) c[threadIdx.x] = 0;
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nseg;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t len = seg_off[i + 1] - seg_off[i];
+    if (len <= 1) continue;
+    const int cl = seg_class(len);
+    atomicAdd(&c[cl], 1ull);
+    if (cl == 4) atomicAdd(&c[NCLASS], (unsigned long long)((len + TILE - 1) / TILE));
+  }
+  __syncthreads();
+  if (threadIdx.x < NCLASS + 1 && c[threadIdx.x]) atomicAdd(&counts[threadIdx.x], c[threadIdx.x]);
+}
+
+// Fill per-class segment lists (order irrelevant).
+__global__ void k_classify_fill(const int64_t* __restrict__ seg_off, int64_t nseg,
+                                const int64_t* __restrict__ class_base,
+                                unsigned long long* __restrict__ fill, int64_t* __restrict__ list) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nseg;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t len = seg_off[i + 1] - seg_off[i];
+    if (len <= 1) continue;
+    const int cl = seg_class(len);
+    const unsigned long long pos = atomicAdd(&fill[cl], 1ull);
+    list[class_base[cl] + (int64_t)pos] = i;
+  }
+}
+
+// <= 32 elements: one warp per segment, bitonic network across lanes.
+__global__ void k_sort_warp(uint64_t* __restrict__ key, int32_t* __restrict__ val,
+                            const int64_t* __restrict__ seg_off, const int64_t* __restrict__ list,
+                            const unsigned long long* __restrict__ count_ptr) {
+  const int lane = threadIdx.x & 31;
+  const int64_t cnt = (int64_t)*count_ptr;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t w = w0; w < cnt; w += nw) {
+    const int64_t sg = list[w];
+    const int64_t b = seg_off[sg];
+    const int len = (int)(seg_off[sg + 1] - b);
+    uint64_t k = 0;
+    int32_t v = SENT_V;
+    if (lane < len) { k = key[b + lane]; v = val[b + lane]; }
+#pragma unroll
+    for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        const uint64_t ok = __shfl_xor_sync(0xffffffffu, k, stride);
+        const int32_t ov = __shfl_xor_sync(0xffffffffu, v, stride);
+        const bool lower_lane = (lane & stride) == 0;
+        const bool ascending = (lane & size) == 0;  // "ascending" in the before() order
+        // the lower lane of a pair keeps the element that comes first
+        const bool other_first = before(ok, ov, k, v);
+        const bool take = (lower_lane == ascending) ? other_first : !other_first;
+        if (take) { k = ok; v = ov; }
+      }
+    }
+    if (lane < len) { key[b + lane] = k; val[b + lane] = v; }
+  }
+}
+
+// One CTA sorts up to S elements in shared memory with a bitonic network.
+// Work unit u: segment list[u] (TILED = false) or tile u of the long segments
+// (TILED = true; tile_seg/tile_first map a tile to its segment and offset).
+template <int S, int T, bool TILED>
+__global__ void __launch_bounds__(T)
+k_sort_block(uint64_t* __restrict__ key, int32_t* __restrict__ val,
+             const int64_t* __restrict__ seg_off, const int64_t* __restrict__ list,
+             const unsigned long long* __restrict__ count_ptr,
+             const int64_t* __restrict__ tile_prefix /* TILED: tiles before long segment i */,
+             int64_t nlong) {
+  __shared__ uint64_t sk[S];
+  __shared__ int32_t sv[S];
+  const int64_t cnt = (int64_t)*count_ptr;
+  for (int64_t u = blockIdx.x; u < cnt; u += gridDim.x) {
+    int64_t b, len;
+    if (!TILED) {
+      const int64_t sg = list[u];
+      b = seg_off[sg];
+      len = seg_off[sg + 1] - b;
+    } else {
+      // find long segment i with tile_prefix[i] <= u < tile_prefix[i+1]
+      int64_t lo = 0, hi = nlong;
+      while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (tile_prefix[mid] <= u) lo = mid; else hi = mid;
+      }
+      const int64_t sg = list[lo];
+      const int64_t t = u - tile_prefix[lo];
+      const int64_t sb = seg_off[sg], se = seg_off[sg + 1];
+      b = sb + t * S;
+      len = min((int64_t)S, se - b);
+    }
+    for (int i = threadIdx.x; i < S; i += T) {
+      if (i < len) { sk[i] = key[b + i]; sv[i] = val[b + i]; }
+      else { sk[i] = 0; sv[i] = SENT_V; }
+    }
+    __syncthreads();
+    for (int size = 2; size <= S; size <<= 1) {
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int t = threadIdx.x; t < S / 2; t += T) {
+          // pair (i, i + stride) with i having bit `stride` clear
+          const int i = 2 * t - (t & (stride - 1));
+          const int j = i + stride;
+          const bool ascending = (i & size) == 0;
+          const uint64_t ki = sk[i], kj = sk[j];
+          const int32_t vi = sv[i], vj = sv[j];
+          const bool j_first = before(kj, vj, ki, vi);
+          if (j_first == ascending) {
+            sk[i] = kj; sk[j] = ki;
+            sv[i] = vj; sv[j] = vi;
+          }
+        }
+        __syncthreads();
+      }
+    }
+    for (int i = threadIdx.x; i < len; i += T) { key[b + i] = sk[i]; val[b + i] = sv[i]; }
+    __syncthreads();
+  }
+}
+
+// Tiles per long segment (prefix computed by the caller).
+__global__ void k_long_tiles(const int64_t* __restrict__ seg_off, const int64_t* __restrict__ list,
+                             const unsigned long long* __restrict__ count_ptr,
+                             int64_t* __restrict__ tiles, int64_t* __restrict__ outchunks,
+                             int chunk) {
+  const int64_t cnt = (int64_t)*count_ptr;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t sg = list[i];
+    const int64_t len = seg_off[sg + 1] - seg_off[sg];
+    tiles[i] = (len + TILE - 1) / TILE;
+    outchunks[i] = (len + chunk - 1) / chunk;
+  }
+}
+
+constexpr int MERGE_T = 128;
+constexpr int MERGE_ITEMS = 8;
+constexpr int MERGE_CHUNK = MERGE_T * MERGE_ITEMS;  // output elements per CTA per pass
+
+// Number of elements of A (length la) among the first d of merge(A, B).
+__device__ __forceinline__ int64_t merge_path(const uint64_t* ka, const int32_t* va, int64_t la,
+                                              const uint64_t* kb, const int32_t* vb, int64_t lb,
+                                              int64_t d) {
+  int64_t lo = max((int64_t)0, d - lb), hi = min(d, la);
+  while (lo < hi) {
+    const int64_t i = (lo + hi) >> 1;  // take i from A, d-i from B
+    // if B[d-i-1] comes before A[i], i is large enough... standard: A[i] vs B[d-1-i]
+    if (before(kb[d - 1 - i], vb[d - 1 - i], ka[i], va[i])) hi = i;
+    else lo = i + 1;
+  }
+  return lo;
+}
+
+// One merge pass: within every long segment, runs of length L are merged in
+// pairs from (sk, sv) into (dk, dv). Each CTA writes MERGE_CHUNK outputs.
+__global__ void __launch_bounds__(MERGE_T)
+k_merge_pass(const uint64_t* __restrict__ sk, const int32_t* __restrict__ sv,
+             uint64_t* __restrict__ dk, int32_t* __restrict__ dv,
+             const int64_t* __restrict__ seg_off, const int64_t* __restrict__ list,
+             const int64_t* __restrict__ chunk_prefix, int64_t nlong, int64_t L) {
+  __shared__ uint64_t shk[MERGE_CHUNK];
+  __shared__ int32_t shv[MERGE_CHUNK];
+  __shared__ int64_t s_bounds[4];
+  const int64_t total = chunk_prefix[nlong];
+  for (int64_t c = blockIdx.x; c < total; c += gridDim.x) {
+    int64_t lo = 0, hi = nlong;
+    while (hi - lo > 1) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (chunk_prefix[mid] <= c) lo = mid; else hi = mid;
+    }
+    const int64_t sg = list[lo];
+    const int64_t base = seg_off[sg], len = seg_off[sg + 1] - base;
+    const int64_t o0 = (c - chunk_prefix[lo]) * MERGE_CHUNK;
+    const int64_t o1 = min(len, o0 + MERGE_CHUNK);
+    // run pair containing [o0, o1): MERGE_CHUNK divides 2L
+    const int64_t r0 = (o0 / (2 * L)) * (2 * L);
+    const int64_t a0 = r0, a1 = min(len, r0 + L);
+    const int64_t b0 = a1, b1 = min(len, r0 + 2 * L);
+    const uint64_t* KA = sk + base + a0;
+    const int32_t* VA = sv + base + a0;
+    const uint64_t* KB = sk + base + b0;
+    const int32_t* VB = sv + base + b0;
+    const int64_t la = a1 - a0, lb = b1 - b0;
+    if (threadIdx.x == 0) {
+      const int64_t i0 = merge_path(KA, VA, la, KB, VB, lb, o0 - r0);
+      const int64_t i1 = merge_path(KA, VA, la, KB, VB, lb, o1 - r0);
+      s_bounds[0] = i0;
+      s_bounds[1] = i1;
+      s_bounds[2] = (o0 - r0) - i0;
+      s_bounds[3] = (o1 - r0) - i1;
+    }
+    __syncthreads();
+    const int64_t ia0 = s_bounds[0], ia1 = s_bounds[1], ib0 = s_bounds[2], ib1 = s_bounds[3];
+    const int na = (int)(ia1 - ia0), nb = (int)(ib1 - ib0);
+    for (int i = threadIdx.x; i < na; i += MERGE_T) { shk[i] = KA[ia0 + i]; shv[i] = VA[ia0 + i]; }
+    for (int i = threadIdx.x; i < nb; i += MERGE_T) {
+      shk[na + i] = KB[ib0 + i];
+      shv[na + i] = VB[ib0 + i];
+    }
+    __syncthreads();
+    // each thread merges MERGE_ITEMS outputs from its own diagonal
+    const int d = threadIdx.x * MERGE_ITEMS;
+    const int nout = na + nb;
+    if (d < nout) {
+      int lo2 = max(0, d - nb), hi2 = min(d, na);
+      while (lo2 < hi2) {
+        const int i = (lo2 + hi2) >> 1;
+        if (before(shk[na + d - 1 - i], shv[na + d - 1 - i], shk[i], shv[i])) hi2 = i;
+        else lo2 = i + 1;
+      }
+      int ia = lo2, ib = d - lo2;
+      const int64_t out = base + o0 + d;
+      for (int t = 0; t < MERGE_ITEMS && d + t < nout; ++t) {
+        bool take_a;
+        if (ia >= na) take_a = false;
+        else if (ib >= nb) take_a = true;
+        else take_a = !before(shk[na + ib], shv[na + ib], shk[ia], shv[ia]);
+        if (take_a) { dk[out + t] = shk[ia]; dv[out + t] = shv[ia]; ++ia; }
+        else { dk[out + t] = shk[na + ib]; dv[out + t] = shv[na + ib]; ++ib; }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Copy the long segments from the scratch buffer back.
+__global__ void k_copy_long(const uint64_t* __restrict__ sk, const int32_t* __restrict__ sv,
+                            uint64_t* __restrict__ dk, int32_t* __restrict__ dv,
+                            const int64_t* __restrict__ seg_off, const int64_t* __restrict__ list,
+                            const int64_t* __restrict__ chunk_prefix, int64_t nlong) {
+  const int64_t total = chunk_prefix[nlong];
+  for (int64_t c = blockIdx.x; c < total; c += gridDim.x) {
+    int64_t lo = 0, hi = nlong;
+    while (hi - lo > 1) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (chunk_prefix[mid] <= c) lo = mid; else hi = mid;
+    }
+    const int64_t sg = list[lo];
+    const int64_t base = seg_off[sg], len = seg_off[sg + 1] - base;
+    const int64_t o0 = (c - chunk_prefix[lo]) * MERGE_CHUNK;
+    const int64_t o1 = min(len, o0 + MERGE_CHUNK);
+    for (int64_t i = o0 + threadIdx.x; i < o1; i += blockDim.x) {
+      dk[base + i] = sk[base + i];
+      dv[base + i] = sv[base + i];
+    }
+  }
+}
+
+}  // namespace
+
+int segmented_sort_desc(uint64_t* key, int32_t* val, const int64_t* seg_off, int64_t nseg,
+                        int64_t total, int64_t max_len, Pool& pool, cudaStream_t s) {
+  if (nseg <= 0 || total <= 1 || max_len <= 1) return SCAN_OK;
+  unsigned long long* counts = pool.get<unsigned long long>(2 * (NCLASS + 1));
+  if (!counts) return SCAN_ENOMEM;
+  GS_CUDA(cudaMemsetAsync(counts, 0, 2 * (NCLASS + 1) * sizeof(unsigned long long), s));
+  const unsigned g_seg = (unsigned)std::min<int64_t>((nseg + 255) / 256, 152 * 16);
+  k_classify_count<<<g_seg, 256, 0, s>>>(seg_off, nseg, counts);
+  GS_LAUNCH();
+  unsigned long long hc[NCLASS + 1];
+  GS_CUDA(cudaMemcpyAsync(hc, counts, sizeof(hc), cudaMemcpyDeviceToHost, s));
+  GS_CUDA(cudaStreamSynchronize(s));
+  int64_t base[NCLASS + 1];
+  base[0] = 0;
+  for (int c = 0; c < NCLASS; ++c) base[c + 1] = base[c] + (int64_t)hc[c];
+  int64_t* list = pool.get<int64_t>(base[NCLASS] > 0 ? base[NCLASS] : 1);
+  int64_t* base_dev = pool.get<int64_t>(NCLASS + 1);
+  if (!list || !base_dev) return SCAN_ENOMEM;
+  GS_CUDA(cudaMemcpyAsync(base_dev, base, sizeof(base), cudaMemcpyHostToDevice, s));
+  unsigned long long* fill = counts + (NCLASS + 1);
+  k_classify_fill<<<g_seg, 256, 0, s>>>(seg_off, nseg, base_dev, fill, list);
+  GS_LAUNCH();
+  // per-class counts on the device for the grid-stride kernels: counts[c]
+  auto grid_of = [](int64_t units, int per) {
+    int64_t g = (units + per - 1) / per;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 32));
+  };
+  if (hc[0]) {
+    k_sort_warp<<<grid_of((int64_t)hc[0], 8), 256, 0, s>>>(key, val, seg_off, list + base[0],
+                                                           counts + 0);
+    GS_LAUNCH();
+  }
+  if (hc[1]) {
+    k_sort_block<256, 128, false><<<grid_of((int64_t)hc[1], 1), 128, 0, s>>>(
+        key, val, seg_off, list + base[1], counts + 1, nullptr, 0);
+    GS_LAUNCH();
+  }
+  if (hc[2]) {
+    k_sort_block<1024, 256, false><<<grid_of((int64_t)hc[2], 1), 256, 0, s>>>(
+        key, val, seg_off, list + base[2], counts + 2, nullptr, 0);
+    GS_LAUNCH();
+  }
+  if (hc[3]) {
+    k_sort_block<TILE, 512, false><<<grid_of((int64_t)hc[3], 1), 512, 0, s>>>(
+        key, val, seg_off, list + base[3], counts + 3, nullptr, 0);
+    GS_LAUNCH();
+  }
+  const int64_t nlong = (int64_t)hc[4];
+  if (nlong) {
+    const int64_t* llist = list + base[4];
+    int64_t* tiles = pool.get<int64_t>(nlong);
+    int64_t* tile_prefix = pool.get<int64_t>(nlong + 1);
+    int64_t* chunks = pool.get<int64_t>(nlong);
+    int64_t* chunk_prefix = pool.get<int64_t>(nlong + 1);
+    uint64_t* tk = pool.get<uint64_t>(total);
+    int32_t* tv = pool.get<int32_t>(total);
+    if (!tiles || !tile_prefix || !chunks || !chunk_prefix || !tk || !tv) return SCAN_ENOMEM;
+    k_long_tiles<<<grid_of(nlong, 256), 256, 0, s>>>(seg_off, llist, counts + 4, tiles, chunks,
+                                                     MERGE_CHUNK);
+    GS_LAUNCH();
+    GS_TRY(exclusive_scan_i64(tiles, tile_prefix, nlong, pool, s));
+    GS_TRY(exclusive_scan_i64(chunks, chunk_prefix, nlong, pool, s));
+    const int64_t ntiles = (int64_t)hc[NCLASS];
+    // tile sort (count = ntiles, read from counts[NCLASS])
+    k_sort_block<TILE, 512, true><<<grid_of(ntiles, 1), 512, 0, s>>>(
+        key, val, seg_off, llist, counts + NCLASS, tile_prefix, nlong);
+    GS_LAUNCH();
+    uint64_t *ck = key, *nk = tk;
+    int32_t *cv = val, *nv = tv;
+    const int64_t total_chunks_ub = (total + MERGE_CHUNK - 1) / MERGE_CHUNK + nlong;
+    for (int64_t L = TILE; L < max_len; L <<= 1) {
+      k_merge_pass<<<grid_of(total_chunks_ub, 1), MERGE_T, 0, s>>>(ck, cv, nk, nv, seg_off, llist,
+                                                                  chunk_prefix, nlong, L);
+      GS_LAUNCH();
+      std::swap(ck, nk);
+      std::swap(cv, nv);
+    }
+    if (ck != key) {
+      k_copy_long<<<grid_of(total_chunks_ub, 1), 256, 0, s>>>(ck, cv, key, val, seg_off, llist,
+                                                             chunk_prefix, nlong);
+      GS_LAUNCH();
+    }
+    pool.put(tk);
+    pool.put(tv);
+    pool.put(tiles);
+    pool.put(tile_prefix);
+    pool.put(chunks);
+    pool.put(chunk_prefix);
+  }
+  pool.put(list);
+  pool.put(base_dev);
+  pool.put(counts);
+  return SCAN_OK;
+}
+
+}  // namespace gscan

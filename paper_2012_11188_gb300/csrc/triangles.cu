@@ -1,0 +1,320 @@
+// Closed-neighbourhood counts c(u,v) = |N̄(u) ∩ N̄(v)| = t(u,v) + 2 for every
+// edge, where t(u,v) is the number of triangles on the edge (Section 3.1), and
+// the similarity of every arc computed from them (Section 3.1 cosine; Section
+// 2.1.1 Jaccard).
+//
+// Counting follows the oriented triangle enumeration the paper implements
+// (Section 6.1): edges point from the lower to the higher (degree, id)
+// endpoint, so every out-list is short (at most sqrt(2m) long; 1,756 on R-MAT
+// scale 24). Each triangle u < v < w is found exactly once, at its middle
+// vertex v: the CTA that owns v keeps out(v) in a shared-memory hash table and
+// streams out(u) for the in-neighbours u of v. A hit x = w adds one to
+//   (u,v)  -- summed in registers, one atomic per (u,v) pair,
+//   (v,w)  -- a shared-memory counter indexed by w's slot in out(v),
+//   (u,w)  -- a global atomic at w's slot in out(u).
+// This replaces the paper's merge (which reads sum(d+_u + d+_v)) by a hash
+// probe of out(u) only (sum over u of d+_u squared), the scheme of the paper's
+// Algorithm 1 applied to the oriented lists.
+#include "scan_internal.cuh"
+
+namespace gscan {
+
+namespace {
+
+constexpr int TRI_THREADS = 256;
+constexpr int TRI_WARPS = TRI_THREADS / 32;
+constexpr int CHUNK = 1024;          // CSR positions of N(v) per work item
+constexpr int SMEM_OD_MAX = 4096;    // out(v) sizes handled by the shared-memory table
+
+__device__ __forceinline__ bool lower(int32_t du, int32_t u, int32_t dv, int32_t v) {
+  return du < dv || (du == dv && u < v);
+}
+
+__device__ __forceinline__ uint32_t hslot(int32_t x, int log2h) {
+  return ((uint32_t)x * 0x9E3779B1u) >> (32 - log2h);
+}
+
+// Work items: vertex v contributes ceil(deg/CHUNK) items when it has in-
+// neighbours (every in-arc needs the position of its source in N(v), even when
+// out(v) is empty and no triangle has v in the middle).
+// items[v] -> prefix -> item index maps back to (v, chunk).
+__global__ void k_item_counts(const int64_t* __restrict__ oo, const int32_t* __restrict__ deg,
+                              int64_t n, int32_t* __restrict__ items) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t od = oo[v + 1] - oo[v];
+    const int32_t d = deg[v];
+    int c = 0;
+    if (d - od > 0) c = (int)((d + CHUNK - 1) / CHUNK);
+    items[v] = c;
+  }
+}
+
+__device__ __forceinline__ int64_t find_item_vertex(const int64_t* item_off, int64_t n,
+                                                     int64_t item) {
+  // largest v with item_off[v] <= item
+  int64_t lo = 0, hi = n;  // item_off[n] > item
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (item_off[mid] <= item) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// BIG = out(v) too long for the shared table: probe by binary search in the
+// sorted global out-list and count (v,w) hits with global atomics.
+template <bool BIG>
+__global__ void __launch_bounds__(TRI_THREADS)
+k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+            const int32_t* __restrict__ deg, const int64_t* __restrict__ oo,
+            const int32_t* __restrict__ oadj, int64_t n, const int64_t* __restrict__ item_off,
+            unsigned long long* __restrict__ work, int lsh_T, int od_cap,
+            uint32_t* __restrict__ tcnt, int32_t* __restrict__ twin_rel, unsigned* status) {
+  // shared layout for od_cap (a power of two >= every od handled here):
+  // hkey[2*od_cap] int32 | vcnt[od_cap] uint32 | hpos[2*od_cap] uint16
+  extern __shared__ int32_t smem[];
+  __shared__ long long s_item;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t total = item_off[n];
+  int32_t* hkey = smem;
+  uint32_t* vcnt = (uint32_t*)(smem + 2 * od_cap);
+  uint16_t* hpos = (uint16_t*)(smem + 3 * od_cap);
+  unsigned bad = 0;
+
+  for (;;) {
+    if (threadIdx.x == 0) s_item = (long long)atomicAdd(work, 1ull);
+    __syncthreads();
+    const int64_t item = s_item;
+    if (item >= total) break;
+    const int64_t v = find_item_vertex(item_off, n, item);
+    const int64_t chunk = item - item_off[v];
+    const int32_t dv = deg[v];
+    const int64_t ob = oo[v];
+    const int32_t od = (int32_t)(oo[v + 1] - ob);
+    const bool skip_item = BIG ? (od <= SMEM_OD_MAX) : (od > SMEM_OD_MAX);
+    if (skip_item) { __syncthreads(); continue; }
+    int log2h = 5;
+    if (!BIG && od > 0) {
+      while ((1 << log2h) < 2 * od) ++log2h;
+      const int H = 1 << log2h;
+      for (int i = threadIdx.x; i < H; i += TRI_THREADS) hkey[i] = -1;
+      for (int i = threadIdx.x; i < od; i += TRI_THREADS) vcnt[i] = 0;
+      __syncthreads();
+      for (int j = threadIdx.x; j < od; j += TRI_THREADS) {
+        const int32_t x = oadj[ob + j];
+        uint32_t s = hslot(x, log2h);
+        for (int probe = 0; probe < H; ++probe) {
+          const int32_t prev = atomicCAS(&hkey[s], -1, x);
+          if (prev == -1) { hpos[s] = (uint16_t)j; break; }
+          s = (s + 1) & (H - 1);
+        }
+      }
+      __syncthreads();
+    }
+    const int H = 1 << log2h;
+    const int64_t rb = off[v];
+    const int64_t p_begin = chunk * CHUNK;
+    const int64_t p_end = min((int64_t)dv, p_begin + CHUNK);
+    // each warp takes 32 consecutive CSR positions at a time
+    for (int64_t p0 = p_begin + 32 * wid; p0 < p_end; p0 += 32 * TRI_WARPS) {
+      const int64_t p = p0 + lane;
+      int32_t u = -1;
+      bool is_in = false;
+      if (p < p_end) {
+        u = adj[rb + p];
+        const int32_t du = deg[u];
+        is_in = lower(du, u, dv, (int32_t)v);
+        // LSH mode: if u and v are both above the threshold, every edge of
+        // every triangle u < v < w is approximated, so the scan is not needed
+        if (is_in && lsh_T >= 0 && du > lsh_T) is_in = false;
+      }
+      unsigned m = __ballot_sync(0xffffffffu, is_in);
+      while (m) {
+        const int src = __ffs(m) - 1;
+        m &= m - 1;
+        const int32_t uu = __shfl_sync(0xffffffffu, u, src);
+        const int64_t ub = oo[uu], ue = oo[uu + 1];
+        if (od == 0) {
+          // no triangle has v in the middle: only locate v in the sorted out(u)
+          if (lane == 0) {
+            int64_t lo = ub, hi = ue;
+            while (lo < hi) {
+              const int64_t mid = (lo + hi) >> 1;
+              if (oadj[mid] < (int32_t)v) lo = mid + 1; else hi = mid;
+            }
+            if (lo < ue && oadj[lo] == (int32_t)v) twin_rel[lo] = (int32_t)(p0 + src);
+            else bad = 1;
+          }
+          continue;
+        }
+        unsigned acc = 0;
+        int64_t jv = -1;
+        for (int64_t j = ub + lane; j < ue; j += 32) {
+          const int32_t x = oadj[j];
+          if (x == (int32_t)v) jv = j;
+          int q = -1;
+          if (!BIG) {
+            uint32_t s = hslot(x, log2h);
+            for (int probe = 0; probe < H; ++probe) {
+              const int32_t k = hkey[s];
+              if (k == x) { q = hpos[s]; break; }
+              if (k == -1) break;
+              s = (s + 1) & (H - 1);
+            }
+          } else {
+            int lo = 0, hi = od;
+            while (lo < hi) {
+              const int mid = (lo + hi) >> 1;
+              const int32_t y = oadj[ob + mid];
+              if (y < x) lo = mid + 1; else hi = mid;
+            }
+            if (lo < od && oadj[ob + lo] == x) q = lo;
+          }
+          if (q >= 0) {
+            ++acc;
+            if (!BIG) atomicAdd(&vcnt[q], 1u);
+            else atomicAdd(&tcnt[ob + q], 1u);
+            atomicAdd(&tcnt[j], 1u);
+          }
+        }
+        for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        long long jvl = (long long)jv;
+        for (int o = 16; o; o >>= 1) jvl = max(jvl, __shfl_xor_sync(0xffffffffu, jvl, o));
+        if (lane == 0) {
+          if (jvl < 0) {
+            bad = 1;  // v lists u but u does not list v
+          } else {
+            if (acc) atomicAdd(&tcnt[jvl], acc);
+            twin_rel[jvl] = (int32_t)(p0 + src);  // position of u in N(v)
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (!BIG)
+      for (int j = threadIdx.x; j < od; j += TRI_THREADS) {
+        const uint32_t c = vcnt[j];
+        if (c) atomicAdd(&tcnt[ob + j], c);
+      }
+    __syncthreads();
+  }
+  if (bad) atomicOr(status, (unsigned)DEV_BADGRAPH);
+}
+
+// Cosine (Section 3.1) or Jaccard (Section 2.1.1) from the closed count.
+__device__ __forceinline__ double sim_of(int kind, int64_t c, int64_t du, int64_t dv) {
+  if (kind == SCAN_COSINE) {
+    const int64_t prod = (du + 1) * (dv + 1);
+    return __ddiv_rn((double)c, __dsqrt_rn((double)prod));
+  }
+  return __ddiv_rn((double)c, (double)(du + dv + 2 - c));
+}
+
+// Every oriented edge a->b writes sigma to both of its CSR arcs.
+__global__ void k_expand(int kind, const int64_t* __restrict__ off, const int32_t* __restrict__ deg,
+                         const int64_t* __restrict__ oo, const int32_t* __restrict__ oadj,
+                         const int32_t* __restrict__ opos, const uint32_t* __restrict__ tcnt,
+                         const int32_t* __restrict__ twin_rel, int64_t n, int lsh_T,
+                         double* __restrict__ sim_csr, unsigned* status) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned bad = 0;
+  for (int64_t a = warp; a < n; a += nwarps) {
+    const int64_t ob = oo[a], oe = oo[a + 1];
+    if (ob == oe) continue;
+    const int64_t ra = off[a];
+    const int32_t da = deg[a];
+    for (int64_t j = ob + lane; j < oe; j += 32) {
+      const int32_t b = oadj[j];
+      const int32_t tr = twin_rel[j];
+      // LSH mode: approximated edges are written by the estimate pass
+      if (lsh_T >= 0 && da > lsh_T && deg[b] > lsh_T) continue;
+      const double s = sim_of(kind, (int64_t)tcnt[j] + 2, da, deg[b]);
+      sim_csr[ra + opos[j]] = s;
+      if (tr < 0) bad = 1;
+      else sim_csr[off[b] + tr] = s;
+    }
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, (unsigned)DEV_BADGRAPH);
+}
+
+__global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
+}  // namespace
+
+int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* adj,
+                                  const int32_t* deg, int64_t n, int64_t arcs, const int64_t* oo,
+                                  const int32_t* oadj, const int32_t* opos, int32_t max_od,
+                                  int lsh_T, double* sim_csr, unsigned* status, Pool& pool,
+                                  cudaStream_t s, float* count_ms) {
+  const int64_t m = arcs / 2;
+  uint32_t* tcnt = pool.get<uint32_t>(m);
+  int32_t* twin = pool.get<int32_t>(m);
+  int32_t* items = pool.get<int32_t>(n);
+  int64_t* item_off = pool.get<int64_t>(n + 1);
+  unsigned long long* work = pool.get<unsigned long long>(2);
+  if (!tcnt || !twin || !items || !item_off || !work) return SCAN_ENOMEM;
+  GS_CUDA(cudaMemsetAsync(tcnt, 0, m * sizeof(uint32_t), s));
+  GS_CUDA(cudaMemsetAsync(work, 0, 2 * sizeof(unsigned long long), s));
+  if (m > 0) {
+    k_fill_i32<<<1024, 256, 0, s>>>(twin, m, -1);
+    GS_LAUNCH();
+  }
+  if (n > 0) {
+    k_item_counts<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 64), 256, 0, s>>>(
+        oo, deg, n, items);
+    GS_LAUNCH();
+  }
+  GS_TRY(exclusive_scan_i32_to_i64(items, item_off, n, pool, s));
+  cudaEvent_t e0, e1;
+  GS_CUDA(cudaEventCreate(&e0));
+  GS_CUDA(cudaEventCreate(&e1));
+  GS_CUDA(cudaEventRecord(e0, s));
+  if (n > 0 && m > 0) {
+    int od_cap = 32;
+    while (od_cap < max_od && od_cap < SMEM_OD_MAX) od_cap <<= 1;
+    const size_t smem = (size_t)3 * od_cap * sizeof(int32_t) + (size_t)2 * od_cap * sizeof(uint16_t);
+    const size_t smem_max = (size_t)3 * SMEM_OD_MAX * 4 + (size_t)2 * SMEM_OD_MAX * 2;
+    GS_CUDA(cudaFuncSetAttribute(k_triangles<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_max));
+    int dev = 0, sms = 152, per_sm = 1;
+    GS_CUDA(cudaGetDevice(&dev));
+    GS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    GS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_triangles<false>,
+                                                          TRI_THREADS, smem));
+    if (per_sm < 1) per_sm = 1;
+    k_triangles<false><<<sms * per_sm, TRI_THREADS, smem, s>>>(
+        off, adj, deg, oo, oadj, n, item_off, work, lsh_T, od_cap, tcnt, twin, status);
+    GS_LAUNCH();
+    if (max_od > SMEM_OD_MAX) {
+      k_triangles<true><<<sms * 4, TRI_THREADS, 0, s>>>(off, adj, deg, oo, oadj, n, item_off,
+                                                        work + 1, lsh_T, 0, tcnt, twin, status);
+      GS_LAUNCH();
+    }
+  }
+  GS_CUDA(cudaEventRecord(e1, s));
+  if (n > 0 && m > 0) {
+    k_expand<<<(unsigned)std::min<int64_t>((n + 7) / 8, 152 * 64), 256, 0, s>>>(
+        kind, off, deg, oo, oadj, opos, tcnt, twin, n, lsh_T, sim_csr, status);
+    GS_LAUNCH();
+  }
+  if (count_ms) {
+    GS_CUDA(cudaEventSynchronize(e1));
+    GS_CUDA(cudaEventElapsedTime(count_ms, e0, e1));
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  pool.put(tcnt);
+  pool.put(twin);
+  pool.put(items);
+  pool.put(item_off);
+  pool.put(work);
+  return SCAN_OK;
+}
+
+}  // namespace gscan

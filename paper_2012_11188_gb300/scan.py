@@ -1,0 +1,298 @@
+"""Python binding of libscan.so: argument marshalling only.
+
+Every computation happens in the CUDA library (include/scan.h); this module
+loads it with ctypes, turns numpy arrays / torch tensors into pointers and
+status codes into exceptions. There is no CPU fallback: if the library cannot
+be built or loaded, every entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _build
+
+COSINE, JACCARD = 0, 1
+Q_HUBS = 1
+
+STATUS = {0: "SCAN_OK", -1: "SCAN_EINVAL", -2: "SCAN_ENOMEM", -3: "SCAN_EBADGRAPH",
+          -4: "SCAN_ECUDA", -5: "SCAN_ETIMEOUT", -6: "SCAN_EBUSY"}
+
+
+class ScanError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {STATUS.get(status, status)}")
+        self.status = status
+
+
+class scan_csr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("num_arcs", ctypes.c_int64), ("offsets", ctypes.c_void_p),
+                ("offsets_64", ctypes.c_int), ("adj", ctypes.c_void_p), ("on_device", ctypes.c_int)]
+
+
+class scan_lsh_params(ctypes.Structure):
+    _fields_ = [("enabled", ctypes.c_int), ("simhash_bits", ctypes.c_int),
+                ("minhash_k", ctypes.c_int), ("minhash_kpartition", ctypes.c_int),
+                ("degree_threshold", ctypes.c_int), ("seed", ctypes.c_uint64)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libscan.so, compiling it first if it is missing or stale."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build()
+    lib = ctypes.CDLL(path)
+    P, i32, i64, f64, u = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_uint64
+    sigs = {
+        "scan_set_allocator": (i32, [P, P, P]),
+        "scan_index_build": (i32, [P, i32, P, ctypes.c_size_t, P]),
+        "scan_index_build_batch": (i32, [P, i32, i32, P, ctypes.c_size_t, P]),
+        "scan_query": (i32, [P, i32, f64, P, i32, ctypes.c_size_t]),
+        "scan_query_batch": (i32, [P, i32, P, P, P, i32, ctypes.c_size_t]),
+        "scan_index_export": (i32, [P, P, P, P, P, P, P]),
+        "scan_index_info": (i32, [P, P, P, P, P]),
+        "scan_index_free": (None, [P]),
+        "scan_strerror": (ctypes.c_char_p, [i32]),
+        "scan_last_build_timings": (i32, [P]),
+        "scan_kernel_launches": (i32, [P]),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(lib, name)
+        f.restype, f.argtypes = res, args
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise ScanError(rc, what)
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return int(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def _ptr(a) -> int:
+    if a is None:
+        return 0
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return int(a.data_ptr())  # torch tensor
+
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+_torch_hooks = None
+
+
+def use_torch_allocator(enable: bool = True):
+    """Route the library's device allocations through torch's caching allocator."""
+    global _torch_hooks
+    lib = load()
+    if not enable:
+        _check(lib.scan_set_allocator(None, None, None), "scan_set_allocator")
+        _torch_hooks = None
+        return
+    import torch
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                                      int(stream or 0))
+        except RuntimeError:
+            return None
+
+    def _free(p, nbytes, stream, ctx):
+        torch.cuda.caching_allocator_delete(p)
+
+    hooks = (ALLOC_FN(_alloc), FREE_FN(_free))
+    _check(lib.scan_set_allocator(ctypes.cast(hooks[0], ctypes.c_void_p),
+                                  ctypes.cast(hooks[1], ctypes.c_void_p), None), "scan_set_allocator")
+    _torch_hooks = hooks
+
+
+def make_lsh(kind: int, k: int, threshold: int = 128, seed: int = 1, kpartition: bool = True):
+    p = scan_lsh_params()
+    p.enabled = 1
+    p.simhash_bits = k if kind == COSINE else 64
+    p.minhash_k = k if kind == JACCARD else 64
+    p.minhash_kpartition = 1 if kpartition else 0
+    p.degree_threshold = threshold
+    p.seed = seed
+    return p
+
+
+def _csr_struct(g, device: bool):
+    """scan_csr for a graphgen.CSR-like (off, adj numpy) or a pair of torch tensors.
+
+    Returns (struct, keepalive)."""
+    c = scan_csr()
+    if isinstance(g, tuple):
+        off, adj = g
+    else:
+        off, adj = g.off, g.adj
+    if _is_torch(off):
+        c.on_device = 1 if off.is_cuda else 0
+    elif device:
+        import torch
+        off = torch.from_numpy(np.ascontiguousarray(off)).cuda()
+        adj = torch.from_numpy(np.ascontiguousarray(adj)).cuda()
+        c.on_device = 1
+    else:
+        off = np.ascontiguousarray(off)
+        adj = np.ascontiguousarray(adj)
+        c.on_device = 0
+    dt = str(off.dtype)
+    if dt.endswith("int64"):
+        c.offsets_64 = 1
+    elif dt.endswith("int32"):
+        c.offsets_64 = 0
+    else:
+        raise TypeError("offsets must be int32 or int64")
+    if not str(adj.dtype).endswith("int32"):
+        raise TypeError("adjacency must be int32")
+    c.n = int(off.shape[0]) - 1
+    c.num_arcs = int(adj.shape[0])
+    c.offsets = _ptr(off)
+    c.adj = _ptr(adj)
+    return c, (off, adj)
+
+
+@dataclass
+class BuildTimings:
+    orient_ms: float
+    count_ms: float
+    sims_ms: float
+    neighbor_order_ms: float
+    core_order_ms: float
+    lsh_ms: float
+    total_ms: float
+
+
+def kernel_launches() -> int:
+    c = ctypes.c_uint64()
+    _check(load().scan_kernel_launches(ctypes.byref(c)), "scan_kernel_launches")
+    return c.value
+
+
+def last_build_timings() -> BuildTimings:
+    t = (ctypes.c_double * 7)()
+    _check(load().scan_last_build_timings(t), "scan_last_build_timings")
+    return BuildTimings(*[float(x) for x in t])
+
+
+class ScanIndex:
+    """A SCAN index resident on the GPU (neighbour order NO and core order CO)."""
+
+    def __init__(self, handle: int):
+        self._h = ctypes.c_void_p(handle)
+        n, arcs = ctypes.c_int64(), ctypes.c_int64()
+        md, nb = ctypes.c_int32(), ctypes.c_size_t()
+        _check(load().scan_index_info(self._h, ctypes.byref(n), ctypes.byref(arcs),
+                                      ctypes.byref(md), ctypes.byref(nb)), "scan_index_info")
+        self.n, self.arcs, self.maxdeg, self.device_bytes = n.value, arcs.value, md.value, nb.value
+
+    @classmethod
+    def build(cls, g, kind: int = COSINE, lsh=None, stream=None, device: bool = False) -> "ScanIndex":
+        """Build from a CSR (graphgen.CSR, or (offsets, adj) numpy/torch).
+
+        device=True uploads numpy inputs with torch first; torch CUDA tensors are
+        passed as device pointers; numpy arrays are copied in by the library."""
+        lib = load()
+        c, keep = _csr_struct(g, device)
+        h = ctypes.c_void_p()
+        rc = lib.scan_index_build(ctypes.byref(c), kind, ctypes.byref(lsh) if lsh else None,
+                                  _stream_handle(stream), ctypes.byref(h))
+        del keep
+        _check(rc, "scan_index_build")
+        return cls(h.value)
+
+    @staticmethod
+    def build_batch(graphs, kind: int = COSINE, lsh=None, stream=None, device: bool = False):
+        lib = load()
+        structs, keep = [], []
+        for g in graphs:
+            c, k = _csr_struct(g, device)
+            structs.append(c)
+            keep.append(k)
+        arr = (scan_csr * len(structs))(*structs)
+        out = (ctypes.c_void_p * len(structs))()
+        rc = lib.scan_index_build_batch(arr, len(structs), kind,
+                                        ctypes.byref(lsh) if lsh else None,
+                                        _stream_handle(stream), out)
+        _check(rc, "scan_index_build_batch")
+        return [ScanIndex(h) for h in out]
+
+    def query(self, mu: int, eps: float, hubs: bool = False, out=None, stream=None):
+        """Labels of one (mu, eps) query; `out` may be a numpy array or torch tensor."""
+        if out is None:
+            out = np.empty(self.n, dtype=np.int32)
+        _check(load().scan_query(self._h, int(mu), float(eps), _ptr(out), Q_HUBS if hubs else 0,
+                                 _stream_handle(stream)), "scan_query")
+        return out
+
+    def query_batch(self, mus, epss, hubs: bool = False, out=None, stream=None):
+        mus = np.ascontiguousarray(mus, dtype=np.int32)
+        epss = np.ascontiguousarray(epss, dtype=np.float64)
+        q = mus.shape[0]
+        if out is None:
+            out = np.empty((q, self.n), dtype=np.int32)
+        _check(load().scan_query_batch(self._h, q, mus.ctypes.data, epss.ctypes.data, _ptr(out),
+                                       Q_HUBS if hubs else 0, _stream_handle(stream)),
+               "scan_query_batch")
+        return out
+
+    def export(self) -> dict:
+        A = self.arcs
+        out = {
+            "sim": np.empty(A, np.float64), "no_id": np.empty(A, np.int32),
+            "no_sim": np.empty(A, np.float64), "co_off": np.empty(self.maxdeg + 1, np.int64),
+            "co_id": np.empty(A, np.int32), "co_thr": np.empty(A, np.float64),
+        }
+        _check(load().scan_index_export(self._h, *[_ptr(out[k]) for k in
+                                                   ("sim", "no_id", "no_sim", "co_off", "co_id",
+                                                    "co_thr")]), "scan_index_export")
+        return out
+
+    def free(self):
+        if self._h is not None and self._h.value:
+            load().scan_index_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.free()

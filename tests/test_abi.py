@@ -1,0 +1,59 @@
+"""The C-ABI library builds, loads, and exports every symbol declared in include/*.h.
+
+No compute call is made here (no GPU on this host); only calls that return
+before touching the device (argument validation, status names).
+"""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+import paper_2012_11188_gb300 as gs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        for m in re.finditer(r"\b(scan_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    # typedef'd function pointer types are not symbols
+    return sorted(n for n in names if not n.endswith("_fn"))
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for must in ("scan_index_build", "scan_query", "scan_query_batch", "scan_index_export",
+                 "scan_index_free", "scan_strerror", "scan_index_build_batch"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(gs.library_path() if os.path.exists(gs.library_path()) else gs.build())
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_strerror_and_argument_checks_without_gpu():
+    lib = gs.load()
+    assert lib.scan_strerror(0) == b"ok"
+    assert lib.scan_strerror(-3) == b"not a simple undirected CSR graph"
+    # NULL csr / NULL out are rejected before any device work
+    h = ctypes.c_void_p()
+    assert lib.scan_index_build(None, 0, None, 0, ctypes.byref(h)) == -1
+    assert lib.scan_index_build(None, 0, None, 0, None) == -1
+    assert lib.scan_query(None, 5, 0.5, None, 0, 0) == -1
+    # allocator hooks must come in pairs
+    assert lib.scan_set_allocator(ctypes.c_void_p(1), None, None) == -1
+    assert lib.scan_set_allocator(None, None, None) == 0
+
+
+def test_build_script_targets_sm103a():
+    from paper_2012_11188_gb300 import _build
+    assert "arch=compute_103a,code=sm_103a" in " ".join(_build.NVCC_FLAGS)
