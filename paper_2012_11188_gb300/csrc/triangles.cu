@@ -61,8 +61,18 @@ __device__ __forceinline__ int64_t find_item_vertex(const int64_t* item_off, int
   return lo;
 }
 
+constexpr int FILTER_WORDS = 1024;  // 32768-bit membership filter in front of the table
+constexpr int FILTER_LOG2 = 15;
+
 // BIG = out(v) too long for the shared table: probe by binary search in the
 // sorted global out-list and count (v,w) hits with global atomics.
+//
+// Inner loop (one warp): the in-neighbours u among 32 consecutive positions of
+// N(v) are compacted to lanes 0..k-1; their out-list lengths are prefix-summed
+// and the concatenated lists are walked 32 elements per round, lane l taking
+// element r*32+l. The owner of an element is found from the starts that fall
+// in the round (ballot / or-reduce / popc), so lanes stay busy whatever the
+// list lengths.
 template <bool BIG>
 __global__ void __launch_bounds__(TRI_THREADS)
 k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
@@ -71,14 +81,20 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
             unsigned long long* __restrict__ work, int lsh_T, int od_cap,
             uint32_t* __restrict__ tcnt, int32_t* __restrict__ twin_rel, unsigned* status) {
   // shared layout for od_cap (a power of two >= every od handled here):
-  // hkey[2*od_cap] int32 | vcnt[od_cap] uint32 | hpos[2*od_cap] uint16
+  // filter[FILTER_WORDS] | hkey[2*od_cap] int32 | vcnt[od_cap] uint32 | hpos[2*od_cap] uint16
   extern __shared__ int32_t smem[];
   __shared__ long long s_item;
+  __shared__ int32_t s_u[TRI_WARPS][32];
+  __shared__ int32_t s_p[TRI_WARPS][32];
+  __shared__ uint32_t s_acc[TRI_WARPS][32];
+  __shared__ long long s_jv[TRI_WARPS][32];
+  const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t total = item_off[n];
-  int32_t* hkey = smem;
-  uint32_t* vcnt = (uint32_t*)(smem + 2 * od_cap);
-  uint16_t* hpos = (uint16_t*)(smem + 3 * od_cap);
+  uint32_t* filt = (uint32_t*)smem;
+  int32_t* hkey = smem + FILTER_WORDS;
+  uint32_t* vcnt = (uint32_t*)(smem + FILTER_WORDS + 2 * od_cap);
+  uint16_t* hpos = (uint16_t*)(smem + FILTER_WORDS + 3 * od_cap);
   unsigned bad = 0;
 
   for (;;) {
@@ -99,10 +115,14 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
       const int H = 1 << log2h;
       for (int i = threadIdx.x; i < H; i += TRI_THREADS) hkey[i] = -1;
       for (int i = threadIdx.x; i < od; i += TRI_THREADS) vcnt[i] = 0;
+      for (int i = threadIdx.x; i < FILTER_WORDS; i += TRI_THREADS) filt[i] = 0;
       __syncthreads();
       for (int j = threadIdx.x; j < od; j += TRI_THREADS) {
         const int32_t x = oadj[ob + j];
-        uint32_t s = hslot(x, log2h);
+        const uint32_t hx = (uint32_t)x * 0x9E3779B1u;
+        const uint32_t fb = hx >> (32 - FILTER_LOG2);
+        atomicOr(&filt[fb >> 5], 1u << (fb & 31));
+        uint32_t s = hx >> (32 - log2h);
         for (int probe = 0; probe < H; ++probe) {
           const int32_t prev = atomicCAS(&hkey[s], -1, x);
           if (prev == -1) { hpos[s] = (uint16_t)j; break; }
@@ -115,7 +135,6 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
     const int64_t rb = off[v];
     const int64_t p_begin = chunk * CHUNK;
     const int64_t p_end = min((int64_t)dv, p_begin + CHUNK);
-    // each warp takes 32 consecutive CSR positions at a time
     for (int64_t p0 = p_begin + 32 * wid; p0 < p_end; p0 += 32 * TRI_WARPS) {
       const int64_t p = p0 + lane;
       int32_t u = -1;
@@ -128,67 +147,110 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
         // every triangle u < v < w is approximated, so the scan is not needed
         if (is_in && lsh_T >= 0 && du > lsh_T) is_in = false;
       }
-      unsigned m = __ballot_sync(0xffffffffu, is_in);
-      while (m) {
-        const int src = __ffs(m) - 1;
-        m &= m - 1;
-        const int32_t uu = __shfl_sync(0xffffffffu, u, src);
-        const int64_t ub = oo[uu], ue = oo[uu + 1];
-        if (od == 0) {
-          // no triangle has v in the middle: only locate v in the sorted out(u)
-          if (lane == 0) {
-            int64_t lo = ub, hi = ue;
-            while (lo < hi) {
-              const int64_t mid = (lo + hi) >> 1;
-              if (oadj[mid] < (int32_t)v) lo = mid + 1; else hi = mid;
-            }
-            if (lo < ue && oadj[lo] == (int32_t)v) twin_rel[lo] = (int32_t)(p0 + src);
-            else bad = 1;
+      const unsigned m = __ballot_sync(FULL, is_in);
+      if (!m) continue;
+      const int k = __popc(m);
+      if (is_in) {
+        const int r = __popc(m & ((1u << lane) - 1u));
+        s_u[wid][r] = u;
+        s_p[wid][r] = (int32_t)p;
+      }
+      __syncwarp();
+      int32_t cu = -1, cp = 0, clen = 0;
+      int64_t cub = 0;
+      if (lane < k) {
+        cu = s_u[wid][lane];
+        cp = s_p[wid][lane];
+        cub = oo[cu];
+        clen = (int32_t)(oo[cu + 1] - cub);
+      }
+      if (od == 0) {
+        // no triangle has v in the middle: only locate v in the sorted out(u)
+        if (lane < k) {
+          int64_t lo = cub, hi = cub + clen;
+          while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (oadj[mid] < (int32_t)v) lo = mid + 1; else hi = mid;
           }
-          continue;
+          if (lo < cub + clen && oadj[lo] == (int32_t)v) twin_rel[lo] = cp;
+          else bad = 1;
         }
-        unsigned acc = 0;
-        int64_t jv = -1;
-        for (int64_t j = ub + lane; j < ue; j += 32) {
+        __syncwarp();
+        continue;
+      }
+      int32_t incl = clen;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const int32_t cstart = incl - clen;
+      const int32_t W = __shfl_sync(FULL, incl, 31);
+      s_acc[wid][lane] = 0;
+      s_jv[wid][lane] = -1;
+      __syncwarp();
+      for (int32_t r0 = 0; r0 < W; r0 += 32) {
+        // every list is non-empty (v is in out(u)), so the starts are distinct
+        const bool starts_here = lane < k && cstart >= r0 && cstart < r0 + 32;
+        const unsigned smask = __reduce_or_sync(FULL, starts_here ? (1u << (cstart - r0)) : 0u);
+        const int before = __popc(__ballot_sync(FULL, lane < k && cstart < r0));
+        const int owner = before + __popc(smask & ((2u << lane) - 1u)) - 1;
+        const int own = owner < 0 ? 0 : owner;
+        const int64_t ub_o = __shfl_sync(FULL, cub, own);
+        const int32_t st_o = __shfl_sync(FULL, cstart, own);
+        const int32_t t = r0 + lane;
+        bool hit = false;
+        if (t < W) {
+          const int64_t j = ub_o + (t - st_o);
           const int32_t x = oadj[j];
-          if (x == (int32_t)v) jv = j;
+          if (x == (int32_t)v) s_jv[wid][own] = j;
           int q = -1;
           if (!BIG) {
-            uint32_t s = hslot(x, log2h);
-            for (int probe = 0; probe < H; ++probe) {
-              const int32_t k = hkey[s];
-              if (k == x) { q = hpos[s]; break; }
-              if (k == -1) break;
-              s = (s + 1) & (H - 1);
+            const uint32_t hx = (uint32_t)x * 0x9E3779B1u;
+            const uint32_t fb = hx >> (32 - FILTER_LOG2);
+            if ((filt[fb >> 5] >> (fb & 31)) & 1u) {
+              uint32_t sl = hx >> (32 - log2h);
+              for (int probe = 0; probe < H; ++probe) {
+                const int32_t key = hkey[sl];
+                if (key == x) { q = hpos[sl]; break; }
+                if (key == -1) break;
+                sl = (sl + 1) & (H - 1);
+              }
             }
           } else {
             int lo = 0, hi = od;
             while (lo < hi) {
               const int mid = (lo + hi) >> 1;
-              const int32_t y = oadj[ob + mid];
-              if (y < x) lo = mid + 1; else hi = mid;
+              if (oadj[ob + mid] < x) lo = mid + 1; else hi = mid;
             }
             if (lo < od && oadj[ob + lo] == x) q = lo;
           }
           if (q >= 0) {
-            ++acc;
+            hit = true;
             if (!BIG) atomicAdd(&vcnt[q], 1u);
             else atomicAdd(&tcnt[ob + q], 1u);
             atomicAdd(&tcnt[j], 1u);
           }
         }
-        for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        long long jvl = (long long)jv;
-        for (int o = 16; o; o >>= 1) jvl = max(jvl, __shfl_xor_sync(0xffffffffu, jvl, o));
-        if (lane == 0) {
-          if (jvl < 0) {
-            bad = 1;  // v lists u but u does not list v
-          } else {
-            if (acc) atomicAdd(&tcnt[jvl], acc);
-            twin_rel[jvl] = (int32_t)(p0 + src);  // position of u in N(v)
-          }
+        // hits per owner: lanes of one owner are contiguous; its first lane adds
+        const unsigned hm = __ballot_sync(FULL, hit);
+        const unsigned peers = __match_any_sync(FULL, own);
+        if (hm & peers) {
+          if (lane == __ffs(peers) - 1) s_acc[wid][own] += __popc(hm & peers);
         }
       }
+      __syncwarp();
+      if (lane < k) {
+        const long long jv = s_jv[wid][lane];
+        if (jv < 0) {
+          bad = 1;  // v lists u but u does not list v
+        } else {
+          const uint32_t acc = s_acc[wid][lane];
+          if (acc) atomicAdd(&tcnt[jv], acc);
+          twin_rel[jv] = cp;  // position of u in N(v)
+        }
+      }
+      __syncwarp();
     }
     __syncthreads();
     if (!BIG)
@@ -278,8 +340,10 @@ int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* a
   if (n > 0 && m > 0) {
     int od_cap = 32;
     while (od_cap < max_od && od_cap < SMEM_OD_MAX) od_cap <<= 1;
-    const size_t smem = (size_t)3 * od_cap * sizeof(int32_t) + (size_t)2 * od_cap * sizeof(uint16_t);
-    const size_t smem_max = (size_t)3 * SMEM_OD_MAX * 4 + (size_t)2 * SMEM_OD_MAX * 2;
+    const size_t smem = (size_t)FILTER_WORDS * 4 + (size_t)3 * od_cap * sizeof(int32_t) +
+                        (size_t)2 * od_cap * sizeof(uint16_t);
+    const size_t smem_max = (size_t)FILTER_WORDS * 4 + (size_t)3 * SMEM_OD_MAX * 4 +
+                            (size_t)2 * SMEM_OD_MAX * 2;
     GS_CUDA(cudaFuncSetAttribute(k_triangles<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem_max));
     int dev = 0, sms = 152, per_sm = 1;
