@@ -184,7 +184,7 @@ __global__ void k_hubs(QArgs a) {
 }  // namespace
 
 int run_queries(const IndexData& ix, int Q, const int* mu_host, const double* eps_host,
-                int32_t* labels_dev, int flags, Pool& pool, cudaStream_t s) {
+                int32_t* labels_dev, int flags, Pool& pool, cudaStream_t s, unsigned* status_dev) {
   if (Q <= 0) return SCAN_OK;
   const int64_t n = ix.n;
   int* mu = pool.get<int>(Q);
@@ -197,7 +197,7 @@ int run_queries(const IndexData& ix, int Q, const int* mu_host, const double* ep
   if (n == 0) return SCAN_OK;
   GS_CUDA(cudaMemsetAsync(parent, 0xff, sizeof(int32_t) * (size_t)Q * n, s));
   QArgs a{ix.off, ix.deg, ix.adj, ix.no_id, ix.no_sim, ix.co_off, ix.co_id, ix.co_thr,
-          n, ix.maxdeg, mu, eps, nc, parent, labels_dev, ix.status};
+          n, ix.maxdeg, mu, eps, nc, parent, labels_dev, status_dev};
   k_get_cores<<<(Q + 127) / 128, 128, 0, s>>>(a, Q);
   GS_LAUNCH();
   const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8 / std::min(Q, 8) + 1));

@@ -2,14 +2,11 @@
 // Declarations and argument conventions: include/scan.h.
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <vector>
 
 #include "scan_internal.cuh"
-
-struct scan_index {
-  gscan::IndexData d;
-};
 
 namespace gscan {
 
@@ -59,8 +56,6 @@ void record_timings(const double* ms7) {
   for (int i = 0; i < 7; ++i) g_timings[i] = ms7[i];
 }
 
-namespace {
-
 bool is_device_ptr(const void* p) {
   if (!p) return false;
   cudaPointerAttributes at;
@@ -70,6 +65,15 @@ bool is_device_ptr(const void* p) {
   }
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
+
+size_t build_footprint(int64_t n, int64_t arcs) {
+  // index 28 B/arc + 12 B/vertex; build temporaries: oriented lists, counts,
+  // twins (16 B/edge), sort scratch (12 B/arc), item and scan arrays (~24 B/vertex)
+  return (size_t)arcs * 28 + (size_t)n * 12 + (size_t)(arcs / 2) * 16 + (size_t)arcs * 12 +
+         (size_t)n * 24 + (1u << 20);
+}
+
+namespace {
 
 __global__ void k_off32_to_64(const int32_t* __restrict__ in, int64_t n1, int64_t* __restrict__ out) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n1;
@@ -132,23 +136,107 @@ int validate_lsh(const scan_lsh_params* p, int kind) {
   return SCAN_OK;
 }
 
-// Build one index into ix; on error every block is released by the pool.
-int build_one(const scan_csr* csr, int kind, const scan_lsh_params* lsh, cudaStream_t s,
-              IndexData* ix) {
+// Steps shared by the single and the batched build: CSR checks, degrees,
+// orientation, counts and similarities, LSH estimates, neighbour order.
+// ix holds n, arcs, off (absolute, int64), adj and allocated deg, no_id,
+// no_sim and a 4-word status block; on return ix->maxdeg is set.
+int run_pipeline(IndexData* ix, int kind, const scan_lsh_params* lsh, Pool& pool, cudaStream_t s,
+                 Events& ev, float* count_ms) {
+  const int64_t n = ix->n, arcs = ix->arcs;
+  const bool use_lsh = lsh && lsh->enabled;
+  unsigned* scalars = ix->status;  // [0] status, [1] maxdeg, [2] max out-degree
+  GS_TRY(launch_degrees(ix->off, ix->adj, n, arcs, ix->deg, (int32_t*)scalars + 1, scalars, s));
+  unsigned hs[4];
+  GS_CUDA(cudaMemcpyAsync(hs, scalars, sizeof(hs), cudaMemcpyDeviceToHost, s));
+  GS_CUDA(cudaStreamSynchronize(s));
+  if (hs[0] & DEV_BADGRAPH) return SCAN_EBADGRAPH;
+  ix->maxdeg = (int32_t)hs[1];
+  // ---- orientation (Section 6.1)
+  int64_t* oo = nullptr;
+  int32_t *oadj = nullptr, *opos = nullptr;
+  if (arcs > 0) {
+    GS_TRY(launch_orient(ix->off, ix->adj, ix->deg, n, arcs, pool, &oo, &oadj, &opos,
+                         (int32_t*)scalars + 2, s));
+    GS_CUDA(cudaMemcpyAsync(hs, scalars, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    GS_CUDA(cudaStreamSynchronize(s));
+  }
+  const int32_t max_od = (int32_t)hs[2];
+  GS_TRY(ev.mark(s));
+  // ---- LSH selection (Section 6.3)
+  int32_t* row = nullptr;
+  int64_t nH = 0;
+  if (use_lsh && arcs > 0) {
+    row = pool.get<int32_t>(n);
+    if (!row) return SCAN_ENOMEM;
+    GS_TRY(lsh_select(ix->off, ix->adj, ix->deg, n, lsh->degree_threshold, row, &nH, pool, s));
+  }
+  // ---- counts and similarities (Section 3.1, Section 6.1)
+  if (arcs > 0) {
+    GS_CUDA(cudaMemcpyAsync(ix->no_id, ix->adj, arcs * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    GS_TRY(launch_closed_counts_and_sims(kind, ix->off, ix->adj, ix->deg, n, arcs, oo, oadj, opos,
+                                         max_od, use_lsh ? lsh->degree_threshold : -1,
+                                         ix->no_sim, scalars, pool, s, count_ms));
+    GS_CUDA(cudaMemcpyAsync(hs, scalars, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    GS_CUDA(cudaStreamSynchronize(s));
+    if (hs[0] & DEV_BADGRAPH) return SCAN_EBADGRAPH;
+    pool.put(oo);
+    pool.put(oadj);
+    pool.put(opos);
+  }
+  GS_TRY(ev.mark(s));
+  if (use_lsh && nH > 0)
+    GS_TRY(lsh_apply(*lsh, kind, ix->off, ix->adj, ix->deg, n, arcs, row, nH, ix->no_sim, pool, s));
+  if (row) pool.put(row);
+  GS_TRY(ev.mark(s));
+  // ---- neighbour order (Algorithm 2)
+  GS_TRY(segmented_sort_desc((uint64_t*)ix->no_sim, ix->no_id, ix->off, n, arcs, ix->maxdeg, pool, s));
+  GS_TRY(ev.mark(s));
+  return SCAN_OK;
+}
+
+void store_timings(Events& ev, float count_ms) {
+  double t[7];
+  t[0] = ev.ms(0, 1);
+  t[1] = count_ms;
+  t[2] = ev.ms(1, 2) - count_ms;
+  t[5] = ev.ms(2, 3);
+  t[3] = ev.ms(3, 4);
+  t[4] = ev.ms(4, 5);
+  t[6] = ev.ms(0, 5);
+  record_timings(t);
+}
+
+int check_final_status(const unsigned* scalars, cudaStream_t s) {
+  unsigned hs[4];
+  GS_CUDA(cudaMemcpyAsync(hs, scalars, sizeof(hs), cudaMemcpyDeviceToHost, s));
+  GS_CUDA(cudaStreamSynchronize(s));
+  if (hs[0] & DEV_BADGRAPH) return SCAN_EBADGRAPH;
+  if (hs[0] & DEV_LIMIT) return SCAN_ETIMEOUT;
+  return SCAN_OK;
+}
+
+int check_csr_args(const scan_csr* csr) {
   const int64_t n = csr->n, arcs = csr->num_arcs;
   if (n < 0 || n > 0x7ffffffe || arcs < 0) return SCAN_EINVAL;
   if ((n > 0 && !csr->offsets) || (arcs > 0 && !csr->adj)) return SCAN_EINVAL;
+  if (arcs % 2) return SCAN_EBADGRAPH;
+  return SCAN_OK;
+}
+
+// Build one index into ix; on error every block is released by the pool.
+int build_one(const scan_csr* csr, int kind, const scan_lsh_params* lsh, cudaStream_t s,
+              IndexData* ix) {
+  GS_TRY(check_csr_args(csr));
   if (kind != SCAN_COSINE && kind != SCAN_JACCARD) return SCAN_EINVAL;
   GS_TRY(validate_lsh(lsh, kind));
-  if (arcs % 2) return SCAN_EBADGRAPH;
-  const bool use_lsh = lsh && lsh->enabled;
+  const int64_t n = csr->n, arcs = csr->num_arcs;
   Pool pool(s);
   Events ev;
   GS_TRY(ev.mark(s));
   ix->n = n;
   ix->arcs = arcs;
   ix->kind = kind;
-  ix->lsh = use_lsh;
+  ix->lsh = lsh && lsh->enabled;
   ix->home = 0;  // frees and exports run on the legacy stream after this call has synchronised
   ix->off = pool.get<int64_t>(n + 1);
   ix->deg = pool.get<int32_t>(n > 0 ? n : 1);
@@ -158,8 +246,7 @@ int build_one(const scan_csr* csr, int kind, const scan_lsh_params* lsh, cudaStr
   ix->status = pool.get<unsigned>(4);
   if (!ix->off || !ix->deg || !ix->adj || !ix->no_id || !ix->no_sim || !ix->status)
     return SCAN_ENOMEM;
-  unsigned* scalars = ix->status;  // [0] status, [1] maxdeg, [2] max out-degree
-  GS_CUDA(cudaMemsetAsync(scalars, 0, 4 * sizeof(unsigned), s));
+  GS_CUDA(cudaMemsetAsync(ix->status, 0, 4 * sizeof(unsigned), s));
   // ---- inputs into the index's own arrays
   const bool dev_in = csr->on_device != 0;
   const cudaMemcpyKind k_in = dev_in ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -181,80 +268,282 @@ int build_one(const scan_csr* csr, int kind, const scan_lsh_params* lsh, cudaStr
   int64_t ends[2] = {0, 0};
   GS_CUDA(cudaMemcpyAsync(&ends[0], ix->off, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   GS_CUDA(cudaMemcpyAsync(&ends[1], ix->off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  // ---- degrees, checks, orientation (Section 6.1)
-  GS_TRY(launch_degrees(ix->off, ix->adj, n, arcs, ix->deg, (int32_t*)scalars + 1, scalars, s));
   GS_CUDA(cudaStreamSynchronize(s));
   if (ends[0] != 0 || ends[1] != arcs) return SCAN_EBADGRAPH;
-  unsigned hs[4];
-  GS_CUDA(cudaMemcpy(hs, scalars, sizeof(hs), cudaMemcpyDeviceToHost));
-  if (hs[0] & DEV_BADGRAPH) return SCAN_EBADGRAPH;
-  ix->maxdeg = (int32_t)hs[1];
-  int64_t *oo = nullptr;
-  int32_t *oadj = nullptr, *opos = nullptr;
-  if (arcs > 0) {
-    GS_TRY(launch_orient(ix->off, ix->adj, ix->deg, n, arcs, pool, &oo, &oadj, &opos,
-                         (int32_t*)scalars + 2, s));
-    GS_CUDA(cudaMemcpyAsync(hs, scalars, sizeof(hs), cudaMemcpyDeviceToHost, s));
-    GS_CUDA(cudaStreamSynchronize(s));
-  }
-  const int32_t max_od = (int32_t)hs[2];
-  GS_TRY(ev.mark(s));
-  // ---- LSH selection (Section 6.3)
-  int32_t* row = nullptr;
-  int64_t nH = 0;
-  if (use_lsh && arcs > 0) {
-    row = pool.get<int32_t>(n);
-    if (!row) return SCAN_ENOMEM;
-    GS_TRY(lsh_select(ix->off, ix->adj, ix->deg, n, lsh->degree_threshold, row, &nH, pool, s));
-  }
-  // ---- counts and similarities (Section 3.1, Section 6.1)
   float count_ms = 0;
-  if (arcs > 0) {
-    GS_CUDA(cudaMemcpyAsync(ix->no_id, ix->adj, arcs * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
-    GS_TRY(launch_closed_counts_and_sims(kind, ix->off, ix->adj, ix->deg, n, arcs, oo, oadj, opos,
-                                         max_od, use_lsh ? lsh->degree_threshold : -1,
-                                         ix->no_sim, scalars, pool, s, &count_ms));
-    GS_CUDA(cudaMemcpyAsync(hs, scalars, sizeof(hs), cudaMemcpyDeviceToHost, s));
-    GS_CUDA(cudaStreamSynchronize(s));
-    if (hs[0] & DEV_BADGRAPH) return SCAN_EBADGRAPH;
-    pool.put(oo);
-    pool.put(oadj);
-    pool.put(opos);
-  }
-  GS_TRY(ev.mark(s));
-  if (use_lsh && nH > 0)
-    GS_TRY(lsh_apply(*lsh, kind, ix->off, ix->adj, ix->deg, n, arcs, row, nH, ix->no_sim, pool, s));
-  if (row) pool.put(row);
-  GS_TRY(ev.mark(s));
-  // ---- neighbour order (Algorithm 2)
-  GS_TRY(segmented_sort_desc((uint64_t*)ix->no_sim, ix->no_id, ix->off, n, arcs, ix->maxdeg, pool, s));
-  GS_TRY(ev.mark(s));
+  GS_TRY(run_pipeline(ix, kind, lsh, pool, s, ev, &count_ms));
   // ---- core order (Algorithm 2)
   GS_TRY(build_core_order(*ix, pool, s));
   GS_TRY(ev.mark(s));
-  GS_CUDA(cudaStreamSynchronize(s));
-  GS_CUDA(cudaMemcpy(hs, scalars, sizeof(hs), cudaMemcpyDeviceToHost));
-  if (hs[0] & DEV_BADGRAPH) return SCAN_EBADGRAPH;
-  if (hs[0] & DEV_LIMIT) return SCAN_ETIMEOUT;
-  double t[7];
-  t[0] = ev.ms(0, 1);
-  t[1] = count_ms;
-  t[2] = ev.ms(1, 2) - count_ms;
-  t[5] = ev.ms(2, 3);
-  t[3] = ev.ms(3, 4);
-  t[4] = ev.ms(4, 5);
-  t[6] = ev.ms(0, 5);
-  record_timings(t);
+  GS_TRY(check_final_status(ix->status, s));
+  store_timings(ev, count_ms);
   ix->blocks = pool.detach();
   ix->bytes = 0;
   for (auto& b : ix->blocks) ix->bytes += b.b;
   return SCAN_OK;
 }
 
-void free_index(IndexData* ix) {
+// ---------------------------------------------------------------- batched build
+__device__ __forceinline__ int64_t last_le(const int64_t* a, int64_t cnt, int64_t x) {
+  int64_t lo = 0, hi = cnt;
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (a[mid] <= x) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// union offsets: off[u] = ab_g + raw[u + g] for u in graph g; off[N] = A.
+// raw holds each graph's own n_g+1 offsets, graph g starting at vb_g + g.
+__global__ void k_pack_offsets(const int64_t* __restrict__ raw, const int64_t* __restrict__ vb,
+                               const int64_t* __restrict__ ab, int G, int64_t N,
+                               int64_t* __restrict__ off, unsigned* status) {
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u <= N;
+       u += (int64_t)gridDim.x * blockDim.x) {
+    if (u == N) { off[N] = ab[G]; continue; }
+    const int64_t g = last_le(vb, G, u);
+    const int64_t o = raw[u + g];
+    const int64_t na = ab[g + 1] - ab[g];
+    if (o < 0 || o > na) { atomicOr(status, (unsigned)DEV_BADGRAPH); off[u] = ab[g]; continue; }
+    off[u] = ab[g] + o;
+  }
+}
+
+__global__ void k_check_ends(const int64_t* __restrict__ raw, const int64_t* __restrict__ vb,
+                             const int64_t* __restrict__ ab, int G, unsigned* status) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < G;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = vb[g] + g, ng = vb[g + 1] - vb[g];
+    if (raw[b] != 0 || raw[b + ng] != ab[g + 1] - ab[g]) atomicOr(status, (unsigned)DEV_BADGRAPH);
+  }
+}
+
+// local ids -> union ids (checked against the graph's own n)
+__global__ void k_shift_adj(int32_t* __restrict__ adj, const int64_t* __restrict__ vb,
+                            const int64_t* __restrict__ ab, int G, int64_t A, unsigned* status) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t g = last_le(ab, G, i);
+    const int32_t x = adj[i];
+    const int64_t ng = vb[g + 1] - vb[g];
+    if (x < 0 || x >= ng) { atomicOr(status, (unsigned)DEV_BADGRAPH); adj[i] = (int32_t)vb[g]; continue; }
+    adj[i] = (int32_t)(x + vb[g]);
+  }
+}
+
+__global__ void k_graph_maxdeg(const int32_t* __restrict__ deg, const int64_t* __restrict__ vb, int G,
+                               int64_t N, int32_t* __restrict__ md) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t d = deg[v];
+    if (d > 0) atomicMax(&md[last_le(vb, G, v)], d);
+  }
+}
+
+// union ids -> local ids in adj and NO
+__global__ void k_rebase_ids(int32_t* __restrict__ adj, int32_t* __restrict__ no_id,
+                             const int64_t* __restrict__ vb, const int64_t* __restrict__ ab, int G,
+                             int64_t A) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t b = (int32_t)vb[last_le(ab, G, i)];
+    adj[i] -= b;
+    no_id[i] -= b;
+  }
+}
+
+// per-graph offsets relative to the graph's first arc: graph g's n_g+1 entries
+// start at rb[g] = vb[g] + g (rel_off) / its maxdeg_g+1 CO offsets at cb[g]
+__global__ void k_rebase_offsets(const int64_t* __restrict__ src, const int64_t* __restrict__ base,
+                                 const int64_t* __restrict__ rb, const int64_t* __restrict__ ab,
+                                 int G, int64_t total, int64_t* __restrict__ rel) {
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < total;
+       u += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t g = last_le(rb, G, u);
+    rel[u] = src[base[g] + (u - rb[g])] - ab[g];
+  }
+}
+
+struct Arena {
+  std::vector<Pool::Blk> blocks;
+  ~Arena() {
+    for (auto& b : blocks) dev_free(b.p, b.b, 0);
+  }
+};
+
+int build_batch(const scan_csr* graphs, int G, int kind, const scan_lsh_params* lsh,
+                cudaStream_t s, scan_index** out) {
+  if (kind != SCAN_COSINE && kind != SCAN_JACCARD) return SCAN_EINVAL;
+  GS_TRY(validate_lsh(lsh, kind));
+  std::vector<int64_t> vb(G + 1, 0), ab(G + 1, 0);
+  for (int g = 0; g < G; ++g) {
+    GS_TRY(check_csr_args(&graphs[g]));
+    vb[g + 1] = vb[g] + graphs[g].n;
+    ab[g + 1] = ab[g] + graphs[g].num_arcs;
+  }
+  const int64_t N = vb[G], A = ab[G];
+  if (N > 0x7ffffffe) return SCAN_EINVAL;  // union ids are int32
+  Pool pool(s);
+  Events ev;
+  GS_TRY(ev.mark(s));
+  IndexData u;
+  u.n = N;
+  u.arcs = A;
+  u.kind = kind;
+  u.off = pool.get<int64_t>(N + 1);
+  u.deg = pool.get<int32_t>(N > 0 ? N : 1);
+  u.adj = pool.get<int32_t>(A > 0 ? A : 1);
+  u.no_id = pool.get<int32_t>(A > 0 ? A : 1);
+  u.no_sim = pool.get<double>(A > 0 ? A : 1);
+  u.status = pool.get<unsigned>(4);
+  int64_t* raw = pool.get<int64_t>(N + G);
+  int64_t* meta = pool.get<int64_t>(2 * (size_t)(G + 1));
+  if (!u.off || !u.deg || !u.adj || !u.no_id || !u.no_sim || !u.status || !raw || !meta)
+    return SCAN_ENOMEM;
+  GS_CUDA(cudaMemsetAsync(u.status, 0, 4 * sizeof(unsigned), s));
+  std::vector<int64_t> hmeta(2 * (size_t)(G + 1));
+  std::copy(vb.begin(), vb.end(), hmeta.begin());
+  std::copy(ab.begin(), ab.end(), hmeta.begin() + (G + 1));
+  GS_CUDA(cudaMemcpyAsync(meta, hmeta.data(), hmeta.size() * 8, cudaMemcpyHostToDevice, s));
+  const int64_t* d_vb = meta;
+  const int64_t* d_ab = meta + (G + 1);
+  // ---- pack: raw offsets (int64) and adjacency of every graph into the arena
+  std::vector<std::vector<int64_t>> staged;
+  for (int g = 0; g < G; ++g) {
+    const scan_csr& c = graphs[g];
+    const cudaMemcpyKind k = c.on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    int64_t* dst = raw + vb[g] + g;
+    if (c.offsets_64) {
+      GS_CUDA(cudaMemcpyAsync(dst, c.offsets, (c.n + 1) * 8, k, s));
+    } else if (c.on_device) {
+      k_off32_to_64<<<(unsigned)std::min<int64_t>((c.n + 256) / 256, 4096), 256, 0, s>>>(
+          (const int32_t*)c.offsets, c.n + 1, dst);
+      GS_LAUNCH();
+    } else {
+      staged.emplace_back(c.n + 1);
+      const int32_t* o32 = (const int32_t*)c.offsets;
+      for (int64_t i = 0; i <= c.n; ++i) staged.back()[i] = o32[i];
+      GS_CUDA(cudaMemcpyAsync(dst, staged.back().data(), (c.n + 1) * 8, cudaMemcpyHostToDevice, s));
+    }
+    if (c.num_arcs > 0) GS_CUDA(cudaMemcpyAsync(u.adj + ab[g], c.adj, c.num_arcs * 4, k, s));
+  }
+  const unsigned gN = (unsigned)std::max<int64_t>(1, std::min<int64_t>((N + 256) / 256, 152 * 16));
+  const unsigned gA = (unsigned)std::max<int64_t>(1, std::min<int64_t>((A + 255) / 256, 152 * 16));
+  const unsigned gG = (unsigned)std::max<int64_t>(1, std::min<int64_t>((G + 255) / 256, 152 * 16));
+  k_check_ends<<<gG, 256, 0, s>>>(raw, d_vb, d_ab, G, u.status);
+  GS_LAUNCH();
+  k_pack_offsets<<<gN, 256, 0, s>>>(raw, d_vb, d_ab, G, N, u.off, u.status);
+  GS_LAUNCH();
+  if (A > 0) {
+    k_shift_adj<<<gA, 256, 0, s>>>(u.adj, d_vb, d_ab, G, A, u.status);
+    GS_LAUNCH();
+  }
+  GS_CUDA(cudaStreamSynchronize(s));  // staged host offsets must outlive their copies
+  staged.clear();
+  pool.put(raw);
+  // ---- the shared pipeline over the union (every step is local to a vertex)
+  float count_ms = 0;
+  GS_TRY(run_pipeline(&u, kind, lsh, pool, s, ev, &count_ms));
+  // ---- per-graph core orders
+  int32_t* md_dev = pool.get<int32_t>(G);
+  if (!md_dev) return SCAN_ENOMEM;
+  GS_CUDA(cudaMemsetAsync(md_dev, 0, G * 4, s));
+  k_graph_maxdeg<<<gN, 256, 0, s>>>(u.deg, d_vb, G, N, md_dev);
+  GS_LAUNCH();
+  std::vector<int32_t> md(G);
+  GS_CUDA(cudaMemcpyAsync(md.data(), md_dev, G * 4, cudaMemcpyDeviceToHost, s));
+  GS_CUDA(cudaStreamSynchronize(s));
+  pool.put(md_dev);
+  std::vector<int64_t> sb(G + 1, 0), rb(G + 1, 0), cb(G + 1, 0);
+  for (int g = 0; g < G; ++g) {
+    sb[g + 1] = sb[g] + md[g];
+    rb[g + 1] = rb[g] + (vb[g + 1] - vb[g]) + 1;
+    cb[g + 1] = cb[g] + md[g] + 1;
+  }
+  const int64_t S = sb[G];
+  int64_t* co_off_all = pool.get<int64_t>(S + 1);
+  int32_t* co_id = pool.get<int32_t>(A > 0 ? A : 1);
+  double* co_thr = pool.get<double>(A > 0 ? A : 1);
+  int64_t* off_rel = pool.get<int64_t>(N + G);
+  int64_t* co_off_rel = pool.get<int64_t>(S + G);
+  int64_t* meta2 = pool.get<int64_t>(4 * (size_t)(G + 1));
+  if (!co_off_all || !co_id || !co_thr || !off_rel || !co_off_rel || !meta2) return SCAN_ENOMEM;
+  GS_TRY(build_core_order_multi(N, A, u.off, u.deg, (const uint64_t*)u.no_sim, vb, md, co_off_all,
+                                co_id, (uint64_t*)co_thr, pool, s));
+  GS_TRY(ev.mark(s));
+  // ---- back to per-graph ids and offsets
+  std::vector<int64_t> hm2(4 * (size_t)(G + 1));
+  std::copy(rb.begin(), rb.end(), hm2.begin());
+  std::copy(vb.begin(), vb.end(), hm2.begin() + (G + 1));
+  std::copy(cb.begin(), cb.end(), hm2.begin() + 2 * (G + 1));
+  std::copy(sb.begin(), sb.end(), hm2.begin() + 3 * (G + 1));
+  GS_CUDA(cudaMemcpyAsync(meta2, hm2.data(), hm2.size() * 8, cudaMemcpyHostToDevice, s));
+  if (A > 0) {
+    k_rebase_ids<<<gA, 256, 0, s>>>(u.adj, u.no_id, d_vb, d_ab, G, A);
+    GS_LAUNCH();
+  }
+  k_rebase_offsets<<<gN, 256, 0, s>>>(u.off, meta2 + (G + 1), meta2, d_ab, G, N + G, off_rel);
+  GS_LAUNCH();
+  const unsigned gS = (unsigned)std::max<int64_t>(1, std::min<int64_t>((S + G + 255) / 256, 152 * 16));
+  k_rebase_offsets<<<gS, 256, 0, s>>>(co_off_all, meta2 + 3 * (G + 1), meta2 + 2 * (G + 1), d_ab, G,
+                                      S + G, co_off_rel);
+  GS_LAUNCH();
+  GS_TRY(check_final_status(u.status, s));
+  store_timings(ev, count_ms);
+  pool.put(co_off_all);
+  pool.put(u.off);
+  pool.put(meta2);
+  // ---- handles viewing the shared arena
+  auto arena = std::make_shared<Arena>();
+  size_t total_bytes = 0;
+  for (auto& b : pool.blocks) total_bytes += b.b;
+  std::vector<scan_index*> hs(G, nullptr);
+  for (int g = 0; g < G; ++g) {
+    hs[g] = new (std::nothrow) scan_index();
+    if (!hs[g]) {
+      for (int j = 0; j < g; ++j) delete hs[j];
+      return SCAN_ENOMEM;
+    }
+  }
+  arena->blocks = pool.detach();
+  for (int g = 0; g < G; ++g) {
+    IndexData& d = hs[g]->d;
+    d.n = vb[g + 1] - vb[g];
+    d.arcs = ab[g + 1] - ab[g];
+    d.maxdeg = md[g];
+    d.kind = kind;
+    d.lsh = lsh && lsh->enabled;
+    d.off = off_rel + rb[g];
+    d.deg = u.deg + vb[g];
+    d.adj = u.adj + ab[g];
+    d.no_id = u.no_id + ab[g];
+    d.no_sim = u.no_sim + ab[g];
+    d.co_off = co_off_rel + cb[g];
+    d.co_id = co_id + ab[g];
+    d.co_thr = co_thr + ab[g];
+    d.status = u.status;
+    d.home = 0;
+    d.arena = arena;
+    d.bytes = A > 0 ? (size_t)((double)total_bytes * (double)d.arcs / (double)A) : 0;
+    out[g] = hs[g];
+  }
+  return SCAN_OK;
+}
+
+}  // namespace
+
+int build_index(const scan_csr* csr, int kind, const scan_lsh_params* lsh, cudaStream_t s,
+                IndexData* ix) {
+  return build_one(csr, kind, lsh, s, ix);
+}
+
+void free_index_data(IndexData* ix) {
   for (auto& b : ix->blocks) dev_free(b.p, b.b, ix->home);
   ix->blocks.clear();
+  ix->arena.reset();  // the last view of a batched build releases its arena
 }
+
+namespace {
 
 int copy_out(void* dst, const void* src, size_t bytes, cudaStream_t s) {
   if (!dst || bytes == 0) return SCAN_OK;
@@ -278,11 +567,13 @@ int query_impl(scan_index* index, int q, const int* mu, const double* eps, int32
   const bool dev_out = is_device_ptr(labels);
   int32_t* lab = dev_out ? labels : pool.get<int32_t>((size_t)q * ix.n);
   if (!lab) return SCAN_ENOMEM;
-  GS_CUDA(cudaMemsetAsync(ix.status, 0, sizeof(unsigned), s));
-  GS_TRY(run_queries(ix, q, mu, eps, lab, flags, pool, s));
+  unsigned* st_dev = pool.get<unsigned>(1);
+  if (!st_dev) return SCAN_ENOMEM;
+  GS_CUDA(cudaMemsetAsync(st_dev, 0, sizeof(unsigned), s));
+  GS_TRY(run_queries(ix, q, mu, eps, lab, flags, pool, s, st_dev));
   if (!dev_out) GS_CUDA(cudaMemcpyAsync(labels, lab, bytes, cudaMemcpyDeviceToHost, s));
   unsigned st = 0;
-  GS_CUDA(cudaMemcpyAsync(&st, ix.status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  GS_CUDA(cudaMemcpyAsync(&st, st_dev, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   GS_CUDA(cudaStreamSynchronize(s));
   if (st & DEV_LIMIT) return SCAN_ETIMEOUT;
   return SCAN_OK;
@@ -324,14 +615,13 @@ int scan_index_build_batch(const scan_csr* graphs, int count, scan_sim_kind kind
                            const scan_lsh_params* lsh, uintptr_t stream, scan_index** out) {
   if (!out || count < 0 || (count > 0 && !graphs)) return SCAN_EINVAL;
   for (int i = 0; i < count; ++i) out[i] = nullptr;
-  for (int i = 0; i < count; ++i) {
-    const int rc = scan_index_build(&graphs[i], kind, lsh, stream, &out[i]);
-    if (rc != SCAN_OK) {
-      for (int j = 0; j < i; ++j) { scan_index_free(out[j]); out[j] = nullptr; }
-      return rc;
-    }
+  if (count == 0) return SCAN_OK;
+  const int rc = build_batch(graphs, count, (int)kind, lsh, (cudaStream_t)stream, out);
+  if (rc != SCAN_OK) {
+    cudaStreamSynchronize((cudaStream_t)stream);
+    for (int i = 0; i < count; ++i) out[i] = nullptr;
   }
-  return SCAN_OK;
+  return rc;
 }
 
 int scan_query(scan_index* index, int mu, double eps, int32_t* labels, int flags, uintptr_t stream) {
@@ -381,7 +671,7 @@ int scan_index_info(scan_index* index, int64_t* n, int64_t* num_arcs, int32_t* m
 
 void scan_index_free(scan_index* index) {
   if (!index) return;
-  free_index(&index->d);
+  free_index_data(&index->d);
   delete index;
 }
 

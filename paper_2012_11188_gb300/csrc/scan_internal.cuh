@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <memory>
 #include <vector>
 
 #include "../../include/scan.h"
@@ -105,6 +106,7 @@ struct IndexData {
   double* co_thr = nullptr;  // arcs
   unsigned* status = nullptr;  // one device status word
   std::vector<Pool::Blk> blocks;
+  std::shared_ptr<void> arena;  // batched builds: the arena shared by all graphs' views
   size_t bytes = 0;
   cudaStream_t home = 0;
 };
@@ -140,10 +142,27 @@ int segmented_sort_desc(uint64_t* key, int32_t* val, const int64_t* seg_off, int
 
 // Core order from the neighbour order (Algorithm 2, MakeCoreOrder).
 int build_core_order(IndexData& ix, Pool& pool, cudaStream_t s);
+// The same for G graphs packed in one vertex range: vb[G+1] vertex bases,
+// maxdeg[G]; co_off_all[sum maxdeg + 1] absolute offsets; co_id local ids.
+int build_core_order_multi(int64_t N, int64_t A, const int64_t* off, const int32_t* deg,
+                           const uint64_t* no_key, const std::vector<int64_t>& vb,
+                           const std::vector<int32_t>& maxdeg, int64_t* co_off_all,
+                           int32_t* co_id, uint64_t* co_key, Pool& pool, cudaStream_t s);
 
-// Queries (Algorithms 3-5).
+// Queries (Algorithms 3-5). status_dev: a zeroed device word that receives
+// DEV_LIMIT if a bounded union-find loop gave up.
 int run_queries(const IndexData& ix, int q, const int* mu, const double* eps, int32_t* labels_dev,
-                int flags, Pool& pool, cudaStream_t s);
+                int flags, Pool& pool, cudaStream_t s, unsigned* status_dev);
+
+// Whole index build into ix (scan_api.cu); on error every block is released.
+int build_index(const scan_csr* csr, int kind, const scan_lsh_params* lsh, cudaStream_t s,
+                IndexData* ix);
+// Release an index's device memory.
+void free_index_data(IndexData* ix);
+// Device footprint estimate of a build (temporaries included), bytes.
+size_t build_footprint(int64_t n, int64_t arcs);
+// Host or device pointer?
+bool is_device_ptr(const void* p);
 
 // LSH mode: overwrite the similarities of approximated arcs.
 int lsh_apply(const scan_lsh_params& p, int kind, const int64_t* off, const int32_t* adj,
@@ -161,3 +180,7 @@ int exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, Pool& 
 void record_timings(const double* ms7);
 
 }  // namespace gscan
+
+struct scan_index {
+  gscan::IndexData d;
+};

@@ -134,14 +134,17 @@ k_sort_block(uint64_t* __restrict__ key, int32_t* __restrict__ val,
       b = sb + t * S;
       len = min((int64_t)S, se - b);
     }
-    for (int i = threadIdx.x; i < S; i += T) {
+    // sort only the next power of two at or above the length
+    int se = 2;
+    while (se < len) se <<= 1;
+    for (int i = threadIdx.x; i < se; i += T) {
       if (i < len) { sk[i] = key[b + i]; sv[i] = val[b + i]; }
       else { sk[i] = 0; sv[i] = SENT_V; }
     }
     __syncthreads();
-    for (int size = 2; size <= S; size <<= 1) {
+    for (int size = 2; size <= se; size <<= 1) {
       for (int stride = size >> 1; stride > 0; stride >>= 1) {
-        for (int t = threadIdx.x; t < S / 2; t += T) {
+        for (int t = threadIdx.x; t < se / 2; t += T) {
           // pair (i, i + stride) with i having bit `stride` clear
           const int i = 2 * t - (t & (stride - 1));
           const int j = i + stride;
@@ -177,8 +180,8 @@ __global__ void k_long_tiles(const int64_t* __restrict__ seg_off, const int64_t*
   }
 }
 
-constexpr int MERGE_T = 128;
-constexpr int MERGE_ITEMS = 8;
+constexpr int MERGE_T = 256;
+constexpr int MERGE_ITEMS = 4;
 constexpr int MERGE_CHUNK = MERGE_T * MERGE_ITEMS;  // output elements per CTA per pass
 
 // Number of elements of A (length la) among the first d of merge(A, B).
@@ -188,15 +191,34 @@ __device__ __forceinline__ int64_t merge_path(const uint64_t* ka, const int32_t*
   int64_t lo = max((int64_t)0, d - lb), hi = min(d, la);
   while (lo < hi) {
     const int64_t i = (lo + hi) >> 1;  // take i from A, d-i from B
-    // if B[d-i-1] comes before A[i], i is large enough... standard: A[i] vs B[d-1-i]
     if (before(kb[d - 1 - i], vb[d - 1 - i], ka[i], va[i])) hi = i;
     else lo = i + 1;
   }
   return lo;
 }
 
-// One merge pass: within every long segment, runs of length L are merged in
-// pairs from (sk, sv) into (dk, dv). Each CTA writes MERGE_CHUNK outputs.
+// Passes a segment of length len takes part in: one per run length L = TILE,
+// 2*TILE, ... below len.
+__device__ __forceinline__ int passes_for(int64_t len) {
+  int p = 0;
+  for (int64_t L = TILE; L < len; L <<= 1) ++p;
+  return p;
+}
+
+__device__ __forceinline__ int64_t chunk_segment(const int64_t* chunk_prefix, int64_t nlong,
+                                                 int64_t c) {
+  int64_t lo = 0, hi = nlong;
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (chunk_prefix[mid] <= c) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// One merge pass: within every long segment still longer than L, runs of
+// length L are merged in pairs from (sk, sv) into (dk, dv). Segments of length
+// <= L are finished and stay where they are. Each CTA writes MERGE_CHUNK
+// outputs, staged in shared memory so the global stores are coalesced.
 __global__ void __launch_bounds__(MERGE_T)
 k_merge_pass(const uint64_t* __restrict__ sk, const int32_t* __restrict__ sv,
              uint64_t* __restrict__ dk, int32_t* __restrict__ dv,
@@ -204,17 +226,16 @@ k_merge_pass(const uint64_t* __restrict__ sk, const int32_t* __restrict__ sv,
              const int64_t* __restrict__ chunk_prefix, int64_t nlong, int64_t L) {
   __shared__ uint64_t shk[MERGE_CHUNK];
   __shared__ int32_t shv[MERGE_CHUNK];
+  __shared__ uint64_t ok_[MERGE_CHUNK];
+  __shared__ int32_t ov_[MERGE_CHUNK];
   __shared__ int64_t s_bounds[4];
   const int64_t total = chunk_prefix[nlong];
   for (int64_t c = blockIdx.x; c < total; c += gridDim.x) {
-    int64_t lo = 0, hi = nlong;
-    while (hi - lo > 1) {
-      const int64_t mid = (lo + hi) >> 1;
-      if (chunk_prefix[mid] <= c) lo = mid; else hi = mid;
-    }
-    const int64_t sg = list[lo];
+    const int64_t si = chunk_segment(chunk_prefix, nlong, c);
+    const int64_t sg = list[si];
     const int64_t base = seg_off[sg], len = seg_off[sg + 1] - base;
-    const int64_t o0 = (c - chunk_prefix[lo]) * MERGE_CHUNK;
+    if (len <= L) continue;  // uniform across the CTA
+    const int64_t o0 = (c - chunk_prefix[si]) * MERGE_CHUNK;
     const int64_t o1 = min(len, o0 + MERGE_CHUNK);
     // run pair containing [o0, o1): MERGE_CHUNK divides 2L
     const int64_t r0 = (o0 / (2 * L)) * (2 * L);
@@ -253,35 +274,35 @@ k_merge_pass(const uint64_t* __restrict__ sk, const int32_t* __restrict__ sv,
         else lo2 = i + 1;
       }
       int ia = lo2, ib = d - lo2;
-      const int64_t out = base + o0 + d;
       for (int t = 0; t < MERGE_ITEMS && d + t < nout; ++t) {
         bool take_a;
         if (ia >= na) take_a = false;
         else if (ib >= nb) take_a = true;
         else take_a = !before(shk[na + ib], shv[na + ib], shk[ia], shv[ia]);
-        if (take_a) { dk[out + t] = shk[ia]; dv[out + t] = shv[ia]; ++ia; }
-        else { dk[out + t] = shk[na + ib]; dv[out + t] = shv[na + ib]; ++ib; }
+        if (take_a) { ok_[d + t] = shk[ia]; ov_[d + t] = shv[ia]; ++ia; }
+        else { ok_[d + t] = shk[na + ib]; ov_[d + t] = shv[na + ib]; ++ib; }
       }
     }
+    __syncthreads();
+    const int64_t out = base + o0;
+    for (int i = threadIdx.x; i < nout; i += MERGE_T) { dk[out + i] = ok_[i]; dv[out + i] = ov_[i]; }
     __syncthreads();
   }
 }
 
-// Copy the long segments from the scratch buffer back.
+// Long segments that took an odd number of passes end in the scratch buffer:
+// copy them back.
 __global__ void k_copy_long(const uint64_t* __restrict__ sk, const int32_t* __restrict__ sv,
                             uint64_t* __restrict__ dk, int32_t* __restrict__ dv,
                             const int64_t* __restrict__ seg_off, const int64_t* __restrict__ list,
                             const int64_t* __restrict__ chunk_prefix, int64_t nlong) {
   const int64_t total = chunk_prefix[nlong];
   for (int64_t c = blockIdx.x; c < total; c += gridDim.x) {
-    int64_t lo = 0, hi = nlong;
-    while (hi - lo > 1) {
-      const int64_t mid = (lo + hi) >> 1;
-      if (chunk_prefix[mid] <= c) lo = mid; else hi = mid;
-    }
-    const int64_t sg = list[lo];
+    const int64_t si = chunk_segment(chunk_prefix, nlong, c);
+    const int64_t sg = list[si];
     const int64_t base = seg_off[sg], len = seg_off[sg + 1] - base;
-    const int64_t o0 = (c - chunk_prefix[lo]) * MERGE_CHUNK;
+    if ((passes_for(len) & 1) == 0) continue;
+    const int64_t o0 = (c - chunk_prefix[si]) * MERGE_CHUNK;
     const int64_t o1 = min(len, o0 + MERGE_CHUNK);
     for (int64_t i = o0 + threadIdx.x; i < o1; i += blockDim.x) {
       dk[base + i] = sk[base + i];
@@ -369,11 +390,10 @@ int segmented_sort_desc(uint64_t* key, int32_t* val, const int64_t* seg_off, int
       std::swap(ck, nk);
       std::swap(cv, nv);
     }
-    if (ck != key) {
-      k_copy_long<<<grid_of(total_chunks_ub, 1), 256, 0, s>>>(ck, cv, key, val, seg_off, llist,
-                                                             chunk_prefix, nlong);
-      GS_LAUNCH();
-    }
+    // segments that took an odd number of passes end in the scratch buffer
+    k_copy_long<<<grid_of(total_chunks_ub, 1), 256, 0, s>>>(tk, tv, key, val, seg_off, llist,
+                                                           chunk_prefix, nlong);
+    GS_LAUNCH();
     pool.put(tk);
     pool.put(tv);
     pool.put(tiles);

@@ -1,0 +1,416 @@
+// Continuous-batching request loop over resident SCAN indexes (include/scan_serve.h).
+//
+// Two worker threads own two CUDA streams:
+//  - the query worker takes every query queued for one (index, flags) pair, up
+//    to max_batch, and answers them with one batched pass (run_queries: one
+//    launch per phase for the whole batch). Queries that arrive meanwhile wait
+//    in the queue and join the next batch as soon as this one completes.
+//  - the build worker admits build requests in arrival order when their
+//    footprint fits the memory budget and the device's free memory, and builds
+//    them on its own stream, overlapping with the query batches.
+// Latencies are measured on the host from submit to completion.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/scan_serve.h"
+#include "scan_internal.cuh"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+  uint64_t ticket = 0;
+  bool is_build = false;
+  // query
+  scan_index* ix = nullptr;
+  int mu = 0;
+  double eps = 0;
+  int32_t* labels = nullptr;
+  int flags = 0;
+  // build
+  scan_csr csr{};
+  int kind = 0;
+  bool has_lsh = false;
+  scan_lsh_params lsh{};
+  size_t est = 0;
+  // completion
+  int status = SCAN_OK;
+  bool done = false;
+  scan_index* built = nullptr;
+  Clock::time_point t_submit, t_done;
+};
+
+}  // namespace
+
+struct scan_server {
+  scan_serve_params p{};
+  int device = 0;
+  cudaStream_t qs = nullptr, bs = nullptr;
+  std::mutex mu;
+  std::condition_variable cv_q, cv_b, cv_done;
+  std::deque<Request*> qq, bq;
+  std::unordered_map<uint64_t, Request*> reqs;
+  uint64_t next_ticket = 1;
+  size_t inflight_build_bytes = 0;
+  bool stop = false;
+  std::thread qt, bt;
+  // stats
+  std::vector<double> lat_ms;
+  Clock::time_point stats_t0;
+  bool stats_started = false;
+  Clock::time_point stats_last;
+};
+
+namespace {
+
+void finish(scan_server* s, Request* r, int status) {
+  std::lock_guard<std::mutex> lk(s->mu);
+  r->status = status;
+  r->done = true;
+  r->t_done = Clock::now();
+  if (!r->is_build) {
+    s->lat_ms.push_back(std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count());
+    s->stats_last = r->t_done;
+  }
+  s->cv_done.notify_all();
+}
+
+void query_worker(scan_server* s) {
+  cudaSetDevice(s->device);
+  const int max_batch = s->p.max_batch > 0 ? s->p.max_batch : 256;
+  std::vector<Request*> batch;
+  std::vector<int> mus;
+  std::vector<double> epss;
+  for (;;) {
+    batch.clear();
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->cv_q.wait(lk, [&] { return s->stop || !s->qq.empty(); });
+      if (s->qq.empty() && s->stop) return;
+      // everything queued for the front request's (index, flags), up to max_batch
+      scan_index* ix = s->qq.front()->ix;
+      const int flags = s->qq.front()->flags;
+      for (auto it = s->qq.begin(); it != s->qq.end() && (int)batch.size() < max_batch;) {
+        if ((*it)->ix == ix && (*it)->flags == flags) {
+          batch.push_back(*it);
+          it = s->qq.erase(it);
+        } else {
+          ++it;
+        }
+      }
+    }
+    const gscan::IndexData& d = batch[0]->ix->d;
+    const int Q = (int)batch.size();
+    mus.resize(Q);
+    epss.resize(Q);
+    for (int i = 0; i < Q; ++i) { mus[i] = batch[i]->mu; epss[i] = batch[i]->eps; }
+    int rc = SCAN_OK;
+    {
+      gscan::Pool pool(s->qs);
+      int32_t* lab = pool.get<int32_t>((size_t)Q * (size_t)(d.n > 0 ? d.n : 1));
+      unsigned* st = pool.get<unsigned>(1);
+      if (!lab || !st) rc = SCAN_ENOMEM;
+      if (rc == SCAN_OK && cudaMemsetAsync(st, 0, sizeof(unsigned), s->qs) != cudaSuccess) rc = SCAN_ECUDA;
+      if (rc == SCAN_OK)
+        rc = gscan::run_queries(d, Q, mus.data(), epss.data(), lab, batch[0]->flags, pool, s->qs, st);
+      for (int i = 0; rc == SCAN_OK && i < Q; ++i) {
+        if (d.n == 0) break;
+        const cudaMemcpyKind k = gscan::is_device_ptr(batch[i]->labels) ? cudaMemcpyDeviceToDevice
+                                                                        : cudaMemcpyDeviceToHost;
+        if (cudaMemcpyAsync(batch[i]->labels, lab + (size_t)i * d.n, (size_t)d.n * sizeof(int32_t),
+                            k, s->qs) != cudaSuccess)
+          rc = SCAN_ECUDA;
+      }
+      unsigned hst = 0;
+      if (rc == SCAN_OK &&
+          cudaMemcpyAsync(&hst, st, sizeof(unsigned), cudaMemcpyDeviceToHost, s->qs) != cudaSuccess)
+        rc = SCAN_ECUDA;
+      if (cudaStreamSynchronize(s->qs) != cudaSuccess && rc == SCAN_OK) rc = SCAN_ECUDA;
+      if (rc == SCAN_OK && (hst & gscan::DEV_LIMIT)) rc = SCAN_ETIMEOUT;
+    }
+    cudaStreamSynchronize(s->qs);  // the pool's frees are ordered on the stream
+    for (Request* r : batch) finish(s, r, rc);
+  }
+}
+
+size_t free_device_bytes() {
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return 0;
+  return fr;
+}
+
+void build_worker(scan_server* s) {
+  cudaSetDevice(s->device);
+  for (;;) {
+    Request* r = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->cv_b.wait(lk, [&] { return s->stop || !s->bq.empty(); });
+      if (s->bq.empty() && s->stop) return;
+      r = s->bq.front();
+      s->bq.pop_front();
+      s->inflight_build_bytes += r->est;
+    }
+    // admission by device memory: wait (bounded) for room next to resident data
+    int rc = SCAN_OK;
+    for (int tries = 0; r->est > free_device_bytes(); ++tries) {
+      if (tries > 2000) { rc = SCAN_EBUSY; break; }  // ~10 s
+      std::this_thread::sleep_for(std::chrono::milliseconds(5));
+    }
+    scan_index* h = nullptr;
+    if (rc == SCAN_OK) {
+      h = new (std::nothrow) scan_index();
+      if (!h) rc = SCAN_ENOMEM;
+    }
+    if (rc == SCAN_OK) {
+      rc = gscan::build_index(&r->csr, r->kind, r->has_lsh ? &r->lsh : nullptr, s->bs, &h->d);
+      if (rc != SCAN_OK) { delete h; h = nullptr; }
+    }
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->inflight_build_bytes -= r->est;
+      r->built = h;
+    }
+    finish(s, r, rc);
+  }
+}
+
+int submit(scan_server* s, Request* r, uint64_t* ticket) {
+  std::lock_guard<std::mutex> lk(s->mu);
+  const int max_pending = s->p.max_pending > 0 ? s->p.max_pending : (1 << 20);
+  if ((int)(s->qq.size() + s->bq.size()) >= max_pending) return SCAN_EBUSY;
+  r->ticket = s->next_ticket++;
+  r->t_submit = Clock::now();
+  if (!r->is_build && !s->stats_started) {
+    s->stats_started = true;
+    s->stats_t0 = r->t_submit;
+  }
+  s->reqs[r->ticket] = r;
+  if (r->is_build) {
+    s->bq.push_back(r);
+    s->cv_b.notify_one();
+  } else {
+    s->qq.push_back(r);
+    s->cv_q.notify_one();
+  }
+  *ticket = r->ticket;
+  return SCAN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int scan_serve_create(const scan_serve_params* params, scan_server** out) {
+  if (!out) return SCAN_EINVAL;
+  *out = nullptr;
+  scan_server* s = new (std::nothrow) scan_server();
+  if (!s) return SCAN_ENOMEM;
+  if (params) s->p = *params;
+  if (s->p.max_batch < 0 || s->p.max_pending < 0) { delete s; return SCAN_EINVAL; }
+  s->device = s->p.device;
+  if (cudaSetDevice(s->device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->qs, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->bs, cudaStreamNonBlocking) != cudaSuccess) {
+    if (s->qs) cudaStreamDestroy(s->qs);
+    delete s;
+    return SCAN_ECUDA;
+  }
+  s->qt = std::thread(query_worker, s);
+  s->bt = std::thread(build_worker, s);
+  *out = s;
+  return SCAN_OK;
+}
+
+int scan_serve_submit_query(scan_server* s, scan_index* index, int mu, double eps, int32_t* labels,
+                            int flags, uint64_t* ticket) {
+  if (!s || !index || !ticket || (!labels && index->d.n > 0)) return SCAN_EINVAL;
+  if (mu < 2 || !(eps >= 0.0 && eps <= 1.0) || (flags & ~SCAN_Q_HUBS)) return SCAN_EINVAL;
+  Request* r = new (std::nothrow) Request();
+  if (!r) return SCAN_ENOMEM;
+  r->ix = index;
+  r->mu = mu;
+  r->eps = eps;
+  r->labels = labels;
+  r->flags = flags;
+  const int rc = submit(s, r, ticket);
+  if (rc != SCAN_OK) delete r;
+  return rc;
+}
+
+int scan_serve_submit_build(scan_server* s, const scan_csr* csr, scan_sim_kind kind,
+                            const scan_lsh_params* lsh, uint64_t* ticket) {
+  if (!s || !csr || !ticket) return SCAN_EINVAL;
+  if (csr->n < 0 || csr->num_arcs < 0) return SCAN_EINVAL;
+  Request* r = new (std::nothrow) Request();
+  if (!r) return SCAN_ENOMEM;
+  r->is_build = true;
+  r->csr = *csr;
+  r->kind = (int)kind;
+  if (lsh) { r->has_lsh = true; r->lsh = *lsh; }
+  r->est = gscan::build_footprint(csr->n, csr->num_arcs);
+  if (s->p.memory_budget_bytes && r->est > s->p.memory_budget_bytes) {
+    delete r;
+    return SCAN_EBUSY;  // would never fit
+  }
+  const int rc = submit(s, r, ticket);
+  if (rc != SCAN_OK) delete r;
+  return rc;
+}
+
+int scan_serve_wait(scan_server* s, uint64_t ticket, int timeout_ms, scan_index** built) {
+  if (!s) return SCAN_EINVAL;
+  if (built) *built = nullptr;
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return SCAN_EINVAL;
+  Request* r = it->second;
+  auto pred = [&] { return r->done; };
+  if (timeout_ms < 0) {
+    s->cv_done.wait(lk, pred);
+  } else if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), pred)) {
+    return SCAN_ETIMEOUT;
+  }
+  const int rc = r->status;
+  scan_index* h = r->built;
+  s->reqs.erase(it);
+  lk.unlock();
+  if (built) *built = h;
+  else if (h) scan_index_free(h);
+  delete r;
+  return rc;
+}
+
+int scan_serve_stats(scan_server* s, double* p50_ms, double* p99_ms, double* qps, int64_t* completed) {
+  if (!s) return SCAN_EINVAL;
+  std::vector<double> v;
+  double span = 0;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    v = s->lat_ms;
+    if (s->stats_started && !v.empty())
+      span = std::chrono::duration<double>(s->stats_last - s->stats_t0).count();
+  }
+  auto pct = [&](double q) {
+    if (v.empty()) return 0.0;
+    size_t k = (size_t)(q * (double)(v.size() - 1) + 0.5);
+    std::nth_element(v.begin(), v.begin() + k, v.end());
+    return v[k];
+  };
+  if (p50_ms) *p50_ms = pct(0.50);
+  if (p99_ms) *p99_ms = pct(0.99);
+  if (qps) *qps = span > 0 ? (double)v.size() / span : 0.0;
+  if (completed) *completed = (int64_t)v.size();
+  return SCAN_OK;
+}
+
+int scan_serve_reset_stats(scan_server* s) {
+  if (!s) return SCAN_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->lat_ms.clear();
+  s->stats_started = false;
+  return SCAN_OK;
+}
+
+int scan_serve_replay(scan_server* s, scan_index* index, int64_t nq, const double* q_arrival_s,
+                      const int* q_mu, const double* q_eps, int flags, int32_t* labels,
+                      double* latency_ms, int64_t nb, const double* b_arrival_s,
+                      const scan_csr* b_graphs, scan_sim_kind b_kind, int timeout_ms) {
+  if (!s || !index || nq < 0 || nb < 0) return SCAN_EINVAL;
+  if (nq > 0 && (!q_arrival_s || !q_mu || !q_eps)) return SCAN_EINVAL;
+  if (nb > 0 && (!b_arrival_s || !b_graphs)) return SCAN_EINVAL;
+  const int64_t n = index->d.n;
+  // per-query label destinations: caller's rows, or one device scratch row set
+  gscan::Pool pool(0);
+  int32_t* scratch = nullptr;
+  if (!labels && n > 0) {
+    scratch = pool.get<int32_t>((size_t)n);
+    if (!scratch) return SCAN_ENOMEM;
+  }
+  std::vector<uint64_t> qt((size_t)nq, 0), bt((size_t)nb, 0);
+  std::vector<int> qrc((size_t)nq, SCAN_OK);
+  int rc_all = SCAN_OK;
+  const auto t0 = Clock::now();
+  int64_t i = 0, j = 0;
+  while (i < nq || j < nb) {
+    const bool take_q = j >= nb || (i < nq && q_arrival_s[i] <= b_arrival_s[j]);
+    const double at = take_q ? q_arrival_s[i] : b_arrival_s[j];
+    const auto when = t0 + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(at));
+    // sleep until shortly before the arrival, then spin
+    auto now = Clock::now();
+    if (when - now > std::chrono::microseconds(300))
+      std::this_thread::sleep_until(when - std::chrono::microseconds(200));
+    while (Clock::now() < when) {
+    }
+    int rc;
+    if (take_q) {
+      int32_t* dst = labels ? labels + (size_t)i * n : scratch;
+      rc = scan_serve_submit_query(s, index, q_mu[i], q_eps[i], dst, flags, &qt[i]);
+      if (rc != SCAN_OK) qrc[i] = rc;
+      ++i;
+    } else {
+      rc = scan_serve_submit_build(s, &b_graphs[j], b_kind, nullptr, &bt[j]);
+      ++j;
+    }
+    if (rc != SCAN_OK && rc_all == SCAN_OK) rc_all = rc;
+  }
+  // collect
+  const auto deadline = t0 + std::chrono::milliseconds(timeout_ms < 0 ? 1LL << 40 : timeout_ms);
+  for (int64_t k = 0; k < nq; ++k) {
+    if (!qt[k]) continue;
+    Request* r = nullptr;
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      auto it = s->reqs.find(qt[k]);
+      if (it != s->reqs.end()) r = it->second;
+    }
+    const int left = (int)std::max<int64_t>(
+        0, std::chrono::duration_cast<std::chrono::milliseconds>(deadline - Clock::now()).count());
+    double lat = -1;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      if (r && s->cv_done.wait_for(lk, std::chrono::milliseconds(left), [&] { return r->done; }))
+        lat = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+    }
+    const int rc = scan_serve_wait(s, qt[k], 0, nullptr);
+    if (latency_ms) latency_ms[k] = lat;
+    if (rc != SCAN_OK && rc_all == SCAN_OK) rc_all = rc;
+  }
+  for (int64_t k = 0; k < nb; ++k) {
+    if (!bt[k]) continue;
+    const int left = (int)std::max<int64_t>(
+        0, std::chrono::duration_cast<std::chrono::milliseconds>(deadline - Clock::now()).count());
+    const int rc = scan_serve_wait(s, bt[k], left, nullptr);
+    if (rc != SCAN_OK && rc_all == SCAN_OK) rc_all = rc;
+  }
+  cudaDeviceSynchronize();
+  return rc_all;
+}
+
+void scan_serve_destroy(scan_server* s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv_q.notify_all();
+  s->cv_b.notify_all();
+  if (s->qt.joinable()) s->qt.join();
+  if (s->bt.joinable()) s->bt.join();
+  for (auto& kv : s->reqs) {
+    if (kv.second->built) scan_index_free(kv.second->built);
+    delete kv.second;
+  }
+  cudaStreamDestroy(s->qs);
+  cudaStreamDestroy(s->bs);
+  delete s;
+}
+
+}  // extern "C"

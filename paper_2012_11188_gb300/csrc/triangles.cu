@@ -21,17 +21,13 @@ namespace gscan {
 
 namespace {
 
-constexpr int TRI_THREADS = 256;
+constexpr int TRI_THREADS = 512;
 constexpr int TRI_WARPS = TRI_THREADS / 32;
 constexpr int CHUNK = 1024;          // CSR positions of N(v) per work item
 constexpr int SMEM_OD_MAX = 4096;    // out(v) sizes handled by the shared-memory table
 
 __device__ __forceinline__ bool lower(int32_t du, int32_t u, int32_t dv, int32_t v) {
   return du < dv || (du == dv && u < v);
-}
-
-__device__ __forceinline__ uint32_t hslot(int32_t x, int log2h) {
-  return ((uint32_t)x * 0x9E3779B1u) >> (32 - log2h);
 }
 
 // Work items: vertex v contributes ceil(deg/CHUNK) items when it has in-
@@ -74,7 +70,7 @@ constexpr int FILTER_LOG2 = 15;
 // in the round (ballot / or-reduce / popc), so lanes stay busy whatever the
 // list lengths.
 template <bool BIG>
-__global__ void __launch_bounds__(TRI_THREADS)
+__global__ void __launch_bounds__(TRI_THREADS, 3)
 k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
             const int32_t* __restrict__ deg, const int64_t* __restrict__ oo,
             const int32_t* __restrict__ oadj, int64_t n, const int64_t* __restrict__ item_off,
@@ -84,6 +80,7 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
   // filter[FILTER_WORDS] | hkey[2*od_cap] int32 | vcnt[od_cap] uint32 | hpos[2*od_cap] uint16
   extern __shared__ int32_t smem[];
   __shared__ long long s_item;
+  __shared__ int s_next;  // next 32-position slice of the item's CSR range
   __shared__ int32_t s_u[TRI_WARPS][32];
   __shared__ int32_t s_p[TRI_WARPS][32];
   __shared__ uint32_t s_acc[TRI_WARPS][32];
@@ -98,7 +95,10 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
   unsigned bad = 0;
 
   for (;;) {
-    if (threadIdx.x == 0) s_item = (long long)atomicAdd(work, 1ull);
+    if (threadIdx.x == 0) {
+      s_item = (long long)atomicAdd(work, 1ull);
+      s_next = 0;
+    }
     __syncthreads();
     const int64_t item = s_item;
     if (item >= total) break;
@@ -135,7 +135,13 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
     const int64_t rb = off[v];
     const int64_t p_begin = chunk * CHUNK;
     const int64_t p_end = min((int64_t)dv, p_begin + CHUNK);
-    for (int64_t p0 = p_begin + 32 * wid; p0 < p_end; p0 += 32 * TRI_WARPS) {
+    for (;;) {
+      // warps pull 32-position slices until the item's range is exhausted
+      int slice = 0;
+      if (lane == 0) slice = atomicAdd(&s_next, 32);
+      slice = __shfl_sync(FULL, slice, 0);
+      const int64_t p0 = p_begin + slice;
+      if (p0 >= p_end) break;
       const int64_t p = p0 + lane;
       int32_t u = -1;
       bool is_in = false;
@@ -189,54 +195,69 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
       s_acc[wid][lane] = 0;
       s_jv[wid][lane] = -1;
       __syncwarp();
-      for (int32_t r0 = 0; r0 < W; r0 += 32) {
-        // every list is non-empty (v is in out(u)), so the starts are distinct
-        const bool starts_here = lane < k && cstart >= r0 && cstart < r0 + 32;
-        const unsigned smask = __reduce_or_sync(FULL, starts_here ? (1u << (cstart - r0)) : 0u);
-        const int before = __popc(__ballot_sync(FULL, lane < k && cstart < r0));
-        const int owner = before + __popc(smask & ((2u << lane) - 1u)) - 1;
-        const int own = owner < 0 ? 0 : owner;
-        const int64_t ub_o = __shfl_sync(FULL, cub, own);
-        const int32_t st_o = __shfl_sync(FULL, cstart, own);
-        const int32_t t = r0 + lane;
-        bool hit = false;
-        if (t < W) {
-          const int64_t j = ub_o + (t - st_o);
-          const int32_t x = oadj[j];
-          if (x == (int32_t)v) s_jv[wid][own] = j;
-          int q = -1;
-          if (!BIG) {
-            const uint32_t hx = (uint32_t)x * 0x9E3779B1u;
-            const uint32_t fb = hx >> (32 - FILTER_LOG2);
-            if ((filt[fb >> 5] >> (fb & 31)) & 1u) {
-              uint32_t sl = hx >> (32 - log2h);
-              for (int probe = 0; probe < H; ++probe) {
-                const int32_t key = hkey[sl];
-                if (key == x) { q = hpos[sl]; break; }
-                if (key == -1) break;
-                sl = (sl + 1) & (H - 1);
-              }
-            }
-          } else {
-            int lo = 0, hi = od;
-            while (lo < hi) {
-              const int mid = (lo + hi) >> 1;
-              if (oadj[ob + mid] < x) lo = mid + 1; else hi = mid;
-            }
-            if (lo < od && oadj[ob + lo] == x) q = lo;
-          }
-          if (q >= 0) {
-            hit = true;
-            if (!BIG) atomicAdd(&vcnt[q], 1u);
-            else atomicAdd(&tcnt[ob + q], 1u);
-            atomicAdd(&tcnt[j], 1u);
-          }
+      constexpr int R = 4;  // rounds whose loads are issued before any probe
+      for (int32_t rb = 0; rb < W; rb += 32 * R) {
+        int32_t xs[R];
+        int64_t js[R];
+        int owns[R];
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr) {
+          const int32_t r0 = rb + 32 * rr;
+          // every list is non-empty (v is in out(u)), so the starts are distinct
+          const bool starts_here = lane < k && cstart >= r0 && cstart < r0 + 32;
+          const unsigned smask = __reduce_or_sync(FULL, starts_here ? (1u << (cstart - r0)) : 0u);
+          const int before = __popc(__ballot_sync(FULL, lane < k && cstart < r0));
+          const int owner = before + __popc(smask & ((2u << lane) - 1u)) - 1;
+          const int own = owner < 0 ? 0 : owner;
+          const int64_t ub_o = __shfl_sync(FULL, cub, own);
+          const int32_t st_o = __shfl_sync(FULL, cstart, own);
+          const int32_t t = r0 + lane;
+          owns[rr] = own;
+          js[rr] = t < W ? ub_o + (t - st_o) : -1;
+          xs[rr] = t < W ? oadj[js[rr]] : -1;
         }
-        // hits per owner: lanes of one owner are contiguous; its first lane adds
-        const unsigned hm = __ballot_sync(FULL, hit);
-        const unsigned peers = __match_any_sync(FULL, own);
-        if (hm & peers) {
-          if (lane == __ffs(peers) - 1) s_acc[wid][own] += __popc(hm & peers);
+#pragma unroll
+        for (int rr = 0; rr < R; ++rr) {
+          const int32_t x = xs[rr];
+          const int64_t j = js[rr];
+          const int own = owns[rr];
+          bool hit = false;
+          if (j >= 0) {
+            if (x == (int32_t)v) s_jv[wid][own] = j;
+            int q = -1;
+            if (!BIG) {
+              const uint32_t hx = (uint32_t)x * 0x9E3779B1u;
+              const uint32_t fb = hx >> (32 - FILTER_LOG2);
+              if ((filt[fb >> 5] >> (fb & 31)) & 1u) {
+                uint32_t sl = hx >> (32 - log2h);
+                for (int probe = 0; probe < H; ++probe) {
+                  const int32_t key = hkey[sl];
+                  if (key == x) { q = hpos[sl]; break; }
+                  if (key == -1) break;
+                  sl = (sl + 1) & (H - 1);
+                }
+              }
+            } else {
+              int lo = 0, hi = od;
+              while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (oadj[ob + mid] < x) lo = mid + 1; else hi = mid;
+              }
+              if (lo < od && oadj[ob + lo] == x) q = lo;
+            }
+            if (q >= 0) {
+              hit = true;
+              if (!BIG) atomicAdd(&vcnt[q], 1u);
+              else atomicAdd(&tcnt[ob + q], 1u);
+              atomicAdd(&tcnt[j], 1u);
+            }
+          }
+          // hits per owner: lanes of one owner are contiguous; its first lane adds
+          const unsigned hm = __ballot_sync(FULL, hit);
+          if (hm) {
+            const unsigned peers = __match_any_sync(FULL, own);
+            if ((hm & peers) && lane == __ffs(peers) - 1) s_acc[wid][own] += __popc(hm & peers);
+          }
         }
       }
       __syncwarp();

@@ -296,3 +296,124 @@ class ScanIndex:
 
     def __exit__(self, *exc):
         self.free()
+
+
+# ---------------------------------------------------------------- serving
+class scan_serve_params(ctypes.Structure):
+    _fields_ = [("memory_budget_bytes", ctypes.c_size_t), ("max_batch", ctypes.c_int),
+                ("max_pending", ctypes.c_int), ("device", ctypes.c_int)]
+
+
+def _load_serve():
+    lib = load()
+    if getattr(lib, "_serve_bound", False):
+        return lib
+    P, i32, i64, f64, u64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_uint64
+    sigs = {
+        "scan_serve_create": (i32, [P, P]),
+        "scan_serve_submit_query": (i32, [P, P, i32, f64, P, i32, P]),
+        "scan_serve_submit_build": (i32, [P, P, i32, P, P]),
+        "scan_serve_wait": (i32, [P, u64, i32, P]),
+        "scan_serve_stats": (i32, [P, P, P, P, P]),
+        "scan_serve_reset_stats": (i32, [P]),
+        "scan_serve_replay": (i32, [P, P, i64, P, P, P, i32, P, P, i64, P, P, i32, i32]),
+        "scan_serve_destroy": (None, [P]),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(lib, name)
+        f.restype, f.argtypes = res, args
+    lib._serve_bound = True
+    return lib
+
+
+class Server:
+    """Continuous-batching query/build server (include/scan_serve.h)."""
+
+    def __init__(self, memory_budget: int = 0, max_batch: int = 256, max_pending: int = 0,
+                 device: int = 0):
+        lib = _load_serve()
+        p = scan_serve_params(memory_budget, max_batch, max_pending, device)
+        h = ctypes.c_void_p()
+        _check(lib.scan_serve_create(ctypes.byref(p), ctypes.byref(h)), "scan_serve_create")
+        self._h = h
+        self._keep = {}
+
+    def submit_query(self, index: "ScanIndex", mu: int, eps: float, out, hubs: bool = False) -> int:
+        t = ctypes.c_uint64()
+        _check(_load_serve().scan_serve_submit_query(self._h, index._h, int(mu), float(eps), _ptr(out),
+                                                     Q_HUBS if hubs else 0, ctypes.byref(t)),
+               "scan_serve_submit_query")
+        self._keep[t.value] = out
+        return t.value
+
+    def submit_build(self, g, kind: int = COSINE, lsh=None, device: bool = False) -> int:
+        c, keep = _csr_struct(g, device)
+        t = ctypes.c_uint64()
+        _check(_load_serve().scan_serve_submit_build(self._h, ctypes.byref(c), kind,
+                                                     ctypes.byref(lsh) if lsh else None,
+                                                     ctypes.byref(t)), "scan_serve_submit_build")
+        self._keep[t.value] = (c, keep)
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        h = ctypes.c_void_p()
+        rc = _load_serve().scan_serve_wait(self._h, ticket, timeout_ms, ctypes.byref(h))
+        if rc != -5:
+            self._keep.pop(ticket, None)
+        _check(rc, "scan_serve_wait")
+        return ScanIndex(h.value) if h.value else None
+
+    def stats(self) -> dict:
+        p50, p99, qps = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        done = ctypes.c_int64()
+        _check(_load_serve().scan_serve_stats(self._h, ctypes.byref(p50), ctypes.byref(p99),
+                                              ctypes.byref(qps), ctypes.byref(done)), "scan_serve_stats")
+        return {"p50_ms": p50.value, "p99_ms": p99.value, "qps": qps.value, "completed": done.value}
+
+    def reset_stats(self):
+        _check(_load_serve().scan_serve_reset_stats(self._h), "scan_serve_reset_stats")
+
+    def replay(self, index: "ScanIndex", arrivals, mus, epss, hubs: bool = False, labels=None,
+               build_arrivals=None, build_graphs=None, build_kind: int = COSINE,
+               timeout_ms: int = 600000):
+        """Open-loop trace replay driven by a C++ thread; returns per-query latencies (ms)."""
+        arrivals = np.ascontiguousarray(arrivals, dtype=np.float64)
+        mus = np.ascontiguousarray(mus, dtype=np.int32)
+        epss = np.ascontiguousarray(epss, dtype=np.float64)
+        nq = arrivals.shape[0]
+        lat = np.zeros(nq, dtype=np.float64)
+        nb = 0
+        barr, bstructs, keep = None, None, []
+        if build_graphs:
+            nb = len(build_graphs)
+            barr = np.ascontiguousarray(build_arrivals, dtype=np.float64)
+            structs = []
+            for g in build_graphs:
+                c, k = _csr_struct(g, False)
+                structs.append(c)
+                keep.append(k)
+            bstructs = (scan_csr * nb)(*structs)
+        rc = _load_serve().scan_serve_replay(
+            self._h, index._h, nq, arrivals.ctypes.data, mus.ctypes.data, epss.ctypes.data,
+            Q_HUBS if hubs else 0, _ptr(labels), lat.ctypes.data, nb,
+            barr.ctypes.data if barr is not None else None, bstructs, build_kind, timeout_ms)
+        _check(rc, "scan_serve_replay")
+        return lat
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            _load_serve().scan_serve_destroy(self._h)
+        self._h = None
+        self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
