@@ -215,6 +215,34 @@ __device__ __forceinline__ int64_t chunk_segment(const int64_t* chunk_prefix, in
   return lo;
 }
 
+// Merge-path splits of every output chunk of a pass, all in parallel (one
+// thread per chunk): split[2c] / split[2c+1] = elements of run A among the
+// first o0 / o1 outputs of the chunk's run pair.
+__global__ void k_merge_partition(const uint64_t* __restrict__ sk, const int32_t* __restrict__ sv,
+                                  const int64_t* __restrict__ seg_off,
+                                  const int64_t* __restrict__ list,
+                                  const int64_t* __restrict__ chunk_prefix, int64_t nlong, int64_t L,
+                                  int64_t* __restrict__ split) {
+  const int64_t total = chunk_prefix[nlong];
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < total;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t si = chunk_segment(chunk_prefix, nlong, c);
+    const int64_t sg = list[si];
+    const int64_t base = seg_off[sg], len = seg_off[sg + 1] - base;
+    if (len <= L) continue;
+    const int64_t o0 = (c - chunk_prefix[si]) * MERGE_CHUNK;
+    const int64_t o1 = min(len, o0 + MERGE_CHUNK);
+    const int64_t r0 = (o0 / (2 * L)) * (2 * L);
+    const int64_t a1 = min(len, r0 + L), b1 = min(len, r0 + 2 * L);
+    const uint64_t* KA = sk + base + r0;
+    const int32_t* VA = sv + base + r0;
+    const uint64_t* KB = sk + base + a1;
+    const int32_t* VB = sv + base + a1;
+    split[2 * c] = merge_path(KA, VA, a1 - r0, KB, VB, b1 - a1, o0 - r0);
+    split[2 * c + 1] = merge_path(KA, VA, a1 - r0, KB, VB, b1 - a1, o1 - r0);
+  }
+}
+
 // One merge pass: within every long segment still longer than L, runs of
 // length L are merged in pairs from (sk, sv) into (dk, dv). Segments of length
 // <= L are finished and stay where they are. Each CTA writes MERGE_CHUNK
@@ -223,7 +251,8 @@ __global__ void __launch_bounds__(MERGE_T)
 k_merge_pass(const uint64_t* __restrict__ sk, const int32_t* __restrict__ sv,
              uint64_t* __restrict__ dk, int32_t* __restrict__ dv,
              const int64_t* __restrict__ seg_off, const int64_t* __restrict__ list,
-             const int64_t* __restrict__ chunk_prefix, int64_t nlong, int64_t L) {
+             const int64_t* __restrict__ chunk_prefix, int64_t nlong, int64_t L,
+             const int64_t* __restrict__ split) {
   __shared__ uint64_t shk[MERGE_CHUNK];
   __shared__ int32_t shv[MERGE_CHUNK];
   __shared__ uint64_t ok_[MERGE_CHUNK];
@@ -247,14 +276,16 @@ k_merge_pass(const uint64_t* __restrict__ sk, const int32_t* __restrict__ sv,
     const int32_t* VB = sv + base + b0;
     const int64_t la = a1 - a0, lb = b1 - b0;
     if (threadIdx.x == 0) {
-      const int64_t i0 = merge_path(KA, VA, la, KB, VB, lb, o0 - r0);
-      const int64_t i1 = merge_path(KA, VA, la, KB, VB, lb, o1 - r0);
+      const int64_t i0 = split[2 * c];
+      const int64_t i1 = split[2 * c + 1];
       s_bounds[0] = i0;
       s_bounds[1] = i1;
       s_bounds[2] = (o0 - r0) - i0;
       s_bounds[3] = (o1 - r0) - i1;
     }
     __syncthreads();
+    (void)la;
+    (void)lb;
     const int64_t ia0 = s_bounds[0], ia1 = s_bounds[1], ib0 = s_bounds[2], ib1 = s_bounds[3];
     const int na = (int)(ia1 - ia0), nb = (int)(ib1 - ib0);
     for (int i = threadIdx.x; i < na; i += MERGE_T) { shk[i] = KA[ia0 + i]; shv[i] = VA[ia0 + i]; }
@@ -383,9 +414,14 @@ int segmented_sort_desc(uint64_t* key, int32_t* val, const int64_t* seg_off, int
     uint64_t *ck = key, *nk = tk;
     int32_t *cv = val, *nv = tv;
     const int64_t total_chunks_ub = (total + MERGE_CHUNK - 1) / MERGE_CHUNK + nlong;
+    int64_t* split = pool.get<int64_t>(2 * (size_t)total_chunks_ub);
+    if (!split) return SCAN_ENOMEM;
     for (int64_t L = TILE; L < max_len; L <<= 1) {
+      k_merge_partition<<<grid_of(total_chunks_ub, 256), 256, 0, s>>>(ck, cv, seg_off, llist,
+                                                                       chunk_prefix, nlong, L, split);
+      GS_LAUNCH();
       k_merge_pass<<<grid_of(total_chunks_ub, 1), MERGE_T, 0, s>>>(ck, cv, nk, nv, seg_off, llist,
-                                                                  chunk_prefix, nlong, L);
+                                                                  chunk_prefix, nlong, L, split);
       GS_LAUNCH();
       std::swap(ck, nk);
       std::swap(cv, nv);
@@ -394,6 +430,7 @@ int segmented_sort_desc(uint64_t* key, int32_t* val, const int64_t* seg_off, int
     k_copy_long<<<grid_of(total_chunks_ub, 1), 256, 0, s>>>(tk, tv, key, val, seg_off, llist,
                                                            chunk_prefix, nlong);
     GS_LAUNCH();
+    pool.put(split);
     pool.put(tk);
     pool.put(tv);
     pool.put(tiles);

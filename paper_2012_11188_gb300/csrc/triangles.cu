@@ -30,10 +30,14 @@ __device__ __forceinline__ bool lower(int32_t du, int32_t u, int32_t dv, int32_t
   return du < dv || (du == dv && u < v);
 }
 
-// Work items: vertex v contributes ceil(deg/CHUNK) items when it has in-
-// neighbours (every in-arc needs the position of its source in N(v), even when
-// out(v) is empty and no triangle has v in the middle).
-// items[v] -> prefix -> item index maps back to (v, chunk).
+constexpr int SMALL_DEG = 256;  // rows up to this long are handled by one warp
+constexpr int SW_SLOTS = 2 * SMALL_DEG;
+constexpr int SW_WARPS = 8;
+
+// Work items of the CTA kernel: a vertex v with deg > SMALL_DEG contributes
+// ceil(deg/CHUNK) items when it has in-neighbours (every in-arc needs the
+// position of its source in N(v), even when out(v) is empty and no triangle
+// has v in the middle). items[v] -> prefix -> item index maps to (v, chunk).
 __global__ void k_item_counts(const int64_t* __restrict__ oo, const int32_t* __restrict__ deg,
                               int64_t n, int32_t* __restrict__ items) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
@@ -41,7 +45,7 @@ __global__ void k_item_counts(const int64_t* __restrict__ oo, const int32_t* __r
     const int64_t od = oo[v + 1] - oo[v];
     const int32_t d = deg[v];
     int c = 0;
-    if (d - od > 0) c = (int)((d + CHUNK - 1) / CHUNK);
+    if (d > SMALL_DEG && d - od > 0) c = (int)((d + CHUNK - 1) / CHUNK);
     items[v] = c;
   }
 }
@@ -57,18 +61,204 @@ __device__ __forceinline__ int64_t find_item_vertex(const int64_t* item_off, int
   return lo;
 }
 
-constexpr int FILTER_WORDS = 1024;  // 32768-bit membership filter in front of the table
+constexpr int FILTER_WORDS = 1024;  // 32768-bit membership filter in front of the CTA table
 constexpr int FILTER_LOG2 = 15;
 
-// BIG = out(v) too long for the shared table: probe by binary search in the
-// sorted global out-list and count (v,w) hits with global atomics.
-//
-// Inner loop (one warp): the in-neighbours u among 32 consecutive positions of
-// N(v) are compacted to lanes 0..k-1; their out-list lengths are prefix-summed
-// and the concatenated lists are walked 32 elements per round, lane l taking
-// element r*32+l. The owner of an element is found from the starts that fall
-// in the round (ballot / or-reduce / popc), so lanes stay busy whatever the
-// list lengths.
+// Lookup of out(v): open-addressing table in shared memory (slot -> position),
+// optionally behind a bit filter, or (BIG) binary search in the sorted global list.
+struct OutTable {
+  const int32_t* hkey;
+  const uint16_t* hpos;
+  const uint32_t* filt;  // nullptr: no filter
+  int log2h;
+  const int32_t* glist;  // BIG: out(v) in global memory
+  int32_t od;
+};
+
+template <bool BIG>
+__device__ __forceinline__ int table_lookup(const OutTable& t, int32_t x) {
+  if (BIG) {
+    int lo = 0, hi = t.od;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (t.glist[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return (lo < t.od && t.glist[lo] == x) ? lo : -1;
+  }
+  const uint32_t hx = (uint32_t)x * 0x9E3779B1u;
+  if (t.filt) {
+    const uint32_t fb = hx >> (32 - FILTER_LOG2);
+    if (!((t.filt[fb >> 5] >> (fb & 31)) & 1u)) return -1;
+  }
+  const int H = 1 << t.log2h;
+  uint32_t sl = hx >> (32 - t.log2h);
+  for (int probe = 0; probe < H; ++probe) {
+    const int32_t key = t.hkey[sl];
+    if (key == x) return t.hpos[sl];
+    if (key == -1) return -1;
+    sl = (sl + 1) & (H - 1);
+  }
+  return -1;
+}
+
+// Insert out(v) into a shared table; `stride` threads starting at `tid`.
+__device__ __forceinline__ void table_fill(int32_t* hkey, uint16_t* hpos, uint32_t* filt, int log2h,
+                                           const int32_t* list, int32_t od, int tid, int stride) {
+  const int H = 1 << log2h;
+  for (int j = tid; j < od; j += stride) {
+    const int32_t x = list[j];
+    const uint32_t hx = (uint32_t)x * 0x9E3779B1u;
+    if (filt) {
+      const uint32_t fb = hx >> (32 - FILTER_LOG2);
+      atomicOr(&filt[fb >> 5], 1u << (fb & 31));
+    }
+    uint32_t s = hx >> (32 - log2h);
+    for (int probe = 0; probe < H; ++probe) {
+      if (atomicCAS(&hkey[s], -1, x) == -1) { hpos[s] = (uint16_t)j; break; }
+      s = (s + 1) & (H - 1);
+    }
+  }
+}
+
+// Per-warp scratch for one 32-position slice.
+struct SliceSmem {
+  int32_t* u;
+  int32_t* p;
+  uint32_t* acc;
+  long long* jv;
+};
+
+// One warp: triangles u < v < w for the in-neighbours u of v among the CSR
+// positions [p0, min(p0+32, p_end)) of N(v). The in-neighbours are compacted
+// to lanes 0..k-1, their out-list lengths prefix-summed, and the concatenated
+// lists walked 32 elements per round (lane l takes element r*32+l, four rounds
+// of loads in flight); the owner of an element comes from the starts that fall
+// in its round (ballot / or-reduce / popc). A hit w adds one to (v,w) in vcnt
+// (shared; global for BIG), to (u,w) at its slot of out(u), and to (u,v).
+template <bool BIG>
+__device__ __forceinline__ void process_slice(
+    int64_t p0, int64_t p_end, int64_t rb, int32_t v, int32_t dv, int32_t od, int64_t ob,
+    const int32_t* __restrict__ adj, const int32_t* __restrict__ deg,
+    const int64_t* __restrict__ oo, const int32_t* __restrict__ oadj, int lsh_T,
+    const OutTable& tab, uint32_t* vcnt, const SliceSmem& sm, uint32_t* __restrict__ tcnt,
+    int32_t* __restrict__ twin_rel, unsigned& bad) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int64_t p = p0 + lane;
+  int32_t u = -1;
+  bool is_in = false;
+  if (p < p_end) {
+    u = adj[rb + p];
+    const int32_t du = deg[u];
+    is_in = lower(du, u, dv, v);
+    // LSH mode: if u and v are both above the threshold, every edge of
+    // every triangle u < v < w is approximated, so the scan is not needed
+    if (is_in && lsh_T >= 0 && du > lsh_T) is_in = false;
+  }
+  const unsigned m = __ballot_sync(FULL, is_in);
+  if (!m) return;
+  const int k = __popc(m);
+  if (is_in) {
+    const int r = __popc(m & ((1u << lane) - 1u));
+    sm.u[r] = u;
+    sm.p[r] = (int32_t)p;
+  }
+  __syncwarp();
+  int32_t cu = -1, cp = 0, clen = 0;
+  int64_t cub = 0;
+  if (lane < k) {
+    cu = sm.u[lane];
+    cp = sm.p[lane];
+    cub = oo[cu];
+    clen = (int32_t)(oo[cu + 1] - cub);
+  }
+  if (od == 0) {
+    // no triangle has v in the middle: only locate v in the sorted out(u)
+    if (lane < k) {
+      int64_t lo = cub, hi = cub + clen;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (oadj[mid] < v) lo = mid + 1; else hi = mid;
+      }
+      if (lo < cub + clen && oadj[lo] == v) twin_rel[lo] = cp;
+      else bad = 1;
+    }
+    __syncwarp();
+    return;
+  }
+  int32_t incl = clen;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t y = __shfl_up_sync(FULL, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const int32_t cstart = incl - clen;
+  const int32_t W = __shfl_sync(FULL, incl, 31);
+  sm.acc[lane] = 0;
+  sm.jv[lane] = -1;
+  __syncwarp();
+  constexpr int R = 4;  // rounds whose loads are issued before any probe
+  for (int32_t rbase = 0; rbase < W; rbase += 32 * R) {
+    int32_t xs[R];
+    int64_t js[R];
+    int owns[R];
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr) {
+      const int32_t r0 = rbase + 32 * rr;
+      // every list is non-empty (v is in out(u)), so the starts are distinct
+      const bool starts_here = lane < k && cstart >= r0 && cstart < r0 + 32;
+      const unsigned smask = __reduce_or_sync(FULL, starts_here ? (1u << (cstart - r0)) : 0u);
+      const int before = __popc(__ballot_sync(FULL, lane < k && cstart < r0));
+      const int owner = before + __popc(smask & ((2u << lane) - 1u)) - 1;
+      const int own = owner < 0 ? 0 : owner;
+      const int64_t ub_o = __shfl_sync(FULL, cub, own);
+      const int32_t st_o = __shfl_sync(FULL, cstart, own);
+      const int32_t t = r0 + lane;
+      owns[rr] = own;
+      js[rr] = t < W ? ub_o + (t - st_o) : -1;
+      xs[rr] = t < W ? oadj[js[rr]] : -1;
+    }
+#pragma unroll
+    for (int rr = 0; rr < R; ++rr) {
+      const int32_t x = xs[rr];
+      const int64_t j = js[rr];
+      const int own = owns[rr];
+      bool hit = false;
+      if (j >= 0) {
+        if (x == v) sm.jv[own] = j;
+        const int q = table_lookup<BIG>(tab, x);
+        if (q >= 0) {
+          hit = true;
+          if (!BIG) atomicAdd(&vcnt[q], 1u);
+          else atomicAdd(&tcnt[ob + q], 1u);
+          atomicAdd(&tcnt[j], 1u);
+        }
+      }
+      // hits per owner: lanes of one owner are contiguous; its first lane adds
+      const unsigned hm = __ballot_sync(FULL, hit);
+      if (hm) {
+        const unsigned peers = __match_any_sync(FULL, own);
+        if ((hm & peers) && lane == __ffs(peers) - 1) sm.acc[own] += __popc(hm & peers);
+      }
+    }
+  }
+  __syncwarp();
+  if (lane < k) {
+    const long long jv = sm.jv[lane];
+    if (jv < 0) {
+      bad = 1;  // v lists u but u does not list v
+    } else {
+      const uint32_t acc = sm.acc[lane];
+      if (acc) atomicAdd(&tcnt[jv], acc);
+      twin_rel[jv] = cp;  // position of u in N(v)
+    }
+  }
+  __syncwarp();
+}
+
+// CTA kernel for rows longer than SMALL_DEG: the CTA shares out(v)'s table and
+// its warps pull 32-position slices of the item's CSR range.
+// BIG = out(v) too long for the shared table (binary search, global counters).
 template <bool BIG>
 __global__ void __launch_bounds__(TRI_THREADS, 3)
 k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
@@ -92,6 +282,7 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
   int32_t* hkey = smem + FILTER_WORDS;
   uint32_t* vcnt = (uint32_t*)(smem + FILTER_WORDS + 2 * od_cap);
   uint16_t* hpos = (uint16_t*)(smem + FILTER_WORDS + 3 * od_cap);
+  const SliceSmem sm{s_u[wid], s_p[wid], s_acc[wid], s_jv[wid]};
   unsigned bad = 0;
 
   for (;;) {
@@ -117,21 +308,10 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
       for (int i = threadIdx.x; i < od; i += TRI_THREADS) vcnt[i] = 0;
       for (int i = threadIdx.x; i < FILTER_WORDS; i += TRI_THREADS) filt[i] = 0;
       __syncthreads();
-      for (int j = threadIdx.x; j < od; j += TRI_THREADS) {
-        const int32_t x = oadj[ob + j];
-        const uint32_t hx = (uint32_t)x * 0x9E3779B1u;
-        const uint32_t fb = hx >> (32 - FILTER_LOG2);
-        atomicOr(&filt[fb >> 5], 1u << (fb & 31));
-        uint32_t s = hx >> (32 - log2h);
-        for (int probe = 0; probe < H; ++probe) {
-          const int32_t prev = atomicCAS(&hkey[s], -1, x);
-          if (prev == -1) { hpos[s] = (uint16_t)j; break; }
-          s = (s + 1) & (H - 1);
-        }
-      }
+      table_fill(hkey, hpos, filt, log2h, oadj + ob, od, threadIdx.x, TRI_THREADS);
       __syncthreads();
     }
-    const int H = 1 << log2h;
+    const OutTable tab{hkey, hpos, filt, log2h, oadj + ob, od};
     const int64_t rb = off[v];
     const int64_t p_begin = chunk * CHUNK;
     const int64_t p_end = min((int64_t)dv, p_begin + CHUNK);
@@ -142,136 +322,8 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
       slice = __shfl_sync(FULL, slice, 0);
       const int64_t p0 = p_begin + slice;
       if (p0 >= p_end) break;
-      const int64_t p = p0 + lane;
-      int32_t u = -1;
-      bool is_in = false;
-      if (p < p_end) {
-        u = adj[rb + p];
-        const int32_t du = deg[u];
-        is_in = lower(du, u, dv, (int32_t)v);
-        // LSH mode: if u and v are both above the threshold, every edge of
-        // every triangle u < v < w is approximated, so the scan is not needed
-        if (is_in && lsh_T >= 0 && du > lsh_T) is_in = false;
-      }
-      const unsigned m = __ballot_sync(FULL, is_in);
-      if (!m) continue;
-      const int k = __popc(m);
-      if (is_in) {
-        const int r = __popc(m & ((1u << lane) - 1u));
-        s_u[wid][r] = u;
-        s_p[wid][r] = (int32_t)p;
-      }
-      __syncwarp();
-      int32_t cu = -1, cp = 0, clen = 0;
-      int64_t cub = 0;
-      if (lane < k) {
-        cu = s_u[wid][lane];
-        cp = s_p[wid][lane];
-        cub = oo[cu];
-        clen = (int32_t)(oo[cu + 1] - cub);
-      }
-      if (od == 0) {
-        // no triangle has v in the middle: only locate v in the sorted out(u)
-        if (lane < k) {
-          int64_t lo = cub, hi = cub + clen;
-          while (lo < hi) {
-            const int64_t mid = (lo + hi) >> 1;
-            if (oadj[mid] < (int32_t)v) lo = mid + 1; else hi = mid;
-          }
-          if (lo < cub + clen && oadj[lo] == (int32_t)v) twin_rel[lo] = cp;
-          else bad = 1;
-        }
-        __syncwarp();
-        continue;
-      }
-      int32_t incl = clen;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int32_t y = __shfl_up_sync(FULL, incl, o);
-        if (lane >= o) incl += y;
-      }
-      const int32_t cstart = incl - clen;
-      const int32_t W = __shfl_sync(FULL, incl, 31);
-      s_acc[wid][lane] = 0;
-      s_jv[wid][lane] = -1;
-      __syncwarp();
-      constexpr int R = 4;  // rounds whose loads are issued before any probe
-      for (int32_t rb = 0; rb < W; rb += 32 * R) {
-        int32_t xs[R];
-        int64_t js[R];
-        int owns[R];
-#pragma unroll
-        for (int rr = 0; rr < R; ++rr) {
-          const int32_t r0 = rb + 32 * rr;
-          // every list is non-empty (v is in out(u)), so the starts are distinct
-          const bool starts_here = lane < k && cstart >= r0 && cstart < r0 + 32;
-          const unsigned smask = __reduce_or_sync(FULL, starts_here ? (1u << (cstart - r0)) : 0u);
-          const int before = __popc(__ballot_sync(FULL, lane < k && cstart < r0));
-          const int owner = before + __popc(smask & ((2u << lane) - 1u)) - 1;
-          const int own = owner < 0 ? 0 : owner;
-          const int64_t ub_o = __shfl_sync(FULL, cub, own);
-          const int32_t st_o = __shfl_sync(FULL, cstart, own);
-          const int32_t t = r0 + lane;
-          owns[rr] = own;
-          js[rr] = t < W ? ub_o + (t - st_o) : -1;
-          xs[rr] = t < W ? oadj[js[rr]] : -1;
-        }
-#pragma unroll
-        for (int rr = 0; rr < R; ++rr) {
-          const int32_t x = xs[rr];
-          const int64_t j = js[rr];
-          const int own = owns[rr];
-          bool hit = false;
-          if (j >= 0) {
-            if (x == (int32_t)v) s_jv[wid][own] = j;
-            int q = -1;
-            if (!BIG) {
-              const uint32_t hx = (uint32_t)x * 0x9E3779B1u;
-              const uint32_t fb = hx >> (32 - FILTER_LOG2);
-              if ((filt[fb >> 5] >> (fb & 31)) & 1u) {
-                uint32_t sl = hx >> (32 - log2h);
-                for (int probe = 0; probe < H; ++probe) {
-                  const int32_t key = hkey[sl];
-                  if (key == x) { q = hpos[sl]; break; }
-                  if (key == -1) break;
-                  sl = (sl + 1) & (H - 1);
-                }
-              }
-            } else {
-              int lo = 0, hi = od;
-              while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (oadj[ob + mid] < x) lo = mid + 1; else hi = mid;
-              }
-              if (lo < od && oadj[ob + lo] == x) q = lo;
-            }
-            if (q >= 0) {
-              hit = true;
-              if (!BIG) atomicAdd(&vcnt[q], 1u);
-              else atomicAdd(&tcnt[ob + q], 1u);
-              atomicAdd(&tcnt[j], 1u);
-            }
-          }
-          // hits per owner: lanes of one owner are contiguous; its first lane adds
-          const unsigned hm = __ballot_sync(FULL, hit);
-          if (hm) {
-            const unsigned peers = __match_any_sync(FULL, own);
-            if ((hm & peers) && lane == __ffs(peers) - 1) s_acc[wid][own] += __popc(hm & peers);
-          }
-        }
-      }
-      __syncwarp();
-      if (lane < k) {
-        const long long jv = s_jv[wid][lane];
-        if (jv < 0) {
-          bad = 1;  // v lists u but u does not list v
-        } else {
-          const uint32_t acc = s_acc[wid][lane];
-          if (acc) atomicAdd(&tcnt[jv], acc);
-          twin_rel[jv] = cp;  // position of u in N(v)
-        }
-      }
-      __syncwarp();
+      process_slice<BIG>(p0, p_end, rb, (int32_t)v, dv, od, ob, adj, deg, oo, oadj, lsh_T, tab,
+                         vcnt, sm, tcnt, twin_rel, bad);
     }
     __syncthreads();
     if (!BIG)
@@ -280,6 +332,67 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
         if (c) atomicAdd(&tcnt[ob + j], c);
       }
     __syncthreads();
+  }
+  if (bad) atomicOr(status, (unsigned)DEV_BADGRAPH);
+}
+
+// Warp kernel for rows of at most SMALL_DEG positions: each warp owns one
+// vertex at a time, with its own table of out(v) (no CTA barrier). Warps take
+// 32 vertices per atomic fetch.
+__global__ void __launch_bounds__(SW_WARPS * 32, 5)
+k_tri_small(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+            const int32_t* __restrict__ deg, const int64_t* __restrict__ oo,
+            const int32_t* __restrict__ oadj, int64_t n, unsigned long long* __restrict__ work,
+            int lsh_T, uint32_t* __restrict__ tcnt, int32_t* __restrict__ twin_rel,
+            unsigned* status) {
+  __shared__ int32_t s_key[SW_WARPS][SW_SLOTS];
+  __shared__ uint16_t s_pos[SW_WARPS][SW_SLOTS];
+  __shared__ uint32_t s_cnt[SW_WARPS][SMALL_DEG];
+  __shared__ int32_t s_u[SW_WARPS][32];
+  __shared__ int32_t s_p[SW_WARPS][32];
+  __shared__ uint32_t s_acc[SW_WARPS][32];
+  __shared__ long long s_jv[SW_WARPS][32];
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int32_t* hkey = s_key[wid];
+  uint16_t* hpos = s_pos[wid];
+  uint32_t* vcnt = s_cnt[wid];
+  const SliceSmem sm{s_u[wid], s_p[wid], s_acc[wid], s_jv[wid]};
+  unsigned bad = 0;
+  for (;;) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(work, 32ull);
+    base = __shfl_sync(FULL, base, 0);
+    if ((int64_t)base >= n) break;
+    const int64_t vend = min(n, (int64_t)base + 32);
+    for (int64_t vv = (int64_t)base; vv < vend; ++vv) {
+      const int32_t dv = deg[vv];
+      if (dv == 0 || dv > SMALL_DEG) continue;
+      const int64_t ob = oo[vv];
+      const int32_t od = (int32_t)(oo[vv + 1] - ob);
+      if (dv - od == 0) continue;  // no in-neighbours
+      int log2h = 5;
+      if (od > 0) {
+        while ((1 << log2h) < 2 * od) ++log2h;
+        const int H = 1 << log2h;
+        for (int i = lane; i < H; i += 32) hkey[i] = -1;
+        for (int i = lane; i < od; i += 32) vcnt[i] = 0;
+        __syncwarp();
+        table_fill(hkey, hpos, nullptr, log2h, oadj + ob, od, lane, 32);
+        __syncwarp();
+      }
+      const OutTable tab{hkey, hpos, nullptr, log2h, oadj + ob, od};
+      const int64_t rb = off[vv];
+      for (int64_t p0 = 0; p0 < dv; p0 += 32)
+        process_slice<false>(p0, dv, rb, (int32_t)vv, dv, od, ob, adj, deg, oo, oadj, lsh_T, tab,
+                             vcnt, sm, tcnt, twin_rel, bad);
+      __syncwarp();
+      for (int j = lane; j < od; j += 32) {
+        const uint32_t c = vcnt[j];
+        if (c) atomicAdd(&tcnt[ob + j], c);
+      }
+      __syncwarp();
+    }
   }
   if (bad) atomicOr(status, (unsigned)DEV_BADGRAPH);
 }
@@ -340,10 +453,10 @@ int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* a
   int32_t* twin = pool.get<int32_t>(m);
   int32_t* items = pool.get<int32_t>(n);
   int64_t* item_off = pool.get<int64_t>(n + 1);
-  unsigned long long* work = pool.get<unsigned long long>(2);
+  unsigned long long* work = pool.get<unsigned long long>(3);
   if (!tcnt || !twin || !items || !item_off || !work) return SCAN_ENOMEM;
   GS_CUDA(cudaMemsetAsync(tcnt, 0, m * sizeof(uint32_t), s));
-  GS_CUDA(cudaMemsetAsync(work, 0, 2 * sizeof(unsigned long long), s));
+  GS_CUDA(cudaMemsetAsync(work, 0, 3 * sizeof(unsigned long long), s));
   if (m > 0) {
     k_fill_i32<<<1024, 256, 0, s>>>(twin, m, -1);
     GS_LAUNCH();
@@ -376,6 +489,15 @@ int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* a
     k_triangles<false><<<sms * per_sm, TRI_THREADS, smem, s>>>(
         off, adj, deg, oo, oadj, n, item_off, work, lsh_T, od_cap, tcnt, twin, status);
     GS_LAUNCH();
+    {
+      int small_per_sm = 1;
+      GS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&small_per_sm, k_tri_small,
+                                                            SW_WARPS * 32, 0));
+      if (small_per_sm < 1) small_per_sm = 1;
+      k_tri_small<<<sms * small_per_sm, SW_WARPS * 32, 0, s>>>(off, adj, deg, oo, oadj, n, work + 2,
+                                                               lsh_T, tcnt, twin, status);
+      GS_LAUNCH();
+    }
     if (max_od > SMEM_OD_MAX) {
       k_triangles<true><<<sms * 4, TRI_THREADS, 0, s>>>(off, adj, deg, oo, oadj, n, item_off,
                                                         work + 1, lsh_T, 0, tcnt, twin, status);
