@@ -129,6 +129,31 @@ int scan_query(scan_index* index, int mu, double eps, int32_t* labels, int flags
 int scan_query_batch(scan_index* index, int q, const int* mu, const double* eps,
                      int32_t* labels, int flags, uintptr_t stream);
 
+/* The same query as scan_query, for callers that must not allocate device
+ * memory while they answer it -- for example a service that has handed all
+ * device memory to its own pool up front, or a latency-critical loop that
+ * cannot afford an allocation stalling it. No counterpart exists in the
+ * paper.
+ *
+ * Nothing is allocated: the per-call scratch (union-find parents for every
+ * vertex plus a few words) is one array compiled into the library, so every
+ * GPU that loads the library holds about 16 MiB for it until the process
+ * exits. Limits and rules:
+ *  - the index may have at most SCAN_NOALLOC_MAX_VERTICES vertices; a larger
+ *    index returns SCAN_EINVAL;
+ *  - labels must be device memory (n int32); host memory returns SCAN_EINVAL;
+ *  - the first call on a device looks up the scratch address for that device
+ *    (cudaGetSymbolAddress, with the device current); make that first call
+ *    before any stream capture;
+ *  - every call on a device shares the same scratch, and the scratch keeps
+ *    the last call's contents: calls whose work overlaps on the GPU race and
+ *    give wrong labels, so issue them one after another (this function
+ *    synchronises `stream` before it returns).
+ * Other arguments and results are those of scan_query. */
+#define SCAN_NOALLOC_MAX_VERTICES 4194304
+int scan_query_noalloc(scan_index* index, int mu, double eps, int32_t* labels, int flags,
+                       uintptr_t stream);
+
 /* Copy the index out (test hook; any pointer may be NULL, each host or
  * device): sim[num_arcs] in CSR arc order, no_id/no_sim[num_arcs] (NO[v]
  * occupies the slots of v's CSR row), co_off[max_deg+1], co_id/co_thr

@@ -219,4 +219,32 @@ int run_queries(const IndexData& ix, int Q, const int* mu_host, const double* ep
   return SCAN_OK;
 }
 
+// The same launches as run_queries with every scratch array supplied by the
+// caller (mu, eps, core counts and parents already in device memory); used by
+// the entry point that must not allocate.
+int run_queries_prealloc(const IndexData& ix, int Q, const int* mu_dev, const double* eps_dev,
+                         int64_t* nc_dev, int32_t* parent, int32_t* labels_dev, int flags,
+                         cudaStream_t s, unsigned* status_dev) {
+  if (Q <= 0 || ix.n == 0) return SCAN_OK;
+  const int64_t n = ix.n;
+  GS_CUDA(cudaMemsetAsync(parent, 0xff, sizeof(int32_t) * (size_t)Q * n, s));
+  QArgs a{ix.off, ix.deg, ix.adj, ix.no_id, ix.no_sim, ix.co_off, ix.co_id, ix.co_thr,
+          n, ix.maxdeg, mu_dev, eps_dev, nc_dev, parent, labels_dev, status_dev};
+  k_get_cores<<<(Q + 127) / 128, 128, 0, s>>>(a, Q);
+  GS_LAUNCH();
+  const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8));
+  k_mark_cores<<<dim3(gx, Q), 256, 0, s>>>(a);
+  GS_LAUNCH();
+  const unsigned gw = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 7) / 8, 152 * 16));
+  k_union<<<dim3(gw, Q), 256, 0, s>>>(a);
+  GS_LAUNCH();
+  k_finalize<<<dim3(gx, Q), 256, 0, s>>>(a);
+  GS_LAUNCH();
+  if (flags & SCAN_Q_HUBS) {
+    k_hubs<<<dim3(gw, Q), 256, 0, s>>>(a);
+    GS_LAUNCH();
+  }
+  return SCAN_OK;
+}
+
 }  // namespace gscan

@@ -154,6 +154,12 @@ int build_core_order_multi(int64_t N, int64_t A, const int64_t* off, const int32
 int run_queries(const IndexData& ix, int q, const int* mu, const double* eps, int32_t* labels_dev,
                 int flags, Pool& pool, cudaStream_t s, unsigned* status_dev);
 
+// run_queries with caller-supplied device scratch: mu_dev/eps_dev/nc_dev hold
+// Q entries, parent Q*n; nothing is allocated.
+int run_queries_prealloc(const IndexData& ix, int Q, const int* mu_dev, const double* eps_dev,
+                         int64_t* nc_dev, int32_t* parent, int32_t* labels_dev, int flags,
+                         cudaStream_t s, unsigned* status_dev);
+
 // Whole index build into ix (scan_api.cu); on error every block is released.
 int build_index(const scan_csr* csr, int kind, const scan_lsh_params* lsh, cudaStream_t s,
                 IndexData* ix);
