@@ -47,6 +47,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batched", action="store_true", help="skip the 2048-graph batched build")
     p.add_argument("--no-serving", action="store_true", help="skip the serving comparison")
+    p.add_argument("--no-lsh", action="store_true", help="skip the LSH build and quality gate")
     p.add_argument("--batch-graphs", type=int, default=2048)
     p.add_argument("--serve-queries", type=int, default=20000)
     return p.parse_args()
@@ -261,6 +262,69 @@ def bench_serving(gs, kind: int, nq: int, seed: int, stream):
     return results
 
 
+def adjusted_rand_index(a, b):
+    """ARI (Hubert and Arabie) of two labelings; negative labels are singletons."""
+    import numpy as np
+    n = a.shape[0]
+    idx = np.arange(n, dtype=np.int64)
+    ka = np.where(a >= 0, a.astype(np.int64), -1 - idx)
+    kb = np.where(b >= 0, b.astype(np.int64), -1 - idx)
+    _, ia = np.unique(ka, return_inverse=True)
+    _, ib = np.unique(kb, return_inverse=True)
+    pair = ia.astype(np.int64) * (int(ib.max()) + 1) + ib
+    _, nij = np.unique(pair, return_counts=True)
+    c2 = lambda x: (x.astype(np.float64) * (x - 1)).sum() / 2.0
+    sij = c2(nij)
+    si = c2(np.bincount(ia))
+    sj = c2(np.bincount(ib))
+    expected = si * sj / (n * (n - 1) / 2.0)
+    mx = (si + sj) / 2.0
+    return 1.0 if mx == expected else float((sij - expected) / (mx - expected))
+
+
+def bench_lsh(gs, off_d, adj_d, g, stream):
+    """LSH index mode on the same graph: SimHash 64/256 bits for cosine and
+    k-partition MinHash k=64 for Jaccard, degree threshold 128; build time, and
+    ARI / misclassified-edge fraction against the exact index at mu=5,
+    eps in {.3, .5, .7}."""
+    import numpy as np
+    import torch
+    out = {}
+    for kind, name, ks in ((gs.COSINE, "simhash", (64, 256)), (gs.JACCARD, "minhash", (64,))):
+        exact = gs.ScanIndex.build((off_d, adj_d), kind, stream=stream)
+        ex_sim = torch.empty(g.arcs, dtype=torch.float64, device="cuda")
+        gs.load().scan_index_export(exact._h, ex_sim.data_ptr(), None, None, None, None, None)
+        labs_exact = {e: exact.query(5, e) for e in (0.3, 0.5, 0.7)}
+        exact.free()
+        for k in ks:
+            lsh = gs.make_lsh(kind, k, 128, seed=1)
+            ix = gs.ScanIndex.build((off_d, adj_d), kind, lsh=lsh, stream=stream)
+            ts = []
+            for _ in range(3):
+                ix.free()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                ix = gs.ScanIndex.build((off_d, adj_d), kind, lsh=lsh, stream=stream)
+                b.record(stream)
+                b.synchronize()
+                ts.append(a.elapsed_time(b))
+            ap_sim = torch.empty(g.arcs, dtype=torch.float64, device="cuda")
+            gs.load().scan_index_export(ix._h, ap_sim.data_ptr(), None, None, None, None, None)
+            rec = {"build_ms": round(statistics.median(ts), 2),
+                   "edges_per_s": g.edges / (statistics.median(ts) / 1000.0)}
+            for e in (0.3, 0.5, 0.7):
+                lab = ix.query(5, e)
+                mis = ((ex_sim >= e) != (ap_sim >= e)).sum().item() / g.arcs
+                rec[f"eps{e}"] = {"ari": round(adjusted_rand_index(labs_exact[e], lab), 4),
+                                  "misclassified_edge_fraction": mis}
+            ix.free()
+            del ap_sim
+            out[f"{name}_k{k}"] = rec
+        del ex_sim
+    return out
+
+
 def cpu_baseline(edgefactor: int, seed: int, kind: int, repeats: int = 2):
     import graphgen
     import oracle
@@ -456,6 +520,8 @@ def main():
         "clocks": clocks,
         "graph_generation_s": round(t_gen, 1),
     }
+    if not args.no_lsh:
+        out["lsh"] = bench_lsh(gs, off_d, adj_d, g, stream)
     if not args.no_batched:
         out["batched_build"] = bench_batched(gs, kind, args.batch_graphs, args.seed, stream)
     if not args.no_serving:

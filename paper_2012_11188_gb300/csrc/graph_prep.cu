@@ -135,41 +135,24 @@ __device__ __forceinline__ bool lower(int32_t du, int32_t u, int32_t dv, int32_t
   return du < dv || (du == dv && u < v);
 }
 
-// Out-degree of each vertex: neighbours of larger (degree, id). Warp per row.
-__global__ void k_outdeg(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
-                         const int32_t* __restrict__ deg, int64_t n, int32_t* __restrict__ od,
-                         int32_t* max_od) {
+// Orientation in place: the out-arcs of v (neighbours of larger (degree, id))
+// are compacted, in id order, to the front of v's own CSR slot range, so
+// out(v) = oadj[off[v] .. off[v] + od[v]) needs no separate offsets; opos
+// holds each out-arc's position in the row. One warp per row.
+__global__ void k_orient_inplace(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+                                 const int32_t* __restrict__ deg, int64_t n,
+                                 int32_t* __restrict__ od, int32_t* __restrict__ oadj,
+                                 int32_t* __restrict__ opos, int32_t* max_od,
+                                 unsigned long long* sum_od) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long local_sum = 0;
+  int32_t local_max = 0;
   for (int64_t v = warp; v < n; v += nwarps) {
     const int64_t b = off[v], e = off[v + 1];
     const int32_t dv = deg[v];
-    int c = 0;
-    for (int64_t i = b + lane; i < e; i += 32) {
-      const int32_t x = adj[i];
-      c += lower(dv, (int32_t)v, deg[x], x);
-    }
-    for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if (lane == 0) {
-      od[v] = c;
-      if (c) atomicMax(max_od, c);
-    }
-  }
-}
-
-// Compact each row to its out-arcs, keeping id order; opos = index in the row.
-__global__ void k_orient(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
-                         const int32_t* __restrict__ deg, int64_t n,
-                         const int64_t* __restrict__ oo, int32_t* __restrict__ oadj,
-                         int32_t* __restrict__ opos) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t v = warp; v < n; v += nwarps) {
-    const int64_t b = off[v], e = off[v + 1];
-    const int32_t dv = deg[v];
-    int64_t w = oo[v];
+    int64_t w = b;
     for (int64_t i0 = b; i0 < e; i0 += 32) {
       const int64_t i = i0 + lane;
       bool up = false;
@@ -183,6 +166,13 @@ __global__ void k_orient(const int64_t* __restrict__ off, const int32_t* __restr
       }
       w += __popc(m);
     }
+    if (lane == 0) od[v] = (int32_t)(w - b);
+    local_sum += (unsigned long long)(w - b);
+    local_max = max(local_max, (int32_t)(w - b));
+  }
+  if (lane == 0) {
+    if (local_sum) atomicAdd(sum_od, local_sum);
+    if (local_max) atomicMax(max_od, local_max);
   }
 }
 
@@ -213,30 +203,19 @@ int launch_degrees(const int64_t* off, const int32_t* adj, int64_t n, int64_t ar
 }
 
 int launch_orient(const int64_t* off, const int32_t* adj, const int32_t* deg, int64_t n,
-                  int64_t arcs, Pool& pool, int64_t** oo_out, int32_t** oadj_out,
-                  int32_t** opos_out, int32_t* max_od_dev, cudaStream_t s) {
-  int32_t* od = pool.get<int32_t>(n);
-  int64_t* oo = pool.get<int64_t>(n + 1);
-  int32_t* oadj = pool.get<int32_t>(arcs / 2 + 1);
-  int32_t* opos = pool.get<int32_t>(arcs / 2 + 1);
-  if (!od || !oo || !oadj || !opos) return SCAN_ENOMEM;
+                  int64_t arcs, Pool& pool, int32_t** od_out, int32_t** oadj_out,
+                  int32_t** opos_out, int32_t* max_od_dev, unsigned long long* sum_od_dev,
+                  cudaStream_t s) {
+  int32_t* od = pool.get<int32_t>(n > 0 ? n : 1);
+  int32_t* oadj = pool.get<int32_t>(arcs > 0 ? arcs : 1);
+  int32_t* opos = pool.get<int32_t>(arcs > 0 ? arcs : 1);
+  if (!od || !oadj || !opos) return SCAN_ENOMEM;
   if (n > 0) {
-    k_outdeg<<<grid_for(n, 8), 256, 0, s>>>(off, adj, deg, n, od, max_od_dev);
+    k_orient_inplace<<<grid_for(n, 8), 256, 0, s>>>(off, adj, deg, n, od, oadj, opos, max_od_dev,
+                                                    sum_od_dev);
     GS_LAUNCH();
   }
-  GS_TRY(exclusive_scan_i32_to_i64(od, oo, n, pool, s));
-  // a symmetric graph orients exactly arcs/2 edges; anything else would not
-  // fit the out-list arrays, so it is rejected before they are written
-  int64_t m_or = -1;
-  GS_CUDA(cudaMemcpyAsync(&m_or, oo + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  GS_CUDA(cudaStreamSynchronize(s));
-  if (m_or != arcs / 2) return SCAN_EBADGRAPH;
-  if (n > 0) {
-    k_orient<<<grid_for(n, 8), 256, 0, s>>>(off, adj, deg, n, oo, oadj, opos);
-    GS_LAUNCH();
-  }
-  pool.put(od);
-  *oo_out = oo;
+  *od_out = od;
   *oadj_out = oadj;
   *opos_out = opos;
   return SCAN_OK;

@@ -13,7 +13,11 @@
 //  3. AssignNonCores (Algorithm 4) with the deterministic rule of Section
 //     7.3.4: a non-core takes the label of the first core in its own
 //     eps-prefix of NO -- the most similar eps-similar core, smallest id among
-//     equal similarities (NO breaks ties by id).
+//     equal similarities (NO breaks ties by id). Only the non-cores found in
+//     the cores' eps-prefixes are visited (each claimed once by a CAS on its
+//     label), and a non-core's own eps-prefix is shorter than mu-1, so the
+//     query's work follows the eps-edges of its clusters (Theorem 4.3's O(Z))
+//     plus two memsets of n words; every other label stays -1.
 //  4. With SCAN_Q_HUBS (Section 4.3): an unclustered vertex whose neighbours
 //     carry two distinct labels becomes -2.
 #include "scan_internal.cuh"
@@ -128,29 +132,55 @@ __global__ void k_union(QArgs a) {
   if (__any_sync(0xffffffffu, fail) && lane == 0) atomicOr(a.status, (unsigned)DEV_LIMIT);
 }
 
-// thread per vertex: cores take their root, non-cores the first core of their eps-prefix
-__global__ void k_finalize(QArgs a) {
+// labels of the cores: their union-find root (the smallest id of the cluster)
+__global__ void k_core_labels(QArgs a) {
   const int q = blockIdx.y;
-  const double eps = a.eps[q];
-  const bool any = a.ncores[q] > 0;
+  const int64_t nc = a.ncores[q];
+  if (nc == 0) return;
+  const int64_t cb = a.co_off[a.mu[q] - 2];
   int32_t* parent = a.parent + (int64_t)q * a.n;
   int32_t* lab = a.labels + (int64_t)q * a.n;
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < a.n;
-       v += (int64_t)gridDim.x * blockDim.x) {
-    int32_t l = -1;
-    if (any) {
-      if (ld_volatile(parent + v) >= 0) {
-        l = uf_find(parent, (int32_t)v);
-      } else {
-        const int64_t rb = a.off[v], re = rb + a.deg[v];
-        for (int64_t j = rb; j < re; ++j) {
-          if (a.no_sim[j] < eps) break;
-          const int32_t x = a.no_id[j];
-          if (ld_volatile(parent + x) >= 0) { l = uf_find(parent, x); break; }
-        }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nc;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t u = a.co_id[cb + i];
+    lab[u] = uf_find(parent, u);
+  }
+}
+
+constexpr int32_t CLAIMED = -3;
+
+// warp per core: every non-core x in the core's eps-prefix is a border. The
+// first thread to claim x scans x's own eps-prefix of NO for its first core
+// (most similar, smallest id on ties); sigma is symmetric, so that prefix
+// holds at least this core.
+__global__ void k_borders(QArgs a) {
+  const int q = blockIdx.y;
+  const int64_t nc = a.ncores[q];
+  if (nc == 0) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t cb = a.co_off[a.mu[q] - 2];
+  const double eps = a.eps[q];
+  int32_t* parent = a.parent + (int64_t)q * a.n;
+  int32_t* lab = a.labels + (int64_t)q * a.n;
+  for (int64_t i = w0; i < nc; i += nw) {
+    const int32_t u = a.co_id[cb + i];
+    const int64_t rb = a.off[u];
+    const int64_t pu = prefix_ge(a.no_sim + rb, a.deg[u], eps);
+    for (int64_t j = lane; j < pu; j += 32) {
+      const int32_t x = a.no_id[rb + j];
+      if (ld_volatile(parent + x) >= 0) continue;
+      if (atomicCAS(lab + x, -1, CLAIMED) != -1) continue;
+      int32_t l = -1;
+      const int64_t xb = a.off[x], xe = xb + a.deg[x];
+      for (int64_t t = xb; t < xe; ++t) {
+        if (a.no_sim[t] < eps) break;
+        const int32_t y = a.no_id[t];
+        if (ld_volatile(parent + y) >= 0) { l = uf_find(parent, y); break; }
       }
+      lab[x] = l;
     }
-    lab[v] = l;
   }
 }
 
@@ -196,6 +226,7 @@ int run_queries(const IndexData& ix, int Q, const int* mu_host, const double* ep
   GS_CUDA(cudaMemcpyAsync(eps, eps_host, sizeof(double) * Q, cudaMemcpyHostToDevice, s));
   if (n == 0) return SCAN_OK;
   GS_CUDA(cudaMemsetAsync(parent, 0xff, sizeof(int32_t) * (size_t)Q * n, s));
+  GS_CUDA(cudaMemsetAsync(labels_dev, 0xff, sizeof(int32_t) * (size_t)Q * n, s));
   QArgs a{ix.off, ix.deg, ix.adj, ix.no_id, ix.no_sim, ix.co_off, ix.co_id, ix.co_thr,
           n, ix.maxdeg, mu, eps, nc, parent, labels_dev, status_dev};
   k_get_cores<<<(Q + 127) / 128, 128, 0, s>>>(a, Q);
@@ -206,7 +237,9 @@ int run_queries(const IndexData& ix, int Q, const int* mu_host, const double* ep
   const unsigned gw = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 7) / 8, 152 * 16 / std::min(Q, 16) + 1));
   k_union<<<dim3(gw, Q), 256, 0, s>>>(a);
   GS_LAUNCH();
-  k_finalize<<<dim3(gx, Q), 256, 0, s>>>(a);
+  k_core_labels<<<dim3(gx, Q), 256, 0, s>>>(a);
+  GS_LAUNCH();
+  k_borders<<<dim3(gw, Q), 256, 0, s>>>(a);
   GS_LAUNCH();
   if (flags & SCAN_Q_HUBS) {
     k_hubs<<<dim3(gw, Q), 256, 0, s>>>(a);
@@ -228,6 +261,7 @@ int run_queries_prealloc(const IndexData& ix, int Q, const int* mu_dev, const do
   if (Q <= 0 || ix.n == 0) return SCAN_OK;
   const int64_t n = ix.n;
   GS_CUDA(cudaMemsetAsync(parent, 0xff, sizeof(int32_t) * (size_t)Q * n, s));
+  GS_CUDA(cudaMemsetAsync(labels_dev, 0xff, sizeof(int32_t) * (size_t)Q * n, s));
   QArgs a{ix.off, ix.deg, ix.adj, ix.no_id, ix.no_sim, ix.co_off, ix.co_id, ix.co_thr,
           n, ix.maxdeg, mu_dev, eps_dev, nc_dev, parent, labels_dev, status_dev};
   k_get_cores<<<(Q + 127) / 128, 128, 0, s>>>(a, Q);
@@ -238,7 +272,9 @@ int run_queries_prealloc(const IndexData& ix, int Q, const int* mu_dev, const do
   const unsigned gw = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 7) / 8, 152 * 16));
   k_union<<<dim3(gw, Q), 256, 0, s>>>(a);
   GS_LAUNCH();
-  k_finalize<<<dim3(gx, Q), 256, 0, s>>>(a);
+  k_core_labels<<<dim3(gx, Q), 256, 0, s>>>(a);
+  GS_LAUNCH();
+  k_borders<<<dim3(gw, Q), 256, 0, s>>>(a);
   GS_LAUNCH();
   if (flags & SCAN_Q_HUBS) {
     k_hubs<<<dim3(gw, Q), 256, 0, s>>>(a);

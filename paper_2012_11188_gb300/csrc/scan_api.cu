@@ -139,7 +139,7 @@ int validate_lsh(const scan_lsh_params* p, int kind) {
 // Steps shared by the single and the batched build: CSR checks, degrees,
 // orientation, counts and similarities, LSH estimates, neighbour order.
 // ix holds n, arcs, off (absolute, int64), adj and allocated deg, no_id,
-// no_sim and a 4-word status block; on return ix->maxdeg is set.
+// no_sim and an 8-word status block; on return ix->maxdeg is set.
 int run_pipeline(IndexData* ix, int kind, const scan_lsh_params* lsh, Pool& pool, cudaStream_t s,
                  Events& ev, float* count_ms) {
   const int64_t n = ix->n, arcs = ix->arcs;
@@ -152,13 +152,17 @@ int run_pipeline(IndexData* ix, int kind, const scan_lsh_params* lsh, Pool& pool
   if (hs[0] & DEV_BADGRAPH) return SCAN_EBADGRAPH;
   ix->maxdeg = (int32_t)hs[1];
   // ---- orientation (Section 6.1)
-  int64_t* oo = nullptr;
-  int32_t *oadj = nullptr, *opos = nullptr;
+  int32_t *od = nullptr, *oadj = nullptr, *opos = nullptr;
   if (arcs > 0) {
-    GS_TRY(launch_orient(ix->off, ix->adj, ix->deg, n, arcs, pool, &oo, &oadj, &opos,
-                         (int32_t*)scalars + 2, s));
+    unsigned long long* sum_od = (unsigned long long*)(scalars + 4);
+    GS_TRY(launch_orient(ix->off, ix->adj, ix->deg, n, arcs, pool, &od, &oadj, &opos,
+                         (int32_t*)scalars + 2, sum_od, s));
+    unsigned long long hsum = 0;
     GS_CUDA(cudaMemcpyAsync(hs, scalars, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    GS_CUDA(cudaMemcpyAsync(&hsum, sum_od, sizeof(hsum), cudaMemcpyDeviceToHost, s));
     GS_CUDA(cudaStreamSynchronize(s));
+    // a symmetric graph orients exactly arcs/2 edges
+    if ((int64_t)hsum != arcs / 2) return SCAN_EBADGRAPH;
   }
   const int32_t max_od = (int32_t)hs[2];
   GS_TRY(ev.mark(s));
@@ -173,13 +177,13 @@ int run_pipeline(IndexData* ix, int kind, const scan_lsh_params* lsh, Pool& pool
   // ---- counts and similarities (Section 3.1, Section 6.1)
   if (arcs > 0) {
     GS_CUDA(cudaMemcpyAsync(ix->no_id, ix->adj, arcs * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
-    GS_TRY(launch_closed_counts_and_sims(kind, ix->off, ix->adj, ix->deg, n, arcs, oo, oadj, opos,
+    GS_TRY(launch_closed_counts_and_sims(kind, ix->off, ix->adj, ix->deg, n, arcs, od, oadj, opos,
                                          max_od, use_lsh ? lsh->degree_threshold : -1,
                                          ix->no_sim, scalars, pool, s, count_ms));
     GS_CUDA(cudaMemcpyAsync(hs, scalars, sizeof(hs), cudaMemcpyDeviceToHost, s));
     GS_CUDA(cudaStreamSynchronize(s));
     if (hs[0] & DEV_BADGRAPH) return SCAN_EBADGRAPH;
-    pool.put(oo);
+    pool.put(od);
     pool.put(oadj);
     pool.put(opos);
   }
@@ -243,10 +247,10 @@ int build_one(const scan_csr* csr, int kind, const scan_lsh_params* lsh, cudaStr
   ix->adj = pool.get<int32_t>(arcs > 0 ? arcs : 1);
   ix->no_id = pool.get<int32_t>(arcs > 0 ? arcs : 1);
   ix->no_sim = pool.get<double>(arcs > 0 ? arcs : 1);
-  ix->status = pool.get<unsigned>(4);
+  ix->status = pool.get<unsigned>(8);
   if (!ix->off || !ix->deg || !ix->adj || !ix->no_id || !ix->no_sim || !ix->status)
     return SCAN_ENOMEM;
-  GS_CUDA(cudaMemsetAsync(ix->status, 0, 4 * sizeof(unsigned), s));
+  GS_CUDA(cudaMemsetAsync(ix->status, 0, 8 * sizeof(unsigned), s));
   // ---- inputs into the index's own arrays
   const bool dev_in = csr->on_device != 0;
   const cudaMemcpyKind k_in = dev_in ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -395,12 +399,12 @@ int build_batch(const scan_csr* graphs, int G, int kind, const scan_lsh_params* 
   u.adj = pool.get<int32_t>(A > 0 ? A : 1);
   u.no_id = pool.get<int32_t>(A > 0 ? A : 1);
   u.no_sim = pool.get<double>(A > 0 ? A : 1);
-  u.status = pool.get<unsigned>(4);
+  u.status = pool.get<unsigned>(8);
   int64_t* raw = pool.get<int64_t>(N + G);
   int64_t* meta = pool.get<int64_t>(2 * (size_t)(G + 1));
   if (!u.off || !u.deg || !u.adj || !u.no_id || !u.no_sim || !u.status || !raw || !meta)
     return SCAN_ENOMEM;
-  GS_CUDA(cudaMemsetAsync(u.status, 0, 4 * sizeof(unsigned), s));
+  GS_CUDA(cudaMemsetAsync(u.status, 0, 8 * sizeof(unsigned), s));
   std::vector<int64_t> hmeta(2 * (size_t)(G + 1));
   std::copy(vb.begin(), vb.end(), hmeta.begin());
   std::copy(ab.begin(), ab.end(), hmeta.begin() + (G + 1));

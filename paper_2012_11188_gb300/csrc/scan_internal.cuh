@@ -118,18 +118,19 @@ struct IndexData {
 int launch_degrees(const int64_t* off, const int32_t* adj, int64_t n, int64_t arcs, int32_t* deg,
                    int32_t* maxdeg_dev, unsigned* status, cudaStream_t s);
 
-// Orientation by (degree, id): out-degree, out offsets, out lists and the
-// position of each out-arc inside its source's CSR row.
+// Orientation by (degree, id), in place: out(v) = oadj[off[v] .. off[v]+od[v]),
+// in id order; opos = position of each out-arc inside its source's CSR row.
+// max_od_dev receives the largest out-degree, sum_od_dev the number of out-arcs.
 int launch_orient(const int64_t* off, const int32_t* adj, const int32_t* deg, int64_t n,
-                  int64_t arcs, Pool& pool, int64_t** oo, int32_t** oadj, int32_t** opos,
-                  int32_t* max_od_dev, cudaStream_t s);
+                  int64_t arcs, Pool& pool, int32_t** od, int32_t** oadj, int32_t** opos,
+                  int32_t* max_od_dev, unsigned long long* sum_od_dev, cudaStream_t s);
 
 // Closed counts of every edge by oriented triangle enumeration, then the
 // similarity of every CSR arc written to sim_csr (the unsorted NO). With
 // lsh_T >= 0, edges whose endpoints both have degree > lsh_T are left for the
 // LSH estimate (their sim_csr entries are overwritten later).
 int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* adj,
-                                  const int32_t* deg, int64_t n, int64_t arcs, const int64_t* oo,
+                                  const int32_t* deg, int64_t n, int64_t arcs, const int32_t* od,
                                   const int32_t* oadj, const int32_t* opos, int32_t max_od,
                                   int lsh_T, double* sim_csr, unsigned* status, Pool& pool,
                                   cudaStream_t s, float* count_ms);

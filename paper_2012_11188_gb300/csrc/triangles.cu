@@ -23,7 +23,7 @@ namespace {
 
 constexpr int TRI_THREADS = 512;
 constexpr int TRI_WARPS = TRI_THREADS / 32;
-constexpr int CHUNK = 1024;          // CSR positions of N(v) per work item
+constexpr int CHUNK = 4096;          // CSR positions of N(v) per work item
 constexpr int SMEM_OD_MAX = 4096;    // out(v) sizes handled by the shared-memory table
 
 __device__ __forceinline__ bool lower(int32_t du, int32_t u, int32_t dv, int32_t v) {
@@ -38,11 +38,11 @@ constexpr int SW_WARPS = 8;
 // ceil(deg/CHUNK) items when it has in-neighbours (every in-arc needs the
 // position of its source in N(v), even when out(v) is empty and no triangle
 // has v in the middle). items[v] -> prefix -> item index maps to (v, chunk).
-__global__ void k_item_counts(const int64_t* __restrict__ oo, const int32_t* __restrict__ deg,
+__global__ void k_item_counts(const int32_t* __restrict__ odeg, const int32_t* __restrict__ deg,
                               int64_t n, int32_t* __restrict__ items) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
        v += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t od = oo[v + 1] - oo[v];
+    const int64_t od = odeg[v];
     const int32_t d = deg[v];
     int c = 0;
     if (d > SMALL_DEG && d - od > 0) c = (int)((d + CHUNK - 1) / CHUNK);
@@ -139,8 +139,8 @@ template <bool BIG>
 __device__ __forceinline__ void process_slice(
     int64_t p0, int64_t p_end, int64_t rb, int32_t v, int32_t dv, int32_t od, int64_t ob,
     const int32_t* __restrict__ adj, const int32_t* __restrict__ deg,
-    const int64_t* __restrict__ oo, const int32_t* __restrict__ oadj, int lsh_T,
-    const OutTable& tab, uint32_t* vcnt, const SliceSmem& sm, uint32_t* __restrict__ tcnt,
+    const int64_t* __restrict__ off, const int32_t* __restrict__ odeg,
+    const int32_t* __restrict__ oadj, int lsh_T, const OutTable& tab, uint32_t* vcnt, const SliceSmem& sm, uint32_t* __restrict__ tcnt,
     int32_t* __restrict__ twin_rel, unsigned& bad) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -169,8 +169,8 @@ __device__ __forceinline__ void process_slice(
   if (lane < k) {
     cu = sm.u[lane];
     cp = sm.p[lane];
-    cub = oo[cu];
-    clen = (int32_t)(oo[cu + 1] - cub);
+    cub = off[cu];
+    clen = odeg[cu];
   }
   if (od == 0) {
     // no triangle has v in the middle: only locate v in the sorted out(u)
@@ -198,25 +198,45 @@ __device__ __forceinline__ void process_slice(
   sm.jv[lane] = -1;
   __syncwarp();
   constexpr int R = 4;  // rounds whose loads are issued before any probe
+  // the list holding element r0 (warp-uniform); a round that lies inside one
+  // list needs no owner search
+  int cur = 0;
+  int32_t cur_start = 0;
+  int32_t cur_end = __shfl_sync(FULL, incl, 0);
+  int64_t cur_ub = __shfl_sync(FULL, cub, 0);
   for (int32_t rbase = 0; rbase < W; rbase += 32 * R) {
     int32_t xs[R];
     int64_t js[R];
     int owns[R];
+    bool single[R];
 #pragma unroll
     for (int rr = 0; rr < R; ++rr) {
       const int32_t r0 = rbase + 32 * rr;
-      // every list is non-empty (v is in out(u)), so the starts are distinct
-      const bool starts_here = lane < k && cstart >= r0 && cstart < r0 + 32;
-      const unsigned smask = __reduce_or_sync(FULL, starts_here ? (1u << (cstart - r0)) : 0u);
-      const int before = __popc(__ballot_sync(FULL, lane < k && cstart < r0));
-      const int owner = before + __popc(smask & ((2u << lane) - 1u)) - 1;
-      const int own = owner < 0 ? 0 : owner;
-      const int64_t ub_o = __shfl_sync(FULL, cub, own);
-      const int32_t st_o = __shfl_sync(FULL, cstart, own);
+      if (r0 >= cur_end && r0 < W) {
+        cur = __popc(__ballot_sync(FULL, lane < k && cstart <= r0)) - 1;
+        cur_start = __shfl_sync(FULL, cstart, cur);
+        cur_end = __shfl_sync(FULL, incl, cur);
+        cur_ub = __shfl_sync(FULL, cub, cur);
+      }
       const int32_t t = r0 + lane;
-      owns[rr] = own;
-      js[rr] = t < W ? ub_o + (t - st_o) : -1;
-      xs[rr] = t < W ? oadj[js[rr]] : -1;
+      if (r0 + 32 <= cur_end) {
+        single[rr] = true;
+        owns[rr] = cur;
+        js[rr] = cur_ub + (t - cur_start);
+      } else {
+        single[rr] = false;
+        // every list is non-empty (v is in out(u)), so the starts are distinct
+        const bool starts_here = lane < k && cstart >= r0 && cstart < r0 + 32;
+        const unsigned smask = __reduce_or_sync(FULL, starts_here ? (1u << (cstart - r0)) : 0u);
+        const int before = __popc(__ballot_sync(FULL, lane < k && cstart < r0));
+        const int owner = before + __popc(smask & ((2u << lane) - 1u)) - 1;
+        const int own = owner < 0 ? 0 : owner;
+        const int64_t ub_o = __shfl_sync(FULL, cub, own);
+        const int32_t st_o = __shfl_sync(FULL, cstart, own);
+        owns[rr] = own;
+        js[rr] = t < W ? ub_o + (t - st_o) : -1;
+      }
+      xs[rr] = js[rr] >= 0 ? oadj[js[rr]] : -1;
     }
 #pragma unroll
     for (int rr = 0; rr < R; ++rr) {
@@ -234,11 +254,15 @@ __device__ __forceinline__ void process_slice(
           atomicAdd(&tcnt[j], 1u);
         }
       }
-      // hits per owner: lanes of one owner are contiguous; its first lane adds
       const unsigned hm = __ballot_sync(FULL, hit);
       if (hm) {
-        const unsigned peers = __match_any_sync(FULL, own);
-        if ((hm & peers) && lane == __ffs(peers) - 1) sm.acc[own] += __popc(hm & peers);
+        if (single[rr]) {
+          if (lane == 0) sm.acc[own] += __popc(hm);
+        } else {
+          // lanes of one owner are contiguous; its first lane adds
+          const unsigned peers = __match_any_sync(FULL, own);
+          if ((hm & peers) && lane == __ffs(peers) - 1) sm.acc[own] += __popc(hm & peers);
+        }
       }
     }
   }
@@ -262,7 +286,7 @@ __device__ __forceinline__ void process_slice(
 template <bool BIG>
 __global__ void __launch_bounds__(TRI_THREADS, 3)
 k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
-            const int32_t* __restrict__ deg, const int64_t* __restrict__ oo,
+            const int32_t* __restrict__ deg, const int32_t* __restrict__ odeg,
             const int32_t* __restrict__ oadj, int64_t n, const int64_t* __restrict__ item_off,
             unsigned long long* __restrict__ work, int lsh_T, int od_cap,
             uint32_t* __restrict__ tcnt, int32_t* __restrict__ twin_rel, unsigned* status) {
@@ -296,8 +320,8 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
     const int64_t v = find_item_vertex(item_off, n, item);
     const int64_t chunk = item - item_off[v];
     const int32_t dv = deg[v];
-    const int64_t ob = oo[v];
-    const int32_t od = (int32_t)(oo[v + 1] - ob);
+    const int64_t ob = off[v];
+    const int32_t od = odeg[v];
     const bool skip_item = BIG ? (od <= SMEM_OD_MAX) : (od > SMEM_OD_MAX);
     if (skip_item) { __syncthreads(); continue; }
     int log2h = 5;
@@ -322,7 +346,7 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
       slice = __shfl_sync(FULL, slice, 0);
       const int64_t p0 = p_begin + slice;
       if (p0 >= p_end) break;
-      process_slice<BIG>(p0, p_end, rb, (int32_t)v, dv, od, ob, adj, deg, oo, oadj, lsh_T, tab,
+      process_slice<BIG>(p0, p_end, rb, (int32_t)v, dv, od, ob, adj, deg, off, odeg, oadj, lsh_T, tab,
                          vcnt, sm, tcnt, twin_rel, bad);
     }
     __syncthreads();
@@ -341,7 +365,7 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
 // 32 vertices per atomic fetch.
 __global__ void __launch_bounds__(SW_WARPS * 32, 5)
 k_tri_small(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
-            const int32_t* __restrict__ deg, const int64_t* __restrict__ oo,
+            const int32_t* __restrict__ deg, const int32_t* __restrict__ odeg,
             const int32_t* __restrict__ oadj, int64_t n, unsigned long long* __restrict__ work,
             int lsh_T, uint32_t* __restrict__ tcnt, int32_t* __restrict__ twin_rel,
             unsigned* status) {
@@ -368,8 +392,8 @@ k_tri_small(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
     for (int64_t vv = (int64_t)base; vv < vend; ++vv) {
       const int32_t dv = deg[vv];
       if (dv == 0 || dv > SMALL_DEG) continue;
-      const int64_t ob = oo[vv];
-      const int32_t od = (int32_t)(oo[vv + 1] - ob);
+      const int64_t ob = off[vv];
+      const int32_t od = odeg[vv];
       if (dv - od == 0) continue;  // no in-neighbours
       int log2h = 5;
       if (od > 0) {
@@ -384,7 +408,7 @@ k_tri_small(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
       const OutTable tab{hkey, hpos, nullptr, log2h, oadj + ob, od};
       const int64_t rb = off[vv];
       for (int64_t p0 = 0; p0 < dv; p0 += 32)
-        process_slice<false>(p0, dv, rb, (int32_t)vv, dv, od, ob, adj, deg, oo, oadj, lsh_T, tab,
+        process_slice<false>(p0, dv, rb, (int32_t)vv, dv, od, ob, adj, deg, off, odeg, oadj, lsh_T, tab,
                              vcnt, sm, tcnt, twin_rel, bad);
       __syncwarp();
       for (int j = lane; j < od; j += 32) {
@@ -408,7 +432,7 @@ __device__ __forceinline__ double sim_of(int kind, int64_t c, int64_t du, int64_
 
 // Every oriented edge a->b writes sigma to both of its CSR arcs.
 __global__ void k_expand(int kind, const int64_t* __restrict__ off, const int32_t* __restrict__ deg,
-                         const int64_t* __restrict__ oo, const int32_t* __restrict__ oadj,
+                         const int32_t* __restrict__ odeg, const int32_t* __restrict__ oadj,
                          const int32_t* __restrict__ opos, const uint32_t* __restrict__ tcnt,
                          const int32_t* __restrict__ twin_rel, int64_t n, int lsh_T,
                          double* __restrict__ sim_csr, unsigned* status) {
@@ -417,7 +441,7 @@ __global__ void k_expand(int kind, const int64_t* __restrict__ off, const int32_
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   unsigned bad = 0;
   for (int64_t a = warp; a < n; a += nwarps) {
-    const int64_t ob = oo[a], oe = oo[a + 1];
+    const int64_t ob = off[a], oe = ob + odeg[a];
     if (ob == oe) continue;
     const int64_t ra = off[a];
     const int32_t da = deg[a];
@@ -444,11 +468,11 @@ __global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v) {
 }  // namespace
 
 int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* adj,
-                                  const int32_t* deg, int64_t n, int64_t arcs, const int64_t* oo,
+                                  const int32_t* deg, int64_t n, int64_t arcs, const int32_t* odeg,
                                   const int32_t* oadj, const int32_t* opos, int32_t max_od,
                                   int lsh_T, double* sim_csr, unsigned* status, Pool& pool,
                                   cudaStream_t s, float* count_ms) {
-  const int64_t m = arcs / 2;
+  const int64_t m = arcs;  // out-lists live in CSR slots: counts and twins are indexed by arc
   uint32_t* tcnt = pool.get<uint32_t>(m);
   int32_t* twin = pool.get<int32_t>(m);
   int32_t* items = pool.get<int32_t>(n);
@@ -463,7 +487,7 @@ int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* a
   }
   if (n > 0) {
     k_item_counts<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 64), 256, 0, s>>>(
-        oo, deg, n, items);
+        odeg, deg, n, items);
     GS_LAUNCH();
   }
   GS_TRY(exclusive_scan_i32_to_i64(items, item_off, n, pool, s));
@@ -487,19 +511,19 @@ int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* a
                                                           TRI_THREADS, smem));
     if (per_sm < 1) per_sm = 1;
     k_triangles<false><<<sms * per_sm, TRI_THREADS, smem, s>>>(
-        off, adj, deg, oo, oadj, n, item_off, work, lsh_T, od_cap, tcnt, twin, status);
+        off, adj, deg, odeg, oadj, n, item_off, work, lsh_T, od_cap, tcnt, twin, status);
     GS_LAUNCH();
     {
       int small_per_sm = 1;
       GS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&small_per_sm, k_tri_small,
                                                             SW_WARPS * 32, 0));
       if (small_per_sm < 1) small_per_sm = 1;
-      k_tri_small<<<sms * small_per_sm, SW_WARPS * 32, 0, s>>>(off, adj, deg, oo, oadj, n, work + 2,
+      k_tri_small<<<sms * small_per_sm, SW_WARPS * 32, 0, s>>>(off, adj, deg, odeg, oadj, n, work + 2,
                                                                lsh_T, tcnt, twin, status);
       GS_LAUNCH();
     }
     if (max_od > SMEM_OD_MAX) {
-      k_triangles<true><<<sms * 4, TRI_THREADS, 0, s>>>(off, adj, deg, oo, oadj, n, item_off,
+      k_triangles<true><<<sms * 4, TRI_THREADS, 0, s>>>(off, adj, deg, odeg, oadj, n, item_off,
                                                         work + 1, lsh_T, 0, tcnt, twin, status);
       GS_LAUNCH();
     }
@@ -507,7 +531,7 @@ int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* a
   GS_CUDA(cudaEventRecord(e1, s));
   if (n > 0 && m > 0) {
     k_expand<<<(unsigned)std::min<int64_t>((n + 7) / 8, 152 * 64), 256, 0, s>>>(
-        kind, off, deg, oo, oadj, opos, tcnt, twin, n, lsh_T, sim_csr, status);
+        kind, off, deg, odeg, oadj, opos, tcnt, twin, n, lsh_T, sim_csr, status);
     GS_LAUNCH();
   }
   if (count_ms) {
