@@ -34,7 +34,7 @@ typedef struct scan_server scan_server;
 
 typedef struct scan_serve_params {
   size_t memory_budget_bytes; /* device bytes builds may use (0 = no limit) */
-  int max_batch;              /* queries per batch (1 = one launch per query) */
+  int max_batch;              /* queries per batch (1 = one launch per query; 0 = 64) */
   int max_pending;            /* queued requests before submit returns SCAN_EBUSY (0 = 1<<20) */
   int device;                 /* CUDA device ordinal */
 } scan_serve_params;

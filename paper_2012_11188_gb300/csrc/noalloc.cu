@@ -16,10 +16,10 @@ namespace {
 
 // scratch layout, in int32 words:
 //   [0, NOALLOC_MAX_N)            parents
-//   NOALLOC_MAX_N + 0 .. +1       core count (int64)
-//   NOALLOC_MAX_N + 2             mu (int32)
-//   NOALLOC_MAX_N + 4 .. +5       eps (double)
-//   NOALLOC_MAX_N + 6             status word
+//   NOALLOC_MAX_N + 0 .. +5       core count and its prefix sums (3 x int64)
+//   NOALLOC_MAX_N + 6             mu (int32)
+//   NOALLOC_MAX_N + 8 .. +9       eps (double)
+//   NOALLOC_MAX_N + 10            status word
 constexpr int64_t NOALLOC_MAX_N = (int64_t)1 << 22;
 constexpr int64_t NOALLOC_WORDS = NOALLOC_MAX_N + 64;
 
@@ -59,9 +59,9 @@ extern "C" int scan_query_noalloc(scan_index* index, int mu, double eps, int32_t
   cudaStream_t s = (cudaStream_t)stream;
   int32_t* parent = base;
   int64_t* ncores = (int64_t*)(base + NOALLOC_MAX_N);
-  int* mu_dev = (int*)(base + NOALLOC_MAX_N + 2);
-  double* eps_dev = (double*)(base + NOALLOC_MAX_N + 4);
-  unsigned* status = (unsigned*)(base + NOALLOC_MAX_N + 6);
+  int* mu_dev = (int*)(base + NOALLOC_MAX_N + 6);
+  double* eps_dev = (double*)(base + NOALLOC_MAX_N + 8);
+  unsigned* status = (unsigned*)(base + NOALLOC_MAX_N + 10);
   // the scratch keeps the previous call's contents: reset what must start clear
   GS_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned), s));
   GS_CUDA(cudaMemcpyAsync(mu_dev, &mu, sizeof(int), cudaMemcpyHostToDevice, s));

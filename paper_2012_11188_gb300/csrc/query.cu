@@ -78,10 +78,42 @@ struct QArgs {
   const int* mu;       // Q
   const double* eps;   // Q
   int64_t* ncores;     // Q
+  int64_t* ncp;        // Q+1: exclusive prefix of ncores (flattened (query, core) items)
+  int Q;
   int32_t* parent;     // Q * n (-1 = not a core)
-  int32_t* labels;     // Q * n
+  int32_t* labels;     // Q * n, used when lab_ptrs is null
+  int32_t* const* lab_ptrs;  // Q destinations (device), or null
   unsigned* status;
 };
+
+__device__ __forceinline__ int32_t* labels_of(const QArgs& a, int q) {
+  return a.lab_ptrs ? a.lab_ptrs[q] : a.labels + (int64_t)q * a.n;
+}
+
+__global__ void k_init_labels(QArgs a) {
+  int32_t* lab = labels_of(a, blockIdx.y);
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < a.n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    lab[v] = -1;
+}
+
+// item i of the flattened (query, core) list -> query q, core index i - ncp[q]
+__device__ __forceinline__ int item_query(const QArgs& a, int64_t i) {
+  int lo = 0, hi = a.Q;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (a.ncp[mid] <= i) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void k_core_prefix(QArgs a) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    int64_t acc = 0;
+    for (int q = 0; q < a.Q; ++q) { a.ncp[q] = acc; acc += a.ncores[q]; }
+    a.ncp[a.Q] = acc;
+  }
+}
 
 __global__ void k_get_cores(QArgs a, int Q) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
@@ -96,32 +128,27 @@ __global__ void k_get_cores(QArgs a, int Q) {
 }
 
 __global__ void k_mark_cores(QArgs a) {
-  const int q = blockIdx.y;
-  const int64_t nc = a.ncores[q];
-  if (nc == 0) return;
-  const int64_t b = a.co_off[a.mu[q] - 2];
-  int32_t* parent = a.parent + (int64_t)q * a.n;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nc;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t v = a.co_id[b + i];
-    parent[v] = v;
+  const int64_t total = a.ncp[a.Q];
+  for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < total;
+       it += (int64_t)gridDim.x * blockDim.x) {
+    const int q = item_query(a, it);
+    const int32_t v = a.co_id[a.co_off[a.mu[q] - 2] + (it - a.ncp[q])];
+    a.parent[(int64_t)q * a.n + v] = v;
   }
 }
 
-// warp per core
+// warp per (query, core) item
 __global__ void k_union(QArgs a) {
-  const int q = blockIdx.y;
-  const int64_t nc = a.ncores[q];
-  if (nc == 0) return;
   const int lane = threadIdx.x & 31;
   const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int64_t cb = a.co_off[a.mu[q] - 2];
-  const double eps = a.eps[q];
-  int32_t* parent = a.parent + (int64_t)q * a.n;
+  const int64_t total = a.ncp[a.Q];
   bool fail = false;
-  for (int64_t i = w0; i < nc; i += nw) {
-    const int32_t u = a.co_id[cb + i];
+  for (int64_t it = w0; it < total; it += nw) {
+    const int q = item_query(a, it);
+    const double eps = a.eps[q];
+    int32_t* parent = a.parent + (int64_t)q * a.n;
+    const int32_t u = a.co_id[a.co_off[a.mu[q] - 2] + (it - a.ncp[q])];
     const int64_t rb = a.off[u];
     const int64_t pu = prefix_ge(a.no_sim + rb, a.deg[u], eps);
     for (int64_t j = lane; j < pu; j += 32) {
@@ -134,16 +161,12 @@ __global__ void k_union(QArgs a) {
 
 // labels of the cores: their union-find root (the smallest id of the cluster)
 __global__ void k_core_labels(QArgs a) {
-  const int q = blockIdx.y;
-  const int64_t nc = a.ncores[q];
-  if (nc == 0) return;
-  const int64_t cb = a.co_off[a.mu[q] - 2];
-  int32_t* parent = a.parent + (int64_t)q * a.n;
-  int32_t* lab = a.labels + (int64_t)q * a.n;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nc;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t u = a.co_id[cb + i];
-    lab[u] = uf_find(parent, u);
+  const int64_t total = a.ncp[a.Q];
+  for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < total;
+       it += (int64_t)gridDim.x * blockDim.x) {
+    const int q = item_query(a, it);
+    const int32_t u = a.co_id[a.co_off[a.mu[q] - 2] + (it - a.ncp[q])];
+    labels_of(a, q)[u] = uf_find(a.parent + (int64_t)q * a.n, u);
   }
 }
 
@@ -154,18 +177,16 @@ constexpr int32_t CLAIMED = -3;
 // (most similar, smallest id on ties); sigma is symmetric, so that prefix
 // holds at least this core.
 __global__ void k_borders(QArgs a) {
-  const int q = blockIdx.y;
-  const int64_t nc = a.ncores[q];
-  if (nc == 0) return;
   const int lane = threadIdx.x & 31;
   const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int64_t cb = a.co_off[a.mu[q] - 2];
-  const double eps = a.eps[q];
-  int32_t* parent = a.parent + (int64_t)q * a.n;
-  int32_t* lab = a.labels + (int64_t)q * a.n;
-  for (int64_t i = w0; i < nc; i += nw) {
-    const int32_t u = a.co_id[cb + i];
+  const int64_t total = a.ncp[a.Q];
+  for (int64_t it = w0; it < total; it += nw) {
+    const int q = item_query(a, it);
+    const double eps = a.eps[q];
+    int32_t* parent = a.parent + (int64_t)q * a.n;
+    int32_t* lab = labels_of(a, q);
+    const int32_t u = a.co_id[a.co_off[a.mu[q] - 2] + (it - a.ncp[q])];
     const int64_t rb = a.off[u];
     const int64_t pu = prefix_ge(a.no_sim + rb, a.deg[u], eps);
     for (int64_t j = lane; j < pu; j += 32) {
@@ -187,7 +208,7 @@ __global__ void k_borders(QArgs a) {
 // warp per unclustered vertex
 __global__ void k_hubs(QArgs a) {
   const int q = blockIdx.y;
-  int32_t* lab = a.labels + (int64_t)q * a.n;
+  int32_t* lab = labels_of(a, q);
   const int lane = threadIdx.x & 31;
   const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -213,38 +234,56 @@ __global__ void k_hubs(QArgs a) {
 
 }  // namespace
 
+// Launch sequence of a batch of Q queries; every pointer is device memory.
+int launch_query_batch(const IndexData& ix, int Q, const int* mu, const double* eps, int64_t* nc,
+                       int32_t* parent, int32_t* labels, int32_t* const* lab_ptrs, int flags,
+                       cudaStream_t s, unsigned* status_dev) {
+  const int64_t n = ix.n;
+  GS_CUDA(cudaMemsetAsync(parent, 0xff, sizeof(int32_t) * (size_t)Q * n, s));
+  // nc holds 2Q+1 words: Q core counts, then their Q+1 prefix sums
+  QArgs a{ix.off, ix.deg, ix.adj, ix.no_id, ix.no_sim, ix.co_off, ix.co_id, ix.co_thr,
+          n, ix.maxdeg, mu, eps, nc, nc + Q, Q, parent, labels, lab_ptrs, status_dev};
+  const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8 / std::min(Q, 8) + 1));
+  const unsigned gw = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 7) / 8, 152 * 16 / std::min(Q, 16) + 1));
+  if (lab_ptrs) {
+    k_init_labels<<<dim3(gx, Q), 256, 0, s>>>(a);
+    GS_LAUNCH();
+  } else {
+    GS_CUDA(cudaMemsetAsync(labels, 0xff, sizeof(int32_t) * (size_t)Q * n, s));
+  }
+  k_get_cores<<<(Q + 127) / 128, 128, 0, s>>>(a, Q);
+  GS_LAUNCH();
+  k_core_prefix<<<1, 32, 0, s>>>(a);
+  GS_LAUNCH();
+  // the (query, core) items of the whole batch share one grid
+  k_mark_cores<<<152 * 8, 256, 0, s>>>(a);
+  GS_LAUNCH();
+  k_union<<<152 * 16, 256, 0, s>>>(a);
+  GS_LAUNCH();
+  k_core_labels<<<152 * 8, 256, 0, s>>>(a);
+  GS_LAUNCH();
+  k_borders<<<152 * 16, 256, 0, s>>>(a);
+  GS_LAUNCH();
+  if (flags & SCAN_Q_HUBS) {
+    k_hubs<<<dim3(gw, Q), 256, 0, s>>>(a);
+    GS_LAUNCH();
+  }
+  return SCAN_OK;
+}
+
 int run_queries(const IndexData& ix, int Q, const int* mu_host, const double* eps_host,
                 int32_t* labels_dev, int flags, Pool& pool, cudaStream_t s, unsigned* status_dev) {
   if (Q <= 0) return SCAN_OK;
   const int64_t n = ix.n;
   int* mu = pool.get<int>(Q);
   double* eps = pool.get<double>(Q);
-  int64_t* nc = pool.get<int64_t>(Q);
+  int64_t* nc = pool.get<int64_t>(2 * (size_t)Q + 1);
   int32_t* parent = pool.get<int32_t>((size_t)Q * (size_t)(n > 0 ? n : 1));
   if (!mu || !eps || !nc || !parent) return SCAN_ENOMEM;
   GS_CUDA(cudaMemcpyAsync(mu, mu_host, sizeof(int) * Q, cudaMemcpyHostToDevice, s));
   GS_CUDA(cudaMemcpyAsync(eps, eps_host, sizeof(double) * Q, cudaMemcpyHostToDevice, s));
   if (n == 0) return SCAN_OK;
-  GS_CUDA(cudaMemsetAsync(parent, 0xff, sizeof(int32_t) * (size_t)Q * n, s));
-  GS_CUDA(cudaMemsetAsync(labels_dev, 0xff, sizeof(int32_t) * (size_t)Q * n, s));
-  QArgs a{ix.off, ix.deg, ix.adj, ix.no_id, ix.no_sim, ix.co_off, ix.co_id, ix.co_thr,
-          n, ix.maxdeg, mu, eps, nc, parent, labels_dev, status_dev};
-  k_get_cores<<<(Q + 127) / 128, 128, 0, s>>>(a, Q);
-  GS_LAUNCH();
-  const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8 / std::min(Q, 8) + 1));
-  k_mark_cores<<<dim3(gx, Q), 256, 0, s>>>(a);
-  GS_LAUNCH();
-  const unsigned gw = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 7) / 8, 152 * 16 / std::min(Q, 16) + 1));
-  k_union<<<dim3(gw, Q), 256, 0, s>>>(a);
-  GS_LAUNCH();
-  k_core_labels<<<dim3(gx, Q), 256, 0, s>>>(a);
-  GS_LAUNCH();
-  k_borders<<<dim3(gw, Q), 256, 0, s>>>(a);
-  GS_LAUNCH();
-  if (flags & SCAN_Q_HUBS) {
-    k_hubs<<<dim3(gw, Q), 256, 0, s>>>(a);
-    GS_LAUNCH();
-  }
+  GS_TRY(launch_query_batch(ix, Q, mu, eps, nc, parent, labels_dev, nullptr, flags, s, status_dev));
   pool.put(mu);
   pool.put(eps);
   pool.put(nc);
@@ -259,28 +298,8 @@ int run_queries_prealloc(const IndexData& ix, int Q, const int* mu_dev, const do
                          int64_t* nc_dev, int32_t* parent, int32_t* labels_dev, int flags,
                          cudaStream_t s, unsigned* status_dev) {
   if (Q <= 0 || ix.n == 0) return SCAN_OK;
-  const int64_t n = ix.n;
-  GS_CUDA(cudaMemsetAsync(parent, 0xff, sizeof(int32_t) * (size_t)Q * n, s));
-  GS_CUDA(cudaMemsetAsync(labels_dev, 0xff, sizeof(int32_t) * (size_t)Q * n, s));
-  QArgs a{ix.off, ix.deg, ix.adj, ix.no_id, ix.no_sim, ix.co_off, ix.co_id, ix.co_thr,
-          n, ix.maxdeg, mu_dev, eps_dev, nc_dev, parent, labels_dev, status_dev};
-  k_get_cores<<<(Q + 127) / 128, 128, 0, s>>>(a, Q);
-  GS_LAUNCH();
-  const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8));
-  k_mark_cores<<<dim3(gx, Q), 256, 0, s>>>(a);
-  GS_LAUNCH();
-  const unsigned gw = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 7) / 8, 152 * 16));
-  k_union<<<dim3(gw, Q), 256, 0, s>>>(a);
-  GS_LAUNCH();
-  k_core_labels<<<dim3(gx, Q), 256, 0, s>>>(a);
-  GS_LAUNCH();
-  k_borders<<<dim3(gw, Q), 256, 0, s>>>(a);
-  GS_LAUNCH();
-  if (flags & SCAN_Q_HUBS) {
-    k_hubs<<<dim3(gw, Q), 256, 0, s>>>(a);
-    GS_LAUNCH();
-  }
-  return SCAN_OK;
+  return launch_query_batch(ix, Q, mu_dev, eps_dev, nc_dev, parent, labels_dev, nullptr, flags, s,
+                            status_dev);
 }
 
 }  // namespace gscan

@@ -155,8 +155,15 @@ int build_core_order_multi(int64_t N, int64_t A, const int64_t* off, const int32
 int run_queries(const IndexData& ix, int q, const int* mu, const double* eps, int32_t* labels_dev,
                 int flags, Pool& pool, cudaStream_t s, unsigned* status_dev);
 
-// run_queries with caller-supplied device scratch: mu_dev/eps_dev/nc_dev hold
-// Q entries, parent Q*n; nothing is allocated.
+// Launch sequence of a batch of Q queries on device arrays: mu/eps hold Q
+// entries, nc 2Q+1 (core counts and their prefix sums), parent Q*n; labels either Q*n contiguous (lab_ptrs null) or Q
+// device destinations listed in lab_ptrs.
+int launch_query_batch(const IndexData& ix, int Q, const int* mu, const double* eps, int64_t* nc,
+                       int32_t* parent, int32_t* labels, int32_t* const* lab_ptrs, int flags,
+                       cudaStream_t s, unsigned* status_dev);
+
+// run_queries with caller-supplied device scratch: mu_dev/eps_dev hold Q
+// entries, nc_dev 2Q+1, parent Q*n; nothing is allocated.
 int run_queries_prealloc(const IndexData& ix, int Q, const int* mu_dev, const double* eps_dev,
                          int64_t* nc_dev, int32_t* parent, int32_t* labels_dev, int flags,
                          cudaStream_t s, unsigned* status_dev);

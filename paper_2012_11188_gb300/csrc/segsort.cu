@@ -8,18 +8,20 @@
 // does not depend on stability: equal similarities come out in ascending id,
 // the tie rule of the paper's deterministic experiments.
 //
-// Segments are bucketed by length: <= 32 (one warp, registers and shuffles),
-// <= 256 / 1024 / 4096 (one CTA, bitonic network in shared memory), longer
-// (4096-element tiles sorted by CTAs, then merge-path passes that double the
-// run length, ping-ponging between the data and a scratch buffer).
+// Segments are bucketed by length: <= 32 (one warp, one element per lane),
+// <= 256 (one warp, bitonic network on up to 8 elements per lane in
+// registers), longer (256-element tiles sorted the same way, then merge-path
+// passes that double the run length, ping-ponging between the data and a
+// scratch buffer; a pass costs about one read and one write of the data).
 #include "scan_internal.cuh"
 
 namespace gscan {
 
 namespace {
 
-constexpr int TILE = 4096;
-constexpr int NCLASS = 5;  // <=32, <=256, <=1024, <=4096, >4096
+constexpr int WTILE = 256;   // one warp sorts up to this many elements in registers
+constexpr int TILE = 4096;   // one CTA sorts a tile of this many (16 warp sorts + 4 merges)
+constexpr int NCLASS = 5;    // <=32, <=256, <=1024, <=4096, >4096
 
 struct KV {
   uint64_t k;
@@ -34,7 +36,7 @@ __device__ __forceinline__ bool before(uint64_t ka, int32_t va, uint64_t kb, int
 constexpr int32_t SENT_V = 0x7fffffff;  // sorts after every real element (key 0, val max)
 
 __device__ __forceinline__ int seg_class(int64_t len) {
-  return len <= 32 ? 0 : len <= 256 ? 1 : len <= 1024 ? 2 : len <= TILE ? 3 : 4;
+  return len <= 32 ? 0 : len <= WTILE ? 1 : len <= 1024 ? 2 : len <= TILE ? 3 : 4;
 }
 
 // Count segments per class and number of tiles of long segments.
@@ -102,18 +104,124 @@ __global__ void k_sort_warp(uint64_t* __restrict__ key, int32_t* __restrict__ va
   }
 }
 
-// One CTA sorts up to S elements in shared memory with a bitonic network.
-// Work unit u: segment list[u] (TILED = false) or tile u of the long segments
-// (TILED = true; tile_seg/tile_first map a tile to its segment and offset).
-template <int S, int T, bool TILED>
-__global__ void __launch_bounds__(T)
-k_sort_block(uint64_t* __restrict__ key, int32_t* __restrict__ val,
-             const int64_t* __restrict__ seg_off, const int64_t* __restrict__ list,
-             const unsigned long long* __restrict__ count_ptr,
-             const int64_t* __restrict__ tile_prefix /* TILED: tiles before long segment i */,
-             int64_t nlong) {
-  __shared__ uint64_t sk[S];
-  __shared__ int32_t sv[S];
+// Warp-level bitonic sort of 32*RI elements held in registers, blocked: lane l
+// holds elements RI*l .. RI*l+RI-1. Strides below RI compare inside a thread,
+// larger ones exchange with lane l ^ (stride/RI) by shuffles; no shared memory
+// and no barrier, so every warp sorts its own segment or tile.
+template <int J, int RI>
+__device__ __forceinline__ void reg_stage(uint64_t (&K)[RI], int32_t (&V)[RI], int lane, int k) {
+#pragma unroll
+  for (int r = 0; r < RI; ++r) {
+    const int rp = r ^ J;
+    if (rp > r) {
+      const bool asc = ((RI * lane + r) & k) == 0;  // r is the lower index of the pair
+      const bool swap = asc ? before(K[rp], V[rp], K[r], V[r]) : before(K[r], V[r], K[rp], V[rp]);
+      if (swap) {
+        const uint64_t tk = K[r]; K[r] = K[rp]; K[rp] = tk;
+        const int32_t tv = V[r]; V[r] = V[rp]; V[rp] = tv;
+      }
+    }
+  }
+}
+
+template <int RI>
+__device__ __forceinline__ void warp_sort_reg(uint64_t (&K)[RI], int32_t (&V)[RI], int lane) {
+  constexpr int S = 32 * RI;
+#pragma unroll
+  for (int k = 2; k <= S; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j >= RI) {
+#pragma unroll
+        for (int r = 0; r < RI; ++r) {
+          const uint64_t pk = __shfl_xor_sync(0xffffffffu, K[r], j / RI);
+          const int32_t pv = __shfl_xor_sync(0xffffffffu, V[r], j / RI);
+          const int i = RI * lane + r;
+          const bool asc = (i & k) == 0, low = (i & j) == 0;
+          const bool partner_first = before(pk, pv, K[r], V[r]);
+          if (partner_first == (low == asc)) { K[r] = pk; V[r] = pv; }
+        }
+      } else if (j == 4) {
+        if constexpr (RI > 4) reg_stage<4, RI>(K, V, lane, k);
+      } else if (j == 2) {
+        if constexpr (RI > 2) reg_stage<2, RI>(K, V, lane, k);
+      } else {
+        if constexpr (RI > 1) reg_stage<1, RI>(K, V, lane, k);
+      }
+    }
+  }
+}
+
+template <int RI>
+__device__ __forceinline__ void warp_sort_range(uint64_t* __restrict__ key, int32_t* __restrict__ val,
+                                                int64_t b, int64_t len, int lane) {
+  uint64_t K[RI];
+  int32_t V[RI];
+#pragma unroll
+  for (int r = 0; r < RI; ++r) {
+    const int64_t i = RI * lane + r;
+    if (i < len) { K[r] = key[b + i]; V[r] = val[b + i]; }
+    else { K[r] = 0; V[r] = SENT_V; }
+  }
+  warp_sort_reg<RI>(K, V, lane);
+#pragma unroll
+  for (int r = 0; r < RI; ++r) {
+    const int64_t i = RI * lane + r;
+    if (i < len) { key[b + i] = K[r]; val[b + i] = V[r]; }
+  }
+}
+
+
+// One warp per segment of 33..256 elements, sorted at the next power of two.
+__global__ void __launch_bounds__(256, 4)
+k_sort_warp_reg(uint64_t* __restrict__ key, int32_t* __restrict__ val,
+                const int64_t* __restrict__ seg_off, const int64_t* __restrict__ list,
+                const unsigned long long* __restrict__ count_ptr) {
+  const int lane = threadIdx.x & 31;
+  const int64_t cnt = (int64_t)*count_ptr;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t u = w0; u < cnt; u += nw) {
+    const int64_t sg = list[u];
+    const int64_t b = seg_off[sg];
+    const int64_t len = seg_off[sg + 1] - b;
+    if (len <= 64) warp_sort_range<2>(key, val, b, len, lane);
+    else if (len <= 128) warp_sort_range<4>(key, val, b, len, lane);
+    else warp_sort_range<8>(key, val, b, len, lane);
+  }
+}
+
+// Merge path inside shared memory: elements of A (length la) among the first
+// d outputs of merge(A, B).
+__device__ __forceinline__ int smem_merge_path(const uint64_t* ka, const int32_t* va, int la,
+                                               const uint64_t* kb, const int32_t* vb, int lb, int d) {
+  int lo = max(0, d - lb), hi = min(d, la);
+  while (lo < hi) {
+    const int i = (lo + hi) >> 1;
+    if (before(kb[d - 1 - i], vb[d - 1 - i], ka[i], va[i])) hi = i;
+    else lo = i + 1;
+  }
+  return lo;
+}
+
+// One CTA of TT threads sorts a tile of up to TT*8 elements at the next power
+// of two SE >= max(len, 256): SE/256 warps sort 256 elements each in
+// registers, then merge-path levels in shared memory double the runs up to
+// SE, each thread writing 8 outputs. Tiles are whole segments (TILED = false)
+// or TILE-element pieces of longer segments (TILED = true, TT*8 = TILE).
+template <int TT, bool TILED>
+__global__ void __launch_bounds__(TT)
+k_sort_tile(uint64_t* __restrict__ key, int32_t* __restrict__ val,
+            const int64_t* __restrict__ seg_off, const int64_t* __restrict__ list,
+            const unsigned long long* __restrict__ count_ptr,
+            const int64_t* __restrict__ tile_prefix, int64_t nlong) {
+  constexpr int CAP = TT * 8;
+  extern __shared__ uint64_t tsm[];
+  uint64_t* k0 = tsm;
+  uint64_t* k1 = tsm + CAP;
+  int32_t* v0 = (int32_t*)(tsm + 2 * CAP);
+  int32_t* v1 = v0 + CAP;
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   const int64_t cnt = (int64_t)*count_ptr;
   for (int64_t u = blockIdx.x; u < cnt; u += gridDim.x) {
     int64_t b, len;
@@ -122,47 +230,72 @@ k_sort_block(uint64_t* __restrict__ key, int32_t* __restrict__ val,
       b = seg_off[sg];
       len = seg_off[sg + 1] - b;
     } else {
-      // find long segment i with tile_prefix[i] <= u < tile_prefix[i+1]
       int64_t lo = 0, hi = nlong;
       while (hi - lo > 1) {
         const int64_t mid = (lo + hi) >> 1;
         if (tile_prefix[mid] <= u) lo = mid; else hi = mid;
       }
       const int64_t sg = list[lo];
-      const int64_t t = u - tile_prefix[lo];
-      const int64_t sb = seg_off[sg], se = seg_off[sg + 1];
-      b = sb + t * S;
-      len = min((int64_t)S, se - b);
+      b = seg_off[sg] + (u - tile_prefix[lo]) * CAP;
+      len = min((int64_t)CAP, seg_off[sg + 1] - b);
     }
-    // sort only the next power of two at or above the length
-    int se = 2;
+    int se = WTILE;
     while (se < len) se <<= 1;
-    for (int i = threadIdx.x; i < se; i += T) {
-      if (i < len) { sk[i] = key[b + i]; sv[i] = val[b + i]; }
-      else { sk[i] = 0; sv[i] = SENT_V; }
-    }
-    __syncthreads();
-    for (int size = 2; size <= se; size <<= 1) {
-      for (int stride = size >> 1; stride > 0; stride >>= 1) {
-        for (int t = threadIdx.x; t < se / 2; t += T) {
-          // pair (i, i + stride) with i having bit `stride` clear
-          const int i = 2 * t - (t & (stride - 1));
-          const int j = i + stride;
-          const bool ascending = (i & size) == 0;
-          const uint64_t ki = sk[i], kj = sk[j];
-          const int32_t vi = sv[i], vj = sv[j];
-          const bool j_first = before(kj, vj, ki, vi);
-          if (j_first == ascending) {
-            sk[i] = kj; sk[j] = ki;
-            sv[i] = vj; sv[j] = vi;
-          }
-        }
-        __syncthreads();
+    // 1. the first se/256 warps sort 256 elements each in registers
+    if (wid * WTILE < se) {
+      uint64_t K[8];
+      int32_t V[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int64_t i = (int64_t)wid * WTILE + 8 * lane + r;
+        if (i < len) { K[r] = key[b + i]; V[r] = val[b + i]; }
+        else { K[r] = 0; V[r] = SENT_V; }
+      }
+      warp_sort_reg<8>(K, V, lane);
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int i = wid * WTILE + 8 * lane + r;
+        k0[i] = K[r];
+        v0[i] = V[r];
       }
     }
-    for (int i = threadIdx.x; i < len; i += T) { key[b + i] = sk[i]; val[b + i] = sv[i]; }
+    __syncthreads();
+    // 2. merge levels in shared memory: runs of w -> 2w, ping-pong k0/v0 <-> k1/v1
+    uint64_t *ks = k0, *kd = k1;
+    int32_t *vs = v0, *vd = v1;
+    for (int w = WTILE; w < se; w <<= 1) {
+      const int o = 8 * t;  // first output of this thread
+      if (o < se) {
+        const int p0 = (o / (2 * w)) * (2 * w);
+        const uint64_t* KA = ks + p0;
+        const int32_t* VA = vs + p0;
+        const uint64_t* KB = ks + p0 + w;
+        const int32_t* VB = vs + p0 + w;
+        const int d = o - p0;
+        int ia = smem_merge_path(KA, VA, w, KB, VB, w, d);
+        int ib = d - ia;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          bool take_a;
+          if (ia >= w) take_a = false;
+          else if (ib >= w) take_a = true;
+          else take_a = !before(KB[ib], VB[ib], KA[ia], VA[ia]);
+          if (take_a) { kd[o + q] = KA[ia]; vd[o + q] = VA[ia]; ++ia; }
+          else { kd[o + q] = KB[ib]; vd[o + q] = VB[ib]; ++ib; }
+        }
+      }
+      __syncthreads();
+      uint64_t* tk = ks; ks = kd; kd = tk;
+      int32_t* tv = vs; vs = vd; vd = tv;
+    }
+    for (int i = t; i < len; i += TT) { key[b + i] = ks[i]; val[b + i] = vs[i]; }
     __syncthreads();
   }
+}
+
+template <int TT>
+constexpr size_t tile_smem_bytes() {
+  return (size_t)TT * 8 * (2 * sizeof(uint64_t) + 2 * sizeof(int32_t));
 }
 
 // Tiles per long segment (prefix computed by the caller).
@@ -181,7 +314,7 @@ __global__ void k_long_tiles(const int64_t* __restrict__ seg_off, const int64_t*
 }
 
 constexpr int MERGE_T = 256;
-constexpr int MERGE_ITEMS = 4;
+constexpr int MERGE_ITEMS = 4;  // MERGE_CHUNK = 1024 divides 2 * TILE
 constexpr int MERGE_CHUNK = MERGE_T * MERGE_ITEMS;  // output elements per CTA per pass
 
 // Number of elements of A (length la) among the first d of merge(A, B).
@@ -377,17 +510,21 @@ int segmented_sort_desc(uint64_t* key, int32_t* val, const int64_t* seg_off, int
     GS_LAUNCH();
   }
   if (hc[1]) {
-    k_sort_block<256, 128, false><<<grid_of((int64_t)hc[1], 1), 128, 0, s>>>(
-        key, val, seg_off, list + base[1], counts + 1, nullptr, 0);
+    k_sort_warp_reg<<<grid_of((int64_t)hc[1], 8), 256, 0, s>>>(key, val, seg_off, list + base[1],
+                                                                counts + 1);
     GS_LAUNCH();
   }
+  GS_CUDA(cudaFuncSetAttribute(k_sort_tile<512, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)tile_smem_bytes<512>()));
+  GS_CUDA(cudaFuncSetAttribute(k_sort_tile<512, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)tile_smem_bytes<512>()));
   if (hc[2]) {
-    k_sort_block<1024, 256, false><<<grid_of((int64_t)hc[2], 1), 256, 0, s>>>(
+    k_sort_tile<128, false><<<grid_of((int64_t)hc[2], 1), 128, tile_smem_bytes<128>(), s>>>(
         key, val, seg_off, list + base[2], counts + 2, nullptr, 0);
     GS_LAUNCH();
   }
   if (hc[3]) {
-    k_sort_block<TILE, 512, false><<<grid_of((int64_t)hc[3], 1), 512, 0, s>>>(
+    k_sort_tile<512, false><<<grid_of((int64_t)hc[3], 1), 512, tile_smem_bytes<512>(), s>>>(
         key, val, seg_off, list + base[3], counts + 3, nullptr, 0);
     GS_LAUNCH();
   }
@@ -408,7 +545,7 @@ int segmented_sort_desc(uint64_t* key, int32_t* val, const int64_t* seg_off, int
     GS_TRY(exclusive_scan_i64(chunks, chunk_prefix, nlong, pool, s));
     const int64_t ntiles = (int64_t)hc[NCLASS];
     // tile sort (count = ntiles, read from counts[NCLASS])
-    k_sort_block<TILE, 512, true><<<grid_of(ntiles, 1), 512, 0, s>>>(
+    k_sort_tile<512, true><<<grid_of(ntiles, 1), 512, tile_smem_bytes<512>(), s>>>(
         key, val, seg_off, llist, counts + NCLASS, tile_prefix, nlong);
     GS_LAUNCH();
     uint64_t *ck = key, *nk = tk;

@@ -2,9 +2,11 @@
 //
 // Two worker threads own two CUDA streams:
 //  - the query worker takes every query queued for one (index, flags) pair, up
-//    to max_batch, and answers them with one batched pass (run_queries: one
-//    launch per phase for the whole batch). Queries that arrive meanwhile wait
-//    in the queue and join the next batch as soon as this one completes.
+//    to max_batch (default 64), and answers them with one batched pass (one
+//    launch per phase for the whole batch, labels written straight into device
+//    destinations; host destinations go through staging rows). Its scratch is
+//    kept across batches. Queries that arrive meanwhile wait in the queue and
+//    join the next batch as soon as this one completes.
 //  - the build worker admits build requests in arrival order when their
 //    footprint fits the memory budget and the device's free memory, and builds
 //    them on its own stream, overlapping with the query batches.
@@ -82,18 +84,108 @@ void finish(scan_server* s, Request* r, int status) {
   s->cv_done.notify_all();
 }
 
+// Scratch of the query worker, kept across batches and grown on demand:
+// parents (cap x n), a device table of label destinations, mu/eps/core
+// counts, a status word, and staging rows for host destinations.
+struct QueryScratch {
+  int cap = 0;
+  int64_t n = 0;
+  int32_t* parent = nullptr;
+  int32_t** ptrs = nullptr;
+  int* mu = nullptr;
+  double* eps = nullptr;
+  int64_t* nc = nullptr;
+  unsigned* status = nullptr;
+  int32_t* staging = nullptr;
+  int staging_rows = 0;
+  std::vector<std::pair<void*, size_t>> held;  // every block, for release
+  template <class T>
+  T* get(size_t count, cudaStream_t s) {
+    const size_t b = count * sizeof(T) > 0 ? count * sizeof(T) : 16;
+    void* p = gscan::dev_alloc(b, s);
+    if (p) held.emplace_back(p, b);
+    return (T*)p;
+  }
+  void release(cudaStream_t s) {
+    for (auto& h : held) gscan::dev_free(h.first, h.second, s);
+    *this = QueryScratch();
+  }
+  int ensure(int c, int64_t nn, cudaStream_t s) {
+    if (c <= cap && nn <= n) return SCAN_OK;
+    release(s);
+    cap = c;
+    n = nn;
+    parent = get<int32_t>((size_t)c * (size_t)nn, s);
+    ptrs = get<int32_t*>(c, s);
+    mu = get<int>(c, s);
+    eps = get<double>(c, s);
+    nc = get<int64_t>(2 * (size_t)c + 1, s);
+    status = get<unsigned>(1, s);
+    if (!parent || !ptrs || !mu || !eps || !nc || !status) {
+      release(s);
+      return SCAN_ENOMEM;
+    }
+    return SCAN_OK;
+  }
+  int ensure_staging(int rows, cudaStream_t s) {
+    if (rows <= staging_rows) return SCAN_OK;
+    staging = get<int32_t>((size_t)rows * (size_t)n, s);  // the smaller one is released with the rest
+    if (!staging) return SCAN_ENOMEM;
+    staging_rows = rows;
+    return SCAN_OK;
+  }
+};
+
+int run_batch(scan_server* s, QueryScratch& qs, const std::vector<Request*>& batch) {
+  const gscan::IndexData& d = batch[0]->ix->d;
+  const int Q = (int)batch.size();
+  if (d.n == 0) return SCAN_OK;
+  GS_TRY(qs.ensure(std::max(Q, s->p.max_batch > 0 ? s->p.max_batch : 64), d.n, s->qs));
+  std::vector<int> mus(Q);
+  std::vector<double> epss(Q);
+  std::vector<int32_t*> dst(Q);
+  std::vector<int> host_rows;
+  for (int i = 0; i < Q; ++i) {
+    mus[i] = batch[i]->mu;
+    epss[i] = batch[i]->eps;
+    if (gscan::is_device_ptr(batch[i]->labels)) {
+      dst[i] = batch[i]->labels;
+    } else {
+      host_rows.push_back(i);
+      dst[i] = nullptr;
+    }
+  }
+  if (!host_rows.empty()) {
+    GS_TRY(qs.ensure_staging((int)host_rows.size(), s->qs));
+    for (size_t r = 0; r < host_rows.size(); ++r) dst[host_rows[r]] = qs.staging + r * (size_t)d.n;
+  }
+  GS_CUDA(cudaMemcpyAsync(qs.mu, mus.data(), sizeof(int) * Q, cudaMemcpyHostToDevice, s->qs));
+  GS_CUDA(cudaMemcpyAsync(qs.eps, epss.data(), sizeof(double) * Q, cudaMemcpyHostToDevice, s->qs));
+  GS_CUDA(cudaMemcpyAsync(qs.ptrs, dst.data(), sizeof(int32_t*) * Q, cudaMemcpyHostToDevice, s->qs));
+  GS_CUDA(cudaMemsetAsync(qs.status, 0, sizeof(unsigned), s->qs));
+  GS_TRY(gscan::launch_query_batch(d, Q, qs.mu, qs.eps, qs.nc, qs.parent, nullptr, qs.ptrs,
+                                   batch[0]->flags, s->qs, qs.status));
+  for (size_t r = 0; r < host_rows.size(); ++r)
+    GS_CUDA(cudaMemcpyAsync(batch[host_rows[r]]->labels, qs.staging + r * (size_t)d.n,
+                            sizeof(int32_t) * (size_t)d.n, cudaMemcpyDeviceToHost, s->qs));
+  unsigned hst = 0;
+  GS_CUDA(cudaMemcpyAsync(&hst, qs.status, sizeof(unsigned), cudaMemcpyDeviceToHost, s->qs));
+  GS_CUDA(cudaStreamSynchronize(s->qs));
+  if (hst & gscan::DEV_LIMIT) return SCAN_ETIMEOUT;
+  return SCAN_OK;
+}
+
 void query_worker(scan_server* s) {
   cudaSetDevice(s->device);
-  const int max_batch = s->p.max_batch > 0 ? s->p.max_batch : 256;
+  const int max_batch = s->p.max_batch > 0 ? s->p.max_batch : 64;
+  QueryScratch qs;
   std::vector<Request*> batch;
-  std::vector<int> mus;
-  std::vector<double> epss;
   for (;;) {
     batch.clear();
     {
       std::unique_lock<std::mutex> lk(s->mu);
       s->cv_q.wait(lk, [&] { return s->stop || !s->qq.empty(); });
-      if (s->qq.empty() && s->stop) return;
+      if (s->qq.empty() && s->stop) break;
       // everything queued for the front request's (index, flags), up to max_batch
       scan_index* ix = s->qq.front()->ix;
       const int flags = s->qq.front()->flags;
@@ -106,38 +198,12 @@ void query_worker(scan_server* s) {
         }
       }
     }
-    const gscan::IndexData& d = batch[0]->ix->d;
-    const int Q = (int)batch.size();
-    mus.resize(Q);
-    epss.resize(Q);
-    for (int i = 0; i < Q; ++i) { mus[i] = batch[i]->mu; epss[i] = batch[i]->eps; }
-    int rc = SCAN_OK;
-    {
-      gscan::Pool pool(s->qs);
-      int32_t* lab = pool.get<int32_t>((size_t)Q * (size_t)(d.n > 0 ? d.n : 1));
-      unsigned* st = pool.get<unsigned>(1);
-      if (!lab || !st) rc = SCAN_ENOMEM;
-      if (rc == SCAN_OK && cudaMemsetAsync(st, 0, sizeof(unsigned), s->qs) != cudaSuccess) rc = SCAN_ECUDA;
-      if (rc == SCAN_OK)
-        rc = gscan::run_queries(d, Q, mus.data(), epss.data(), lab, batch[0]->flags, pool, s->qs, st);
-      for (int i = 0; rc == SCAN_OK && i < Q; ++i) {
-        if (d.n == 0) break;
-        const cudaMemcpyKind k = gscan::is_device_ptr(batch[i]->labels) ? cudaMemcpyDeviceToDevice
-                                                                        : cudaMemcpyDeviceToHost;
-        if (cudaMemcpyAsync(batch[i]->labels, lab + (size_t)i * d.n, (size_t)d.n * sizeof(int32_t),
-                            k, s->qs) != cudaSuccess)
-          rc = SCAN_ECUDA;
-      }
-      unsigned hst = 0;
-      if (rc == SCAN_OK &&
-          cudaMemcpyAsync(&hst, st, sizeof(unsigned), cudaMemcpyDeviceToHost, s->qs) != cudaSuccess)
-        rc = SCAN_ECUDA;
-      if (cudaStreamSynchronize(s->qs) != cudaSuccess && rc == SCAN_OK) rc = SCAN_ECUDA;
-      if (rc == SCAN_OK && (hst & gscan::DEV_LIMIT)) rc = SCAN_ETIMEOUT;
-    }
-    cudaStreamSynchronize(s->qs);  // the pool's frees are ordered on the stream
+    const int rc = run_batch(s, qs, batch);
+    cudaStreamSynchronize(s->qs);
     for (Request* r : batch) finish(s, r, rc);
   }
+  qs.release(s->qs);
+  cudaStreamSynchronize(s->qs);
 }
 
 size_t free_device_bytes() {

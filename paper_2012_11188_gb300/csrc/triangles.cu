@@ -21,6 +21,10 @@ namespace gscan {
 
 namespace {
 
+#ifndef GS_TRI_ROUNDS
+#define GS_TRI_ROUNDS 4  // 32-element rounds of loads in flight per warp in the counting loop
+#endif
+
 constexpr int TRI_THREADS = 512;
 constexpr int TRI_WARPS = TRI_THREADS / 32;
 constexpr int CHUNK = 4096;          // CSR positions of N(v) per work item
@@ -135,7 +139,7 @@ struct SliceSmem {
 // of loads in flight); the owner of an element comes from the starts that fall
 // in its round (ballot / or-reduce / popc). A hit w adds one to (v,w) in vcnt
 // (shared; global for BIG), to (u,w) at its slot of out(u), and to (u,v).
-template <bool BIG>
+template <bool BIG, typename IT>
 __device__ __forceinline__ void process_slice(
     int64_t p0, int64_t p_end, int64_t rb, int32_t v, int32_t dv, int32_t od, int64_t ob,
     const int32_t* __restrict__ adj, const int32_t* __restrict__ deg,
@@ -165,11 +169,11 @@ __device__ __forceinline__ void process_slice(
   }
   __syncwarp();
   int32_t cu = -1, cp = 0, clen = 0;
-  int64_t cub = 0;
+  IT cub = 0;
   if (lane < k) {
     cu = sm.u[lane];
     cp = sm.p[lane];
-    cub = off[cu];
+    cub = (IT)off[cu];
     clen = odeg[cu];
   }
   if (od == 0) {
@@ -197,16 +201,16 @@ __device__ __forceinline__ void process_slice(
   sm.acc[lane] = 0;
   sm.jv[lane] = -1;
   __syncwarp();
-  constexpr int R = 4;  // rounds whose loads are issued before any probe
+  constexpr int R = GS_TRI_ROUNDS;  // rounds whose loads are issued before any probe
   // the list holding element r0 (warp-uniform); a round that lies inside one
   // list needs no owner search
   int cur = 0;
   int32_t cur_start = 0;
   int32_t cur_end = __shfl_sync(FULL, incl, 0);
-  int64_t cur_ub = __shfl_sync(FULL, cub, 0);
+  IT cur_ub = __shfl_sync(FULL, cub, 0);
   for (int32_t rbase = 0; rbase < W; rbase += 32 * R) {
     int32_t xs[R];
-    int64_t js[R];
+    IT js[R];
     int owns[R];
     bool single[R];
 #pragma unroll
@@ -222,7 +226,7 @@ __device__ __forceinline__ void process_slice(
       if (r0 + 32 <= cur_end) {
         single[rr] = true;
         owns[rr] = cur;
-        js[rr] = cur_ub + (t - cur_start);
+        js[rr] = cur_ub + (IT)(t - cur_start);
       } else {
         single[rr] = false;
         // every list is non-empty (v is in out(u)), so the starts are distinct
@@ -231,17 +235,17 @@ __device__ __forceinline__ void process_slice(
         const int before = __popc(__ballot_sync(FULL, lane < k && cstart < r0));
         const int owner = before + __popc(smask & ((2u << lane) - 1u)) - 1;
         const int own = owner < 0 ? 0 : owner;
-        const int64_t ub_o = __shfl_sync(FULL, cub, own);
+        const IT ub_o = __shfl_sync(FULL, cub, own);
         const int32_t st_o = __shfl_sync(FULL, cstart, own);
         owns[rr] = own;
-        js[rr] = t < W ? ub_o + (t - st_o) : -1;
+        js[rr] = t < W ? ub_o + (IT)(t - st_o) : (IT)-1;
       }
       xs[rr] = js[rr] >= 0 ? oadj[js[rr]] : -1;
     }
 #pragma unroll
     for (int rr = 0; rr < R; ++rr) {
       const int32_t x = xs[rr];
-      const int64_t j = js[rr];
+      const IT j = js[rr];
       const int own = owns[rr];
       bool hit = false;
       if (j >= 0) {
@@ -283,7 +287,7 @@ __device__ __forceinline__ void process_slice(
 // CTA kernel for rows longer than SMALL_DEG: the CTA shares out(v)'s table and
 // its warps pull 32-position slices of the item's CSR range.
 // BIG = out(v) too long for the shared table (binary search, global counters).
-template <bool BIG>
+template <bool BIG, typename IT>
 __global__ void __launch_bounds__(TRI_THREADS, 3)
 k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
             const int32_t* __restrict__ deg, const int32_t* __restrict__ odeg,
@@ -291,7 +295,7 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
             unsigned long long* __restrict__ work, int lsh_T, int od_cap,
             uint32_t* __restrict__ tcnt, int32_t* __restrict__ twin_rel, unsigned* status) {
   // shared layout for od_cap (a power of two >= every od handled here):
-  // filter[FILTER_WORDS] | hkey[2*od_cap] int32 | vcnt[od_cap] uint32 | hpos[2*od_cap] uint16
+  // filter[FILTER_WORDS] | hkey[4*od_cap] int32 | vcnt[od_cap] uint32 | hpos[4*od_cap] uint16
   extern __shared__ int32_t smem[];
   __shared__ long long s_item;
   __shared__ int s_next;  // next 32-position slice of the item's CSR range
@@ -304,8 +308,8 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
   const int64_t total = item_off[n];
   uint32_t* filt = (uint32_t*)smem;
   int32_t* hkey = smem + FILTER_WORDS;
-  uint32_t* vcnt = (uint32_t*)(smem + FILTER_WORDS + 2 * od_cap);
-  uint16_t* hpos = (uint16_t*)(smem + FILTER_WORDS + 3 * od_cap);
+  uint32_t* vcnt = (uint32_t*)(smem + FILTER_WORDS + 4 * od_cap);
+  uint16_t* hpos = (uint16_t*)(smem + FILTER_WORDS + 5 * od_cap);
   const SliceSmem sm{s_u[wid], s_p[wid], s_acc[wid], s_jv[wid]};
   unsigned bad = 0;
 
@@ -326,7 +330,7 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
     if (skip_item) { __syncthreads(); continue; }
     int log2h = 5;
     if (!BIG && od > 0) {
-      while ((1 << log2h) < 2 * od) ++log2h;
+      while ((1 << log2h) < 4 * od) ++log2h;  // load factor <= 1/4: short probes
       const int H = 1 << log2h;
       for (int i = threadIdx.x; i < H; i += TRI_THREADS) hkey[i] = -1;
       for (int i = threadIdx.x; i < od; i += TRI_THREADS) vcnt[i] = 0;
@@ -346,7 +350,7 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
       slice = __shfl_sync(FULL, slice, 0);
       const int64_t p0 = p_begin + slice;
       if (p0 >= p_end) break;
-      process_slice<BIG>(p0, p_end, rb, (int32_t)v, dv, od, ob, adj, deg, off, odeg, oadj, lsh_T, tab,
+      process_slice<BIG, IT>(p0, p_end, rb, (int32_t)v, dv, od, ob, adj, deg, off, odeg, oadj, lsh_T, tab,
                          vcnt, sm, tcnt, twin_rel, bad);
     }
     __syncthreads();
@@ -363,6 +367,7 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
 // Warp kernel for rows of at most SMALL_DEG positions: each warp owns one
 // vertex at a time, with its own table of out(v) (no CTA barrier). Warps take
 // 32 vertices per atomic fetch.
+template <typename IT>
 __global__ void __launch_bounds__(SW_WARPS * 32, 5)
 k_tri_small(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
             const int32_t* __restrict__ deg, const int32_t* __restrict__ odeg,
@@ -408,7 +413,7 @@ k_tri_small(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
       const OutTable tab{hkey, hpos, nullptr, log2h, oadj + ob, od};
       const int64_t rb = off[vv];
       for (int64_t p0 = 0; p0 < dv; p0 += 32)
-        process_slice<false>(p0, dv, rb, (int32_t)vv, dv, od, ob, adj, deg, off, odeg, oadj, lsh_T, tab,
+        process_slice<false, IT>(p0, dv, rb, (int32_t)vv, dv, od, ob, adj, deg, off, odeg, oadj, lsh_T, tab,
                              vcnt, sm, tcnt, twin_rel, bad);
       __syncwarp();
       for (int j = lane; j < od; j += 32) {
@@ -467,6 +472,45 @@ __global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v) {
 
 }  // namespace
 
+// The three counting kernels; IT indexes elements of the CSR (32-bit when the
+// graph has fewer than 2^31 arcs, which halves the index arithmetic).
+template <typename IT>
+int launch_counting(const int64_t* off, const int32_t* adj, const int32_t* deg, const int32_t* odeg,
+                    const int32_t* oadj, int64_t n, const int64_t* item_off,
+                    unsigned long long* work, int lsh_T, int32_t max_od, uint32_t* tcnt,
+                    int32_t* twin, unsigned* status, cudaStream_t s) {
+  int od_cap = 32;
+  while (od_cap < max_od && od_cap < SMEM_OD_MAX) od_cap <<= 1;
+  const size_t smem = (size_t)FILTER_WORDS * 4 + (size_t)5 * od_cap * sizeof(int32_t) +
+                      (size_t)4 * od_cap * sizeof(uint16_t);
+  const size_t smem_max = (size_t)FILTER_WORDS * 4 + (size_t)5 * SMEM_OD_MAX * 4 +
+                          (size_t)4 * SMEM_OD_MAX * 2;
+  GS_CUDA(cudaFuncSetAttribute(k_triangles<false, IT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem_max));
+  int dev = 0, sms = 152, per_sm = 1;
+  GS_CUDA(cudaGetDevice(&dev));
+  GS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  GS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_triangles<false, IT>,
+                                                        TRI_THREADS, smem));
+  if (per_sm < 1) per_sm = 1;
+  k_triangles<false, IT><<<sms * per_sm, TRI_THREADS, smem, s>>>(
+      off, adj, deg, odeg, oadj, n, item_off, work, lsh_T, od_cap, tcnt, twin, status);
+  GS_LAUNCH();
+  int small_per_sm = 1;
+  GS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&small_per_sm, k_tri_small<IT>,
+                                                        SW_WARPS * 32, 0));
+  if (small_per_sm < 1) small_per_sm = 1;
+  k_tri_small<IT><<<sms * small_per_sm, SW_WARPS * 32, 0, s>>>(off, adj, deg, odeg, oadj, n,
+                                                               work + 2, lsh_T, tcnt, twin, status);
+  GS_LAUNCH();
+  if (max_od > SMEM_OD_MAX) {
+    k_triangles<true, IT><<<sms * 4, TRI_THREADS, 0, s>>>(off, adj, deg, odeg, oadj, n, item_off,
+                                                          work + 1, lsh_T, 0, tcnt, twin, status);
+    GS_LAUNCH();
+  }
+  return SCAN_OK;
+}
+
 int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* adj,
                                   const int32_t* deg, int64_t n, int64_t arcs, const int32_t* odeg,
                                   const int32_t* oadj, const int32_t* opos, int32_t max_od,
@@ -496,36 +540,12 @@ int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* a
   GS_CUDA(cudaEventCreate(&e1));
   GS_CUDA(cudaEventRecord(e0, s));
   if (n > 0 && m > 0) {
-    int od_cap = 32;
-    while (od_cap < max_od && od_cap < SMEM_OD_MAX) od_cap <<= 1;
-    const size_t smem = (size_t)FILTER_WORDS * 4 + (size_t)3 * od_cap * sizeof(int32_t) +
-                        (size_t)2 * od_cap * sizeof(uint16_t);
-    const size_t smem_max = (size_t)FILTER_WORDS * 4 + (size_t)3 * SMEM_OD_MAX * 4 +
-                            (size_t)2 * SMEM_OD_MAX * 2;
-    GS_CUDA(cudaFuncSetAttribute(k_triangles<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem_max));
-    int dev = 0, sms = 152, per_sm = 1;
-    GS_CUDA(cudaGetDevice(&dev));
-    GS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    GS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_triangles<false>,
-                                                          TRI_THREADS, smem));
-    if (per_sm < 1) per_sm = 1;
-    k_triangles<false><<<sms * per_sm, TRI_THREADS, smem, s>>>(
-        off, adj, deg, odeg, oadj, n, item_off, work, lsh_T, od_cap, tcnt, twin, status);
-    GS_LAUNCH();
-    {
-      int small_per_sm = 1;
-      GS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&small_per_sm, k_tri_small,
-                                                            SW_WARPS * 32, 0));
-      if (small_per_sm < 1) small_per_sm = 1;
-      k_tri_small<<<sms * small_per_sm, SW_WARPS * 32, 0, s>>>(off, adj, deg, odeg, oadj, n, work + 2,
-                                                               lsh_T, tcnt, twin, status);
-      GS_LAUNCH();
-    }
-    if (max_od > SMEM_OD_MAX) {
-      k_triangles<true><<<sms * 4, TRI_THREADS, 0, s>>>(off, adj, deg, odeg, oadj, n, item_off,
-                                                        work + 1, lsh_T, 0, tcnt, twin, status);
-      GS_LAUNCH();
+    if (m < ((int64_t)1 << 31) - 1) {
+      GS_TRY(launch_counting<int32_t>(off, adj, deg, odeg, oadj, n, item_off, work, lsh_T, max_od,
+                                      tcnt, twin, status, s));
+    } else {
+      GS_TRY(launch_counting<int64_t>(off, adj, deg, odeg, oadj, n, item_off, work, lsh_T, max_od,
+                                      tcnt, twin, status, s));
     }
   }
   GS_CUDA(cudaEventRecord(e1, s));

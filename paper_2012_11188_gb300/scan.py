@@ -329,7 +329,7 @@ def _load_serve():
 class Server:
     """Continuous-batching query/build server (include/scan_serve.h)."""
 
-    def __init__(self, memory_budget: int = 0, max_batch: int = 256, max_pending: int = 0,
+    def __init__(self, memory_budget: int = 0, max_batch: int = 64, max_pending: int = 0,
                  device: int = 0):
         lib = _load_serve()
         p = scan_serve_params(memory_budget, max_batch, max_pending, device)
