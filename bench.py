@@ -301,14 +301,19 @@ def adjusted_rand_index(a, b):
     return 1.0 if mx == expected else float((sij - expected) / (mx - expected))
 
 
-def bench_lsh(gs, off_d, adj_d, g, stream):
-    """LSH index mode on the same graph: SimHash 64/256 bits for cosine and
+def lsh_quality(gs, off_d, adj_d, g, stream, timed: bool):
+    """LSH index mode on one graph: SimHash 64/256 bits for cosine and
     k-partition MinHash k=64 for Jaccard, degree threshold 128; build time, and
     ARI / misclassified-edge fraction against the exact index at mu=5,
-    eps in {.3, .5, .7}."""
-    import numpy as np
+    eps in {.3, .5, .7}, with the number of clustered vertices on each side
+    (ARI is 0 whenever one side clusters nothing and the other something)."""
     import torch
     out = {}
+    deg = (off_d[1:] - off_d[:-1])
+    src = torch.repeat_interleave(torch.arange(g.n, device=off_d.device), deg)
+    approx = ((deg[src] > 128) & (deg[adj_d.long()] > 128))
+    out["approximated_edge_fraction"] = approx.sum().item() / g.arcs
+    del src
     for kind, name, ks in ((gs.COSINE, "simhash", (64, 256)), (gs.JACCARD, "minhash", (64,))):
         exact = gs.ScanIndex.build((off_d, adj_d), kind, stream=stream)
         ex_sim = torch.empty(g.arcs, dtype=torch.float64, device="cuda")
@@ -318,29 +323,51 @@ def bench_lsh(gs, off_d, adj_d, g, stream):
         for k in ks:
             lsh = gs.make_lsh(kind, k, 128, seed=1)
             ix = gs.ScanIndex.build((off_d, adj_d), kind, lsh=lsh, stream=stream)
-            ts = []
-            for _ in range(3):
-                ix.free()
-                a = torch.cuda.Event(enable_timing=True)
-                b = torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                ix = gs.ScanIndex.build((off_d, adj_d), kind, lsh=lsh, stream=stream)
-                b.record(stream)
-                b.synchronize()
-                ts.append(a.elapsed_time(b))
+            rec = {}
+            if timed:
+                ts = []
+                for _ in range(3):
+                    ix.free()
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    ix = gs.ScanIndex.build((off_d, adj_d), kind, lsh=lsh, stream=stream)
+                    b.record(stream)
+                    b.synchronize()
+                    ts.append(a.elapsed_time(b))
+                rec = {"build_ms": round(statistics.median(ts), 2),
+                       "edges_per_s": g.edges / (statistics.median(ts) / 1000.0)}
             ap_sim = torch.empty(g.arcs, dtype=torch.float64, device="cuda")
             gs.load().scan_index_export(ix._h, ap_sim.data_ptr(), None, None, None, None, None)
-            rec = {"build_ms": round(statistics.median(ts), 2),
-                   "edges_per_s": g.edges / (statistics.median(ts) / 1000.0)}
             for e in (0.3, 0.5, 0.7):
                 lab = ix.query(5, e)
-                mis = ((ex_sim >= e) != (ap_sim >= e)).sum().item() / g.arcs
-                rec[f"eps{e}"] = {"ari": round(adjusted_rand_index(labs_exact[e], lab), 4),
-                                  "misclassified_edge_fraction": mis}
+                flip = (ex_sim >= e) != (ap_sim >= e)
+                rec[f"eps{e}"] = {
+                    "ari": round(adjusted_rand_index(labs_exact[e], lab), 4),
+                    "misclassified_edge_fraction": flip.sum().item() / g.arcs,
+                    "clustered_exact": int((labs_exact[e] >= 0).sum()),
+                    "clustered_lsh": int((lab >= 0).sum())}
             ix.free()
             del ap_sim
             out[f"{name}_k{k}"] = rec
         del ex_sim
+    return out
+
+
+def bench_lsh(gs, off_d, adj_d, g, stream):
+    """LSH quality on the benchmark graph (timed builds), and on a dense SBM
+    whose in-block edges are all approximated, so that the exact clustering
+    has clusters for the ARI to compare."""
+    import graphgen
+    import torch
+    out = lsh_quality(gs, off_d, adj_d, g, stream, timed=True)
+    sb = graphgen.sbm(100_000, 100, 0.6, 4e-5, seed=1)
+    so = torch.from_numpy(sb.off).to("cuda")
+    sa = torch.from_numpy(sb.adj).to("cuda")
+    q = lsh_quality(gs, so, sa, sb, stream, timed=False)
+    q["workload"] = (f"SBM n=100000, 100 blocks, p_in .6, p_out 4e-5, seed 1 "
+                     f"({sb.edges} edges)")
+    out["sbm_dense"] = q
     return out
 
 

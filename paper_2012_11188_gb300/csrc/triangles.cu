@@ -35,7 +35,7 @@ __device__ __forceinline__ bool lower(int32_t du, int32_t u, int32_t dv, int32_t
 }
 
 constexpr int SMALL_DEG = 256;  // rows up to this long are handled by one warp
-constexpr int SW_SLOTS = 2 * SMALL_DEG;
+constexpr int SW_SLOTS = 2 * SMALL_DEG;  // 2^table_log2(SMALL_DEG) slots per table
 constexpr int SW_WARPS = 8;
 
 // Work items of the CTA kernel: a vertex v with deg > SMALL_DEG contributes
@@ -65,63 +65,117 @@ __device__ __forceinline__ int64_t find_item_vertex(const int64_t* item_off, int
   return lo;
 }
 
-constexpr int FILTER_WORDS = 1024;  // 32768-bit membership filter in front of the CTA table
-constexpr int FILTER_LOG2 = 15;
+// Lookup of out(v): a two-table cuckoo hash in shared memory, or (BIG, and
+// in the unlikely case that no cuckoo placement was found) binary search in
+// the sorted global list.
+//
+// Each table has 2^L slots of 32 bits; out(v) has at most 2^(L-1) entries,
+// so the load of the pair is at most 1/4. A key x hashes to h_i = x * C_i
+// (mod 2^32, a bijection for odd C_i); the slot is the top L bits of h_i and
+// the entry stores the remaining 32 - L bits of h_i (the tag) above the
+// (L-1)-bit position of x in out(v), with bit 31 clear. Slot and tag together
+// determine h_i and hence x, so a lookup is one load per table and an exact
+// compare, with no probing loop; an empty slot (all ones) never matches.
+constexpr uint32_t EMPTY_SLOT = 0xffffffffu;
+constexpr int CUCKOO_KICKS = 64;     // evictions before an insertion gives up
+constexpr int CUCKOO_ATTEMPTS = 4;   // multiplier pairs tried before binary search
 
-// Lookup of out(v): open-addressing table in shared memory (slot -> position),
-// optionally behind a bit filter, or (BIG) binary search in the sorted global list.
+constexpr uint32_t mul_inverse(uint32_t c) {  // inverse of an odd c mod 2^32 (Newton)
+  uint32_t y = c;
+  for (int i = 0; i < 5; ++i) y *= 2u - c * y;
+  return y;
+}
+// odd multipliers (from the golden ratio and common 32-bit hash primes)
+__constant__ uint32_t CUCKOO_MUL[2 * CUCKOO_ATTEMPTS] = {
+    0x9E3779B1u, 0x85EBCA77u, 0xC2B2AE3Du, 0x27D4EB2Fu,
+    0x165667B1u, 0xD3A2646Du, 0xFD7046C5u, 0xB55A4F09u};
+
 struct OutTable {
-  const int32_t* hkey;
-  const uint16_t* hpos;
-  const uint32_t* filt;  // nullptr: no filter
-  int log2h;
-  const int32_t* glist;  // BIG: out(v) in global memory
+  const uint32_t* t0;
+  const uint32_t* t1;
+  int L;                 // log2 of the slots per table
+  uint32_t c0, c1;       // multipliers of the two tables
+  const int32_t* glist;  // out(v) in global memory (binary search)
   int32_t od;
+  bool bsearch;          // no cuckoo placement: search glist
 };
+
+__device__ __forceinline__ int glist_search(const int32_t* list, int32_t od, int32_t x) {
+  int lo = 0, hi = od;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (list[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  return (lo < od && list[lo] == x) ? lo : -1;
+}
 
 template <bool BIG>
 __device__ __forceinline__ int table_lookup(const OutTable& t, int32_t x) {
-  if (BIG) {
-    int lo = 0, hi = t.od;
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (t.glist[mid] < x) lo = mid + 1; else hi = mid;
-    }
-    return (lo < t.od && t.glist[lo] == x) ? lo : -1;
-  }
-  const uint32_t hx = (uint32_t)x * 0x9E3779B1u;
-  if (t.filt) {
-    const uint32_t fb = hx >> (32 - FILTER_LOG2);
-    if (!((t.filt[fb >> 5] >> (fb & 31)) & 1u)) return -1;
-  }
-  const int H = 1 << t.log2h;
-  uint32_t sl = hx >> (32 - t.log2h);
-  for (int probe = 0; probe < H; ++probe) {
-    const int32_t key = t.hkey[sl];
-    if (key == x) return t.hpos[sl];
-    if (key == -1) return -1;
-    sl = (sl + 1) & (H - 1);
-  }
-  return -1;
+  if (BIG || t.bsearch) return glist_search(t.glist, t.od, x);
+  const uint32_t h0 = (uint32_t)x * t.c0, h1 = (uint32_t)x * t.c1;
+  const uint32_t e0 = t.t0[h0 >> (32 - t.L)];
+  const uint32_t e1 = t.t1[h1 >> (32 - t.L)];
+  const uint32_t d0 = e0 ^ ((h0 << t.L) >> 1);
+  const uint32_t d1 = e1 ^ ((h1 << t.L) >> 1);
+  const uint32_t pmax = 1u << (t.L - 1);
+  return d0 < pmax ? (int)d0 : (d1 < pmax ? (int)d1 : -1);
 }
 
-// Insert out(v) into a shared table; `stride` threads starting at `tid`.
-__device__ __forceinline__ void table_fill(int32_t* hkey, uint16_t* hpos, uint32_t* filt, int log2h,
-                                           const int32_t* list, int32_t od, int tid, int stride) {
-  const int H = 1 << log2h;
-  for (int j = tid; j < od; j += stride) {
-    const int32_t x = list[j];
-    const uint32_t hx = (uint32_t)x * 0x9E3779B1u;
-    if (filt) {
-      const uint32_t fb = hx >> (32 - FILTER_LOG2);
-      atomicOr(&filt[fb >> 5], 1u << (fb & 31));
-    }
-    uint32_t s = hx >> (32 - log2h);
-    for (int probe = 0; probe < H; ++probe) {
-      if (atomicCAS(&hkey[s], -1, x) == -1) { hpos[s] = (uint16_t)j; break; }
-      s = (s + 1) & (H - 1);
-    }
+// Cuckoo insertion of (x, pos): place in table 0, move an evicted entry to
+// its slot in the other table, and so on. Returns false if an entry is still
+// homeless after CUCKOO_KICKS moves (the table must then be rebuilt).
+__device__ __forceinline__ bool cuckoo_insert(uint32_t* t0, uint32_t* t1, int L, uint32_t c0,
+                                              uint32_t c1, int32_t x, uint32_t pos) {
+  const uint32_t i0 = mul_inverse(c0), i1 = mul_inverse(c1);
+  int which = 0;
+  for (int kick = 0; kick < CUCKOO_KICKS; ++kick) {
+    const uint32_t h = (uint32_t)x * (which ? c1 : c0);
+    const uint32_t slot = h >> (32 - L);
+    const uint32_t old = atomicExch(&(which ? t1 : t0)[slot], ((h << L) >> 1) | pos);
+    if (old == EMPTY_SLOT) return true;
+    pos = old & ((1u << (L - 1)) - 1u);
+    const uint32_t hold = (slot << (32 - L)) | ((old << 1) >> L);
+    x = (int32_t)(hold * (which ? i1 : i0));
+    which ^= 1;
   }
+  return false;
+}
+
+// log2 of the slots per table for an out-list of od entries (at least 32).
+__device__ __forceinline__ int table_log2(int32_t od) {
+  int L = 5;
+  while ((1 << (L - 1)) < od) ++L;
+  return L;
+}
+
+// Builds the table of out(v) = list[0..od) with `nthreads` threads (tid in
+// [0, nthreads)); `sync` is the group barrier and `any` its OR-reduction.
+// Returns the OutTable, with bsearch set if no attempt placed every entry.
+template <typename Sync, typename Any>
+__device__ __forceinline__ OutTable table_build(uint32_t* t0, uint32_t* t1, uint32_t* vcnt,
+                                                const int32_t* list, int32_t od, int tid,
+                                                int nthreads, Sync sync, Any any) {
+  const int L = table_log2(od);
+  const int H = 1 << L;
+  int attempt = 0;
+  bool failed = true;
+  for (; attempt < CUCKOO_ATTEMPTS && failed; ++attempt) {
+    uint4* w0 = reinterpret_cast<uint4*>(t0);
+    uint4* w1 = reinterpret_cast<uint4*>(t1);
+    const uint4 e4 = make_uint4(EMPTY_SLOT, EMPTY_SLOT, EMPTY_SLOT, EMPTY_SLOT);
+    for (int i = tid; i < H / 4; i += nthreads) { w0[i] = e4; w1[i] = e4; }
+    sync();
+    bool ok = true;
+    const uint32_t c0 = CUCKOO_MUL[2 * attempt], c1 = CUCKOO_MUL[2 * attempt + 1];
+    for (int j = tid; j < od; j += nthreads)
+      ok &= cuckoo_insert(t0, t1, L, c0, c1, list[j], (uint32_t)j);
+    failed = any(!ok);
+  }
+  for (int i = tid; i < od; i += nthreads) vcnt[i] = 0;
+  sync();
+  --attempt;
+  return OutTable{t0, t1, L, CUCKOO_MUL[2 * attempt], CUCKOO_MUL[2 * attempt + 1], list, od,
+                  failed};
 }
 
 // Per-warp scratch for one 32-position slice.
@@ -202,6 +256,8 @@ __device__ __forceinline__ void process_slice(
   sm.jv[lane] = -1;
   __syncwarp();
   constexpr int R = GS_TRI_ROUNDS;  // rounds whose loads are issued before any probe
+  int run_own = 0;
+  uint32_t run_acc = 0;
   // the list holding element r0 (warp-uniform); a round that lies inside one
   // list needs no owner search
   int cur = 0;
@@ -244,32 +300,34 @@ __device__ __forceinline__ void process_slice(
     }
 #pragma unroll
     for (int rr = 0; rr < R; ++rr) {
-      const int32_t x = xs[rr];
+      const int32_t x = xs[rr];  // -1 past the end: never in a table
       const IT j = js[rr];
       const int own = owns[rr];
-      bool hit = false;
-      if (j >= 0) {
-        if (x == v) sm.jv[own] = j;
-        const int q = table_lookup<BIG>(tab, x);
-        if (q >= 0) {
-          hit = true;
-          if (!BIG) atomicAdd(&vcnt[q], 1u);
-          else atomicAdd(&tcnt[ob + q], 1u);
-          atomicAdd(&tcnt[j], 1u);
-        }
+      if (x == v) sm.jv[own] = j;
+      const int q = table_lookup<BIG>(tab, x);
+      const bool hit = q >= 0;
+      if (hit) {
+        if (!BIG) atomicAdd(&vcnt[q], 1u);
+        else atomicAdd(&tcnt[ob + q], 1u);
+        atomicAdd(&tcnt[j], 1u);
       }
       const unsigned hm = __ballot_sync(FULL, hit);
-      if (hm) {
-        if (single[rr]) {
-          if (lane == 0) sm.acc[own] += __popc(hm);
-        } else {
-          // lanes of one owner are contiguous; its first lane adds
-          const unsigned peers = __match_any_sync(FULL, own);
-          if ((hm & peers) && lane == __ffs(peers) - 1) sm.acc[own] += __popc(hm & peers);
+      if (single[rr]) {
+        // (u,v) hits of a run of rounds inside one list stay in a register
+        if (own != run_own) {
+          if (lane == 0 && run_acc) sm.acc[run_own] += run_acc;
+          run_own = own;
+          run_acc = 0;
         }
+        run_acc += __popc(hm);
+      } else if (hm) {
+        // lanes of one owner are contiguous; its first lane adds
+        const unsigned peers = __match_any_sync(FULL, own);
+        if ((hm & peers) && lane == __ffs(peers) - 1) sm.acc[own] += __popc(hm & peers);
       }
     }
   }
+  if (lane == 0 && run_acc) sm.acc[run_own] += run_acc;
   __syncwarp();
   if (lane < k) {
     const long long jv = sm.jv[lane];
@@ -294,9 +352,9 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
             const int32_t* __restrict__ oadj, int64_t n, const int64_t* __restrict__ item_off,
             unsigned long long* __restrict__ work, int lsh_T, int od_cap,
             uint32_t* __restrict__ tcnt, int32_t* __restrict__ twin_rel, unsigned* status) {
-  // shared layout for od_cap (a power of two >= every od handled here):
-  // filter[FILTER_WORDS] | hkey[4*od_cap] int32 | vcnt[od_cap] uint32 | hpos[4*od_cap] uint16
-  extern __shared__ int32_t smem[];
+  // shared layout for od_cap (a power of two >= every od handled here) and
+  // Lc = table_log2(od_cap): t0[2^Lc] | t1[2^Lc] | vcnt[od_cap]
+  extern __shared__ uint4 smem4[];
   __shared__ long long s_item;
   __shared__ int s_next;  // next 32-position slice of the item's CSR range
   __shared__ int32_t s_u[TRI_WARPS][32];
@@ -306,10 +364,10 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t total = item_off[n];
-  uint32_t* filt = (uint32_t*)smem;
-  int32_t* hkey = smem + FILTER_WORDS;
-  uint32_t* vcnt = (uint32_t*)(smem + FILTER_WORDS + 4 * od_cap);
-  uint16_t* hpos = (uint16_t*)(smem + FILTER_WORDS + 5 * od_cap);
+  const int Lc = table_log2(od_cap);
+  uint32_t* t0 = reinterpret_cast<uint32_t*>(smem4);
+  uint32_t* t1 = t0 + (1 << Lc);
+  uint32_t* vcnt = t1 + (1 << Lc);
   const SliceSmem sm{s_u[wid], s_p[wid], s_acc[wid], s_jv[wid]};
   unsigned bad = 0;
 
@@ -328,18 +386,10 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
     const int32_t od = odeg[v];
     const bool skip_item = BIG ? (od <= SMEM_OD_MAX) : (od > SMEM_OD_MAX);
     if (skip_item) { __syncthreads(); continue; }
-    int log2h = 5;
-    if (!BIG && od > 0) {
-      while ((1 << log2h) < 4 * od) ++log2h;  // load factor <= 1/4: short probes
-      const int H = 1 << log2h;
-      for (int i = threadIdx.x; i < H; i += TRI_THREADS) hkey[i] = -1;
-      for (int i = threadIdx.x; i < od; i += TRI_THREADS) vcnt[i] = 0;
-      for (int i = threadIdx.x; i < FILTER_WORDS; i += TRI_THREADS) filt[i] = 0;
-      __syncthreads();
-      table_fill(hkey, hpos, filt, log2h, oadj + ob, od, threadIdx.x, TRI_THREADS);
-      __syncthreads();
-    }
-    const OutTable tab{hkey, hpos, filt, log2h, oadj + ob, od};
+    OutTable tab{nullptr, nullptr, 5, 0u, 0u, oadj + ob, od, true};
+    if (!BIG && od > 0)
+      tab = table_build(t0, t1, vcnt, oadj + ob, od, threadIdx.x, TRI_THREADS,
+                        [] { __syncthreads(); }, [](bool b) { return __syncthreads_or(b) != 0; });
     const int64_t rb = off[v];
     const int64_t p_begin = chunk * CHUNK;
     const int64_t p_end = min((int64_t)dv, p_begin + CHUNK);
@@ -374,8 +424,8 @@ k_tri_small(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
             const int32_t* __restrict__ oadj, int64_t n, unsigned long long* __restrict__ work,
             int lsh_T, uint32_t* __restrict__ tcnt, int32_t* __restrict__ twin_rel,
             unsigned* status) {
-  __shared__ int32_t s_key[SW_WARPS][SW_SLOTS];
-  __shared__ uint16_t s_pos[SW_WARPS][SW_SLOTS];
+  __shared__ __align__(16) uint32_t s_t0[SW_WARPS][SW_SLOTS];
+  __shared__ __align__(16) uint32_t s_t1[SW_WARPS][SW_SLOTS];
   __shared__ uint32_t s_cnt[SW_WARPS][SMALL_DEG];
   __shared__ int32_t s_u[SW_WARPS][32];
   __shared__ int32_t s_p[SW_WARPS][32];
@@ -383,8 +433,6 @@ k_tri_small(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
   __shared__ long long s_jv[SW_WARPS][32];
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int32_t* hkey = s_key[wid];
-  uint16_t* hpos = s_pos[wid];
   uint32_t* vcnt = s_cnt[wid];
   const SliceSmem sm{s_u[wid], s_p[wid], s_acc[wid], s_jv[wid]};
   unsigned bad = 0;
@@ -400,17 +448,11 @@ k_tri_small(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
       const int64_t ob = off[vv];
       const int32_t od = odeg[vv];
       if (dv - od == 0) continue;  // no in-neighbours
-      int log2h = 5;
-      if (od > 0) {
-        while ((1 << log2h) < 2 * od) ++log2h;
-        const int H = 1 << log2h;
-        for (int i = lane; i < H; i += 32) hkey[i] = -1;
-        for (int i = lane; i < od; i += 32) vcnt[i] = 0;
-        __syncwarp();
-        table_fill(hkey, hpos, nullptr, log2h, oadj + ob, od, lane, 32);
-        __syncwarp();
-      }
-      const OutTable tab{hkey, hpos, nullptr, log2h, oadj + ob, od};
+      OutTable tab{nullptr, nullptr, 5, 0u, 0u, oadj + ob, od, true};
+      if (od > 0)
+        tab = table_build(s_t0[wid], s_t1[wid], vcnt, oadj + ob, od, lane, 32,
+                          [] { __syncwarp(); },
+                          [](bool b) { __syncwarp(); return __any_sync(0xffffffffu, b) != 0; });
       const int64_t rb = off[vv];
       for (int64_t p0 = 0; p0 < dv; p0 += 32)
         process_slice<false, IT>(p0, dv, rb, (int32_t)vv, dv, od, ob, adj, deg, off, odeg, oadj, lsh_T, tab,
@@ -479,12 +521,11 @@ int launch_counting(const int64_t* off, const int32_t* adj, const int32_t* deg, 
                     const int32_t* oadj, int64_t n, const int64_t* item_off,
                     unsigned long long* work, int lsh_T, int32_t max_od, uint32_t* tcnt,
                     int32_t* twin, unsigned* status, cudaStream_t s) {
-  int od_cap = 32;
+  int od_cap = 16;
   while (od_cap < max_od && od_cap < SMEM_OD_MAX) od_cap <<= 1;
-  const size_t smem = (size_t)FILTER_WORDS * 4 + (size_t)5 * od_cap * sizeof(int32_t) +
-                      (size_t)4 * od_cap * sizeof(uint16_t);
-  const size_t smem_max = (size_t)FILTER_WORDS * 4 + (size_t)5 * SMEM_OD_MAX * 4 +
-                          (size_t)4 * SMEM_OD_MAX * 2;
+  // two tables of 2^table_log2(od_cap) = 2 * od_cap slots, then the counters
+  const size_t smem = (size_t)5 * od_cap * sizeof(uint32_t);
+  const size_t smem_max = (size_t)5 * SMEM_OD_MAX * sizeof(uint32_t);
   GS_CUDA(cudaFuncSetAttribute(k_triangles<false, IT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem_max));
   int dev = 0, sms = 152, per_sm = 1;
