@@ -24,6 +24,9 @@ namespace {
 #ifndef GS_TRI_ROUNDS
 #define GS_TRI_ROUNDS 4  // 32-element rounds of loads in flight per warp in the counting loop
 #endif
+#ifndef GS_TRI_FAST_ROUNDS
+#define GS_TRI_FAST_ROUNDS 8  // the same for batches of rounds that lie inside one list
+#endif
 
 constexpr int TRI_THREADS = 512;
 constexpr int TRI_WARPS = TRI_THREADS / 32;
@@ -34,11 +37,22 @@ __device__ __forceinline__ bool lower(int32_t du, int32_t u, int32_t dv, int32_t
   return du < dv || (du == dv && u < v);
 }
 
-constexpr int SMALL_DEG = 256;  // rows up to this long are handled by one warp
-constexpr int SW_SLOTS = 2 * SMALL_DEG;  // 2^table_log2(SMALL_DEG) slots per table
+#ifndef GS_TRI_WARP_DEG
+#define GS_TRI_WARP_DEG 512
+#endif
+// A vertex whose row has at most WARP_DEG positions and whose out-list has at
+// most SMALL_OD entries is handled by one warp with its own table; the rest
+// by the CTA kernel.
+constexpr int WARP_DEG = GS_TRI_WARP_DEG;
+constexpr int SMALL_OD = 256;
+constexpr int SW_SLOTS = 2 * SMALL_OD;  // 2^table_log2(SMALL_OD) slots per table
+
+__host__ __device__ __forceinline__ bool warp_vertex(int64_t d, int64_t od) {
+  return d <= WARP_DEG && od <= SMALL_OD;
+}
 constexpr int SW_WARPS = 8;
 
-// Work items of the CTA kernel: a vertex v with deg > SMALL_DEG contributes
+// Work items of the CTA kernel: a vertex v not handled by a warp contributes
 // ceil(deg/CHUNK) items when it has in-neighbours (every in-arc needs the
 // position of its source in N(v), even when out(v) is empty and no triangle
 // has v in the middle). items[v] -> prefix -> item index maps to (v, chunk).
@@ -49,7 +63,7 @@ __global__ void k_item_counts(const int32_t* __restrict__ odeg, const int32_t* _
     const int64_t od = odeg[v];
     const int32_t d = deg[v];
     int c = 0;
-    if (d > SMALL_DEG && d - od > 0) c = (int)((d + CHUNK - 1) / CHUNK);
+    if (!warp_vertex(d, od) && d - od > 0) c = (int)((d + CHUNK - 1) / CHUNK);
     items[v] = c;
   }
 }
@@ -264,7 +278,44 @@ __device__ __forceinline__ void process_slice(
   int32_t cur_start = 0;
   int32_t cur_end = __shfl_sync(FULL, incl, 0);
   IT cur_ub = __shfl_sync(FULL, cub, 0);
-  for (int32_t rbase = 0; rbase < W; rbase += 32 * R) {
+  constexpr int RF = GS_TRI_FAST_ROUNDS;
+  for (int32_t rbase = 0; rbase < W;) {
+    if (rbase >= cur_end) {
+      cur = __popc(__ballot_sync(FULL, lane < k && cstart <= rbase)) - 1;
+      cur_start = __shfl_sync(FULL, cstart, cur);
+      cur_end = __shfl_sync(FULL, incl, cur);
+      cur_ub = __shfl_sync(FULL, cub, cur);
+    }
+    if (rbase + 32 * RF <= cur_end) {
+      // fast batch: all RF rounds inside list `cur`
+      const IT jb = cur_ub + (IT)(rbase - cur_start + lane);
+      int32_t xs[RF];
+#pragma unroll
+      for (int rr = 0; rr < RF; ++rr) xs[rr] = oadj[jb + (IT)(32 * rr)];
+      uint32_t hits = 0;
+#pragma unroll
+      for (int rr = 0; rr < RF; ++rr) {
+        const int32_t x = xs[rr];
+        const IT j = jb + (IT)(32 * rr);
+        if (x == v) sm.jv[cur] = j;
+        const int q = table_lookup<BIG>(tab, x);
+        const bool hit = q >= 0;
+        if (hit) {
+          if (!BIG) atomicAdd(&vcnt[q], 1u);
+          else atomicAdd(&tcnt[ob + q], 1u);
+          atomicAdd(&tcnt[j], 1u);
+        }
+        hits += __popc(__ballot_sync(FULL, hit));
+      }
+      if (cur != run_own) {
+        if (lane == 0 && run_acc) sm.acc[run_own] += run_acc;
+        run_own = cur;
+        run_acc = 0;
+      }
+      run_acc += hits;
+      rbase += 32 * RF;
+      continue;
+    }
     int32_t xs[R];
     IT js[R];
     int owns[R];
@@ -326,6 +377,7 @@ __device__ __forceinline__ void process_slice(
         if ((hm & peers) && lane == __ffs(peers) - 1) sm.acc[own] += __popc(hm & peers);
       }
     }
+    rbase += 32 * R;
   }
   if (lane == 0 && run_acc) sm.acc[run_own] += run_acc;
   __syncwarp();
@@ -342,7 +394,7 @@ __device__ __forceinline__ void process_slice(
   __syncwarp();
 }
 
-// CTA kernel for rows longer than SMALL_DEG: the CTA shares out(v)'s table and
+// CTA kernel for the other rows: the CTA shares out(v)'s table and
 // its warps pull 32-position slices of the item's CSR range.
 // BIG = out(v) too long for the shared table (binary search, global counters).
 template <bool BIG, typename IT>
@@ -414,11 +466,12 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
   if (bad) atomicOr(status, (unsigned)DEV_BADGRAPH);
 }
 
-// Warp kernel for rows of at most SMALL_DEG positions: each warp owns one
+// Warp kernel for rows of at most WARP_DEG positions with out-lists of at
+// most SMALL_OD entries: each warp owns one
 // vertex at a time, with its own table of out(v) (no CTA barrier). Warps take
 // 32 vertices per atomic fetch.
 template <typename IT>
-__global__ void __launch_bounds__(SW_WARPS * 32, 5)
+__global__ void __launch_bounds__(SW_WARPS * 32, 4)
 k_tri_small(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
             const int32_t* __restrict__ deg, const int32_t* __restrict__ odeg,
             const int32_t* __restrict__ oadj, int64_t n, unsigned long long* __restrict__ work,
@@ -426,7 +479,7 @@ k_tri_small(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
             unsigned* status) {
   __shared__ __align__(16) uint32_t s_t0[SW_WARPS][SW_SLOTS];
   __shared__ __align__(16) uint32_t s_t1[SW_WARPS][SW_SLOTS];
-  __shared__ uint32_t s_cnt[SW_WARPS][SMALL_DEG];
+  __shared__ uint32_t s_cnt[SW_WARPS][SMALL_OD];
   __shared__ int32_t s_u[SW_WARPS][32];
   __shared__ int32_t s_p[SW_WARPS][32];
   __shared__ uint32_t s_acc[SW_WARPS][32];
@@ -444,10 +497,10 @@ k_tri_small(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
     const int64_t vend = min(n, (int64_t)base + 32);
     for (int64_t vv = (int64_t)base; vv < vend; ++vv) {
       const int32_t dv = deg[vv];
-      if (dv == 0 || dv > SMALL_DEG) continue;
-      const int64_t ob = off[vv];
+      if (dv == 0) continue;
       const int32_t od = odeg[vv];
-      if (dv - od == 0) continue;  // no in-neighbours
+      if (!warp_vertex(dv, od) || dv - od == 0) continue;  // CTA kernel, or no in-neighbours
+      const int64_t ob = off[vv];
       OutTable tab{nullptr, nullptr, 5, 0u, 0u, oadj + ob, od, true};
       if (od > 0)
         tab = table_build(s_t0[wid], s_t1[wid], vcnt, oadj + ob, od, lane, 32,
