@@ -178,7 +178,7 @@ int run_pipeline(IndexData* ix, int kind, const scan_lsh_params* lsh, Pool& pool
   if (arcs > 0) {
     GS_CUDA(cudaMemcpyAsync(ix->no_id, ix->adj, arcs * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
     GS_TRY(launch_closed_counts_and_sims(kind, ix->off, ix->adj, ix->deg, n, arcs, od, oadj, opos,
-                                         max_od, use_lsh ? lsh->degree_threshold : -1,
+                                         ix->maxdeg, max_od, use_lsh ? lsh->degree_threshold : -1,
                                          ix->no_sim, scalars, pool, s, count_ms));
     GS_CUDA(cudaMemcpyAsync(hs, scalars, sizeof(hs), cudaMemcpyDeviceToHost, s));
     GS_CUDA(cudaStreamSynchronize(s));

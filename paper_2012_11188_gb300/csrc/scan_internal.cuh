@@ -131,9 +131,9 @@ int launch_orient(const int64_t* off, const int32_t* adj, const int32_t* deg, in
 // LSH estimate (their sim_csr entries are overwritten later).
 int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* adj,
                                   const int32_t* deg, int64_t n, int64_t arcs, const int32_t* od,
-                                  const int32_t* oadj, const int32_t* opos, int32_t max_od,
-                                  int lsh_T, double* sim_csr, unsigned* status, Pool& pool,
-                                  cudaStream_t s, float* count_ms);
+                                  const int32_t* oadj, const int32_t* opos, int32_t maxdeg,
+                                  int32_t max_od, int lsh_T, double* sim_csr, unsigned* status,
+                                  Pool& pool, cudaStream_t s, float* count_ms);
 
 // Sort every segment [seg_off[i], seg_off[i+1]) of (key, val) pairs by key
 // descending, then val ascending. Keys are non-negative doubles viewed as

@@ -191,6 +191,29 @@ k_sort_warp_reg(uint64_t* __restrict__ key, int32_t* __restrict__ val,
   }
 }
 
+#ifndef GS_SORT_WARP_BIG
+#define GS_SORT_WARP_BIG 0  // 1: segments of 257..1024 elements sorted by one warp in registers
+#endif
+
+// One warp per segment of 257..1024 elements: 16 or 32 elements per lane in
+// registers, no shared memory and no barrier.
+__global__ void __launch_bounds__(128)
+k_sort_warp_big(uint64_t* __restrict__ key, int32_t* __restrict__ val,
+                const int64_t* __restrict__ seg_off, const int64_t* __restrict__ list,
+                const unsigned long long* __restrict__ count_ptr) {
+  const int lane = threadIdx.x & 31;
+  const int64_t cnt = (int64_t)*count_ptr;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t u = w0; u < cnt; u += nw) {
+    const int64_t sg = list[u];
+    const int64_t b = seg_off[sg];
+    const int64_t len = seg_off[sg + 1] - b;
+    if (len <= 512) warp_sort_range<16>(key, val, b, len, lane);
+    else warp_sort_range<32>(key, val, b, len, lane);
+  }
+}
+
 // Merge path inside shared memory: elements of A (length la) among the first
 // d outputs of merge(A, B).
 __device__ __forceinline__ int smem_merge_path(const uint64_t* ka, const int32_t* va, int la,
@@ -376,82 +399,132 @@ __global__ void k_merge_partition(const uint64_t* __restrict__ sk, const int32_t
   }
 }
 
+// Asynchronous global -> shared copies (sm_80+ cp.async), so the next chunk's
+// inputs are in flight while the current chunk is merged.
+__device__ __forceinline__ void cp_async8(void* dst_smem, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst_smem, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Where one output chunk of a pass reads from: run A = [ia0, ia1) and run B =
+// [ib0, ib1) (relative to the segment base), written to base + o0.
+struct MergeChunk {
+  int64_t base, o0, ia0, ib0;
+  int na, nb;
+  bool active;  // false: the segment is already finished (len <= L)
+};
+
+__device__ __forceinline__ MergeChunk merge_chunk(const int64_t* seg_off, const int64_t* list,
+                                                  const int64_t* chunk_prefix, int64_t nlong,
+                                                  int64_t L, const int64_t* split, int64_t c) {
+  MergeChunk m;
+  const int64_t si = chunk_segment(chunk_prefix, nlong, c);
+  const int64_t sg = list[si];
+  m.base = seg_off[sg];
+  const int64_t len = seg_off[sg + 1] - m.base;
+  m.active = len > L;
+  if (!m.active) return m;
+  m.o0 = (c - chunk_prefix[si]) * MERGE_CHUNK;
+  const int64_t o1 = min(len, m.o0 + MERGE_CHUNK);
+  // run pair containing [o0, o1): MERGE_CHUNK divides 2L
+  const int64_t r0 = (m.o0 / (2 * L)) * (2 * L);
+  const int64_t a1 = min(len, r0 + L);
+  const int64_t i0 = split[2 * c], i1 = split[2 * c + 1];
+  m.ia0 = r0 + i0;
+  m.na = (int)(i1 - i0);
+  m.ib0 = a1 + (m.o0 - r0) - i0;
+  m.nb = (int)((o1 - r0) - i1 - ((m.o0 - r0) - i0));
+  return m;
+}
+
 // One merge pass: within every long segment still longer than L, runs of
 // length L are merged in pairs from (sk, sv) into (dk, dv). Segments of length
-// <= L are finished and stay where they are. Each CTA writes MERGE_CHUNK
-// outputs, staged in shared memory so the global stores are coalesced.
+// <= L are finished and stay where they are. Each CTA takes chunks of
+// MERGE_CHUNK outputs; the inputs of its next chunk are copied into shared
+// memory (cp.async) while it merges the current one, and outputs are staged
+// in shared memory so the global stores are coalesced.
 __global__ void __launch_bounds__(MERGE_T)
 k_merge_pass(const uint64_t* __restrict__ sk, const int32_t* __restrict__ sv,
              uint64_t* __restrict__ dk, int32_t* __restrict__ dv,
              const int64_t* __restrict__ seg_off, const int64_t* __restrict__ list,
              const int64_t* __restrict__ chunk_prefix, int64_t nlong, int64_t L,
              const int64_t* __restrict__ split) {
-  __shared__ uint64_t shk[MERGE_CHUNK];
-  __shared__ int32_t shv[MERGE_CHUNK];
+  __shared__ uint64_t ink[2][MERGE_CHUNK];
+  __shared__ int32_t inv[2][MERGE_CHUNK];
   __shared__ uint64_t ok_[MERGE_CHUNK];
   __shared__ int32_t ov_[MERGE_CHUNK];
-  __shared__ int64_t s_bounds[4];
   const int64_t total = chunk_prefix[nlong];
-  for (int64_t c = blockIdx.x; c < total; c += gridDim.x) {
-    const int64_t si = chunk_segment(chunk_prefix, nlong, c);
-    const int64_t sg = list[si];
-    const int64_t base = seg_off[sg], len = seg_off[sg + 1] - base;
-    if (len <= L) continue;  // uniform across the CTA
-    const int64_t o0 = (c - chunk_prefix[si]) * MERGE_CHUNK;
-    const int64_t o1 = min(len, o0 + MERGE_CHUNK);
-    // run pair containing [o0, o1): MERGE_CHUNK divides 2L
-    const int64_t r0 = (o0 / (2 * L)) * (2 * L);
-    const int64_t a0 = r0, a1 = min(len, r0 + L);
-    const int64_t b0 = a1, b1 = min(len, r0 + 2 * L);
-    const uint64_t* KA = sk + base + a0;
-    const int32_t* VA = sv + base + a0;
-    const uint64_t* KB = sk + base + b0;
-    const int32_t* VB = sv + base + b0;
-    const int64_t la = a1 - a0, lb = b1 - b0;
-    if (threadIdx.x == 0) {
-      const int64_t i0 = split[2 * c];
-      const int64_t i1 = split[2 * c + 1];
-      s_bounds[0] = i0;
-      s_bounds[1] = i1;
-      s_bounds[2] = (o0 - r0) - i0;
-      s_bounds[3] = (o1 - r0) - i1;
-    }
-    __syncthreads();
-    (void)la;
-    (void)lb;
-    const int64_t ia0 = s_bounds[0], ia1 = s_bounds[1], ib0 = s_bounds[2], ib1 = s_bounds[3];
-    const int na = (int)(ia1 - ia0), nb = (int)(ib1 - ib0);
-    for (int i = threadIdx.x; i < na; i += MERGE_T) { shk[i] = KA[ia0 + i]; shv[i] = VA[ia0 + i]; }
-    for (int i = threadIdx.x; i < nb; i += MERGE_T) {
-      shk[na + i] = KB[ib0 + i];
-      shv[na + i] = VB[ib0 + i];
-    }
-    __syncthreads();
-    // each thread merges MERGE_ITEMS outputs from its own diagonal
-    const int d = threadIdx.x * MERGE_ITEMS;
-    const int nout = na + nb;
-    if (d < nout) {
-      int lo2 = max(0, d - nb), hi2 = min(d, na);
-      while (lo2 < hi2) {
-        const int i = (lo2 + hi2) >> 1;
-        if (before(shk[na + d - 1 - i], shv[na + d - 1 - i], shk[i], shv[i])) hi2 = i;
-        else lo2 = i + 1;
+  const int t = threadIdx.x;
+  // issue the copies of chunk c into buffer b (an empty group when inactive)
+  auto stage = [&](int64_t c, int b) -> MergeChunk {
+    MergeChunk m;
+    m.active = false;
+    if (c < total) m = merge_chunk(seg_off, list, chunk_prefix, nlong, L, split, c);
+    if (m.active) {
+      const uint64_t* KA = sk + m.base + m.ia0;
+      const int32_t* VA = sv + m.base + m.ia0;
+      const uint64_t* KB = sk + m.base + m.ib0;
+      const int32_t* VB = sv + m.base + m.ib0;
+      for (int i = t; i < m.na; i += MERGE_T) {
+        cp_async8(&ink[b][i], KA + i);
+        cp_async4(&inv[b][i], VA + i);
       }
-      int ia = lo2, ib = d - lo2;
-      for (int t = 0; t < MERGE_ITEMS && d + t < nout; ++t) {
-        bool take_a;
-        if (ia >= na) take_a = false;
-        else if (ib >= nb) take_a = true;
-        else take_a = !before(shk[na + ib], shv[na + ib], shk[ia], shv[ia]);
-        if (take_a) { ok_[d + t] = shk[ia]; ov_[d + t] = shv[ia]; ++ia; }
-        else { ok_[d + t] = shk[na + ib]; ov_[d + t] = shv[na + ib]; ++ib; }
+      for (int i = t; i < m.nb; i += MERGE_T) {
+        cp_async8(&ink[b][m.na + i], KB + i);
+        cp_async4(&inv[b][m.na + i], VB + i);
       }
     }
+    cp_async_commit();
+    return m;
+  };
+  int64_t c = blockIdx.x;
+  int b = 0;
+  MergeChunk cur = stage(c, b);
+  for (; c < total; c += gridDim.x) {
+    const MergeChunk nxt = stage(c + gridDim.x, b ^ 1);
+    cp_async_wait<1>();  // the current chunk's copies have landed
     __syncthreads();
-    const int64_t out = base + o0;
-    for (int i = threadIdx.x; i < nout; i += MERGE_T) { dk[out + i] = ok_[i]; dv[out + i] = ov_[i]; }
-    __syncthreads();
+    if (cur.active) {
+      const uint64_t* shk = ink[b];
+      const int32_t* shv = inv[b];
+      const int na = cur.na, nb = cur.nb, nout = na + nb;
+      // each thread merges MERGE_ITEMS outputs from its own diagonal
+      const int d = t * MERGE_ITEMS;
+      if (d < nout) {
+        int lo2 = max(0, d - nb), hi2 = min(d, na);
+        while (lo2 < hi2) {
+          const int i = (lo2 + hi2) >> 1;
+          if (before(shk[na + d - 1 - i], shv[na + d - 1 - i], shk[i], shv[i])) hi2 = i;
+          else lo2 = i + 1;
+        }
+        int ia = lo2, ib = d - lo2;
+        for (int q = 0; q < MERGE_ITEMS && d + q < nout; ++q) {
+          bool take_a;
+          if (ia >= na) take_a = false;
+          else if (ib >= nb) take_a = true;
+          else take_a = !before(shk[na + ib], shv[na + ib], shk[ia], shv[ia]);
+          if (take_a) { ok_[d + q] = shk[ia]; ov_[d + q] = shv[ia]; ++ia; }
+          else { ok_[d + q] = shk[na + ib]; ov_[d + q] = shv[na + ib]; ++ib; }
+        }
+      }
+      __syncthreads();
+      const int64_t out = cur.base + cur.o0;
+      for (int i = t; i < nout; i += MERGE_T) { dk[out + i] = ok_[i]; dv[out + i] = ov_[i]; }
+    }
+    __syncthreads();  // buffer b and the staging area are free again
+    cur = nxt;
+    b ^= 1;
   }
+  cp_async_wait<0>();
 }
 
 // Long segments that took an odd number of passes end in the scratch buffer:
@@ -519,8 +592,13 @@ int segmented_sort_desc(uint64_t* key, int32_t* val, const int64_t* seg_off, int
   GS_CUDA(cudaFuncSetAttribute(k_sort_tile<512, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)tile_smem_bytes<512>()));
   if (hc[2]) {
-    k_sort_tile<128, false><<<grid_of((int64_t)hc[2], 1), 128, tile_smem_bytes<128>(), s>>>(
-        key, val, seg_off, list + base[2], counts + 2, nullptr, 0);
+    if (GS_SORT_WARP_BIG) {
+      k_sort_warp_big<<<grid_of((int64_t)hc[2], 4), 128, 0, s>>>(key, val, seg_off, list + base[2],
+                                                                  counts + 2);
+    } else {
+      k_sort_tile<128, false><<<grid_of((int64_t)hc[2], 1), 128, tile_smem_bytes<128>(), s>>>(
+          key, val, seg_off, list + base[2], counts + 2, nullptr, 0);
+    }
     GS_LAUNCH();
   }
   if (hc[3]) {

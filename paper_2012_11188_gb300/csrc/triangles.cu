@@ -25,8 +25,12 @@ namespace {
 #define GS_TRI_ROUNDS 4  // 32-element rounds of loads in flight per warp in the counting loop
 #endif
 #ifndef GS_TRI_FAST_ROUNDS
-#define GS_TRI_FAST_ROUNDS 8  // the same for batches of rounds that lie inside one list
+#define GS_TRI_FAST_ROUNDS 8  // the same for out-lists streamed one at a time
 #endif
+#ifndef GS_TRI_LONG_LIST
+#define GS_TRI_LONG_LIST 128  // out-lists at least this long are streamed one at a time
+#endif
+constexpr int LONG_LIST = GS_TRI_LONG_LIST;
 
 constexpr int TRI_THREADS = 512;
 constexpr int TRI_WARPS = TRI_THREADS / 32;
@@ -66,6 +70,39 @@ __global__ void k_item_counts(const int32_t* __restrict__ odeg, const int32_t* _
     if (!warp_vertex(d, od) && d - od > 0) c = (int)((d + CHUNK - 1) / CHUNK);
     items[v] = c;
   }
+}
+
+// Order in which the CTA kernel takes its vertices: non-increasing degree.
+// In-neighbours are shared far more among vertices of similar (high) degree
+// than among vertices of consecutive ids, so their out-lists and counters
+// are re-read from L2 instead of DRAM. bin(v) = maxdeg - d_v for vertices
+// with items; equal degrees come in any order (the counts are sums).
+__global__ void k_item_hist(const int32_t* __restrict__ items, const int32_t* __restrict__ deg,
+                            int64_t n, int32_t maxdeg, unsigned long long* __restrict__ hist) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    if (items[v] > 0) atomicAdd(&hist[maxdeg - deg[v]], 1ull);
+}
+
+__global__ void k_item_place(const int32_t* __restrict__ items, const int32_t* __restrict__ deg,
+                             int64_t n, int32_t maxdeg, const int64_t* __restrict__ start,
+                             unsigned long long* __restrict__ fill, int32_t* __restrict__ order) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    if (items[v] > 0) {
+      const int64_t b = maxdeg - deg[v];
+      order[start[b] + (int64_t)atomicAdd(&fill[b], 1ull)] = (int32_t)v;
+    }
+}
+
+// items of the i-th vertex of the order (0 past the placed vertices)
+__global__ void k_item_gather(const int32_t* __restrict__ items, const int32_t* __restrict__ order,
+                              const int64_t* __restrict__ start, int32_t maxdeg, int64_t n,
+                              int32_t* __restrict__ items_sorted) {
+  const int64_t placed = start[maxdeg + 1];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    items_sorted[i] = i < placed ? items[order[i]] : 0;
 }
 
 __device__ __forceinline__ int64_t find_item_vertex(const int64_t* item_off, int64_t n,
@@ -200,20 +237,35 @@ struct SliceSmem {
   long long* jv;
 };
 
+// One probe of the stream element x at position j of out(u): a hit w = x
+// adds one to (v,w) in vcnt (shared; global for BIG) and to (u,w) at j.
+template <bool BIG, typename IT>
+__device__ __forceinline__ bool probe(const OutTable& tab, int32_t x, IT j, int64_t ob,
+                                      uint32_t* vcnt, uint32_t* __restrict__ tcnt) {
+  const int q = table_lookup<BIG>(tab, x);
+  if (q < 0) return false;
+  if (!BIG) atomicAdd(&vcnt[q], 1u);
+  else atomicAdd(&tcnt[ob + q], 1u);
+  atomicAdd(&tcnt[j], 1u);
+  return true;
+}
+
 // One warp: triangles u < v < w for the in-neighbours u of v among the CSR
 // positions [p0, min(p0+32, p_end)) of N(v). The in-neighbours are compacted
-// to lanes 0..k-1, their out-list lengths prefix-summed, and the concatenated
-// lists walked 32 elements per round (lane l takes element r*32+l, four rounds
-// of loads in flight); the owner of an element comes from the starts that fall
-// in its round (ballot / or-reduce / popc). A hit w adds one to (v,w) in vcnt
-// (shared; global for BIG), to (u,w) at its slot of out(u), and to (u,v).
+// to lanes 0..k-1. Out-lists of at least LONG_LIST entries are streamed one
+// at a time, lane l taking elements l, l+32, ... (RF rounds of loads in
+// flight); the shorter ones are concatenated and walked 32 elements per round
+// (R rounds in flight), the owner of an element coming from the list starts
+// that fall in its round (ballot / or-reduce / popc). Hits on (u,v) are
+// counted per list; the position of v in out(u) is found in the stream.
 template <bool BIG, typename IT>
 __device__ __forceinline__ void process_slice(
     int64_t p0, int64_t p_end, int64_t rb, int32_t v, int32_t dv, int32_t od, int64_t ob,
     const int32_t* __restrict__ adj, const int32_t* __restrict__ deg,
     const int64_t* __restrict__ off, const int32_t* __restrict__ odeg,
-    const int32_t* __restrict__ oadj, int lsh_T, const OutTable& tab, uint32_t* vcnt, const SliceSmem& sm, uint32_t* __restrict__ tcnt,
-    int32_t* __restrict__ twin_rel, unsigned& bad) {
+    const int32_t* __restrict__ oadj, int lsh_T, const OutTable& tab, uint32_t* vcnt,
+    const SliceSmem& sm, uint32_t* __restrict__ tcnt, int32_t* __restrict__ twin_rel,
+    unsigned& bad) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int64_t p = p0 + lane;
@@ -258,128 +310,92 @@ __device__ __forceinline__ void process_slice(
     __syncwarp();
     return;
   }
-  int32_t incl = clen;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int32_t y = __shfl_up_sync(FULL, incl, o);
-    if (lane >= o) incl += y;
-  }
-  const int32_t cstart = incl - clen;
-  const int32_t W = __shfl_sync(FULL, incl, 31);
   sm.acc[lane] = 0;
   sm.jv[lane] = -1;
   __syncwarp();
-  constexpr int R = GS_TRI_ROUNDS;  // rounds whose loads are issued before any probe
-  int run_own = 0;
-  uint32_t run_acc = 0;
-  // the list holding element r0 (warp-uniform); a round that lies inside one
-  // list needs no owner search
-  int cur = 0;
-  int32_t cur_start = 0;
-  int32_t cur_end = __shfl_sync(FULL, incl, 0);
-  IT cur_ub = __shfl_sync(FULL, cub, 0);
+
+  // 1. long out-lists, one at a time
   constexpr int RF = GS_TRI_FAST_ROUNDS;
-  for (int32_t rbase = 0; rbase < W;) {
-    if (rbase >= cur_end) {
-      cur = __popc(__ballot_sync(FULL, lane < k && cstart <= rbase)) - 1;
-      cur_start = __shfl_sync(FULL, cstart, cur);
-      cur_end = __shfl_sync(FULL, incl, cur);
-      cur_ub = __shfl_sync(FULL, cub, cur);
-    }
-    if (rbase + 32 * RF <= cur_end) {
-      // fast batch: all RF rounds inside list `cur`
-      const IT jb = cur_ub + (IT)(rbase - cur_start + lane);
+  unsigned lm = __ballot_sync(FULL, lane < k && clen >= LONG_LIST);
+  while (lm) {
+    const int i = __ffs(lm) - 1;
+    lm &= lm - 1;
+    const IT ub = __shfl_sync(FULL, cub, i);
+    const int32_t len = __shfl_sync(FULL, clen, i);
+    uint32_t hits = 0;
+    for (int32_t t0 = 0; t0 < len; t0 += 32 * RF) {
       int32_t xs[RF];
 #pragma unroll
-      for (int rr = 0; rr < RF; ++rr) xs[rr] = oadj[jb + (IT)(32 * rr)];
-      uint32_t hits = 0;
+      for (int rr = 0; rr < RF; ++rr) {
+        const int32_t t = t0 + 32 * rr + lane;
+        xs[rr] = t < len ? oadj[ub + (IT)t] : -1;  // -1: never in a table
+      }
 #pragma unroll
       for (int rr = 0; rr < RF; ++rr) {
-        const int32_t x = xs[rr];
-        const IT j = jb + (IT)(32 * rr);
-        if (x == v) sm.jv[cur] = j;
-        const int q = table_lookup<BIG>(tab, x);
-        const bool hit = q >= 0;
-        if (hit) {
-          if (!BIG) atomicAdd(&vcnt[q], 1u);
-          else atomicAdd(&tcnt[ob + q], 1u);
-          atomicAdd(&tcnt[j], 1u);
-        }
+        if (t0 + 32 * rr >= len) break;
+        const IT j = ub + (IT)(t0 + 32 * rr + lane);
+        if (xs[rr] == v) sm.jv[i] = j;
+        const bool hit = probe<BIG, IT>(tab, xs[rr], j, ob, vcnt, tcnt);
         hits += __popc(__ballot_sync(FULL, hit));
       }
-      if (cur != run_own) {
-        if (lane == 0 && run_acc) sm.acc[run_own] += run_acc;
-        run_own = cur;
-        run_acc = 0;
-      }
-      run_acc += hits;
-      rbase += 32 * RF;
-      continue;
     }
-    int32_t xs[R];
-    IT js[R];
-    int owns[R];
-    bool single[R];
+    if (lane == 0) sm.acc[i] += hits;
+  }
+
+  // 2. short out-lists, concatenated: lane r takes the r-th short list
+  const bool is_short = lane < k && clen < LONG_LIST;
+  const unsigned shm = __ballot_sync(FULL, is_short);
+  if (shm) {
+    const int k2 = __popc(shm);
+    if (is_short) sm.u[__popc(shm & ((1u << lane) - 1u))] = lane;
+    __syncwarp();
+    const int orig = lane < k2 ? sm.u[lane] : 0;  // index of the list among the k
+    const IT sub = __shfl_sync(FULL, cub, orig);
+    const int32_t sl = __shfl_sync(FULL, clen, orig);
+    const int32_t slen = lane < k2 ? sl : 0;
+    int32_t incl = slen;
 #pragma unroll
-    for (int rr = 0; rr < R; ++rr) {
-      const int32_t r0 = rbase + 32 * rr;
-      if (r0 >= cur_end && r0 < W) {
-        cur = __popc(__ballot_sync(FULL, lane < k && cstart <= r0)) - 1;
-        cur_start = __shfl_sync(FULL, cstart, cur);
-        cur_end = __shfl_sync(FULL, incl, cur);
-        cur_ub = __shfl_sync(FULL, cub, cur);
-      }
-      const int32_t t = r0 + lane;
-      if (r0 + 32 <= cur_end) {
-        single[rr] = true;
-        owns[rr] = cur;
-        js[rr] = cur_ub + (IT)(t - cur_start);
-      } else {
-        single[rr] = false;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t y = __shfl_up_sync(FULL, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int32_t cstart = incl - slen;
+    const int32_t W = __shfl_sync(FULL, incl, 31);
+    constexpr int R = GS_TRI_ROUNDS;
+    for (int32_t rbase = 0; rbase < W; rbase += 32 * R) {
+      int32_t xs[R];
+      IT js[R];
+      int owns[R];
+#pragma unroll
+      for (int rr = 0; rr < R; ++rr) {
+        const int32_t r0 = rbase + 32 * rr;
+        const int32_t t = r0 + lane;
         // every list is non-empty (v is in out(u)), so the starts are distinct
-        const bool starts_here = lane < k && cstart >= r0 && cstart < r0 + 32;
+        const bool starts_here = lane < k2 && cstart >= r0 && cstart < r0 + 32;
         const unsigned smask = __reduce_or_sync(FULL, starts_here ? (1u << (cstart - r0)) : 0u);
-        const int before = __popc(__ballot_sync(FULL, lane < k && cstart < r0));
+        const int before = __popc(__ballot_sync(FULL, lane < k2 && cstart < r0));
         const int owner = before + __popc(smask & ((2u << lane) - 1u)) - 1;
         const int own = owner < 0 ? 0 : owner;
-        const IT ub_o = __shfl_sync(FULL, cub, own);
+        const IT ub_o = __shfl_sync(FULL, sub, own);
         const int32_t st_o = __shfl_sync(FULL, cstart, own);
-        owns[rr] = own;
+        owns[rr] = __shfl_sync(FULL, orig, own);
         js[rr] = t < W ? ub_o + (IT)(t - st_o) : (IT)-1;
+        xs[rr] = t < W ? oadj[js[rr]] : -1;
       }
-      xs[rr] = js[rr] >= 0 ? oadj[js[rr]] : -1;
-    }
 #pragma unroll
-    for (int rr = 0; rr < R; ++rr) {
-      const int32_t x = xs[rr];  // -1 past the end: never in a table
-      const IT j = js[rr];
-      const int own = owns[rr];
-      if (x == v) sm.jv[own] = j;
-      const int q = table_lookup<BIG>(tab, x);
-      const bool hit = q >= 0;
-      if (hit) {
-        if (!BIG) atomicAdd(&vcnt[q], 1u);
-        else atomicAdd(&tcnt[ob + q], 1u);
-        atomicAdd(&tcnt[j], 1u);
-      }
-      const unsigned hm = __ballot_sync(FULL, hit);
-      if (single[rr]) {
-        // (u,v) hits of a run of rounds inside one list stay in a register
-        if (own != run_own) {
-          if (lane == 0 && run_acc) sm.acc[run_own] += run_acc;
-          run_own = own;
-          run_acc = 0;
+      for (int rr = 0; rr < R; ++rr) {
+        const int own = owns[rr];
+        if (xs[rr] == v) sm.jv[own] = js[rr];
+        const bool hit = probe<BIG, IT>(tab, xs[rr], js[rr], ob, vcnt, tcnt);
+        const unsigned hm = __ballot_sync(FULL, hit);
+        if (hm) {
+          // lanes of one owner are contiguous; its first lane adds
+          const unsigned peers = __match_any_sync(FULL, own);
+          if ((hm & peers) && lane == __ffs(peers) - 1) sm.acc[own] += __popc(hm & peers);
         }
-        run_acc += __popc(hm);
-      } else if (hm) {
-        // lanes of one owner are contiguous; its first lane adds
-        const unsigned peers = __match_any_sync(FULL, own);
-        if ((hm & peers) && lane == __ffs(peers) - 1) sm.acc[own] += __popc(hm & peers);
       }
     }
-    rbase += 32 * R;
   }
-  if (lane == 0 && run_acc) sm.acc[run_own] += run_acc;
   __syncwarp();
   if (lane < k) {
     const long long jv = sm.jv[lane];
@@ -402,7 +418,8 @@ __global__ void __launch_bounds__(TRI_THREADS, 3)
 k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
             const int32_t* __restrict__ deg, const int32_t* __restrict__ odeg,
             const int32_t* __restrict__ oadj, int64_t n, const int64_t* __restrict__ item_off,
-            unsigned long long* __restrict__ work, int lsh_T, int od_cap,
+            const int32_t* __restrict__ order, unsigned long long* __restrict__ work, int lsh_T,
+            int od_cap,
             uint32_t* __restrict__ tcnt, int32_t* __restrict__ twin_rel, unsigned* status) {
   // shared layout for od_cap (a power of two >= every od handled here) and
   // Lc = table_log2(od_cap): t0[2^Lc] | t1[2^Lc] | vcnt[od_cap]
@@ -431,8 +448,9 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
     __syncthreads();
     const int64_t item = s_item;
     if (item >= total) break;
-    const int64_t v = find_item_vertex(item_off, n, item);
-    const int64_t chunk = item - item_off[v];
+    const int64_t idx = find_item_vertex(item_off, n, item);
+    const int64_t v = order[idx];
+    const int64_t chunk = item - item_off[idx];
     const int32_t dv = deg[v];
     const int64_t ob = off[v];
     const int32_t od = odeg[v];
@@ -571,7 +589,7 @@ __global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v) {
 // graph has fewer than 2^31 arcs, which halves the index arithmetic).
 template <typename IT>
 int launch_counting(const int64_t* off, const int32_t* adj, const int32_t* deg, const int32_t* odeg,
-                    const int32_t* oadj, int64_t n, const int64_t* item_off,
+                    const int32_t* oadj, int64_t n, const int64_t* item_off, const int32_t* order,
                     unsigned long long* work, int lsh_T, int32_t max_od, uint32_t* tcnt,
                     int32_t* twin, unsigned* status, cudaStream_t s) {
   int od_cap = 16;
@@ -588,7 +606,7 @@ int launch_counting(const int64_t* off, const int32_t* adj, const int32_t* deg, 
                                                         TRI_THREADS, smem));
   if (per_sm < 1) per_sm = 1;
   k_triangles<false, IT><<<sms * per_sm, TRI_THREADS, smem, s>>>(
-      off, adj, deg, odeg, oadj, n, item_off, work, lsh_T, od_cap, tcnt, twin, status);
+      off, adj, deg, odeg, oadj, n, item_off, order, work, lsh_T, od_cap, tcnt, twin, status);
   GS_LAUNCH();
   int small_per_sm = 1;
   GS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&small_per_sm, k_tri_small<IT>,
@@ -599,7 +617,8 @@ int launch_counting(const int64_t* off, const int32_t* adj, const int32_t* deg, 
   GS_LAUNCH();
   if (max_od > SMEM_OD_MAX) {
     k_triangles<true, IT><<<sms * 4, TRI_THREADS, 0, s>>>(off, adj, deg, odeg, oadj, n, item_off,
-                                                          work + 1, lsh_T, 0, tcnt, twin, status);
+                                                          order, work + 1, lsh_T, 0, tcnt, twin,
+                                                          status);
     GS_LAUNCH();
   }
   return SCAN_OK;
@@ -607,39 +626,54 @@ int launch_counting(const int64_t* off, const int32_t* adj, const int32_t* deg, 
 
 int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* adj,
                                   const int32_t* deg, int64_t n, int64_t arcs, const int32_t* odeg,
-                                  const int32_t* oadj, const int32_t* opos, int32_t max_od,
-                                  int lsh_T, double* sim_csr, unsigned* status, Pool& pool,
-                                  cudaStream_t s, float* count_ms) {
+                                  const int32_t* oadj, const int32_t* opos, int32_t maxdeg,
+                                  int32_t max_od, int lsh_T, double* sim_csr, unsigned* status,
+                                  Pool& pool, cudaStream_t s, float* count_ms) {
   const int64_t m = arcs;  // out-lists live in CSR slots: counts and twins are indexed by arc
+  const int64_t nbins = (int64_t)maxdeg + 1;
   uint32_t* tcnt = pool.get<uint32_t>(m);
   int32_t* twin = pool.get<int32_t>(m);
   int32_t* items = pool.get<int32_t>(n);
+  int32_t* items_sorted = pool.get<int32_t>(n);
+  int32_t* order = pool.get<int32_t>(n);
   int64_t* item_off = pool.get<int64_t>(n + 1);
+  unsigned long long* hist = pool.get<unsigned long long>(2 * nbins);  // counts | fill cursors
+  int64_t* start = pool.get<int64_t>(nbins + 1);
   unsigned long long* work = pool.get<unsigned long long>(3);
-  if (!tcnt || !twin || !items || !item_off || !work) return SCAN_ENOMEM;
+  if (!tcnt || !twin || !items || !items_sorted || !order || !item_off || !hist || !start ||
+      !work)
+    return SCAN_ENOMEM;
   GS_CUDA(cudaMemsetAsync(tcnt, 0, m * sizeof(uint32_t), s));
   GS_CUDA(cudaMemsetAsync(work, 0, 3 * sizeof(unsigned long long), s));
+  GS_CUDA(cudaMemsetAsync(hist, 0, 2 * nbins * sizeof(unsigned long long), s));
   if (m > 0) {
     k_fill_i32<<<1024, 256, 0, s>>>(twin, m, -1);
     GS_LAUNCH();
   }
   if (n > 0) {
-    k_item_counts<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 64), 256, 0, s>>>(
-        odeg, deg, n, items);
+    const unsigned g = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 64);
+    k_item_counts<<<g, 256, 0, s>>>(odeg, deg, n, items);
+    GS_LAUNCH();
+    k_item_hist<<<g, 256, 0, s>>>(items, deg, n, maxdeg, hist);
+    GS_LAUNCH();
+    GS_TRY(exclusive_scan_i64(reinterpret_cast<const int64_t*>(hist), start, nbins, pool, s));
+    k_item_place<<<g, 256, 0, s>>>(items, deg, n, maxdeg, start, hist + nbins, order);
+    GS_LAUNCH();
+    k_item_gather<<<g, 256, 0, s>>>(items, order, start, maxdeg, n, items_sorted);
     GS_LAUNCH();
   }
-  GS_TRY(exclusive_scan_i32_to_i64(items, item_off, n, pool, s));
+  GS_TRY(exclusive_scan_i32_to_i64(items_sorted, item_off, n, pool, s));
   cudaEvent_t e0, e1;
   GS_CUDA(cudaEventCreate(&e0));
   GS_CUDA(cudaEventCreate(&e1));
   GS_CUDA(cudaEventRecord(e0, s));
   if (n > 0 && m > 0) {
     if (m < ((int64_t)1 << 31) - 1) {
-      GS_TRY(launch_counting<int32_t>(off, adj, deg, odeg, oadj, n, item_off, work, lsh_T, max_od,
-                                      tcnt, twin, status, s));
+      GS_TRY(launch_counting<int32_t>(off, adj, deg, odeg, oadj, n, item_off, order, work, lsh_T,
+                                      max_od, tcnt, twin, status, s));
     } else {
-      GS_TRY(launch_counting<int64_t>(off, adj, deg, odeg, oadj, n, item_off, work, lsh_T, max_od,
-                                      tcnt, twin, status, s));
+      GS_TRY(launch_counting<int64_t>(off, adj, deg, odeg, oadj, n, item_off, order, work, lsh_T,
+                                      max_od, tcnt, twin, status, s));
     }
   }
   GS_CUDA(cudaEventRecord(e1, s));
@@ -657,6 +691,10 @@ int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* a
   pool.put(tcnt);
   pool.put(twin);
   pool.put(items);
+  pool.put(items_sorted);
+  pool.put(order);
+  pool.put(hist);
+  pool.put(start);
   pool.put(item_off);
   pool.put(work);
   return SCAN_OK;
