@@ -191,37 +191,20 @@ k_sort_warp_reg(uint64_t* __restrict__ key, int32_t* __restrict__ val,
   }
 }
 
-#ifndef GS_SORT_WARP_BIG
-#define GS_SORT_WARP_BIG 0  // 1: segments of 257..1024 elements sorted by one warp in registers
-#endif
+// Shared-memory slot of tile element i: one pad slot per 8 elements, so that
+// a warp whose lanes hold 8 consecutive elements each (lane l: 8l .. 8l+7)
+// touches distinct banks when it stores or loads them.
+__device__ __forceinline__ int pslot(int i) { return i + (i >> 3); }
 
-// One warp per segment of 257..1024 elements: 16 or 32 elements per lane in
-// registers, no shared memory and no barrier.
-__global__ void __launch_bounds__(128)
-k_sort_warp_big(uint64_t* __restrict__ key, int32_t* __restrict__ val,
-                const int64_t* __restrict__ seg_off, const int64_t* __restrict__ list,
-                const unsigned long long* __restrict__ count_ptr) {
-  const int lane = threadIdx.x & 31;
-  const int64_t cnt = (int64_t)*count_ptr;
-  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t u = w0; u < cnt; u += nw) {
-    const int64_t sg = list[u];
-    const int64_t b = seg_off[sg];
-    const int64_t len = seg_off[sg + 1] - b;
-    if (len <= 512) warp_sort_range<16>(key, val, b, len, lane);
-    else warp_sort_range<32>(key, val, b, len, lane);
-  }
-}
-
-// Merge path inside shared memory: elements of A (length la) among the first
-// d outputs of merge(A, B).
-__device__ __forceinline__ int smem_merge_path(const uint64_t* ka, const int32_t* va, int la,
-                                               const uint64_t* kb, const int32_t* vb, int lb, int d) {
+// Merge path over padded shared runs: elements of A = [a0, a0+la) among the
+// first d outputs of merge(A, B), B = [b0, b0+lb).
+__device__ __forceinline__ int smem_merge_path_p(const uint64_t* k, const int32_t* v, int a0,
+                                                 int la, int b0, int lb, int d) {
   int lo = max(0, d - lb), hi = min(d, la);
   while (lo < hi) {
     const int i = (lo + hi) >> 1;
-    if (before(kb[d - 1 - i], vb[d - 1 - i], ka[i], va[i])) hi = i;
+    const int pb = pslot(b0 + d - 1 - i), pa = pslot(a0 + i);
+    if (before(k[pb], v[pb], k[pa], v[pa])) hi = i;
     else lo = i + 1;
   }
   return lo;
@@ -233,17 +216,18 @@ __device__ __forceinline__ int smem_merge_path(const uint64_t* ka, const int32_t
 // SE, each thread writing 8 outputs. Tiles are whole segments (TILED = false)
 // or TILE-element pieces of longer segments (TILED = true, TT*8 = TILE).
 template <int TT, bool TILED>
-__global__ void __launch_bounds__(TT)
+__global__ void __launch_bounds__(TT, 1024 / TT)
 k_sort_tile(uint64_t* __restrict__ key, int32_t* __restrict__ val,
             const int64_t* __restrict__ seg_off, const int64_t* __restrict__ list,
             const unsigned long long* __restrict__ count_ptr,
             const int64_t* __restrict__ tile_prefix, int64_t nlong) {
   constexpr int CAP = TT * 8;
+  constexpr int PCAP = CAP + CAP / 8;  // padded slots per buffer
   extern __shared__ uint64_t tsm[];
   uint64_t* k0 = tsm;
-  uint64_t* k1 = tsm + CAP;
-  int32_t* v0 = (int32_t*)(tsm + 2 * CAP);
-  int32_t* v1 = v0 + CAP;
+  uint64_t* k1 = tsm + PCAP;
+  int32_t* v0 = (int32_t*)(tsm + 2 * PCAP);
+  int32_t* v1 = v0 + PCAP;
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   const int64_t cnt = (int64_t)*count_ptr;
   for (int64_t u = blockIdx.x; u < cnt; u += gridDim.x) {
@@ -277,7 +261,7 @@ k_sort_tile(uint64_t* __restrict__ key, int32_t* __restrict__ val,
       warp_sort_reg<8>(K, V, lane);
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
-        const int i = wid * WTILE + 8 * lane + r;
+        const int i = pslot(wid * WTILE + 8 * lane + r);
         k0[i] = K[r];
         v0[i] = V[r];
       }
@@ -289,36 +273,39 @@ k_sort_tile(uint64_t* __restrict__ key, int32_t* __restrict__ val,
     for (int w = WTILE; w < se; w <<= 1) {
       const int o = 8 * t;  // first output of this thread
       if (o < se) {
-        const int p0 = (o / (2 * w)) * (2 * w);
-        const uint64_t* KA = ks + p0;
-        const int32_t* VA = vs + p0;
-        const uint64_t* KB = ks + p0 + w;
-        const int32_t* VB = vs + p0 + w;
-        const int d = o - p0;
-        int ia = smem_merge_path(KA, VA, w, KB, VB, w, d);
+        const int a0 = (o / (2 * w)) * (2 * w);
+        const int b0 = a0 + w;
+        const int d = o - a0;
+        int ia = smem_merge_path_p(ks, vs, a0, w, b0, w, d);
         int ib = d - ia;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           bool take_a;
+          const int pa = pslot(a0 + ia), pb = pslot(b0 + ib);
           if (ia >= w) take_a = false;
           else if (ib >= w) take_a = true;
-          else take_a = !before(KB[ib], VB[ib], KA[ia], VA[ia]);
-          if (take_a) { kd[o + q] = KA[ia]; vd[o + q] = VA[ia]; ++ia; }
-          else { kd[o + q] = KB[ib]; vd[o + q] = VB[ib]; ++ib; }
+          else take_a = !before(ks[pb], vs[pb], ks[pa], vs[pa]);
+          const int po = pslot(o + q);
+          if (take_a) { kd[po] = ks[pa]; vd[po] = vs[pa]; ++ia; }
+          else { kd[po] = ks[pb]; vd[po] = vs[pb]; ++ib; }
         }
       }
       __syncthreads();
       uint64_t* tk = ks; ks = kd; kd = tk;
       int32_t* tv = vs; vs = vd; vd = tv;
     }
-    for (int i = t; i < len; i += TT) { key[b + i] = ks[i]; val[b + i] = vs[i]; }
+    for (int i = t; i < len; i += TT) {
+      const int pi = pslot(i);
+      key[b + i] = ks[pi];
+      val[b + i] = vs[pi];
+    }
     __syncthreads();
   }
 }
 
 template <int TT>
 constexpr size_t tile_smem_bytes() {
-  return (size_t)TT * 8 * (2 * sizeof(uint64_t) + 2 * sizeof(int32_t));
+  return (size_t)(TT * 8 + TT) * (2 * sizeof(uint64_t) + 2 * sizeof(int32_t));
 }
 
 // Tiles per long segment (prefix computed by the caller).
@@ -460,10 +447,13 @@ k_merge_pass(const uint64_t* __restrict__ sk, const int32_t* __restrict__ sv,
              const int64_t* __restrict__ split) {
   __shared__ uint64_t ink[2][MERGE_CHUNK];
   __shared__ int32_t inv[2][MERGE_CHUNK];
-  __shared__ uint64_t ok_[MERGE_CHUNK];
-  __shared__ int32_t ov_[MERGE_CHUNK];
+  // output staging, one pad slot per MERGE_ITEMS (a thread's consecutive
+  // outputs) so that the lanes of a warp write distinct banks
+  __shared__ uint64_t ok_[MERGE_CHUNK + MERGE_CHUNK / MERGE_ITEMS];
+  __shared__ int32_t ov_[MERGE_CHUNK + MERGE_CHUNK / MERGE_ITEMS];
   const int64_t total = chunk_prefix[nlong];
   const int t = threadIdx.x;
+  auto po = [](int i) { return i + i / MERGE_ITEMS; };
   // issue the copies of chunk c into buffer b (an empty group when inactive)
   auto stage = [&](int64_t c, int b) -> MergeChunk {
     MergeChunk m;
@@ -512,13 +502,17 @@ k_merge_pass(const uint64_t* __restrict__ sk, const int32_t* __restrict__ sv,
           if (ia >= na) take_a = false;
           else if (ib >= nb) take_a = true;
           else take_a = !before(shk[na + ib], shv[na + ib], shk[ia], shv[ia]);
-          if (take_a) { ok_[d + q] = shk[ia]; ov_[d + q] = shv[ia]; ++ia; }
-          else { ok_[d + q] = shk[na + ib]; ov_[d + q] = shv[na + ib]; ++ib; }
+          const int pq = po(d + q);
+          if (take_a) { ok_[pq] = shk[ia]; ov_[pq] = shv[ia]; ++ia; }
+          else { ok_[pq] = shk[na + ib]; ov_[pq] = shv[na + ib]; ++ib; }
         }
       }
       __syncthreads();
       const int64_t out = cur.base + cur.o0;
-      for (int i = t; i < nout; i += MERGE_T) { dk[out + i] = ok_[i]; dv[out + i] = ov_[i]; }
+      for (int i = t; i < nout; i += MERGE_T) {
+        dk[out + i] = ok_[po(i)];
+        dv[out + i] = ov_[po(i)];
+      }
     }
     __syncthreads();  // buffer b and the staging area are free again
     cur = nxt;
@@ -592,13 +586,8 @@ int segmented_sort_desc(uint64_t* key, int32_t* val, const int64_t* seg_off, int
   GS_CUDA(cudaFuncSetAttribute(k_sort_tile<512, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)tile_smem_bytes<512>()));
   if (hc[2]) {
-    if (GS_SORT_WARP_BIG) {
-      k_sort_warp_big<<<grid_of((int64_t)hc[2], 4), 128, 0, s>>>(key, val, seg_off, list + base[2],
-                                                                  counts + 2);
-    } else {
-      k_sort_tile<128, false><<<grid_of((int64_t)hc[2], 1), 128, tile_smem_bytes<128>(), s>>>(
-          key, val, seg_off, list + base[2], counts + 2, nullptr, 0);
-    }
+    k_sort_tile<128, false><<<grid_of((int64_t)hc[2], 1), 128, tile_smem_bytes<128>(), s>>>(
+        key, val, seg_off, list + base[2], counts + 2, nullptr, 0);
     GS_LAUNCH();
   }
   if (hc[3]) {

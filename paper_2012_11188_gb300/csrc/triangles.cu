@@ -25,7 +25,7 @@ namespace {
 #define GS_TRI_ROUNDS 4  // 32-element rounds of loads in flight per warp in the counting loop
 #endif
 #ifndef GS_TRI_FAST_ROUNDS
-#define GS_TRI_FAST_ROUNDS 8  // the same for out-lists streamed one at a time
+#define GS_TRI_FAST_ROUNDS 12  // the same for out-lists streamed one at a time
 #endif
 #ifndef GS_TRI_LONG_LIST
 #define GS_TRI_LONG_LIST 128  // out-lists at least this long are streamed one at a time
