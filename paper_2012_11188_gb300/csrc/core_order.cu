@@ -77,13 +77,26 @@ __global__ void k_qtiles(Multi m, int64_t* __restrict__ qt) {
 // order among equal degrees is arbitrary; the final sort does not depend on it).
 __global__ void k_place(const int32_t* __restrict__ deg, int64_t N, Multi m,
                         unsigned long long* __restrict__ fill, int32_t* __restrict__ perm) {
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
-       v += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t d = deg[v];
-    if (d < 1) continue;
-    const int64_t g = m.G == 1 ? 0 : last_le(m.vb, m.G, v);
-    const int64_t pos = cum(m, g, d + 1) + (int64_t)atomicAdd(&fill[m.hb[g] + d], 1ull);
-    perm[m.vb[g] + pos] = (int32_t)v;
+  const int lane = threadIdx.x & 31;
+  // uniform trip count per warp, so that the lanes can aggregate their atomics
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t first = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+  for (int64_t v0 = first; v0 < N; v0 += stride) {
+    const int64_t v = v0 + lane;
+    const int32_t d = v < N ? deg[v] : 0;
+    const bool take = d >= 1;
+    const int64_t g = (!take || m.G == 1) ? 0 : last_le(m.vb, m.G, v);
+    const unsigned long long key = take ? (unsigned long long)(m.hb[g] + d) : ~0ull;
+    // lanes with the same (graph, degree) bin take consecutive slots with one atomic
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const int leader = __ffs(peers) - 1;
+    unsigned long long slot = 0;
+    if (take && lane == leader) slot = atomicAdd(&fill[key], (unsigned long long)__popc(peers));
+    slot = __shfl_sync(0xffffffffu, slot, leader);
+    if (take) {
+      const int64_t pos = cum(m, g, d + 1) + (int64_t)slot + __popc(peers & ((1u << lane) - 1u));
+      perm[m.vb[g] + pos] = (int32_t)v;
+    }
   }
 }
 

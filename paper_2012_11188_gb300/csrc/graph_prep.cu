@@ -138,12 +138,18 @@ __device__ __forceinline__ bool lower(int32_t du, int32_t u, int32_t dv, int32_t
 // Orientation in place: the out-arcs of v (neighbours of larger (degree, id))
 // are compacted, in id order, to the front of v's own CSR slot range, so
 // out(v) = oadj[off[v] .. off[v] + od[v]) needs no separate offsets; opos
-// holds each out-arc's position in the row. One warp per row.
+// holds each out-arc's position in the row. One warp per row; rows longer
+// than LONG_ROW are listed in long_rows for k_orient_long (a warp would walk
+// a hub's row of 10^5 entries alone).
+constexpr int LONG_ROW = 4096;
+constexpr int LONG_T = 1024;
+
 __global__ void k_orient_inplace(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
                                  const int32_t* __restrict__ deg, int64_t n,
                                  int32_t* __restrict__ od, int32_t* __restrict__ oadj,
                                  int32_t* __restrict__ opos, int32_t* max_od,
-                                 unsigned long long* sum_od) {
+                                 unsigned long long* sum_od, int32_t* __restrict__ long_rows,
+                                 unsigned* __restrict__ n_long) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -152,6 +158,10 @@ __global__ void k_orient_inplace(const int64_t* __restrict__ off, const int32_t*
   for (int64_t v = warp; v < n; v += nwarps) {
     const int64_t b = off[v], e = off[v + 1];
     const int32_t dv = deg[v];
+    if (dv > LONG_ROW) {
+      if (lane == 0) long_rows[atomicAdd(n_long, 1u)] = (int32_t)v;
+      continue;
+    }
     int64_t w = b;
     for (int64_t i0 = b; i0 < e; i0 += 32) {
       const int64_t i = i0 + lane;
@@ -173,6 +183,57 @@ __global__ void k_orient_inplace(const int64_t* __restrict__ off, const int32_t*
   if (lane == 0) {
     if (local_sum) atomicAdd(sum_od, local_sum);
     if (local_max) atomicMax(max_od, local_max);
+  }
+}
+
+// One CTA per listed long row: chunks of LONG_T positions, the out-arcs of a
+// chunk placed by a block-wide prefix count (ballots, then a scan of the 32
+// warp counts), so the out-list stays in id order.
+__global__ void __launch_bounds__(LONG_T)
+k_orient_long(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+              const int32_t* __restrict__ deg, const int32_t* __restrict__ long_rows,
+              const unsigned* __restrict__ n_long, int32_t* __restrict__ od,
+              int32_t* __restrict__ oadj, int32_t* __restrict__ opos, int32_t* max_od,
+              unsigned long long* sum_od) {
+  __shared__ int s_cnt[LONG_T / 32];
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  const unsigned cnt = *n_long;
+  for (unsigned r = blockIdx.x; r < cnt; r += gridDim.x) {
+    const int32_t v = long_rows[r];
+    const int64_t b = off[v], e = off[v + 1];
+    const int32_t dv = deg[v];
+    int64_t w = b;
+    for (int64_t i0 = b; i0 < e; i0 += LONG_T) {
+      const int64_t i = i0 + t;
+      bool up = false;
+      int32_t x = 0;
+      if (i < e) { x = adj[i]; up = lower(dv, v, deg[x], x); }
+      const unsigned m = __ballot_sync(0xffffffffu, up);
+      if (lane == 0) s_cnt[wid] = __popc(m);
+      __syncthreads();
+      // warp prefix over the 32 warp counts, computed by every warp
+      int c = s_cnt[lane];
+      int incl = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const int before = __shfl_sync(0xffffffffu, incl - c, wid);
+      const int total = __shfl_sync(0xffffffffu, incl, 31);
+      if (up) {
+        const int64_t dst = w + before + __popc(m & ((1u << lane) - 1u));
+        oadj[dst] = x;
+        opos[dst] = (int32_t)(i - b);
+      }
+      w += total;
+      __syncthreads();  // s_cnt is rewritten by the next chunk
+    }
+    if (t == 0) {
+      od[v] = (int32_t)(w - b);
+      atomicAdd(sum_od, (unsigned long long)(w - b));
+      atomicMax(max_od, (int32_t)(w - b));
+    }
   }
 }
 
@@ -209,12 +270,22 @@ int launch_orient(const int64_t* off, const int32_t* adj, const int32_t* deg, in
   int32_t* od = pool.get<int32_t>(n > 0 ? n : 1);
   int32_t* oadj = pool.get<int32_t>(arcs > 0 ? arcs : 1);
   int32_t* opos = pool.get<int32_t>(arcs > 0 ? arcs : 1);
-  if (!od || !oadj || !opos) return SCAN_ENOMEM;
+  // rows longer than LONG_ROW: at most arcs / LONG_ROW of them
+  const int64_t max_long = arcs / LONG_ROW + 1;
+  int32_t* long_rows = pool.get<int32_t>(max_long);
+  unsigned* n_long = pool.get<unsigned>(1);
+  if (!od || !oadj || !opos || !long_rows || !n_long) return SCAN_ENOMEM;
   if (n > 0) {
+    GS_CUDA(cudaMemsetAsync(n_long, 0, sizeof(unsigned), s));
     k_orient_inplace<<<grid_for(n, 8), 256, 0, s>>>(off, adj, deg, n, od, oadj, opos, max_od_dev,
-                                                    sum_od_dev);
+                                                    sum_od_dev, long_rows, n_long);
+    GS_LAUNCH();
+    k_orient_long<<<(unsigned)std::min<int64_t>(max_long, 152 * 2), LONG_T, 0, s>>>(
+        off, adj, deg, long_rows, n_long, od, oadj, opos, max_od_dev, sum_od_dev);
     GS_LAUNCH();
   }
+  pool.put(long_rows);
+  pool.put(n_long);
   *od_out = od;
   *oadj_out = oadj;
   *opos_out = opos;

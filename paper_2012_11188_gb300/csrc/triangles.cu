@@ -54,7 +54,7 @@ constexpr int SW_SLOTS = 2 * SMALL_OD;  // 2^table_log2(SMALL_OD) slots per tabl
 __host__ __device__ __forceinline__ bool warp_vertex(int64_t d, int64_t od) {
   return d <= WARP_DEG && od <= SMALL_OD;
 }
-constexpr int SW_WARPS = 8;
+constexpr int SW_WARPS = 4;
 
 // Work items of the CTA kernel: a vertex v not handled by a warp contributes
 // ceil(deg/CHUNK) items when it has in-neighbours (every in-arc needs the
@@ -120,14 +120,15 @@ __device__ __forceinline__ int64_t find_item_vertex(const int64_t* item_off, int
 // in the unlikely case that no cuckoo placement was found) binary search in
 // the sorted global list.
 //
-// Each table has 2^L slots of 32 bits; out(v) has at most 2^(L-1) entries,
-// so the load of the pair is at most 1/4. A key x hashes to h_i = x * C_i
-// (mod 2^32, a bijection for odd C_i); the slot is the top L bits of h_i and
-// the entry stores the remaining 32 - L bits of h_i (the tag) above the
-// (L-1)-bit position of x in out(v), with bit 31 clear. Slot and tag together
-// determine h_i and hence x, so a lookup is one load per table and an exact
-// compare, with no probing loop; an empty slot (all ones) never matches.
-constexpr uint32_t EMPTY_SLOT = 0xffffffffu;
+// Each table has 2^L slots; out(v) has at most 2^(L-1) entries, so the load
+// of the pair is at most 1/4. A key x hashes to h_i = x * C_i (mod 2^32, a
+// bijection for odd C_i); its slot is the top L bits of h_i, and the slot
+// stores h_i itself, so a probe is one load and one compare, with no probing
+// loop. The position of x in out(v) sits in a parallel 16-bit array read on
+// hits only. An empty slot of table i holds h_i(-1), which no vertex id
+// produces; stream lanes past the end of a list carry NO_KEY = -2, which
+// matches neither a key nor an empty slot.
+constexpr int32_t NO_KEY = -2;
 constexpr int CUCKOO_KICKS = 64;     // evictions before an insertion gives up
 constexpr int CUCKOO_ATTEMPTS = 4;   // multiplier pairs tried before binary search
 
@@ -141,14 +142,16 @@ __constant__ uint32_t CUCKOO_MUL[2 * CUCKOO_ATTEMPTS] = {
     0x9E3779B1u, 0x85EBCA77u, 0xC2B2AE3Du, 0x27D4EB2Fu,
     0x165667B1u, 0xD3A2646Du, 0xFD7046C5u, 0xB55A4F09u};
 
+// Table memory: t0[hcap] | t1[hcap] (uint32 keys) | p0[hcap] | p1[hcap]
+// (uint16 positions in out(v)), hcap a power of two >= 2^L.
 struct OutTable {
   const uint32_t* t0;
-  const uint32_t* t1;
-  int L;                 // log2 of the slots per table
+  int hcap;
+  int shift;             // 32 - L
   uint32_t c0, c1;       // multipliers of the two tables
   const int32_t* glist;  // out(v) in global memory (binary search)
   int32_t od;
-  bool bsearch;          // no cuckoo placement: search glist
+  bool bsearch;          // no cuckoo placement: the item needs the binary-search path
 };
 
 __device__ __forceinline__ int glist_search(const int32_t* list, int32_t od, int32_t x) {
@@ -162,31 +165,27 @@ __device__ __forceinline__ int glist_search(const int32_t* list, int32_t od, int
 
 template <bool BIG>
 __device__ __forceinline__ int table_lookup(const OutTable& t, int32_t x) {
-  if (BIG || t.bsearch) return glist_search(t.glist, t.od, x);
+  if (BIG) return glist_search(t.glist, t.od, x);
   const uint32_t h0 = (uint32_t)x * t.c0, h1 = (uint32_t)x * t.c1;
-  const uint32_t e0 = t.t0[h0 >> (32 - t.L)];
-  const uint32_t e1 = t.t1[h1 >> (32 - t.L)];
-  const uint32_t d0 = e0 ^ ((h0 << t.L) >> 1);
-  const uint32_t d1 = e1 ^ ((h1 << t.L) >> 1);
-  const uint32_t pmax = 1u << (t.L - 1);
-  return d0 < pmax ? (int)d0 : (d1 < pmax ? (int)d1 : -1);
+  const uint32_t s0 = h0 >> t.shift, s1 = (h1 >> t.shift) + t.hcap;  // slot in t0 / t1
+  const bool m0 = t.t0[s0] == h0, m1 = t.t0[s1] == h1;
+  const uint16_t* pos = reinterpret_cast<const uint16_t*>(t.t0 + 2 * t.hcap);
+  return (m0 || m1) ? (int)pos[m0 ? s0 : s1] : -1;
 }
 
-// Cuckoo insertion of (x, pos): place in table 0, move an evicted entry to
-// its slot in the other table, and so on. Returns false if an entry is still
+// Cuckoo insertion of key x: place h_0(x) in table 0; an evicted key moves
+// to its slot in the other table, and so on. Returns false if a key is still
 // homeless after CUCKOO_KICKS moves (the table must then be rebuilt).
-__device__ __forceinline__ bool cuckoo_insert(uint32_t* t0, uint32_t* t1, int L, uint32_t c0,
-                                              uint32_t c1, int32_t x, uint32_t pos) {
+__device__ __forceinline__ bool cuckoo_insert(uint32_t* t0, uint32_t* t1, int shift, uint32_t c0,
+                                              uint32_t c1, int32_t x) {
+  const uint32_t e0 = 0u - c0, e1 = 0u - c1;  // h_i(-1): empty slots
   const uint32_t i0 = mul_inverse(c0), i1 = mul_inverse(c1);
   int which = 0;
   for (int kick = 0; kick < CUCKOO_KICKS; ++kick) {
     const uint32_t h = (uint32_t)x * (which ? c1 : c0);
-    const uint32_t slot = h >> (32 - L);
-    const uint32_t old = atomicExch(&(which ? t1 : t0)[slot], ((h << L) >> 1) | pos);
-    if (old == EMPTY_SLOT) return true;
-    pos = old & ((1u << (L - 1)) - 1u);
-    const uint32_t hold = (slot << (32 - L)) | ((old << 1) >> L);
-    x = (int32_t)(hold * (which ? i1 : i0));
+    const uint32_t old = atomicExch(&(which ? t1 : t0)[h >> shift], h);
+    if (old == (which ? e1 : e0)) return true;
+    x = (int32_t)(old * (which ? i1 : i0));
     which ^= 1;
   }
   return false;
@@ -201,32 +200,46 @@ __device__ __forceinline__ int table_log2(int32_t od) {
 
 // Builds the table of out(v) = list[0..od) with `nthreads` threads (tid in
 // [0, nthreads)); `sync` is the group barrier and `any` its OR-reduction.
-// Returns the OutTable, with bsearch set if no attempt placed every entry.
+// Keys are placed first, then every key's position is written next to the
+// slot where it ended up. Returns the OutTable, with bsearch set if no
+// attempt placed every key.
 template <typename Sync, typename Any>
-__device__ __forceinline__ OutTable table_build(uint32_t* t0, uint32_t* t1, uint32_t* vcnt,
+__device__ __forceinline__ OutTable table_build(uint32_t* t0, int hcap, uint32_t* vcnt,
                                                 const int32_t* list, int32_t od, int tid,
                                                 int nthreads, Sync sync, Any any) {
+  uint32_t* t1 = t0 + hcap;
+  uint16_t* p0 = reinterpret_cast<uint16_t*>(t0 + 2 * hcap);
+  uint16_t* p1 = p0 + hcap;
   const int L = table_log2(od);
   const int H = 1 << L;
+  const int shift = 32 - L;
   int attempt = 0;
   bool failed = true;
+  uint32_t c0 = 0, c1 = 0;
   for (; attempt < CUCKOO_ATTEMPTS && failed; ++attempt) {
+    c0 = CUCKOO_MUL[2 * attempt];
+    c1 = CUCKOO_MUL[2 * attempt + 1];
     uint4* w0 = reinterpret_cast<uint4*>(t0);
     uint4* w1 = reinterpret_cast<uint4*>(t1);
-    const uint4 e4 = make_uint4(EMPTY_SLOT, EMPTY_SLOT, EMPTY_SLOT, EMPTY_SLOT);
-    for (int i = tid; i < H / 4; i += nthreads) { w0[i] = e4; w1[i] = e4; }
+    const uint32_t e0 = 0u - c0, e1 = 0u - c1;
+    for (int i = tid; i < H / 4; i += nthreads) {
+      w0[i] = make_uint4(e0, e0, e0, e0);
+      w1[i] = make_uint4(e1, e1, e1, e1);
+    }
     sync();
     bool ok = true;
-    const uint32_t c0 = CUCKOO_MUL[2 * attempt], c1 = CUCKOO_MUL[2 * attempt + 1];
-    for (int j = tid; j < od; j += nthreads)
-      ok &= cuckoo_insert(t0, t1, L, c0, c1, list[j], (uint32_t)j);
+    for (int j = tid; j < od; j += nthreads) ok &= cuckoo_insert(t0, t1, shift, c0, c1, list[j]);
     failed = any(!ok);
   }
+  if (!failed)
+    for (int j = tid; j < od; j += nthreads) {
+      const uint32_t h0 = (uint32_t)list[j] * c0;
+      if (t0[h0 >> shift] == h0) p0[h0 >> shift] = (uint16_t)j;
+      else p1[((uint32_t)list[j] * c1) >> shift] = (uint16_t)j;
+    }
   for (int i = tid; i < od; i += nthreads) vcnt[i] = 0;
   sync();
-  --attempt;
-  return OutTable{t0, t1, L, CUCKOO_MUL[2 * attempt], CUCKOO_MUL[2 * attempt + 1], list, od,
-                  failed};
+  return OutTable{t0, hcap, shift, c0, c1, list, od, failed};
 }
 
 // Per-warp scratch for one 32-position slice.
@@ -322,23 +335,23 @@ __device__ __forceinline__ void process_slice(
     lm &= lm - 1;
     const IT ub = __shfl_sync(FULL, cub, i);
     const int32_t len = __shfl_sync(FULL, clen, i);
-    uint32_t hits = 0;
+    unsigned hits = 0;  // this lane's hits on the list
     for (int32_t t0 = 0; t0 < len; t0 += 32 * RF) {
       int32_t xs[RF];
 #pragma unroll
       for (int rr = 0; rr < RF; ++rr) {
         const int32_t t = t0 + 32 * rr + lane;
-        xs[rr] = t < len ? oadj[ub + (IT)t] : -1;  // -1: never in a table
+        xs[rr] = t < len ? oadj[ub + (IT)t] : NO_KEY;
       }
 #pragma unroll
       for (int rr = 0; rr < RF; ++rr) {
         if (t0 + 32 * rr >= len) break;
         const IT j = ub + (IT)(t0 + 32 * rr + lane);
         if (xs[rr] == v) sm.jv[i] = j;
-        const bool hit = probe<BIG, IT>(tab, xs[rr], j, ob, vcnt, tcnt);
-        hits += __popc(__ballot_sync(FULL, hit));
+        hits += probe<BIG, IT>(tab, xs[rr], j, ob, vcnt, tcnt) ? 1u : 0u;
       }
     }
+    hits = __reduce_add_sync(FULL, hits);
     if (lane == 0) sm.acc[i] += hits;
   }
 
@@ -380,7 +393,7 @@ __device__ __forceinline__ void process_slice(
         const int32_t st_o = __shfl_sync(FULL, cstart, own);
         owns[rr] = __shfl_sync(FULL, orig, own);
         js[rr] = t < W ? ub_o + (IT)(t - st_o) : (IT)-1;
-        xs[rr] = t < W ? oadj[js[rr]] : -1;
+        xs[rr] = t < W ? oadj[js[rr]] : NO_KEY;
       }
 #pragma unroll
       for (int rr = 0; rr < R; ++rr) {
@@ -412,17 +425,21 @@ __device__ __forceinline__ void process_slice(
 
 // CTA kernel for the other rows: the CTA shares out(v)'s table and
 // its warps pull 32-position slices of the item's CSR range.
-// BIG = out(v) too long for the shared table (binary search, global counters).
+// BIG = out(v) too long for the shared table (binary search, global counters);
+// the BIG kernel also takes the items listed in `deferred`, whose shared
+// table could not be built (no cuckoo placement).
 template <bool BIG, typename IT>
 __global__ void __launch_bounds__(TRI_THREADS, 3)
 k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
             const int32_t* __restrict__ deg, const int32_t* __restrict__ odeg,
             const int32_t* __restrict__ oadj, int64_t n, const int64_t* __restrict__ item_off,
             const int32_t* __restrict__ order, unsigned long long* __restrict__ work, int lsh_T,
-            int od_cap,
-            uint32_t* __restrict__ tcnt, int32_t* __restrict__ twin_rel, unsigned* status) {
+            int od_cap, int64_t* __restrict__ deferred, unsigned long long* __restrict__ n_deferred,
+            bool deferred_only, uint32_t* __restrict__ tcnt, int32_t* __restrict__ twin_rel,
+            unsigned* status) {
   // shared layout for od_cap (a power of two >= every od handled here) and
-  // Lc = table_log2(od_cap): t0[2^Lc] | t1[2^Lc] | vcnt[od_cap]
+  // hcap = 2^table_log2(od_cap): the table (t0, t1, p0, p1; 12 bytes per
+  // hcap), then vcnt[od_cap]
   extern __shared__ uint4 smem4[];
   __shared__ long long s_item;
   __shared__ int s_next;  // next 32-position slice of the item's CSR range
@@ -432,11 +449,13 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
   __shared__ long long s_jv[TRI_WARPS][32];
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int64_t total = item_off[n];
-  const int Lc = table_log2(od_cap);
+  // BIG: first the items whose out-list is too long for the shared table
+  // (unless deferred_only), then the deferred ones
+  const int64_t total_items = (BIG && deferred_only) ? 0 : item_off[n];
+  const int64_t total = BIG ? total_items + (int64_t)*n_deferred : total_items;
+  const int hcap = 1 << table_log2(od_cap);
   uint32_t* t0 = reinterpret_cast<uint32_t*>(smem4);
-  uint32_t* t1 = t0 + (1 << Lc);
-  uint32_t* vcnt = t1 + (1 << Lc);
+  uint32_t* vcnt = t0 + 3 * hcap;
   const SliceSmem sm{s_u[wid], s_p[wid], s_acc[wid], s_jv[wid]};
   unsigned bad = 0;
 
@@ -446,20 +465,28 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
       s_next = 0;
     }
     __syncthreads();
-    const int64_t item = s_item;
-    if (item >= total) break;
+    const int64_t w = s_item;
+    if (w >= total) break;
+    const bool was_deferred = BIG && w >= total_items;
+    const int64_t item = was_deferred ? deferred[w - total_items] : w;
     const int64_t idx = find_item_vertex(item_off, n, item);
     const int64_t v = order[idx];
     const int64_t chunk = item - item_off[idx];
     const int32_t dv = deg[v];
     const int64_t ob = off[v];
     const int32_t od = odeg[v];
-    const bool skip_item = BIG ? (od <= SMEM_OD_MAX) : (od > SMEM_OD_MAX);
+    const bool skip_item = BIG ? (od <= SMEM_OD_MAX && !was_deferred) : (od > SMEM_OD_MAX);
     if (skip_item) { __syncthreads(); continue; }
-    OutTable tab{nullptr, nullptr, 5, 0u, 0u, oadj + ob, od, true};
-    if (!BIG && od > 0)
-      tab = table_build(t0, t1, vcnt, oadj + ob, od, threadIdx.x, TRI_THREADS,
+    OutTable tab{nullptr, 0, 27, 0u, 0u, oadj + ob, od, true};
+    if (!BIG && od > 0) {
+      tab = table_build(t0, hcap, vcnt, oadj + ob, od, threadIdx.x, TRI_THREADS,
                         [] { __syncthreads(); }, [](bool b) { return __syncthreads_or(b) != 0; });
+      if (tab.bsearch) {  // hand the item to the BIG kernel
+        if (threadIdx.x == 0) deferred[atomicAdd(n_deferred, 1ull)] = item;
+        __syncthreads();
+        continue;
+      }
+    }
     const int64_t rb = off[v];
     const int64_t p_begin = chunk * CHUNK;
     const int64_t p_end = min((int64_t)dv, p_begin + CHUNK);
@@ -468,10 +495,10 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
       int slice = 0;
       if (lane == 0) slice = atomicAdd(&s_next, 32);
       slice = __shfl_sync(FULL, slice, 0);
-      const int64_t p0 = p_begin + slice;
-      if (p0 >= p_end) break;
-      process_slice<BIG, IT>(p0, p_end, rb, (int32_t)v, dv, od, ob, adj, deg, off, odeg, oadj, lsh_T, tab,
-                         vcnt, sm, tcnt, twin_rel, bad);
+      const int64_t pos0 = p_begin + slice;
+      if (pos0 >= p_end) break;
+      process_slice<BIG, IT>(pos0, p_end, rb, (int32_t)v, dv, od, ob, adj, deg, off, odeg, oadj,
+                             lsh_T, tab, vcnt, sm, tcnt, twin_rel, bad);
     }
     __syncthreads();
     if (!BIG)
@@ -489,14 +516,13 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
 // vertex at a time, with its own table of out(v) (no CTA barrier). Warps take
 // 32 vertices per atomic fetch.
 template <typename IT>
-__global__ void __launch_bounds__(SW_WARPS * 32, 4)
+__global__ void __launch_bounds__(SW_WARPS * 32, 8)
 k_tri_small(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
             const int32_t* __restrict__ deg, const int32_t* __restrict__ odeg,
             const int32_t* __restrict__ oadj, int64_t n, unsigned long long* __restrict__ work,
             int lsh_T, uint32_t* __restrict__ tcnt, int32_t* __restrict__ twin_rel,
             unsigned* status) {
-  __shared__ __align__(16) uint32_t s_t0[SW_WARPS][SW_SLOTS];
-  __shared__ __align__(16) uint32_t s_t1[SW_WARPS][SW_SLOTS];
+  __shared__ __align__(16) uint32_t s_tab[SW_WARPS][3 * SW_SLOTS];  // t0 | t1 | p0 p1
   __shared__ uint32_t s_cnt[SW_WARPS][SMALL_OD];
   __shared__ int32_t s_u[SW_WARPS][32];
   __shared__ int32_t s_p[SW_WARPS][32];
@@ -519,20 +545,27 @@ k_tri_small(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
       const int32_t od = odeg[vv];
       if (!warp_vertex(dv, od) || dv - od == 0) continue;  // CTA kernel, or no in-neighbours
       const int64_t ob = off[vv];
-      OutTable tab{nullptr, nullptr, 5, 0u, 0u, oadj + ob, od, true};
+      OutTable tab{nullptr, 0, 27, 0u, 0u, oadj + ob, od, true};
       if (od > 0)
-        tab = table_build(s_t0[wid], s_t1[wid], vcnt, oadj + ob, od, lane, 32,
+        tab = table_build(s_tab[wid], SW_SLOTS, vcnt, oadj + ob, od, lane, 32,
                           [] { __syncwarp(); },
                           [](bool b) { __syncwarp(); return __any_sync(0xffffffffu, b) != 0; });
+      const bool use_table = !tab.bsearch;
       const int64_t rb = off[vv];
-      for (int64_t p0 = 0; p0 < dv; p0 += 32)
-        process_slice<false, IT>(p0, dv, rb, (int32_t)vv, dv, od, ob, adj, deg, off, odeg, oadj, lsh_T, tab,
-                             vcnt, sm, tcnt, twin_rel, bad);
-      __syncwarp();
-      for (int j = lane; j < od; j += 32) {
-        const uint32_t c = vcnt[j];
-        if (c) atomicAdd(&tcnt[ob + j], c);
+      for (int64_t pos0 = 0; pos0 < dv; pos0 += 32) {
+        if (use_table)
+          process_slice<false, IT>(pos0, dv, rb, (int32_t)vv, dv, od, ob, adj, deg, off, odeg,
+                                   oadj, lsh_T, tab, vcnt, sm, tcnt, twin_rel, bad);
+        else
+          process_slice<true, IT>(pos0, dv, rb, (int32_t)vv, dv, od, ob, adj, deg, off, odeg,
+                                  oadj, lsh_T, tab, vcnt, sm, tcnt, twin_rel, bad);
       }
+      __syncwarp();
+      if (use_table)
+        for (int j = lane; j < od; j += 32) {
+          const uint32_t c = vcnt[j];
+          if (c) atomicAdd(&tcnt[ob + j], c);
+        }
       __syncwarp();
     }
   }
@@ -590,13 +623,14 @@ __global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v) {
 template <typename IT>
 int launch_counting(const int64_t* off, const int32_t* adj, const int32_t* deg, const int32_t* odeg,
                     const int32_t* oadj, int64_t n, const int64_t* item_off, const int32_t* order,
-                    unsigned long long* work, int lsh_T, int32_t max_od, uint32_t* tcnt,
-                    int32_t* twin, unsigned* status, cudaStream_t s) {
+                    unsigned long long* work, int lsh_T, int32_t max_od, int64_t* deferred,
+                    unsigned long long* n_deferred, uint32_t* tcnt, int32_t* twin,
+                    unsigned* status, cudaStream_t s) {
   int od_cap = 16;
   while (od_cap < max_od && od_cap < SMEM_OD_MAX) od_cap <<= 1;
-  // two tables of 2^table_log2(od_cap) = 2 * od_cap slots, then the counters
-  const size_t smem = (size_t)5 * od_cap * sizeof(uint32_t);
-  const size_t smem_max = (size_t)5 * SMEM_OD_MAX * sizeof(uint32_t);
+  // the table (12 bytes per slot, 2 * od_cap slots) and the counters
+  const size_t smem = (size_t)28 * od_cap;
+  const size_t smem_max = (size_t)28 * SMEM_OD_MAX;
   GS_CUDA(cudaFuncSetAttribute(k_triangles<false, IT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem_max));
   int dev = 0, sms = 152, per_sm = 1;
@@ -606,7 +640,8 @@ int launch_counting(const int64_t* off, const int32_t* adj, const int32_t* deg, 
                                                         TRI_THREADS, smem));
   if (per_sm < 1) per_sm = 1;
   k_triangles<false, IT><<<sms * per_sm, TRI_THREADS, smem, s>>>(
-      off, adj, deg, odeg, oadj, n, item_off, order, work, lsh_T, od_cap, tcnt, twin, status);
+      off, adj, deg, odeg, oadj, n, item_off, order, work, lsh_T, od_cap, deferred, n_deferred,
+      false, tcnt, twin, status);
   GS_LAUNCH();
   int small_per_sm = 1;
   GS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&small_per_sm, k_tri_small<IT>,
@@ -615,12 +650,13 @@ int launch_counting(const int64_t* off, const int32_t* adj, const int32_t* deg, 
   k_tri_small<IT><<<sms * small_per_sm, SW_WARPS * 32, 0, s>>>(off, adj, deg, odeg, oadj, n,
                                                                work + 2, lsh_T, tcnt, twin, status);
   GS_LAUNCH();
-  if (max_od > SMEM_OD_MAX) {
-    k_triangles<true, IT><<<sms * 4, TRI_THREADS, 0, s>>>(off, adj, deg, odeg, oadj, n, item_off,
-                                                          order, work + 1, lsh_T, 0, tcnt, twin,
-                                                          status);
-    GS_LAUNCH();
-  }
+  // items with out-lists too long for the shared table, and items deferred
+  // by the CTA kernel (normally none: the launch then ends at once)
+  const bool deferred_only = max_od <= SMEM_OD_MAX;
+  k_triangles<true, IT><<<deferred_only ? sms : sms * 4, TRI_THREADS, 0, s>>>(
+      off, adj, deg, odeg, oadj, n, item_off, order, work + 1, lsh_T, 0, deferred, n_deferred,
+      deferred_only, tcnt, twin, status);
+  GS_LAUNCH();
   return SCAN_OK;
 }
 
@@ -639,12 +675,14 @@ int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* a
   int64_t* item_off = pool.get<int64_t>(n + 1);
   unsigned long long* hist = pool.get<unsigned long long>(2 * nbins);  // counts | fill cursors
   int64_t* start = pool.get<int64_t>(nbins + 1);
-  unsigned long long* work = pool.get<unsigned long long>(3);
+  unsigned long long* work = pool.get<unsigned long long>(4);  // 3 counters + deferred count
+  // items: at most one per vertex plus one per CHUNK arcs
+  int64_t* deferred = pool.get<int64_t>(n + m / CHUNK + 1);
   if (!tcnt || !twin || !items || !items_sorted || !order || !item_off || !hist || !start ||
-      !work)
+      !work || !deferred)
     return SCAN_ENOMEM;
   GS_CUDA(cudaMemsetAsync(tcnt, 0, m * sizeof(uint32_t), s));
-  GS_CUDA(cudaMemsetAsync(work, 0, 3 * sizeof(unsigned long long), s));
+  GS_CUDA(cudaMemsetAsync(work, 0, 4 * sizeof(unsigned long long), s));
   GS_CUDA(cudaMemsetAsync(hist, 0, 2 * nbins * sizeof(unsigned long long), s));
   if (m > 0) {
     k_fill_i32<<<1024, 256, 0, s>>>(twin, m, -1);
@@ -670,10 +708,10 @@ int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* a
   if (n > 0 && m > 0) {
     if (m < ((int64_t)1 << 31) - 1) {
       GS_TRY(launch_counting<int32_t>(off, adj, deg, odeg, oadj, n, item_off, order, work, lsh_T,
-                                      max_od, tcnt, twin, status, s));
+                                      max_od, deferred, work + 3, tcnt, twin, status, s));
     } else {
       GS_TRY(launch_counting<int64_t>(off, adj, deg, odeg, oadj, n, item_off, order, work, lsh_T,
-                                      max_od, tcnt, twin, status, s));
+                                      max_od, deferred, work + 3, tcnt, twin, status, s));
     }
   }
   GS_CUDA(cudaEventRecord(e1, s));
@@ -690,6 +728,7 @@ int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* a
   cudaEventDestroy(e1);
   pool.put(tcnt);
   pool.put(twin);
+  pool.put(deferred);
   pool.put(items);
   pool.put(items_sorted);
   pool.put(order);
