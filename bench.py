@@ -48,6 +48,7 @@ def parse():
     p.add_argument("--no-batched", action="store_true", help="skip the 2048-graph batched build")
     p.add_argument("--no-serving", action="store_true", help="skip the serving comparison")
     p.add_argument("--no-lsh", action="store_true", help="skip the LSH build and quality gate")
+    p.add_argument("--no-sweep", action="store_true", help="skip the modularity sweep over Sigma")
     p.add_argument("--batch-graphs", type=int, default=2048)
     p.add_argument("--serve-queries", type=int, default=20000)
     return p.parse_args()
@@ -527,6 +528,20 @@ def main():
     ix.query_batch(mus, epss, out=labq, stream=stream)
     torch.cuda.synchronize()
     qres["batch16_queries_per_s"] = round(nq / (time.perf_counter() - t0), 1)
+    sweep = None
+    if not args.no_sweep:
+        # the paper's parameter sweep: every (mu, eps) of Sigma, clustering
+        # and modularity on the GPU, best pair by modularity
+        smu, seps = gs.paper_sigma()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        qs = ix.sweep(smu, seps, stream=stream)
+        sweep_s = time.perf_counter() - t0
+        bi = int(np.argmax(qs))
+        sweep = {"pairs": int(smu.shape[0]), "seconds": round(sweep_s, 3),
+                 "pairs_per_s": round(smu.shape[0] / sweep_s, 1),
+                 "best": {"mu": int(smu[bi]), "eps": float(seps[bi]),
+                          "modularity": round(float(qs[bi]), 6)}}
     ix.free()
 
     peak, peak_src = measured_peak()
@@ -560,6 +575,7 @@ def main():
                            "achieved_gbs": (alg["touch"] + alg["csr"] + alg["out"])
                            / (statistics.mean(step_ms) / 1000.0) / 1e9},
         "query": qres,
+        "sweep": sweep,
         "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": clocks,

@@ -154,6 +154,24 @@ int scan_query_batch(scan_index* index, int q, const int* mu, const double* eps,
 int scan_query_noalloc(scan_index* index, int mu, double eps, int32_t* labels, int flags,
                        uintptr_t stream);
 
+/* Modularity (Section 7.2) of a clustering of the index's graph, with every
+ * vertex of negative label (outlier, hub, unclustered) as a cluster of its
+ * own:  Q = (arcs inside clusters) / 2m - sum over clusters of (sum of the
+ * degrees in it)^2 / (2m)^2. labels: n int32, host or device, any cluster ids
+ * in [0, n) (the labels of scan_query qualify); a label >= n returns
+ * SCAN_EINVAL. The sums are exact 64-bit integers; *q receives the double
+ * result. Synchronises `stream`. */
+int scan_modularity(scan_index* index, const int32_t* labels, double* q, uintptr_t stream);
+
+/* Parameter sweep (Section 7.3.4): for each of `count` pairs (mu[i], eps[i])
+ * (host arrays, each pair valid for scan_query), the clustering without hub
+ * marks and its modularity, written to q[i] (host). The paper's set Sigma is
+ * mu in {2, 4, ..., 2^18} x eps in {.01, ..., .99}; the pair of highest
+ * modularity is its choice of parameters. Queries run 32 at a time on the
+ * GPU, each followed by its modularity passes. Synchronises `stream`. */
+int scan_sweep(scan_index* index, int count, const int* mu, const double* eps, double* q,
+               uintptr_t stream);
+
 /* Copy the index out (test hook; any pointer may be NULL, each host or
  * device): sim[num_arcs] in CSR arc order, no_id/no_sim[num_arcs] (NO[v]
  * occupies the slots of v's CSR row), co_off[max_deg+1], co_id/co_thr

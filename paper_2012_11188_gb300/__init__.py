@@ -4,8 +4,9 @@ The computation lives in the CUDA library libscan.so (C ABI in include/scan.h);
 this package builds it in-tree and exposes a thin ctypes binding.
 """
 from .scan import (COSINE, JACCARD, Q_HUBS, ScanError, ScanIndex, Server, kernel_launches,
-                   last_build_timings, library_path, load, make_lsh, use_torch_allocator)
+                   last_build_timings, library_path, load, make_lsh, paper_sigma,
+                   use_torch_allocator)
 from ._build import build
 
 __all__ = ["COSINE", "JACCARD", "Q_HUBS", "ScanError", "ScanIndex", "Server", "build", "kernel_launches", "last_build_timings",
-           "library_path", "load", "make_lsh", "use_torch_allocator"]
+           "library_path", "load", "make_lsh", "paper_sigma", "use_torch_allocator"]

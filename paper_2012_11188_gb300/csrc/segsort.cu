@@ -126,6 +126,8 @@ __device__ __forceinline__ void reg_stage(uint64_t (&K)[RI], int32_t (&V)[RI], i
 
 template <int RI>
 __device__ __forceinline__ void warp_sort_reg(uint64_t (&K)[RI], int32_t (&V)[RI], int lane) {
+  static_assert(RI == 1 || RI == 2 || RI == 4 || RI == 8 || RI == 16 || RI == 32,
+                "elements per lane: a power of two up to 32");
   constexpr int S = 32 * RI;
 #pragma unroll
   for (int k = 2; k <= S; k <<= 1) {
@@ -141,6 +143,10 @@ __device__ __forceinline__ void warp_sort_reg(uint64_t (&K)[RI], int32_t (&V)[RI
           const bool partner_first = before(pk, pv, K[r], V[r]);
           if (partner_first == (low == asc)) { K[r] = pk; V[r] = pv; }
         }
+      } else if (j == 16) {
+        if constexpr (RI > 16) reg_stage<16, RI>(K, V, lane, k);
+      } else if (j == 8) {
+        if constexpr (RI > 8) reg_stage<8, RI>(K, V, lane, k);
       } else if (j == 4) {
         if constexpr (RI > 4) reg_stage<4, RI>(K, V, lane, k);
       } else if (j == 2) {

@@ -581,33 +581,58 @@ __device__ __forceinline__ double sim_of(int kind, int64_t c, int64_t du, int64_
   return __ddiv_rn((double)c, (double)(du + dv + 2 - c));
 }
 
-// Every oriented edge a->b writes sigma to both of its CSR arcs.
-__global__ void k_expand(int kind, const int64_t* __restrict__ off, const int32_t* __restrict__ deg,
-                         const int32_t* __restrict__ odeg, const int32_t* __restrict__ oadj,
-                         const int32_t* __restrict__ opos, const uint32_t* __restrict__ tcnt,
-                         const int32_t* __restrict__ twin_rel, int64_t n, int lsh_T,
-                         double* __restrict__ sim_csr, unsigned* status) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  unsigned bad = 0;
-  for (int64_t a = warp; a < n; a += nwarps) {
-    const int64_t ob = off[a], oe = ob + odeg[a];
-    if (ob == oe) continue;
-    const int64_t ra = off[a];
-    const int32_t da = deg[a];
-    for (int64_t j = ob + lane; j < oe; j += 32) {
-      const int32_t b = oadj[j];
-      const int32_t tr = twin_rel[j];
-      // LSH mode: approximated edges are written by the estimate pass
-      if (lsh_T >= 0 && da > lsh_T && deg[b] > lsh_T) continue;
-      const double s = sim_of(kind, (int64_t)tcnt[j] + 2, da, deg[b]);
-      sim_csr[ra + opos[j]] = s;
-      if (tr < 0) bad = 1;
-      else sim_csr[off[b] + tr] = s;
-    }
+// Every oriented edge a->b writes sigma to both of its CSR arcs. Threads run
+// over the oriented edges in order (odp = exclusive prefix of the
+// out-degrees, so edge k is the (k - odp[a])-th out-arc of the vertex a with
+// odp[a] <= k < odp[a+1]); a CTA's EXPAND_T * EXPAND_ITEMS edges span the
+// vertices between two binary searches, and each edge finds its own vertex
+// by a search inside that bracket.
+constexpr int EXPAND_T = 256;
+constexpr int EXPAND_ITEMS = 8;
+
+__device__ __forceinline__ int64_t row_of(const int64_t* __restrict__ odp, int64_t lo, int64_t hi,
+                                          int64_t k) {
+  // largest a in [lo, hi) with odp[a] <= k (odp[lo] <= k)
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (odp[mid] <= k) lo = mid; else hi = mid;
   }
-  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, (unsigned)DEV_BADGRAPH);
+  return lo;
+}
+
+__global__ void __launch_bounds__(EXPAND_T)
+k_expand(int kind, const int64_t* __restrict__ off, const int32_t* __restrict__ deg,
+         const int64_t* __restrict__ odp, const int32_t* __restrict__ oadj,
+         const int32_t* __restrict__ opos, const uint32_t* __restrict__ tcnt,
+         const int32_t* __restrict__ twin_rel, int64_t n, int lsh_T,
+         double* __restrict__ sim_csr, unsigned* status) {
+  __shared__ int64_t s_bracket[2];
+  const int64_t m = odp[n];
+  constexpr int64_t CH = (int64_t)EXPAND_T * EXPAND_ITEMS;
+  unsigned bad = 0;
+  for (int64_t k0 = (int64_t)blockIdx.x * CH; k0 < m; k0 += (int64_t)gridDim.x * CH) {
+    const int64_t k1 = min(m, k0 + CH);
+    if (threadIdx.x == 0) s_bracket[0] = row_of(odp, 0, n + 1, k0);
+    if (threadIdx.x == 1) s_bracket[1] = row_of(odp, 0, n + 1, k1 - 1) + 1;
+    __syncthreads();
+    const int64_t lo = s_bracket[0], hi = s_bracket[1];
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += EXPAND_T) {
+      const int64_t a = row_of(odp, lo, hi, k);
+      const int64_t ra = off[a];
+      const int64_t j = ra + (k - odp[a]);
+      const int32_t b = oadj[j];
+      const int32_t da = deg[a], db = deg[b];
+      // LSH mode: approximated edges are written by the estimate pass
+      if (lsh_T >= 0 && da > lsh_T && db > lsh_T) continue;
+      const double sv = sim_of(kind, (int64_t)tcnt[j] + 2, da, db);
+      sim_csr[ra + opos[j]] = sv;
+      const int32_t tr = twin_rel[j];
+      if (tr < 0) bad = 1;
+      else sim_csr[off[b] + tr] = sv;
+    }
+    __syncthreads();
+  }
+  if (bad) atomicOr(status, (unsigned)DEV_BADGRAPH);
 }
 
 __global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v) {
@@ -716,8 +741,13 @@ int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* a
   }
   GS_CUDA(cudaEventRecord(e1, s));
   if (n > 0 && m > 0) {
-    k_expand<<<(unsigned)std::min<int64_t>((n + 7) / 8, 152 * 64), 256, 0, s>>>(
-        kind, off, deg, odeg, oadj, opos, tcnt, twin, n, lsh_T, sim_csr, status);
+    int64_t* odp = item_off;  // reused: exclusive prefix of the out-degrees
+    GS_TRY(exclusive_scan_i32_to_i64(odeg, odp, n, pool, s));
+    const int64_t edges = m / 2;
+    const int64_t ch = (int64_t)EXPAND_T * EXPAND_ITEMS;
+    k_expand<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((edges + ch - 1) / ch, 152 * 32)),
+               EXPAND_T, 0, s>>>(kind, off, deg, odp, oadj, opos, tcnt, twin, n, lsh_T, sim_csr,
+                                 status);
     GS_LAUNCH();
   }
   if (count_ms) {

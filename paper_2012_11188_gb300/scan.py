@@ -64,6 +64,8 @@ def load():
         "scan_query": (i32, [P, i32, f64, P, i32, ctypes.c_size_t]),
         "scan_query_batch": (i32, [P, i32, P, P, P, i32, ctypes.c_size_t]),
         "scan_index_export": (i32, [P, P, P, P, P, P, P]),
+        "scan_modularity": (i32, [P, P, P, ctypes.c_size_t]),
+        "scan_sweep": (i32, [P, i32, P, P, P, ctypes.c_size_t]),
         "scan_index_info": (i32, [P, P, P, P, P]),
         "scan_index_free": (None, [P]),
         "scan_strerror": (ctypes.c_char_p, [i32]),
@@ -75,6 +77,14 @@ def load():
         f.restype, f.argtypes = res, args
     _lib = lib
     return lib
+
+
+def paper_sigma():
+    """The parameter set of the paper's sweep: mu in {2, 4, ..., 2^18} x
+    eps in {.01, .02, ..., .99} (1782 pairs), as (mus, epss) arrays."""
+    mus = np.repeat(2 ** np.arange(1, 19, dtype=np.int32), 99)
+    epss = np.tile(np.arange(1, 100, dtype=np.float64) / 100.0, 18)
+    return mus, epss
 
 
 def _check(rc: int, what: str):
@@ -267,6 +277,24 @@ class ScanIndex:
                                        Q_HUBS if hubs else 0, _stream_handle(stream)),
                "scan_query_batch")
         return out
+
+    def modularity(self, labels, stream=None) -> float:
+        """Modularity of a clustering of this graph (unclustered = singletons)."""
+        if isinstance(labels, np.ndarray):
+            labels = np.ascontiguousarray(labels, dtype=np.int32)
+        q = ctypes.c_double(0.0)
+        _check(load().scan_modularity(self._h, _ptr(labels), ctypes.byref(q),
+                                      _stream_handle(stream)), "scan_modularity")
+        return q.value
+
+    def sweep(self, mus, epss, stream=None) -> np.ndarray:
+        """Modularity of the clustering of every (mu, eps) pair (no hub marks)."""
+        mus = np.ascontiguousarray(mus, dtype=np.int32)
+        epss = np.ascontiguousarray(epss, dtype=np.float64)
+        q = np.empty(mus.shape[0], dtype=np.float64)
+        _check(load().scan_sweep(self._h, mus.shape[0], mus.ctypes.data, epss.ctypes.data,
+                                 q.ctypes.data, _stream_handle(stream)), "scan_sweep")
+        return q
 
     def export(self) -> dict:
         A = self.arcs
