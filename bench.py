@@ -49,6 +49,7 @@ def parse():
     p.add_argument("--no-serving", action="store_true", help="skip the serving comparison")
     p.add_argument("--no-lsh", action="store_true", help="skip the LSH build and quality gate")
     p.add_argument("--no-sweep", action="store_true", help="skip the modularity sweep over Sigma")
+    p.add_argument("--no-dense", action="store_true", help="skip the dense-graph builds")
     p.add_argument("--batch-graphs", type=int, default=2048)
     p.add_argument("--serve-queries", type=int, default=20000)
     return p.parse_args()
@@ -355,6 +356,60 @@ def lsh_quality(gs, off_d, adj_d, g, stream, timed: bool):
     return out
 
 
+def bench_dense(gs, kind: int, seed: int, stream):
+    """Dense graphs shaped like the paper's blood vessel and cochlea graphs
+    (n = 25,825, average degree 5.4K and 21.9K), as Erdos-Renyi graphs: the
+    closed counts from one bf16 GEMM ((A+I)^2, Section 4.1.1) against the
+    sparse enumeration (blood vessel only; cochlea would take seconds), with
+    the two indexes compared bit for bit."""
+    import graphgen
+    import torch
+    out = {}
+    for name, avg in (("blood_vessel_like", 5400), ("cochlea_like", 21900)):
+        n = 25825
+        p = avg / (n - 1)
+        t0 = time.perf_counter()
+        g = graphgen.sbm(n, 1, p, p, seed=seed)
+        gen_s = time.perf_counter() - t0
+        off = torch.from_numpy(g.off).to("cuda")
+        adj = torch.from_numpy(g.adj).to("cuda")
+        rec = {"n": n, "edges": g.edges, "generation_s": round(gen_s, 1)}
+        modes = [("dense", gs.COUNTS_DENSE)]
+        if avg < 10000:
+            modes.append(("sparse", gs.COUNTS_SPARSE))
+        sims = {}
+        for mname, mode in modes:
+            reps = 3 if mname == "dense" else 1
+            ix = gs.ScanIndex.build((off, adj), kind, stream=stream, counts=mode)  # warm-up
+            ts, cnt = [], []
+            for _ in range(reps):
+                ix.free()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                ix = gs.ScanIndex.build((off, adj), kind, stream=stream, counts=mode)
+                b.record(stream)
+                b.synchronize()
+                ts.append(a.elapsed_time(b))
+                cnt.append(gs.last_build_timings().count_ms)
+            sim = torch.empty(g.arcs, dtype=torch.float64, device="cuda")
+            gs.load().scan_index_export(ix._h, sim.data_ptr(), None, None, None, None, None)
+            sims[mname] = sim
+            ix.free()
+            ms = statistics.median(ts)
+            rec[mname] = {"build_ms": round(ms, 2), "count_ms": round(statistics.median(cnt), 2),
+                          "edges_per_s": g.edges / (ms / 1000.0)}
+            if mname == "dense":
+                rec[mname]["gemm_tflops"] = round(2.0 * n ** 3 / (statistics.median(cnt) / 1000.0) / 1e12, 1)
+        if "sparse" in sims:
+            rec["identical"] = bool(torch.equal(sims["dense"], sims["sparse"]))
+            rec["dense_speedup"] = round(rec["sparse"]["build_ms"] / rec["dense"]["build_ms"], 1)
+        del sims, off, adj, g
+        torch.cuda.empty_cache()
+        out[name] = rec
+    return out
+
+
 def bench_lsh(gs, off_d, adj_d, g, stream):
     """LSH quality on the benchmark graph (timed builds), and on a dense SBM
     whose in-block edges are all approximated, so that the exact clustering
@@ -587,6 +642,8 @@ def main():
         out["batched_build"] = bench_batched(gs, kind, args.batch_graphs, args.seed, stream)
     if not args.no_serving:
         out["serving"] = bench_serving(gs, kind, args.serve_queries, args.seed, stream)
+    if not args.no_dense:
+        out["dense"] = bench_dense(gs, kind, args.seed, stream)
     if ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.edgefactor, args.seed,
                                            0 if args.kind == "cosine" else 1)

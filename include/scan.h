@@ -109,6 +109,21 @@ int scan_set_allocator(scan_alloc_fn alloc, scan_free_fn release, void* ctx);
 int scan_index_build(const scan_csr* csr, scan_sim_kind kind, const scan_lsh_params* lsh,
                      uintptr_t stream, scan_index** out);
 
+/* scan_index_build with a choice of how the closed counts are obtained:
+ *  SCAN_COUNTS_AUTO   - dense when n <= 65536 and the average degree is at
+ *                       least n/16, else sparse (what scan_index_build does);
+ *  SCAN_COUNTS_SPARSE - oriented triangle enumeration (Section 6.1);
+ *  SCAN_COUNTS_DENSE  - ((A+I)^2)[u][v] = |N̄(u) ∩ N̄(v)| (Section 4.1.1) from
+ *                       one bf16 GEMM with fp32 accumulation (exact: 0/1
+ *                       operands, sums below 2^24); needs n <= 65536 (else
+ *                       SCAN_EINVAL) and about 6 n^2 bytes of device memory.
+ * Every choice gives the same index, bit for bit. */
+#define SCAN_COUNTS_AUTO 0
+#define SCAN_COUNTS_SPARSE 1
+#define SCAN_COUNTS_DENSE 2
+int scan_index_build_ex(const scan_csr* csr, scan_sim_kind kind, const scan_lsh_params* lsh,
+                        int counts, uintptr_t stream, scan_index** out);
+
 /* Build `count` independent indexes (one per graph) in one batched pass:
  * the graphs are packed into one device arena and every step runs once over
  * all of them; each handle then behaves exactly like one from

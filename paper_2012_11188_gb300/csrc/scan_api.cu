@@ -141,7 +141,7 @@ int validate_lsh(const scan_lsh_params* p, int kind) {
 // ix holds n, arcs, off (absolute, int64), adj and allocated deg, no_id,
 // no_sim and an 8-word status block; on return ix->maxdeg is set.
 int run_pipeline(IndexData* ix, int kind, const scan_lsh_params* lsh, Pool& pool, cudaStream_t s,
-                 Events& ev, float* count_ms) {
+                 Events& ev, float* count_ms, int counts_mode) {
   const int64_t n = ix->n, arcs = ix->arcs;
   const bool use_lsh = lsh && lsh->enabled;
   unsigned* scalars = ix->status;  // [0] status, [1] maxdeg, [2] max out-degree
@@ -151,6 +151,36 @@ int run_pipeline(IndexData* ix, int kind, const scan_lsh_params* lsh, Pool& pool
   GS_CUDA(cudaStreamSynchronize(s));
   if (hs[0] & DEV_BADGRAPH) return SCAN_EBADGRAPH;
   ix->maxdeg = (int32_t)hs[1];
+  const bool dense = arcs > 0 && (counts_mode == SCAN_COUNTS_DENSE ||
+                                  (counts_mode == SCAN_COUNTS_AUTO && dense_counts_pay(n, arcs)));
+  if (dense) {
+    // closed counts of every arc from one matrix product (Section 4.1.1)
+    if (n > DENSE_MAX_N) return SCAN_EINVAL;
+    GS_TRY(ev.mark(s));
+    int32_t* row = nullptr;
+    int64_t nH = 0;
+    if (use_lsh) {
+      row = pool.get<int32_t>(n);
+      if (!row) return SCAN_ENOMEM;
+      GS_TRY(lsh_select(ix->off, ix->adj, ix->deg, n, lsh->degree_threshold, row, &nH, pool, s));
+    }
+    GS_CUDA(cudaMemcpyAsync(ix->no_id, ix->adj, arcs * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    GS_TRY(dense_counts_and_sims(kind, ix->off, ix->adj, ix->deg, n,
+                                 use_lsh ? lsh->degree_threshold : -1, ix->no_sim, scalars, pool,
+                                 s, count_ms));
+    GS_CUDA(cudaMemcpyAsync(hs, scalars, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    GS_CUDA(cudaStreamSynchronize(s));
+    if (hs[0] & DEV_BADGRAPH) return SCAN_EBADGRAPH;
+    GS_TRY(ev.mark(s));
+    if (use_lsh && nH > 0)
+      GS_TRY(lsh_apply(*lsh, kind, ix->off, ix->adj, ix->deg, n, arcs, row, nH, ix->no_sim, pool, s));
+    if (row) pool.put(row);
+    GS_TRY(ev.mark(s));
+    GS_TRY(segmented_sort_desc((uint64_t*)ix->no_sim, ix->no_id, ix->off, n, arcs, ix->maxdeg, pool,
+                               s));
+    GS_TRY(ev.mark(s));
+    return SCAN_OK;
+  }
   // ---- orientation (Section 6.1)
   int32_t *od = nullptr, *oadj = nullptr, *opos = nullptr;
   if (arcs > 0) {
@@ -229,7 +259,8 @@ int check_csr_args(const scan_csr* csr) {
 
 // Build one index into ix; on error every block is released by the pool.
 int build_one(const scan_csr* csr, int kind, const scan_lsh_params* lsh, cudaStream_t s,
-              IndexData* ix) {
+              IndexData* ix, int counts_mode = SCAN_COUNTS_AUTO) {
+  if (counts_mode < SCAN_COUNTS_AUTO || counts_mode > SCAN_COUNTS_DENSE) return SCAN_EINVAL;
   GS_TRY(check_csr_args(csr));
   if (kind != SCAN_COSINE && kind != SCAN_JACCARD) return SCAN_EINVAL;
   GS_TRY(validate_lsh(lsh, kind));
@@ -275,7 +306,7 @@ int build_one(const scan_csr* csr, int kind, const scan_lsh_params* lsh, cudaStr
   GS_CUDA(cudaStreamSynchronize(s));
   if (ends[0] != 0 || ends[1] != arcs) return SCAN_EBADGRAPH;
   float count_ms = 0;
-  GS_TRY(run_pipeline(ix, kind, lsh, pool, s, ev, &count_ms));
+  GS_TRY(run_pipeline(ix, kind, lsh, pool, s, ev, &count_ms, counts_mode));
   // ---- core order (Algorithm 2)
   GS_TRY(build_core_order(*ix, pool, s));
   GS_TRY(ev.mark(s));
@@ -447,7 +478,7 @@ int build_batch(const scan_csr* graphs, int G, int kind, const scan_lsh_params* 
   pool.put(raw);
   // ---- the shared pipeline over the union (every step is local to a vertex)
   float count_ms = 0;
-  GS_TRY(run_pipeline(&u, kind, lsh, pool, s, ev, &count_ms));
+  GS_TRY(run_pipeline(&u, kind, lsh, pool, s, ev, &count_ms, SCAN_COUNTS_SPARSE));
   // ---- per-graph core orders
   int32_t* md_dev = pool.get<int32_t>(G);
   if (!md_dev) return SCAN_ENOMEM;
@@ -600,12 +631,17 @@ int scan_set_allocator(scan_alloc_fn alloc, scan_free_fn release, void* ctx) {
 
 int scan_index_build(const scan_csr* csr, scan_sim_kind kind, const scan_lsh_params* lsh,
                      uintptr_t stream, scan_index** out) {
+  return scan_index_build_ex(csr, kind, lsh, SCAN_COUNTS_AUTO, stream, out);
+}
+
+int scan_index_build_ex(const scan_csr* csr, scan_sim_kind kind, const scan_lsh_params* lsh,
+                        int counts, uintptr_t stream, scan_index** out) {
   if (!out) return SCAN_EINVAL;
   *out = nullptr;
   if (!csr) return SCAN_EINVAL;
   scan_index* h = new (std::nothrow) scan_index();
   if (!h) return SCAN_ENOMEM;
-  const int rc = build_one(csr, (int)kind, lsh, (cudaStream_t)stream, &h->d);
+  const int rc = build_one(csr, (int)kind, lsh, (cudaStream_t)stream, &h->d, counts);
   if (rc != SCAN_OK) {
     cudaStreamSynchronize((cudaStream_t)stream);
     delete h;  // the build's pool already released every block

@@ -150,6 +150,15 @@ int build_core_order_multi(int64_t N, int64_t A, const int64_t* off, const int32
                            const std::vector<int32_t>& maxdeg, int64_t* co_off_all,
                            int32_t* co_id, uint64_t* co_key, Pool& pool, cudaStream_t s);
 
+// Dense path (dense.cu): closed counts of every arc as ((A+I)^2)[u][v] by one
+// bf16 GEMM with fp32 accumulation, then the similarities; for graphs of at
+// most DENSE_MAX_N vertices.
+constexpr int64_t DENSE_MAX_N = 65536;
+bool dense_counts_pay(int64_t n, int64_t arcs);
+int dense_counts_and_sims(int kind, const int64_t* off, const int32_t* adj, const int32_t* deg,
+                          int64_t n, int lsh_T, double* sim_csr, unsigned* status, Pool& pool,
+                          cudaStream_t s, float* count_ms);
+
 // Queries (Algorithms 3-5). status_dev: a zeroed device word that receives
 // DEV_LIMIT if a bounded union-find loop gave up.
 int run_queries(const IndexData& ix, int q, const int* mu, const double* eps, int32_t* labels_dev,

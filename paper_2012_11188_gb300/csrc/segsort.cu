@@ -57,17 +57,25 @@ __global__ void k_classify_count(const int64_t* __restrict__ seg_off, int64_t ns
   if (threadIdx.x < NCLASS + 1 && c[threadIdx.x]) atomicAdd(&counts[threadIdx.x], c[threadIdx.x]);
 }
 
-// Fill per-class segment lists (order irrelevant).
+// Fill per-class segment lists (order irrelevant). The lanes of a warp that
+// share a class take consecutive slots with one atomic.
 __global__ void k_classify_fill(const int64_t* __restrict__ seg_off, int64_t nseg,
                                 const int64_t* __restrict__ class_base,
                                 unsigned long long* __restrict__ fill, int64_t* __restrict__ list) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nseg;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t len = seg_off[i + 1] - seg_off[i];
-    if (len <= 1) continue;
-    const int cl = seg_class(len);
-    const unsigned long long pos = atomicAdd(&fill[cl], 1ull);
-    list[class_base[cl] + (int64_t)pos] = i;
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < nseg;
+       i0 += stride) {
+    const int64_t i = i0 + lane;
+    const int64_t len = i < nseg ? seg_off[i + 1] - seg_off[i] : 0;
+    const int cl = len <= 1 ? -1 : seg_class(len);
+    const unsigned peers = __match_any_sync(0xffffffffu, cl);
+    const int leader = __ffs(peers) - 1;
+    unsigned long long pos = 0;
+    if (cl >= 0 && lane == leader) pos = atomicAdd(&fill[cl], (unsigned long long)__popc(peers));
+    pos = __shfl_sync(0xffffffffu, pos, leader);
+    if (cl >= 0)
+      list[class_base[cl] + (int64_t)pos + __popc(peers & ((1u << lane) - 1u))] = i;
   }
 }
 
@@ -364,31 +372,47 @@ __device__ __forceinline__ int64_t chunk_segment(const int64_t* chunk_prefix, in
   return lo;
 }
 
+// Where one output chunk of a pass reads from and writes to: run A's part
+// starts at element a0, run B's at b0, the chunk's outputs at out (absolute
+// element indexes); na + nb outputs, 0 when the segment is already finished.
+struct MergeDesc {
+  int64_t a0, b0, out;
+  int32_t na, nb;
+};
+
 // Merge-path splits of every output chunk of a pass, all in parallel (one
-// thread per chunk): split[2c] / split[2c+1] = elements of run A among the
-// first o0 / o1 outputs of the chunk's run pair.
+// thread per chunk), written as chunk descriptors.
 __global__ void k_merge_partition(const uint64_t* __restrict__ sk, const int32_t* __restrict__ sv,
                                   const int64_t* __restrict__ seg_off,
                                   const int64_t* __restrict__ list,
                                   const int64_t* __restrict__ chunk_prefix, int64_t nlong, int64_t L,
-                                  int64_t* __restrict__ split) {
+                                  MergeDesc* __restrict__ desc) {
   const int64_t total = chunk_prefix[nlong];
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < total;
        c += (int64_t)gridDim.x * blockDim.x) {
     const int64_t si = chunk_segment(chunk_prefix, nlong, c);
     const int64_t sg = list[si];
     const int64_t base = seg_off[sg], len = seg_off[sg + 1] - base;
-    if (len <= L) continue;
-    const int64_t o0 = (c - chunk_prefix[si]) * MERGE_CHUNK;
-    const int64_t o1 = min(len, o0 + MERGE_CHUNK);
-    const int64_t r0 = (o0 / (2 * L)) * (2 * L);
-    const int64_t a1 = min(len, r0 + L), b1 = min(len, r0 + 2 * L);
-    const uint64_t* KA = sk + base + r0;
-    const int32_t* VA = sv + base + r0;
-    const uint64_t* KB = sk + base + a1;
-    const int32_t* VB = sv + base + a1;
-    split[2 * c] = merge_path(KA, VA, a1 - r0, KB, VB, b1 - a1, o0 - r0);
-    split[2 * c + 1] = merge_path(KA, VA, a1 - r0, KB, VB, b1 - a1, o1 - r0);
+    MergeDesc d{0, 0, 0, 0, 0};
+    if (len > L) {
+      const int64_t o0 = (c - chunk_prefix[si]) * MERGE_CHUNK;
+      const int64_t o1 = min(len, o0 + MERGE_CHUNK);
+      // run pair containing [o0, o1): MERGE_CHUNK divides 2L
+      const int64_t r0 = (o0 / (2 * L)) * (2 * L);
+      const int64_t a1 = min(len, r0 + L), b1 = min(len, r0 + 2 * L);
+      const uint64_t* KA = sk + base + r0;
+      const int32_t* VA = sv + base + r0;
+      const uint64_t* KB = sk + base + a1;
+      const int32_t* VB = sv + base + a1;
+      const int64_t i0 = merge_path(KA, VA, a1 - r0, KB, VB, b1 - a1, o0 - r0);
+      const int64_t i1 = merge_path(KA, VA, a1 - r0, KB, VB, b1 - a1, o1 - r0);
+      d.a0 = base + r0 + i0;
+      d.b0 = base + a1 + (o0 - r0) - i0;
+      d.out = base + o0;
+      d.na = (int32_t)(i1 - i0);
+      d.nb = (int32_t)((o1 - o0) - (i1 - i0));
+    }
+    desc[c] = d;
   }
 }
 
@@ -408,37 +432,6 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// Where one output chunk of a pass reads from: run A = [ia0, ia1) and run B =
-// [ib0, ib1) (relative to the segment base), written to base + o0.
-struct MergeChunk {
-  int64_t base, o0, ia0, ib0;
-  int na, nb;
-  bool active;  // false: the segment is already finished (len <= L)
-};
-
-__device__ __forceinline__ MergeChunk merge_chunk(const int64_t* seg_off, const int64_t* list,
-                                                  const int64_t* chunk_prefix, int64_t nlong,
-                                                  int64_t L, const int64_t* split, int64_t c) {
-  MergeChunk m;
-  const int64_t si = chunk_segment(chunk_prefix, nlong, c);
-  const int64_t sg = list[si];
-  m.base = seg_off[sg];
-  const int64_t len = seg_off[sg + 1] - m.base;
-  m.active = len > L;
-  if (!m.active) return m;
-  m.o0 = (c - chunk_prefix[si]) * MERGE_CHUNK;
-  const int64_t o1 = min(len, m.o0 + MERGE_CHUNK);
-  // run pair containing [o0, o1): MERGE_CHUNK divides 2L
-  const int64_t r0 = (m.o0 / (2 * L)) * (2 * L);
-  const int64_t a1 = min(len, r0 + L);
-  const int64_t i0 = split[2 * c], i1 = split[2 * c + 1];
-  m.ia0 = r0 + i0;
-  m.na = (int)(i1 - i0);
-  m.ib0 = a1 + (m.o0 - r0) - i0;
-  m.nb = (int)((o1 - r0) - i1 - ((m.o0 - r0) - i0));
-  return m;
-}
-
 // One merge pass: within every long segment still longer than L, runs of
 // length L are merged in pairs from (sk, sv) into (dk, dv). Segments of length
 // <= L are finished and stay where they are. Each CTA takes chunks of
@@ -448,9 +441,8 @@ __device__ __forceinline__ MergeChunk merge_chunk(const int64_t* seg_off, const 
 __global__ void __launch_bounds__(MERGE_T)
 k_merge_pass(const uint64_t* __restrict__ sk, const int32_t* __restrict__ sv,
              uint64_t* __restrict__ dk, int32_t* __restrict__ dv,
-             const int64_t* __restrict__ seg_off, const int64_t* __restrict__ list,
-             const int64_t* __restrict__ chunk_prefix, int64_t nlong, int64_t L,
-             const int64_t* __restrict__ split) {
+             const int64_t* __restrict__ chunk_prefix, int64_t nlong,
+             const MergeDesc* __restrict__ desc) {
   __shared__ uint64_t ink[2][MERGE_CHUNK];
   __shared__ int32_t inv[2][MERGE_CHUNK];
   // output staging, one pad slot per MERGE_ITEMS (a thread's consecutive
@@ -461,35 +453,28 @@ k_merge_pass(const uint64_t* __restrict__ sk, const int32_t* __restrict__ sv,
   const int t = threadIdx.x;
   auto po = [](int i) { return i + i / MERGE_ITEMS; };
   // issue the copies of chunk c into buffer b (an empty group when inactive)
-  auto stage = [&](int64_t c, int b) -> MergeChunk {
-    MergeChunk m;
-    m.active = false;
-    if (c < total) m = merge_chunk(seg_off, list, chunk_prefix, nlong, L, split, c);
-    if (m.active) {
-      const uint64_t* KA = sk + m.base + m.ia0;
-      const int32_t* VA = sv + m.base + m.ia0;
-      const uint64_t* KB = sk + m.base + m.ib0;
-      const int32_t* VB = sv + m.base + m.ib0;
-      for (int i = t; i < m.na; i += MERGE_T) {
-        cp_async8(&ink[b][i], KA + i);
-        cp_async4(&inv[b][i], VA + i);
-      }
-      for (int i = t; i < m.nb; i += MERGE_T) {
-        cp_async8(&ink[b][m.na + i], KB + i);
-        cp_async4(&inv[b][m.na + i], VB + i);
-      }
+  auto stage = [&](int64_t c, int b) -> MergeDesc {
+    MergeDesc m{0, 0, 0, 0, 0};
+    if (c < total) m = desc[c];
+    for (int i = t; i < m.na; i += MERGE_T) {
+      cp_async8(&ink[b][i], sk + m.a0 + i);
+      cp_async4(&inv[b][i], sv + m.a0 + i);
+    }
+    for (int i = t; i < m.nb; i += MERGE_T) {
+      cp_async8(&ink[b][m.na + i], sk + m.b0 + i);
+      cp_async4(&inv[b][m.na + i], sv + m.b0 + i);
     }
     cp_async_commit();
     return m;
   };
   int64_t c = blockIdx.x;
   int b = 0;
-  MergeChunk cur = stage(c, b);
+  MergeDesc cur = stage(c, b);
   for (; c < total; c += gridDim.x) {
-    const MergeChunk nxt = stage(c + gridDim.x, b ^ 1);
+    const MergeDesc nxt = stage(c + gridDim.x, b ^ 1);
     cp_async_wait<1>();  // the current chunk's copies have landed
     __syncthreads();
-    if (cur.active) {
+    if (cur.na + cur.nb > 0) {
       const uint64_t* shk = ink[b];
       const int32_t* shv = inv[b];
       const int na = cur.na, nb = cur.nb, nout = na + nb;
@@ -514,7 +499,7 @@ k_merge_pass(const uint64_t* __restrict__ sk, const int32_t* __restrict__ sv,
         }
       }
       __syncthreads();
-      const int64_t out = cur.base + cur.o0;
+      const int64_t out = cur.out;
       for (int i = t; i < nout; i += MERGE_T) {
         dk[out + i] = ok_[po(i)];
         dv[out + i] = ov_[po(i)];
@@ -624,14 +609,14 @@ int segmented_sort_desc(uint64_t* key, int32_t* val, const int64_t* seg_off, int
     uint64_t *ck = key, *nk = tk;
     int32_t *cv = val, *nv = tv;
     const int64_t total_chunks_ub = (total + MERGE_CHUNK - 1) / MERGE_CHUNK + nlong;
-    int64_t* split = pool.get<int64_t>(2 * (size_t)total_chunks_ub);
-    if (!split) return SCAN_ENOMEM;
+    MergeDesc* desc = pool.get<MergeDesc>((size_t)total_chunks_ub);
+    if (!desc) return SCAN_ENOMEM;
     for (int64_t L = TILE; L < max_len; L <<= 1) {
       k_merge_partition<<<grid_of(total_chunks_ub, 256), 256, 0, s>>>(ck, cv, seg_off, llist,
-                                                                       chunk_prefix, nlong, L, split);
+                                                                       chunk_prefix, nlong, L, desc);
       GS_LAUNCH();
-      k_merge_pass<<<grid_of(total_chunks_ub, 1), MERGE_T, 0, s>>>(ck, cv, nk, nv, seg_off, llist,
-                                                                  chunk_prefix, nlong, L, split);
+      k_merge_pass<<<grid_of(total_chunks_ub, 1), MERGE_T, 0, s>>>(ck, cv, nk, nv, chunk_prefix,
+                                                                  nlong, desc);
       GS_LAUNCH();
       std::swap(ck, nk);
       std::swap(cv, nv);
@@ -640,7 +625,7 @@ int segmented_sort_desc(uint64_t* key, int32_t* val, const int64_t* seg_off, int
     k_copy_long<<<grid_of(total_chunks_ub, 1), 256, 0, s>>>(tk, tv, key, val, seg_off, llist,
                                                            chunk_prefix, nlong);
     GS_LAUNCH();
-    pool.put(split);
+    pool.put(desc);
     pool.put(tk);
     pool.put(tv);
     pool.put(tiles);

@@ -17,6 +17,7 @@ from . import _build
 
 COSINE, JACCARD = 0, 1
 Q_HUBS = 1
+COUNTS_AUTO, COUNTS_SPARSE, COUNTS_DENSE = 0, 1, 2
 
 STATUS = {0: "SCAN_OK", -1: "SCAN_EINVAL", -2: "SCAN_ENOMEM", -3: "SCAN_EBADGRAPH",
           -4: "SCAN_ECUDA", -5: "SCAN_ETIMEOUT", -6: "SCAN_EBUSY"}
@@ -61,6 +62,7 @@ def load():
         "scan_set_allocator": (i32, [P, P, P]),
         "scan_index_build": (i32, [P, i32, P, ctypes.c_size_t, P]),
         "scan_index_build_batch": (i32, [P, i32, i32, P, ctypes.c_size_t, P]),
+        "scan_index_build_ex": (i32, [P, i32, P, i32, ctypes.c_size_t, P]),
         "scan_query": (i32, [P, i32, f64, P, i32, ctypes.c_size_t]),
         "scan_query_batch": (i32, [P, i32, P, P, P, i32, ctypes.c_size_t]),
         "scan_index_export": (i32, [P, P, P, P, P, P, P]),
@@ -229,18 +231,21 @@ class ScanIndex:
         self.n, self.arcs, self.maxdeg, self.device_bytes = n.value, arcs.value, md.value, nb.value
 
     @classmethod
-    def build(cls, g, kind: int = COSINE, lsh=None, stream=None, device: bool = False) -> "ScanIndex":
+    def build(cls, g, kind: int = COSINE, lsh=None, stream=None, device: bool = False,
+              counts: int = None) -> "ScanIndex":
         """Build from a CSR (graphgen.CSR, or (offsets, adj) numpy/torch).
 
         device=True uploads numpy inputs with torch first; torch CUDA tensors are
-        passed as device pointers; numpy arrays are copied in by the library."""
+        passed as device pointers; numpy arrays are copied in by the library.
+        counts: COUNTS_AUTO (default), COUNTS_SPARSE or COUNTS_DENSE."""
         lib = load()
         c, keep = _csr_struct(g, device)
         h = ctypes.c_void_p()
-        rc = lib.scan_index_build(ctypes.byref(c), kind, ctypes.byref(lsh) if lsh else None,
-                                  _stream_handle(stream), ctypes.byref(h))
+        rc = lib.scan_index_build_ex(ctypes.byref(c), kind, ctypes.byref(lsh) if lsh else None,
+                                     COUNTS_AUTO if counts is None else int(counts),
+                                     _stream_handle(stream), ctypes.byref(h))
         del keep
-        _check(rc, "scan_index_build")
+        _check(rc, "scan_index_build_ex")
         return cls(h.value)
 
     @staticmethod
