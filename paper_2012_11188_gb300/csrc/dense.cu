@@ -20,15 +20,20 @@ namespace gscan {
 
 namespace {
 
-// (A+I) as a dense row-major n x n bf16 matrix (zeroed by the caller).
+// The matrices are np x np with np = n rounded up to DENSE_PAD: zero rows
+// and columns leave the n x n block of the product unchanged, and aligned
+// leading dimensions let the GEMM use its tensor-core tiles.
+constexpr int64_t DENSE_PAD = 128;
+
+// (A+I) as a dense row-major np x np bf16 matrix (zeroed by the caller).
 __global__ void k_dense_fill(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
-                             int64_t n, __nv_bfloat16* __restrict__ M) {
+                             int64_t n, int64_t np, __nv_bfloat16* __restrict__ M) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const __nv_bfloat16 one = __float2bfloat16(1.0f);
   for (int64_t u = warp; u < n; u += nwarps) {
-    __nv_bfloat16* row = M + u * n;
+    __nv_bfloat16* row = M + u * np;
     if (lane == 0) row[u] = one;
     for (int64_t i = off[u] + lane; i < off[u + 1]; i += 32) row[adj[i]] = one;
   }
@@ -44,7 +49,7 @@ __device__ __forceinline__ double sim_from(int kind, int64_t c, int64_t du, int6
 // marks the build SCAN_EBADGRAPH (the sparse path finds it in orientation).
 __global__ void k_dense_sims(int kind, const int64_t* __restrict__ off,
                              const int32_t* __restrict__ adj, const int32_t* __restrict__ deg,
-                             int64_t n, const __nv_bfloat16* __restrict__ M,
+                             int64_t n, int64_t np, const __nv_bfloat16* __restrict__ M,
                              const float* __restrict__ C, int lsh_T, double* __restrict__ sim_csr,
                              unsigned* status) {
   const int lane = threadIdx.x & 31;
@@ -54,10 +59,10 @@ __global__ void k_dense_sims(int kind, const int64_t* __restrict__ off,
   bool bad = false;
   for (int64_t u = warp; u < n; u += nwarps) {
     const int32_t du = deg[u];
-    const float* row = C + u * n;
+    const float* row = C + u * np;
     for (int64_t i = off[u] + lane; i < off[u + 1]; i += 32) {
       const int32_t v = adj[i];
-      if (Mb[(int64_t)v * n + u] == 0) bad = true;
+      if (Mb[(int64_t)v * np + u] == 0) bad = true;
       const int32_t dv = deg[v];
       // LSH mode: approximated edges are written by the estimate pass
       if (lsh_T >= 0 && du > lsh_T && dv > lsh_T) continue;
@@ -83,7 +88,8 @@ int dense_counts_and_sims(int kind, const int64_t* off, const int32_t* adj, cons
                           int64_t n, int lsh_T, double* sim_csr, unsigned* status, Pool& pool,
                           cudaStream_t s, float* count_ms) {
   if (n > DENSE_MAX_N) return SCAN_EINVAL;
-  const size_t nn = (size_t)n * (size_t)n;
+  const int64_t np = (n + DENSE_PAD - 1) / DENSE_PAD * DENSE_PAD;
+  const size_t nn = (size_t)np * (size_t)np;
   __nv_bfloat16* M = pool.get<__nv_bfloat16>(nn);
   float* C = pool.get<float>(nn);
   if (!M || !C) return SCAN_ENOMEM;
@@ -93,7 +99,7 @@ int dense_counts_and_sims(int kind, const int64_t* off, const int32_t* adj, cons
   GS_CUDA(cudaEventRecord(e0, s));
   GS_CUDA(cudaMemsetAsync(M, 0, nn * sizeof(__nv_bfloat16), s));
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 7) / 8, 152 * 16));
-  k_dense_fill<<<grid, 256, 0, s>>>(off, adj, n, M);
+  k_dense_fill<<<grid, 256, 0, s>>>(off, adj, n, np, M);
   GS_LAUNCH();
   {
     std::lock_guard<std::mutex> lock(g_cublas_mu);
@@ -104,7 +110,7 @@ int dense_counts_and_sims(int kind, const int64_t* off, const int32_t* adj, cons
     cublasHandle_t h = g_cublas[dev];
     if (cublasSetStream(h, s) != CUBLAS_STATUS_SUCCESS) return SCAN_ECUDA;
     const float one = 1.0f, zero = 0.0f;
-    const int ni = (int)n;
+    const int ni = (int)np;
     // (A+I) is symmetric, so row- and column-major agree: C = (A+I)(A+I)
     if (cublasGemmEx(h, CUBLAS_OP_N, CUBLAS_OP_N, ni, ni, ni, &one, M, CUDA_R_16BF, ni, M,
                      CUDA_R_16BF, ni, &zero, C, CUDA_R_32F, ni, CUBLAS_COMPUTE_32F,
@@ -112,7 +118,7 @@ int dense_counts_and_sims(int kind, const int64_t* off, const int32_t* adj, cons
       return SCAN_ECUDA;
   }
   GS_CUDA(cudaEventRecord(e1, s));
-  k_dense_sims<<<grid, 256, 0, s>>>(kind, off, adj, deg, n, M, C, lsh_T, sim_csr, status);
+  k_dense_sims<<<grid, 256, 0, s>>>(kind, off, adj, deg, n, np, M, C, lsh_T, sim_csr, status);
   GS_LAUNCH();
   if (count_ms) {
     GS_CUDA(cudaEventSynchronize(e1));
