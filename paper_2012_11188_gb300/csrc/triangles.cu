@@ -251,15 +251,20 @@ struct SliceSmem {
 };
 
 // One probe of the stream element x at position j of out(u): a hit w = x
-// adds one to (v,w) in vcnt (shared; global for BIG) and to (u,w) at j.
+// adds one to (v,w) in vcnt (shared; global for BIG) and to (u,w) at j. The
+// (u,w) count is at most d+(u) - 1 < sqrt(2m) < 2^16 whenever the graph has
+// fewer than 2^31 arcs (IT = int32), so it is kept as a 16-bit half of a
+// 32-bit word (tc16): half the footprint of the most scattered atomics.
 template <bool BIG, typename IT>
 __device__ __forceinline__ bool probe(const OutTable& tab, int32_t x, IT j, int64_t ob,
-                                      uint32_t* vcnt, uint32_t* __restrict__ tcnt) {
+                                      uint32_t* vcnt, uint32_t* __restrict__ tcnt,
+                                      uint32_t* __restrict__ tc16) {
   const int q = table_lookup<BIG>(tab, x);
   if (q < 0) return false;
   if (!BIG) atomicAdd(&vcnt[q], 1u);
   else atomicAdd(&tcnt[ob + q], 1u);
-  atomicAdd(&tcnt[j], 1u);
+  if (sizeof(IT) == 4) atomicAdd(&tc16[j >> 1], 1u << ((j & 1) << 4));
+  else atomicAdd(&tcnt[j], 1u);
   return true;
 }
 
@@ -277,8 +282,8 @@ __device__ __forceinline__ void process_slice(
     const int32_t* __restrict__ adj, const int32_t* __restrict__ deg,
     const int64_t* __restrict__ off, const int32_t* __restrict__ odeg,
     const int32_t* __restrict__ oadj, int lsh_T, const OutTable& tab, uint32_t* vcnt,
-    const SliceSmem& sm, uint32_t* __restrict__ tcnt, int32_t* __restrict__ twin_rel,
-    unsigned& bad) {
+    const SliceSmem& sm, uint32_t* __restrict__ tcnt, uint32_t* __restrict__ tc16,
+    int32_t* __restrict__ twin_rel, unsigned& bad) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int64_t p = p0 + lane;
@@ -348,7 +353,7 @@ __device__ __forceinline__ void process_slice(
         if (t0 + 32 * rr >= len) break;
         const IT j = ub + (IT)(t0 + 32 * rr + lane);
         if (xs[rr] == v) sm.jv[i] = j;
-        hits += probe<BIG, IT>(tab, xs[rr], j, ob, vcnt, tcnt) ? 1u : 0u;
+        hits += probe<BIG, IT>(tab, xs[rr], j, ob, vcnt, tcnt, tc16) ? 1u : 0u;
       }
     }
     hits = __reduce_add_sync(FULL, hits);
@@ -399,7 +404,7 @@ __device__ __forceinline__ void process_slice(
       for (int rr = 0; rr < R; ++rr) {
         const int own = owns[rr];
         if (xs[rr] == v) sm.jv[own] = js[rr];
-        const bool hit = probe<BIG, IT>(tab, xs[rr], js[rr], ob, vcnt, tcnt);
+        const bool hit = probe<BIG, IT>(tab, xs[rr], js[rr], ob, vcnt, tcnt, tc16);
         const unsigned hm = __ballot_sync(FULL, hit);
         if (hm) {
           // lanes of one owner are contiguous; its first lane adds
@@ -435,7 +440,8 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
             const int32_t* __restrict__ oadj, int64_t n, const int64_t* __restrict__ item_off,
             const int32_t* __restrict__ order, unsigned long long* __restrict__ work, int lsh_T,
             int od_cap, int64_t* __restrict__ deferred, unsigned long long* __restrict__ n_deferred,
-            bool deferred_only, uint32_t* __restrict__ tcnt, int32_t* __restrict__ twin_rel,
+            bool deferred_only, uint32_t* __restrict__ tcnt, uint32_t* __restrict__ tc16,
+            int32_t* __restrict__ twin_rel,
             unsigned* status) {
   // shared layout for od_cap (a power of two >= every od handled here) and
   // hcap = 2^table_log2(od_cap): the table (t0, t1, p0, p1; 12 bytes per
@@ -498,7 +504,7 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
       const int64_t pos0 = p_begin + slice;
       if (pos0 >= p_end) break;
       process_slice<BIG, IT>(pos0, p_end, rb, (int32_t)v, dv, od, ob, adj, deg, off, odeg, oadj,
-                             lsh_T, tab, vcnt, sm, tcnt, twin_rel, bad);
+                             lsh_T, tab, vcnt, sm, tcnt, tc16, twin_rel, bad);
     }
     __syncthreads();
     if (!BIG)
@@ -520,7 +526,8 @@ __global__ void __launch_bounds__(SW_WARPS * 32, 8)
 k_tri_small(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
             const int32_t* __restrict__ deg, const int32_t* __restrict__ odeg,
             const int32_t* __restrict__ oadj, int64_t n, unsigned long long* __restrict__ work,
-            int lsh_T, uint32_t* __restrict__ tcnt, int32_t* __restrict__ twin_rel,
+            int lsh_T, uint32_t* __restrict__ tcnt, uint32_t* __restrict__ tc16,
+            int32_t* __restrict__ twin_rel,
             unsigned* status) {
   __shared__ __align__(16) uint32_t s_tab[SW_WARPS][3 * SW_SLOTS];  // t0 | t1 | p0 p1
   __shared__ uint32_t s_cnt[SW_WARPS][SMALL_OD];
@@ -555,10 +562,10 @@ k_tri_small(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
       for (int64_t pos0 = 0; pos0 < dv; pos0 += 32) {
         if (use_table)
           process_slice<false, IT>(pos0, dv, rb, (int32_t)vv, dv, od, ob, adj, deg, off, odeg,
-                                   oadj, lsh_T, tab, vcnt, sm, tcnt, twin_rel, bad);
+                                   oadj, lsh_T, tab, vcnt, sm, tcnt, tc16, twin_rel, bad);
         else
           process_slice<true, IT>(pos0, dv, rb, (int32_t)vv, dv, od, ob, adj, deg, off, odeg,
-                                  oadj, lsh_T, tab, vcnt, sm, tcnt, twin_rel, bad);
+                                  oadj, lsh_T, tab, vcnt, sm, tcnt, tc16, twin_rel, bad);
       }
       __syncwarp();
       if (use_table)
@@ -604,6 +611,7 @@ __global__ void __launch_bounds__(EXPAND_T)
 k_expand(int kind, const int64_t* __restrict__ off, const int32_t* __restrict__ deg,
          const int64_t* __restrict__ odp, const int32_t* __restrict__ oadj,
          const int32_t* __restrict__ opos, const uint32_t* __restrict__ tcnt,
+         const uint32_t* __restrict__ tc16,
          const int32_t* __restrict__ twin_rel, int64_t n, int lsh_T,
          double* __restrict__ sim_csr, unsigned* status) {
   __shared__ int64_t s_bracket[2];
@@ -624,7 +632,9 @@ k_expand(int kind, const int64_t* __restrict__ off, const int32_t* __restrict__ 
       const int32_t da = deg[a], db = deg[b];
       // LSH mode: approximated edges are written by the estimate pass
       if (lsh_T >= 0 && da > lsh_T && db > lsh_T) continue;
-      const double sv = sim_of(kind, (int64_t)tcnt[j] + 2, da, db);
+      int64_t t = tcnt[j];
+      if (tc16) t += (tc16[j >> 1] >> ((j & 1) << 4)) & 0xffffu;
+      const double sv = sim_of(kind, t + 2, da, db);
       sim_csr[ra + opos[j]] = sv;
       const int32_t tr = twin_rel[j];
       if (tr < 0) bad = 1;
@@ -649,7 +659,7 @@ template <typename IT>
 int launch_counting(const int64_t* off, const int32_t* adj, const int32_t* deg, const int32_t* odeg,
                     const int32_t* oadj, int64_t n, const int64_t* item_off, const int32_t* order,
                     unsigned long long* work, int lsh_T, int32_t max_od, int64_t* deferred,
-                    unsigned long long* n_deferred, uint32_t* tcnt, int32_t* twin,
+                    unsigned long long* n_deferred, uint32_t* tcnt, uint32_t* tc16, int32_t* twin,
                     unsigned* status, cudaStream_t s) {
   int od_cap = 16;
   while (od_cap < max_od && od_cap < SMEM_OD_MAX) od_cap <<= 1;
@@ -666,21 +676,22 @@ int launch_counting(const int64_t* off, const int32_t* adj, const int32_t* deg, 
   if (per_sm < 1) per_sm = 1;
   k_triangles<false, IT><<<sms * per_sm, TRI_THREADS, smem, s>>>(
       off, adj, deg, odeg, oadj, n, item_off, order, work, lsh_T, od_cap, deferred, n_deferred,
-      false, tcnt, twin, status);
+      false, tcnt, tc16, twin, status);
   GS_LAUNCH();
   int small_per_sm = 1;
   GS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&small_per_sm, k_tri_small<IT>,
                                                         SW_WARPS * 32, 0));
   if (small_per_sm < 1) small_per_sm = 1;
   k_tri_small<IT><<<sms * small_per_sm, SW_WARPS * 32, 0, s>>>(off, adj, deg, odeg, oadj, n,
-                                                               work + 2, lsh_T, tcnt, twin, status);
+                                                               work + 2, lsh_T, tcnt, tc16, twin,
+                                                               status);
   GS_LAUNCH();
   // items with out-lists too long for the shared table, and items deferred
   // by the CTA kernel (normally none: the launch then ends at once)
   const bool deferred_only = max_od <= SMEM_OD_MAX;
   k_triangles<true, IT><<<deferred_only ? sms : sms * 4, TRI_THREADS, 0, s>>>(
       off, adj, deg, odeg, oadj, n, item_off, order, work + 1, lsh_T, 0, deferred, n_deferred,
-      deferred_only, tcnt, twin, status);
+      deferred_only, tcnt, tc16, twin, status);
   GS_LAUNCH();
   return SCAN_OK;
 }
@@ -693,6 +704,9 @@ int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* a
   const int64_t m = arcs;  // out-lists live in CSR slots: counts and twins are indexed by arc
   const int64_t nbins = (int64_t)maxdeg + 1;
   uint32_t* tcnt = pool.get<uint32_t>(m);
+  // 16-bit (u,w) counters, two per word, when positions fit in 32 bits
+  const bool narrow = m < ((int64_t)1 << 31) - 1;
+  uint32_t* tc16 = narrow ? pool.get<uint32_t>(m / 2 + 1) : nullptr;
   int32_t* twin = pool.get<int32_t>(m);
   int32_t* items = pool.get<int32_t>(n);
   int32_t* items_sorted = pool.get<int32_t>(n);
@@ -703,10 +717,12 @@ int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* a
   unsigned long long* work = pool.get<unsigned long long>(4);  // 3 counters + deferred count
   // items: at most one per vertex plus one per CHUNK arcs
   int64_t* deferred = pool.get<int64_t>(n + m / CHUNK + 1);
-  if (!tcnt || !twin || !items || !items_sorted || !order || !item_off || !hist || !start ||
+  if (!tcnt || (narrow && !tc16) || !twin || !items || !items_sorted || !order || !item_off ||
+      !hist || !start ||
       !work || !deferred)
     return SCAN_ENOMEM;
   GS_CUDA(cudaMemsetAsync(tcnt, 0, m * sizeof(uint32_t), s));
+  if (narrow) GS_CUDA(cudaMemsetAsync(tc16, 0, (m / 2 + 1) * sizeof(uint32_t), s));
   GS_CUDA(cudaMemsetAsync(work, 0, 4 * sizeof(unsigned long long), s));
   GS_CUDA(cudaMemsetAsync(hist, 0, 2 * nbins * sizeof(unsigned long long), s));
   if (m > 0) {
@@ -731,12 +747,12 @@ int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* a
   GS_CUDA(cudaEventCreate(&e1));
   GS_CUDA(cudaEventRecord(e0, s));
   if (n > 0 && m > 0) {
-    if (m < ((int64_t)1 << 31) - 1) {
+    if (narrow) {
       GS_TRY(launch_counting<int32_t>(off, adj, deg, odeg, oadj, n, item_off, order, work, lsh_T,
-                                      max_od, deferred, work + 3, tcnt, twin, status, s));
+                                      max_od, deferred, work + 3, tcnt, tc16, twin, status, s));
     } else {
       GS_TRY(launch_counting<int64_t>(off, adj, deg, odeg, oadj, n, item_off, order, work, lsh_T,
-                                      max_od, deferred, work + 3, tcnt, twin, status, s));
+                                      max_od, deferred, work + 3, tcnt, nullptr, twin, status, s));
     }
   }
   GS_CUDA(cudaEventRecord(e1, s));
@@ -746,7 +762,7 @@ int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* a
     const int64_t edges = m / 2;
     const int64_t ch = (int64_t)EXPAND_T * EXPAND_ITEMS;
     k_expand<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((edges + ch - 1) / ch, 152 * 32)),
-               EXPAND_T, 0, s>>>(kind, off, deg, odp, oadj, opos, tcnt, twin, n, lsh_T, sim_csr,
+               EXPAND_T, 0, s>>>(kind, off, deg, odp, oadj, opos, tcnt, tc16, twin, n, lsh_T, sim_csr,
                                  status);
     GS_LAUNCH();
   }
@@ -757,6 +773,7 @@ int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* a
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   pool.put(tcnt);
+  if (tc16) pool.put(tc16);
   pool.put(twin);
   pool.put(deferred);
   pool.put(items);
