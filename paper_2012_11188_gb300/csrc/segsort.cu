@@ -205,38 +205,58 @@ k_sort_warp_reg(uint64_t* __restrict__ key, int32_t* __restrict__ val,
   }
 }
 
-// Shared-memory slot of tile element i: one pad slot per 8 elements, so that
-// a warp whose lanes hold 8 consecutive elements each (lane l: 8l .. 8l+7)
-// touches distinct banks when it stores or loads them.
-__device__ __forceinline__ int pslot(int i) { return i + (i >> 3); }
+// Passes a segment of length len takes part in: one per run length L = TILE,
+// 2*TILE, ... below len.
+__device__ __forceinline__ int passes_for(int64_t len) {
+  int p = 0;
+  for (int64_t L = TILE; L < len; L <<= 1) ++p;
+  return p;
+}
+
+// Shared-memory slot of tile element i with one pad slot per R elements, so
+// that a warp whose lanes hold R consecutive elements each (lane l: R*l ..
+// R*l+R-1) touches distinct banks when it stores or loads them.
+template <int R>
+__device__ __forceinline__ int pslot(int i) { return i + i / R; }
 
 // Merge path over padded shared runs: elements of A = [a0, a0+la) among the
 // first d outputs of merge(A, B), B = [b0, b0+lb).
+template <int R>
 __device__ __forceinline__ int smem_merge_path_p(const uint64_t* k, const int32_t* v, int a0,
                                                  int la, int b0, int lb, int d) {
   int lo = max(0, d - lb), hi = min(d, la);
   while (lo < hi) {
     const int i = (lo + hi) >> 1;
-    const int pb = pslot(b0 + d - 1 - i), pa = pslot(a0 + i);
+    const int pb = pslot<R>(b0 + d - 1 - i), pa = pslot<R>(a0 + i);
     if (before(k[pb], v[pb], k[pa], v[pa])) hi = i;
     else lo = i + 1;
   }
   return lo;
 }
 
-// One CTA of TT threads sorts a tile of up to TT*8 elements at the next power
-// of two SE >= max(len, 256): SE/256 warps sort 256 elements each in
-// registers, then merge-path levels in shared memory double the runs up to
-// SE, each thread writing 8 outputs. Tiles are whole segments (TILED = false)
-// or TILE-element pieces of longer segments (TILED = true, TT*8 = TILE).
-template <int TT, bool TILED>
-__global__ void __launch_bounds__(TT, 1024 / TT)
+#ifndef GS_SORT_TILE_RI
+#define GS_SORT_TILE_RI 8  // elements per lane of the warp sorts inside a 4096-element tile
+#endif
+
+// One CTA of TT threads sorts a tile of up to TT*RI elements at the next
+// power of two SE >= max(len, 32*RI): SE/(32*RI) warps sort 32*RI elements
+// each in registers (RI per lane), then merge-path levels in shared memory
+// double the runs up to SE, each thread writing RI outputs. Tiles are whole
+// segments (TILED = false) or TILE-element pieces of longer segments
+// (TILED = true, TT*RI = TILE).
+// A tiled segment that takes an odd number of merge passes has its tiles
+// written to the scratch buffer (tk, tv), so that its last pass ends in
+// (key, val).
+template <int TT, int RI, bool TILED>
+__global__ void __launch_bounds__(TT, RI >= 16 ? 2 : 1024 / TT)
 k_sort_tile(uint64_t* __restrict__ key, int32_t* __restrict__ val,
             const int64_t* __restrict__ seg_off, const int64_t* __restrict__ list,
             const unsigned long long* __restrict__ count_ptr,
-            const int64_t* __restrict__ tile_prefix, int64_t nlong) {
-  constexpr int CAP = TT * 8;
-  constexpr int PCAP = CAP + CAP / 8;  // padded slots per buffer
+            const int64_t* __restrict__ tile_prefix, int64_t nlong, uint64_t* __restrict__ tk,
+            int32_t* __restrict__ tv) {
+  constexpr int CAP = TT * RI;
+  constexpr int RUN = 32 * RI;          // elements sorted by one warp in registers
+  constexpr int PCAP = CAP + CAP / RI;  // padded slots per buffer
   extern __shared__ uint64_t tsm[];
   uint64_t* k0 = tsm;
   uint64_t* k1 = tsm + PCAP;
@@ -246,6 +266,8 @@ k_sort_tile(uint64_t* __restrict__ key, int32_t* __restrict__ val,
   const int64_t cnt = (int64_t)*count_ptr;
   for (int64_t u = blockIdx.x; u < cnt; u += gridDim.x) {
     int64_t b, len;
+    uint64_t* ok = key;
+    int32_t* ov = val;
     if (!TILED) {
       const int64_t sg = list[u];
       b = seg_off[sg];
@@ -259,23 +281,24 @@ k_sort_tile(uint64_t* __restrict__ key, int32_t* __restrict__ val,
       const int64_t sg = list[lo];
       b = seg_off[sg] + (u - tile_prefix[lo]) * CAP;
       len = min((int64_t)CAP, seg_off[sg + 1] - b);
+      if (passes_for(seg_off[sg + 1] - seg_off[sg]) & 1) { ok = tk; ov = tv; }
     }
-    int se = WTILE;
+    int se = RUN;
     while (se < len) se <<= 1;
-    // 1. the first se/256 warps sort 256 elements each in registers
-    if (wid * WTILE < se) {
-      uint64_t K[8];
-      int32_t V[8];
+    // 1. the first se/RUN warps sort RUN elements each in registers
+    if (wid * RUN < se) {
+      uint64_t K[RI];
+      int32_t V[RI];
 #pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        const int64_t i = (int64_t)wid * WTILE + 8 * lane + r;
+      for (int r = 0; r < RI; ++r) {
+        const int64_t i = (int64_t)wid * RUN + RI * lane + r;
         if (i < len) { K[r] = key[b + i]; V[r] = val[b + i]; }
         else { K[r] = 0; V[r] = SENT_V; }
       }
-      warp_sort_reg<8>(K, V, lane);
+      warp_sort_reg<RI>(K, V, lane);
 #pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        const int i = pslot(wid * WTILE + 8 * lane + r);
+      for (int r = 0; r < RI; ++r) {
+        const int i = pslot<RI>(wid * RUN + RI * lane + r);
         k0[i] = K[r];
         v0[i] = V[r];
       }
@@ -284,22 +307,22 @@ k_sort_tile(uint64_t* __restrict__ key, int32_t* __restrict__ val,
     // 2. merge levels in shared memory: runs of w -> 2w, ping-pong k0/v0 <-> k1/v1
     uint64_t *ks = k0, *kd = k1;
     int32_t *vs = v0, *vd = v1;
-    for (int w = WTILE; w < se; w <<= 1) {
-      const int o = 8 * t;  // first output of this thread
+    for (int w = RUN; w < se; w <<= 1) {
+      const int o = RI * t;  // first output of this thread
       if (o < se) {
         const int a0 = (o / (2 * w)) * (2 * w);
         const int b0 = a0 + w;
         const int d = o - a0;
-        int ia = smem_merge_path_p(ks, vs, a0, w, b0, w, d);
+        int ia = smem_merge_path_p<RI>(ks, vs, a0, w, b0, w, d);
         int ib = d - ia;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
+        for (int q = 0; q < RI; ++q) {
           bool take_a;
-          const int pa = pslot(a0 + ia), pb = pslot(b0 + ib);
+          const int pa = pslot<RI>(a0 + ia), pb = pslot<RI>(b0 + ib);
           if (ia >= w) take_a = false;
           else if (ib >= w) take_a = true;
           else take_a = !before(ks[pb], vs[pb], ks[pa], vs[pa]);
-          const int po = pslot(o + q);
+          const int po = pslot<RI>(o + q);
           if (take_a) { kd[po] = ks[pa]; vd[po] = vs[pa]; ++ia; }
           else { kd[po] = ks[pb]; vd[po] = vs[pb]; ++ib; }
         }
@@ -309,18 +332,22 @@ k_sort_tile(uint64_t* __restrict__ key, int32_t* __restrict__ val,
       int32_t* tv = vs; vs = vd; vd = tv;
     }
     for (int i = t; i < len; i += TT) {
-      const int pi = pslot(i);
-      key[b + i] = ks[pi];
-      val[b + i] = vs[pi];
+      const int pi = pslot<RI>(i);
+      ok[b + i] = ks[pi];
+      ov[b + i] = vs[pi];
     }
     __syncthreads();
   }
 }
 
-template <int TT>
+template <int TT, int RI>
 constexpr size_t tile_smem_bytes() {
-  return (size_t)(TT * 8 + TT) * (2 * sizeof(uint64_t) + 2 * sizeof(int32_t));
+  return (size_t)(TT * RI + TT) * (2 * sizeof(uint64_t) + 2 * sizeof(int32_t));
 }
+
+// the 4096-element tile kernel: 512 threads x 8, or 256 threads x 16
+constexpr int T4K_RI = GS_SORT_TILE_RI;
+constexpr int T4K_T = TILE / T4K_RI;
 
 // Tiles per long segment (prefix computed by the caller).
 __global__ void k_long_tiles(const int64_t* __restrict__ seg_off, const int64_t* __restrict__ list,
@@ -354,13 +381,6 @@ __device__ __forceinline__ int64_t merge_path(const uint64_t* ka, const int32_t*
   return lo;
 }
 
-// Passes a segment of length len takes part in: one per run length L = TILE,
-// 2*TILE, ... below len.
-__device__ __forceinline__ int passes_for(int64_t len) {
-  int p = 0;
-  for (int64_t L = TILE; L < len; L <<= 1) ++p;
-  return p;
-}
 
 __device__ __forceinline__ int64_t chunk_segment(const int64_t* chunk_prefix, int64_t nlong,
                                                  int64_t c) {
@@ -378,23 +398,30 @@ __device__ __forceinline__ int64_t chunk_segment(const int64_t* chunk_prefix, in
 struct MergeDesc {
   int64_t a0, b0, out;
   int32_t na, nb;
+  int32_t from_tmp;  // runs are read from the scratch buffer and written to (key, val)
 };
 
-// Merge-path splits of every output chunk of a pass, all in parallel (one
-// thread per chunk), written as chunk descriptors.
-__global__ void k_merge_partition(const uint64_t* __restrict__ sk, const int32_t* __restrict__ sv,
+// Merge-path splits of every output chunk of pass `pass` (run length L),
+// all in parallel (one thread per chunk), written as chunk descriptors. A
+// segment with P passes reads pass p from the scratch buffer when P - p is
+// odd, so that its last pass writes (key, val).
+__global__ void k_merge_partition(const uint64_t* __restrict__ key, const int32_t* __restrict__ val,
+                                  const uint64_t* __restrict__ tk, const int32_t* __restrict__ tv,
                                   const int64_t* __restrict__ seg_off,
                                   const int64_t* __restrict__ list,
                                   const int64_t* __restrict__ chunk_prefix, int64_t nlong, int64_t L,
-                                  MergeDesc* __restrict__ desc) {
+                                  int pass, MergeDesc* __restrict__ desc) {
   const int64_t total = chunk_prefix[nlong];
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < total;
        c += (int64_t)gridDim.x * blockDim.x) {
     const int64_t si = chunk_segment(chunk_prefix, nlong, c);
     const int64_t sg = list[si];
     const int64_t base = seg_off[sg], len = seg_off[sg + 1] - base;
-    MergeDesc d{0, 0, 0, 0, 0};
+    MergeDesc d{0, 0, 0, 0, 0, 0};
     if (len > L) {
+      d.from_tmp = (passes_for(len) - pass) & 1;
+      const uint64_t* sk = d.from_tmp ? tk : key;
+      const int32_t* sv = d.from_tmp ? tv : val;
       const int64_t o0 = (c - chunk_prefix[si]) * MERGE_CHUNK;
       const int64_t o1 = min(len, o0 + MERGE_CHUNK);
       // run pair containing [o0, o1): MERGE_CHUNK divides 2L
@@ -439,9 +466,8 @@ __device__ __forceinline__ void cp_async_wait() {
 // memory (cp.async) while it merges the current one, and outputs are staged
 // in shared memory so the global stores are coalesced.
 __global__ void __launch_bounds__(MERGE_T)
-k_merge_pass(const uint64_t* __restrict__ sk, const int32_t* __restrict__ sv,
-             uint64_t* __restrict__ dk, int32_t* __restrict__ dv,
-             const int64_t* __restrict__ chunk_prefix, int64_t nlong,
+k_merge_pass(uint64_t* __restrict__ key, int32_t* __restrict__ val, uint64_t* __restrict__ tk,
+             int32_t* __restrict__ tv, const int64_t* __restrict__ chunk_prefix, int64_t nlong,
              const MergeDesc* __restrict__ desc) {
   __shared__ uint64_t ink[2][MERGE_CHUNK];
   __shared__ int32_t inv[2][MERGE_CHUNK];
@@ -454,8 +480,10 @@ k_merge_pass(const uint64_t* __restrict__ sk, const int32_t* __restrict__ sv,
   auto po = [](int i) { return i + i / MERGE_ITEMS; };
   // issue the copies of chunk c into buffer b (an empty group when inactive)
   auto stage = [&](int64_t c, int b) -> MergeDesc {
-    MergeDesc m{0, 0, 0, 0, 0};
+    MergeDesc m{0, 0, 0, 0, 0, 0};
     if (c < total) m = desc[c];
+    const uint64_t* sk = m.from_tmp ? tk : key;
+    const int32_t* sv = m.from_tmp ? tv : val;
     for (int i = t; i < m.na; i += MERGE_T) {
       cp_async8(&ink[b][i], sk + m.a0 + i);
       cp_async4(&inv[b][i], sv + m.a0 + i);
@@ -500,6 +528,8 @@ k_merge_pass(const uint64_t* __restrict__ sk, const int32_t* __restrict__ sv,
       }
       __syncthreads();
       const int64_t out = cur.out;
+      uint64_t* dk = cur.from_tmp ? key : tk;
+      int32_t* dv = cur.from_tmp ? val : tv;
       for (int i = t; i < nout; i += MERGE_T) {
         dk[out + i] = ok_[po(i)];
         dv[out + i] = ov_[po(i)];
@@ -510,27 +540,6 @@ k_merge_pass(const uint64_t* __restrict__ sk, const int32_t* __restrict__ sv,
     b ^= 1;
   }
   cp_async_wait<0>();
-}
-
-// Long segments that took an odd number of passes end in the scratch buffer:
-// copy them back.
-__global__ void k_copy_long(const uint64_t* __restrict__ sk, const int32_t* __restrict__ sv,
-                            uint64_t* __restrict__ dk, int32_t* __restrict__ dv,
-                            const int64_t* __restrict__ seg_off, const int64_t* __restrict__ list,
-                            const int64_t* __restrict__ chunk_prefix, int64_t nlong) {
-  const int64_t total = chunk_prefix[nlong];
-  for (int64_t c = blockIdx.x; c < total; c += gridDim.x) {
-    const int64_t si = chunk_segment(chunk_prefix, nlong, c);
-    const int64_t sg = list[si];
-    const int64_t base = seg_off[sg], len = seg_off[sg + 1] - base;
-    if ((passes_for(len) & 1) == 0) continue;
-    const int64_t o0 = (c - chunk_prefix[si]) * MERGE_CHUNK;
-    const int64_t o1 = min(len, o0 + MERGE_CHUNK);
-    for (int64_t i = o0 + threadIdx.x; i < o1; i += blockDim.x) {
-      dk[base + i] = sk[base + i];
-      dv[base + i] = sv[base + i];
-    }
-  }
 }
 
 }  // namespace
@@ -572,18 +581,21 @@ int segmented_sort_desc(uint64_t* key, int32_t* val, const int64_t* seg_off, int
                                                                 counts + 1);
     GS_LAUNCH();
   }
-  GS_CUDA(cudaFuncSetAttribute(k_sort_tile<512, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)tile_smem_bytes<512>()));
-  GS_CUDA(cudaFuncSetAttribute(k_sort_tile<512, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)tile_smem_bytes<512>()));
+  GS_CUDA(cudaFuncSetAttribute(k_sort_tile<T4K_T, T4K_RI, true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)tile_smem_bytes<T4K_T, T4K_RI>()));
+  GS_CUDA(cudaFuncSetAttribute(k_sort_tile<T4K_T, T4K_RI, false>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)tile_smem_bytes<T4K_T, T4K_RI>()));
   if (hc[2]) {
-    k_sort_tile<128, false><<<grid_of((int64_t)hc[2], 1), 128, tile_smem_bytes<128>(), s>>>(
-        key, val, seg_off, list + base[2], counts + 2, nullptr, 0);
+    k_sort_tile<128, 8, false><<<grid_of((int64_t)hc[2], 1), 128, tile_smem_bytes<128, 8>(), s>>>(
+        key, val, seg_off, list + base[2], counts + 2, nullptr, 0, nullptr, nullptr);
     GS_LAUNCH();
   }
   if (hc[3]) {
-    k_sort_tile<512, false><<<grid_of((int64_t)hc[3], 1), 512, tile_smem_bytes<512>(), s>>>(
-        key, val, seg_off, list + base[3], counts + 3, nullptr, 0);
+    k_sort_tile<T4K_T, T4K_RI, false><<<grid_of((int64_t)hc[3], 1), T4K_T,
+                                        tile_smem_bytes<T4K_T, T4K_RI>(), s>>>(
+        key, val, seg_off, list + base[3], counts + 3, nullptr, 0, nullptr, nullptr);
     GS_LAUNCH();
   }
   const int64_t nlong = (int64_t)hc[4];
@@ -603,28 +615,24 @@ int segmented_sort_desc(uint64_t* key, int32_t* val, const int64_t* seg_off, int
     GS_TRY(exclusive_scan_i64(chunks, chunk_prefix, nlong, pool, s));
     const int64_t ntiles = (int64_t)hc[NCLASS];
     // tile sort (count = ntiles, read from counts[NCLASS])
-    k_sort_tile<512, true><<<grid_of(ntiles, 1), 512, tile_smem_bytes<512>(), s>>>(
-        key, val, seg_off, llist, counts + NCLASS, tile_prefix, nlong);
+    k_sort_tile<T4K_T, T4K_RI, true><<<grid_of(ntiles, 1), T4K_T, tile_smem_bytes<T4K_T, T4K_RI>(),
+                                       s>>>(key, val, seg_off, llist, counts + NCLASS, tile_prefix,
+                                            nlong, tk, tv);
     GS_LAUNCH();
-    uint64_t *ck = key, *nk = tk;
-    int32_t *cv = val, *nv = tv;
     const int64_t total_chunks_ub = (total + MERGE_CHUNK - 1) / MERGE_CHUNK + nlong;
     MergeDesc* desc = pool.get<MergeDesc>((size_t)total_chunks_ub);
     if (!desc) return SCAN_ENOMEM;
-    for (int64_t L = TILE; L < max_len; L <<= 1) {
-      k_merge_partition<<<grid_of(total_chunks_ub, 256), 256, 0, s>>>(ck, cv, seg_off, llist,
-                                                                       chunk_prefix, nlong, L, desc);
+    // every pass reads each segment from the buffer its parity says and
+    // writes the other; the last pass of every segment writes (key, val)
+    int pass = 0;
+    for (int64_t L = TILE; L < max_len; L <<= 1, ++pass) {
+      k_merge_partition<<<grid_of(total_chunks_ub, 256), 256, 0, s>>>(
+          key, val, tk, tv, seg_off, llist, chunk_prefix, nlong, L, pass, desc);
       GS_LAUNCH();
-      k_merge_pass<<<grid_of(total_chunks_ub, 1), MERGE_T, 0, s>>>(ck, cv, nk, nv, chunk_prefix,
+      k_merge_pass<<<grid_of(total_chunks_ub, 1), MERGE_T, 0, s>>>(key, val, tk, tv, chunk_prefix,
                                                                   nlong, desc);
       GS_LAUNCH();
-      std::swap(ck, nk);
-      std::swap(cv, nv);
     }
-    // segments that took an odd number of passes end in the scratch buffer
-    k_copy_long<<<grid_of(total_chunks_ub, 1), 256, 0, s>>>(tk, tv, key, val, seg_off, llist,
-                                                           chunk_prefix, nlong);
-    GS_LAUNCH();
     pool.put(desc);
     pool.put(tk);
     pool.put(tv);
