@@ -131,7 +131,7 @@ int launch_orient(const int64_t* off, const int32_t* adj, const int32_t* deg, in
 // LSH estimate (their sim_csr entries are overwritten later).
 int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* adj,
                                   const int32_t* deg, int64_t n, int64_t arcs, const int32_t* od,
-                                  const int32_t* oadj, const int32_t* opos, int32_t maxdeg,
+                                  int32_t* oadj, int32_t* opos, int32_t maxdeg,
                                   int32_t max_od, int lsh_T, double* sim_csr, unsigned* status,
                                   Pool& pool, cudaStream_t s, float* count_ms);
 

@@ -28,7 +28,7 @@ namespace {
 #define GS_TRI_FAST_ROUNDS 12  // the same for out-lists streamed one at a time
 #endif
 #ifndef GS_TRI_LONG_LIST
-#define GS_TRI_LONG_LIST 128  // out-lists at least this long are streamed one at a time
+#define GS_TRI_LONG_LIST 64  // suffixes at least this long are streamed one at a time
 #endif
 constexpr int LONG_LIST = GS_TRI_LONG_LIST;
 
@@ -39,6 +39,21 @@ constexpr int SMEM_OD_MAX = 4096;    // out(v) sizes handled by the shared-memor
 
 __device__ __forceinline__ bool lower(int32_t du, int32_t u, int32_t dv, int32_t v) {
   return du < dv || (du == dv && u < v);
+}
+
+// Key of vertex x in the degree order: descending keys = ascending (d_x, x).
+__device__ __forceinline__ uint64_t rank_key(int32_t d, int32_t x) {
+  return ~(((uint64_t)(uint32_t)d << 32) | (uint32_t)x);
+}
+
+// Position of key kv in the descending key list kb[0..len), or -1.
+__device__ __forceinline__ int key_search(const uint64_t* __restrict__ kb, int len, uint64_t kv) {
+  int lo = 0, hi = len;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (kb[mid] > kv) lo = mid + 1; else hi = mid;
+  }
+  return (lo < len && kb[lo] == kv) ? lo : -1;
 }
 
 #ifndef GS_TRI_WARP_DEG
@@ -147,25 +162,17 @@ __constant__ uint32_t CUCKOO_MUL[2 * CUCKOO_ATTEMPTS] = {
 struct OutTable {
   const uint32_t* t0;
   int hcap;
-  int shift;             // 32 - L
-  uint32_t c0, c1;       // multipliers of the two tables
-  const int32_t* glist;  // out(v) in global memory (binary search)
+  int shift;              // 32 - L
+  uint32_t c0, c1;        // multipliers of the two tables
+  const uint64_t* gkey;   // rank keys of out(v) in global memory (binary search)
+  const int32_t* deg;     // degrees, for the rank key of a probed vertex
   int32_t od;
-  bool bsearch;          // no cuckoo placement: the item needs the binary-search path
+  bool bsearch;           // no cuckoo placement: the item needs the binary-search path
 };
-
-__device__ __forceinline__ int glist_search(const int32_t* list, int32_t od, int32_t x) {
-  int lo = 0, hi = od;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (list[mid] < x) lo = mid + 1; else hi = mid;
-  }
-  return (lo < od && list[lo] == x) ? lo : -1;
-}
 
 template <bool BIG>
 __device__ __forceinline__ int table_lookup(const OutTable& t, int32_t x) {
-  if (BIG) return glist_search(t.glist, t.od, x);
+  if (BIG) return x < 0 ? -1 : key_search(t.gkey, t.od, rank_key(t.deg[x], x));
   const uint32_t h0 = (uint32_t)x * t.c0, h1 = (uint32_t)x * t.c1;
   const uint32_t s0 = h0 >> t.shift, s1 = (h1 >> t.shift) + t.hcap;  // slot in t0 / t1
   const bool m0 = t.t0[s0] == h0, m1 = t.t0[s1] == h1;
@@ -205,7 +212,8 @@ __device__ __forceinline__ int table_log2(int32_t od) {
 // attempt placed every key.
 template <typename Sync, typename Any>
 __device__ __forceinline__ OutTable table_build(uint32_t* t0, int hcap, uint32_t* vcnt,
-                                                const int32_t* list, int32_t od, int tid,
+                                                const int32_t* list, const uint64_t* gkey,
+                                                const int32_t* deg, int32_t od, int tid,
                                                 int nthreads, Sync sync, Any any) {
   uint32_t* t1 = t0 + hcap;
   uint16_t* p0 = reinterpret_cast<uint16_t*>(t0 + 2 * hcap);
@@ -239,7 +247,7 @@ __device__ __forceinline__ OutTable table_build(uint32_t* t0, int hcap, uint32_t
     }
   for (int i = tid; i < od; i += nthreads) vcnt[i] = 0;
   sync();
-  return OutTable{t0, hcap, shift, c0, c1, list, od, failed};
+  return OutTable{t0, hcap, shift, c0, c1, gkey, deg, od, failed};
 }
 
 // Per-warp scratch for one 32-position slice.
@@ -247,7 +255,6 @@ struct SliceSmem {
   int32_t* u;
   int32_t* p;
   uint32_t* acc;
-  long long* jv;
 };
 
 // One probe of the stream element x at position j of out(u): a hit w = x
@@ -270,18 +277,22 @@ __device__ __forceinline__ bool probe(const OutTable& tab, int32_t x, IT j, int6
 
 // One warp: triangles u < v < w for the in-neighbours u of v among the CSR
 // positions [p0, min(p0+32, p_end)) of N(v). The in-neighbours are compacted
-// to lanes 0..k-1. Out-lists of at least LONG_LIST entries are streamed one
-// at a time, lane l taking elements l, l+32, ... (RF rounds of loads in
-// flight); the shorter ones are concatenated and walked 32 elements per round
-// (R rounds in flight), the owner of an element coming from the list starts
-// that fall in its round (ballot / or-reduce / popc). Hits on (u,v) are
-// counted per list; the position of v in out(u) is found in the stream.
+// to lanes 0..k-1, and each lane finds v in out(u) (ascending rank) by a
+// binary search of its rank key: that gives the twin position of the arc
+// u->v, and the possible third vertices w > v are the entries after it.
+// Suffixes of at least LONG_LIST entries are streamed one at a time, lane l
+// taking elements l, l+32, ... (RF rounds of loads in flight); the shorter
+// ones are concatenated and walked 32 elements per round (R rounds in
+// flight), the owner of an element coming from the suffix starts that fall
+// in its round (ballot / or-reduce / popc). Hits on (u,v) are counted per
+// list.
 template <bool BIG, typename IT>
 __device__ __forceinline__ void process_slice(
     int64_t p0, int64_t p_end, int64_t rb, int32_t v, int32_t dv, int32_t od, int64_t ob,
     const int32_t* __restrict__ adj, const int32_t* __restrict__ deg,
     const int64_t* __restrict__ off, const int32_t* __restrict__ odeg,
-    const int32_t* __restrict__ oadj, int lsh_T, const OutTable& tab, uint32_t* vcnt,
+    const int32_t* __restrict__ oadj, const uint64_t* __restrict__ okey,
+    const int64_t* __restrict__ odp, int lsh_T, const OutTable& tab, uint32_t* vcnt,
     const SliceSmem& sm, uint32_t* __restrict__ tcnt, uint32_t* __restrict__ tc16,
     int32_t* __restrict__ twin_rel, unsigned& bad) {
   const unsigned FULL = 0xffffffffu;
@@ -306,33 +317,34 @@ __device__ __forceinline__ void process_slice(
     sm.p[r] = (int32_t)p;
   }
   __syncwarp();
-  int32_t cu = -1, cp = 0, clen = 0;
-  IT cub = 0;
+  int32_t cp = 0, clen = 0;  // suffix length after v
+  IT cub = 0, jv = 0;        // suffix start; position of v in out(u)
+  bool found = false;
   if (lane < k) {
-    cu = sm.u[lane];
+    const int32_t cu = sm.u[lane];
     cp = sm.p[lane];
-    cub = (IT)off[cu];
-    clen = odeg[cu];
+    const IT ub = (IT)off[cu];
+    const int32_t len = odeg[cu];
+    const int pos = key_search(okey + odp[cu], len, rank_key(dv, v));
+    found = pos >= 0;
+    if (found) {
+      jv = ub + (IT)pos;
+      cub = jv + 1;
+      clen = len - pos - 1;
+    } else {
+      bad = 1;  // v lists u but u does not list v
+    }
   }
   if (od == 0) {
-    // no triangle has v in the middle: only locate v in the sorted out(u)
-    if (lane < k) {
-      int64_t lo = cub, hi = cub + clen;
-      while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (oadj[mid] < v) lo = mid + 1; else hi = mid;
-      }
-      if (lo < cub + clen && oadj[lo] == v) twin_rel[lo] = cp;
-      else bad = 1;
-    }
+    // no triangle has v in the middle: only the twin positions
+    if (found) twin_rel[jv] = cp;
     __syncwarp();
     return;
   }
   sm.acc[lane] = 0;
-  sm.jv[lane] = -1;
   __syncwarp();
 
-  // 1. long out-lists, one at a time
+  // 1. long suffixes, one at a time
   constexpr int RF = GS_TRI_FAST_ROUNDS;
   unsigned lm = __ballot_sync(FULL, lane < k && clen >= LONG_LIST);
   while (lm) {
@@ -352,7 +364,6 @@ __device__ __forceinline__ void process_slice(
       for (int rr = 0; rr < RF; ++rr) {
         if (t0 + 32 * rr >= len) break;
         const IT j = ub + (IT)(t0 + 32 * rr + lane);
-        if (xs[rr] == v) sm.jv[i] = j;
         hits += probe<BIG, IT>(tab, xs[rr], j, ob, vcnt, tcnt, tc16) ? 1u : 0u;
       }
     }
@@ -360,8 +371,8 @@ __device__ __forceinline__ void process_slice(
     if (lane == 0) sm.acc[i] += hits;
   }
 
-  // 2. short out-lists, concatenated: lane r takes the r-th short list
-  const bool is_short = lane < k && clen < LONG_LIST;
+  // 2. short non-empty suffixes, concatenated: lane r takes the r-th of them
+  const bool is_short = lane < k && clen > 0 && clen < LONG_LIST;
   const unsigned shm = __ballot_sync(FULL, is_short);
   if (shm) {
     const int k2 = __popc(shm);
@@ -388,7 +399,7 @@ __device__ __forceinline__ void process_slice(
       for (int rr = 0; rr < R; ++rr) {
         const int32_t r0 = rbase + 32 * rr;
         const int32_t t = r0 + lane;
-        // every list is non-empty (v is in out(u)), so the starts are distinct
+        // the concatenated suffixes are non-empty, so their starts are distinct
         const bool starts_here = lane < k2 && cstart >= r0 && cstart < r0 + 32;
         const unsigned smask = __reduce_or_sync(FULL, starts_here ? (1u << (cstart - r0)) : 0u);
         const int before = __popc(__ballot_sync(FULL, lane < k2 && cstart < r0));
@@ -403,7 +414,6 @@ __device__ __forceinline__ void process_slice(
 #pragma unroll
       for (int rr = 0; rr < R; ++rr) {
         const int own = owns[rr];
-        if (xs[rr] == v) sm.jv[own] = js[rr];
         const bool hit = probe<BIG, IT>(tab, xs[rr], js[rr], ob, vcnt, tcnt, tc16);
         const unsigned hm = __ballot_sync(FULL, hit);
         if (hm) {
@@ -415,15 +425,10 @@ __device__ __forceinline__ void process_slice(
     }
   }
   __syncwarp();
-  if (lane < k) {
-    const long long jv = sm.jv[lane];
-    if (jv < 0) {
-      bad = 1;  // v lists u but u does not list v
-    } else {
-      const uint32_t acc = sm.acc[lane];
-      if (acc) atomicAdd(&tcnt[jv], acc);
-      twin_rel[jv] = cp;  // position of u in N(v)
-    }
+  if (found) {
+    const uint32_t acc = sm.acc[lane];
+    if (acc) atomicAdd(&tcnt[jv], acc);
+    twin_rel[jv] = cp;  // position of u in N(v)
   }
   __syncwarp();
 }
@@ -437,7 +442,8 @@ template <bool BIG, typename IT>
 __global__ void __launch_bounds__(TRI_THREADS, 3)
 k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
             const int32_t* __restrict__ deg, const int32_t* __restrict__ odeg,
-            const int32_t* __restrict__ oadj, int64_t n, const int64_t* __restrict__ item_off,
+            const int32_t* __restrict__ oadj, const uint64_t* __restrict__ okey,
+            const int64_t* __restrict__ odp, int64_t n, const int64_t* __restrict__ item_off,
             const int32_t* __restrict__ order, unsigned long long* __restrict__ work, int lsh_T,
             int od_cap, int64_t* __restrict__ deferred, unsigned long long* __restrict__ n_deferred,
             bool deferred_only, uint32_t* __restrict__ tcnt, uint32_t* __restrict__ tc16,
@@ -452,7 +458,6 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
   __shared__ int32_t s_u[TRI_WARPS][32];
   __shared__ int32_t s_p[TRI_WARPS][32];
   __shared__ uint32_t s_acc[TRI_WARPS][32];
-  __shared__ long long s_jv[TRI_WARPS][32];
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   // BIG: first the items whose out-list is too long for the shared table
@@ -462,7 +467,7 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
   const int hcap = 1 << table_log2(od_cap);
   uint32_t* t0 = reinterpret_cast<uint32_t*>(smem4);
   uint32_t* vcnt = t0 + 3 * hcap;
-  const SliceSmem sm{s_u[wid], s_p[wid], s_acc[wid], s_jv[wid]};
+  const SliceSmem sm{s_u[wid], s_p[wid], s_acc[wid]};
   unsigned bad = 0;
 
   for (;;) {
@@ -483,9 +488,10 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
     const int32_t od = odeg[v];
     const bool skip_item = BIG ? (od <= SMEM_OD_MAX && !was_deferred) : (od > SMEM_OD_MAX);
     if (skip_item) { __syncthreads(); continue; }
-    OutTable tab{nullptr, 0, 27, 0u, 0u, oadj + ob, od, true};
+    OutTable tab{nullptr, 0, 27, 0u, 0u, okey + odp[v], deg, od, true};
     if (!BIG && od > 0) {
-      tab = table_build(t0, hcap, vcnt, oadj + ob, od, threadIdx.x, TRI_THREADS,
+      tab = table_build(t0, hcap, vcnt, oadj + ob, okey + odp[v], deg, od, threadIdx.x,
+                        TRI_THREADS,
                         [] { __syncthreads(); }, [](bool b) { return __syncthreads_or(b) != 0; });
       if (tab.bsearch) {  // hand the item to the BIG kernel
         if (threadIdx.x == 0) deferred[atomicAdd(n_deferred, 1ull)] = item;
@@ -504,7 +510,7 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
       const int64_t pos0 = p_begin + slice;
       if (pos0 >= p_end) break;
       process_slice<BIG, IT>(pos0, p_end, rb, (int32_t)v, dv, od, ob, adj, deg, off, odeg, oadj,
-                             lsh_T, tab, vcnt, sm, tcnt, tc16, twin_rel, bad);
+                             okey, odp, lsh_T, tab, vcnt, sm, tcnt, tc16, twin_rel, bad);
     }
     __syncthreads();
     if (!BIG)
@@ -525,7 +531,8 @@ template <typename IT>
 __global__ void __launch_bounds__(SW_WARPS * 32, 8)
 k_tri_small(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
             const int32_t* __restrict__ deg, const int32_t* __restrict__ odeg,
-            const int32_t* __restrict__ oadj, int64_t n, unsigned long long* __restrict__ work,
+            const int32_t* __restrict__ oadj, const uint64_t* __restrict__ okey,
+            const int64_t* __restrict__ odp, int64_t n, unsigned long long* __restrict__ work,
             int lsh_T, uint32_t* __restrict__ tcnt, uint32_t* __restrict__ tc16,
             int32_t* __restrict__ twin_rel,
             unsigned* status) {
@@ -534,11 +541,10 @@ k_tri_small(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
   __shared__ int32_t s_u[SW_WARPS][32];
   __shared__ int32_t s_p[SW_WARPS][32];
   __shared__ uint32_t s_acc[SW_WARPS][32];
-  __shared__ long long s_jv[SW_WARPS][32];
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   uint32_t* vcnt = s_cnt[wid];
-  const SliceSmem sm{s_u[wid], s_p[wid], s_acc[wid], s_jv[wid]};
+  const SliceSmem sm{s_u[wid], s_p[wid], s_acc[wid]};
   unsigned bad = 0;
   for (;;) {
     unsigned long long base = 0;
@@ -552,9 +558,9 @@ k_tri_small(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
       const int32_t od = odeg[vv];
       if (!warp_vertex(dv, od) || dv - od == 0) continue;  // CTA kernel, or no in-neighbours
       const int64_t ob = off[vv];
-      OutTable tab{nullptr, 0, 27, 0u, 0u, oadj + ob, od, true};
+      OutTable tab{nullptr, 0, 27, 0u, 0u, okey + odp[vv], deg, od, true};
       if (od > 0)
-        tab = table_build(s_tab[wid], SW_SLOTS, vcnt, oadj + ob, od, lane, 32,
+        tab = table_build(s_tab[wid], SW_SLOTS, vcnt, oadj + ob, okey + odp[vv], deg, od, lane, 32,
                           [] { __syncwarp(); },
                           [](bool b) { __syncwarp(); return __any_sync(0xffffffffu, b) != 0; });
       const bool use_table = !tab.bsearch;
@@ -562,10 +568,12 @@ k_tri_small(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
       for (int64_t pos0 = 0; pos0 < dv; pos0 += 32) {
         if (use_table)
           process_slice<false, IT>(pos0, dv, rb, (int32_t)vv, dv, od, ob, adj, deg, off, odeg,
-                                   oadj, lsh_T, tab, vcnt, sm, tcnt, tc16, twin_rel, bad);
+                                   oadj, okey, odp, lsh_T, tab, vcnt, sm, tcnt, tc16, twin_rel,
+                                   bad);
         else
           process_slice<true, IT>(pos0, dv, rb, (int32_t)vv, dv, od, ob, adj, deg, off, odeg,
-                                  oadj, lsh_T, tab, vcnt, sm, tcnt, tc16, twin_rel, bad);
+                                  oadj, okey, odp, lsh_T, tab, vcnt, sm, tcnt, tc16, twin_rel,
+                                  bad);
       }
       __syncwarp();
       if (use_table)
@@ -645,6 +653,64 @@ k_expand(int kind, const int64_t* __restrict__ off, const int32_t* __restrict__ 
   if (bad) atomicOr(status, (unsigned)DEV_BADGRAPH);
 }
 
+// Out-lists in degree order. Each out(u) = oadj[off[u] .. off[u] + od[u])
+// is re-ordered by the rank (d_x, x) ascending, with opos alongside; okey
+// (compact: out-arc e of u at odp[u] + i) keeps the sorted rank keys, stored
+// as ~(d_x << 32 | x) so that the descending segmented sort yields the
+// ascending rank order. Then, for an in-neighbour u of a middle vertex v, the
+// possible third vertices w > v of out(u) are exactly the entries after v:
+// the streams read sum over u of d+(u)(d+(u)-1)/2 elements, half of
+// sum d+(u)^2, and v's own position (its twin) comes from a binary search
+// instead of a compare on every streamed element.
+
+__global__ void __launch_bounds__(EXPAND_T)
+k_rank_keys(const int64_t* __restrict__ off, const int32_t* __restrict__ deg,
+            const int64_t* __restrict__ odp, const int32_t* __restrict__ oadj,
+            const int32_t* __restrict__ opos, int64_t n, uint64_t* __restrict__ okey,
+            int32_t* __restrict__ oval) {
+  __shared__ int64_t s_bracket[2];
+  const int64_t m = odp[n];
+  constexpr int64_t CH = (int64_t)EXPAND_T * EXPAND_ITEMS;
+  for (int64_t k0 = (int64_t)blockIdx.x * CH; k0 < m; k0 += (int64_t)gridDim.x * CH) {
+    const int64_t k1 = min(m, k0 + CH);
+    if (threadIdx.x == 0) s_bracket[0] = row_of(odp, 0, n + 1, k0);
+    if (threadIdx.x == 1) s_bracket[1] = row_of(odp, 0, n + 1, k1 - 1) + 1;
+    __syncthreads();
+    const int64_t lo = s_bracket[0], hi = s_bracket[1];
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += EXPAND_T) {
+      const int64_t a = row_of(odp, lo, hi, k);
+      const int64_t j = off[a] + (k - odp[a]);
+      const int32_t x = oadj[j];
+      okey[k] = rank_key(deg[x], x);
+      oval[k] = opos[j];
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(EXPAND_T)
+k_rank_scatter(const int64_t* __restrict__ off, const int64_t* __restrict__ odp, int64_t n,
+               const uint64_t* __restrict__ okey, const int32_t* __restrict__ oval,
+               int32_t* __restrict__ oadj, int32_t* __restrict__ opos) {
+  __shared__ int64_t s_bracket[2];
+  const int64_t m = odp[n];
+  constexpr int64_t CH = (int64_t)EXPAND_T * EXPAND_ITEMS;
+  for (int64_t k0 = (int64_t)blockIdx.x * CH; k0 < m; k0 += (int64_t)gridDim.x * CH) {
+    const int64_t k1 = min(m, k0 + CH);
+    if (threadIdx.x == 0) s_bracket[0] = row_of(odp, 0, n + 1, k0);
+    if (threadIdx.x == 1) s_bracket[1] = row_of(odp, 0, n + 1, k1 - 1) + 1;
+    __syncthreads();
+    const int64_t lo = s_bracket[0], hi = s_bracket[1];
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += EXPAND_T) {
+      const int64_t a = row_of(odp, lo, hi, k);
+      const int64_t j = off[a] + (k - odp[a]);
+      oadj[j] = (int32_t)(uint32_t)~okey[k];
+      opos[j] = oval[k];
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -657,7 +723,8 @@ __global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v) {
 // graph has fewer than 2^31 arcs, which halves the index arithmetic).
 template <typename IT>
 int launch_counting(const int64_t* off, const int32_t* adj, const int32_t* deg, const int32_t* odeg,
-                    const int32_t* oadj, int64_t n, const int64_t* item_off, const int32_t* order,
+                    const int32_t* oadj, const uint64_t* okey, const int64_t* odp, int64_t n,
+                    const int64_t* item_off, const int32_t* order,
                     unsigned long long* work, int lsh_T, int32_t max_od, int64_t* deferred,
                     unsigned long long* n_deferred, uint32_t* tcnt, uint32_t* tc16, int32_t* twin,
                     unsigned* status, cudaStream_t s) {
@@ -675,14 +742,16 @@ int launch_counting(const int64_t* off, const int32_t* adj, const int32_t* deg, 
                                                         TRI_THREADS, smem));
   if (per_sm < 1) per_sm = 1;
   k_triangles<false, IT><<<sms * per_sm, TRI_THREADS, smem, s>>>(
-      off, adj, deg, odeg, oadj, n, item_off, order, work, lsh_T, od_cap, deferred, n_deferred,
+      off, adj, deg, odeg, oadj, okey, odp, n, item_off, order, work, lsh_T, od_cap, deferred,
+      n_deferred,
       false, tcnt, tc16, twin, status);
   GS_LAUNCH();
   int small_per_sm = 1;
   GS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&small_per_sm, k_tri_small<IT>,
                                                         SW_WARPS * 32, 0));
   if (small_per_sm < 1) small_per_sm = 1;
-  k_tri_small<IT><<<sms * small_per_sm, SW_WARPS * 32, 0, s>>>(off, adj, deg, odeg, oadj, n,
+  k_tri_small<IT><<<sms * small_per_sm, SW_WARPS * 32, 0, s>>>(off, adj, deg, odeg, oadj, okey,
+                                                               odp, n,
                                                                work + 2, lsh_T, tcnt, tc16, twin,
                                                                status);
   GS_LAUNCH();
@@ -690,7 +759,8 @@ int launch_counting(const int64_t* off, const int32_t* adj, const int32_t* deg, 
   // by the CTA kernel (normally none: the launch then ends at once)
   const bool deferred_only = max_od <= SMEM_OD_MAX;
   k_triangles<true, IT><<<deferred_only ? sms : sms * 4, TRI_THREADS, 0, s>>>(
-      off, adj, deg, odeg, oadj, n, item_off, order, work + 1, lsh_T, 0, deferred, n_deferred,
+      off, adj, deg, odeg, oadj, okey, odp, n, item_off, order, work + 1, lsh_T, 0, deferred,
+      n_deferred,
       deferred_only, tcnt, tc16, twin, status);
   GS_LAUNCH();
   return SCAN_OK;
@@ -698,10 +768,15 @@ int launch_counting(const int64_t* off, const int32_t* adj, const int32_t* deg, 
 
 int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* adj,
                                   const int32_t* deg, int64_t n, int64_t arcs, const int32_t* odeg,
-                                  const int32_t* oadj, const int32_t* opos, int32_t maxdeg,
+                                  int32_t* oadj, int32_t* opos, int32_t maxdeg,
                                   int32_t max_od, int lsh_T, double* sim_csr, unsigned* status,
                                   Pool& pool, cudaStream_t s, float* count_ms) {
   const int64_t m = arcs;  // out-lists live in CSR slots: counts and twins are indexed by arc
+  const int64_t edges = m / 2;  // oriented edges (the orientation checked sum od = arcs / 2)
+  int64_t* odp = pool.get<int64_t>(n + 1);
+  uint64_t* okey = pool.get<uint64_t>(edges > 0 ? edges : 1);
+  int32_t* oval = pool.get<int32_t>(edges > 0 ? edges : 1);
+  if (!odp || !okey || !oval) return SCAN_ENOMEM;
   const int64_t nbins = (int64_t)maxdeg + 1;
   uint32_t* tcnt = pool.get<uint32_t>(m);
   // 16-bit (u,w) counters, two per word, when positions fit in 32 bits
@@ -746,24 +821,32 @@ int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* a
   GS_CUDA(cudaEventCreate(&e0));
   GS_CUDA(cudaEventCreate(&e1));
   GS_CUDA(cudaEventRecord(e0, s));
+  const int64_t ch = (int64_t)EXPAND_T * EXPAND_ITEMS;
+  const unsigned egrid =
+      (unsigned)std::max<int64_t>(1, std::min<int64_t>((edges + ch - 1) / ch, 152 * 32));
   if (n > 0 && m > 0) {
+    // out-lists in ascending degree order, with their rank keys kept for the
+    // searches of the counting kernels
+    GS_TRY(exclusive_scan_i32_to_i64(odeg, odp, n, pool, s));
+    k_rank_keys<<<egrid, EXPAND_T, 0, s>>>(off, deg, odp, oadj, opos, n, okey, oval);
+    GS_LAUNCH();
+    GS_TRY(segmented_sort_desc(okey, oval, odp, n, edges, max_od, pool, s));
+    k_rank_scatter<<<egrid, EXPAND_T, 0, s>>>(off, odp, n, okey, oval, oadj, opos);
+    GS_LAUNCH();
     if (narrow) {
-      GS_TRY(launch_counting<int32_t>(off, adj, deg, odeg, oadj, n, item_off, order, work, lsh_T,
-                                      max_od, deferred, work + 3, tcnt, tc16, twin, status, s));
+      GS_TRY(launch_counting<int32_t>(off, adj, deg, odeg, oadj, okey, odp, n, item_off, order,
+                                      work, lsh_T, max_od, deferred, work + 3, tcnt, tc16, twin,
+                                      status, s));
     } else {
-      GS_TRY(launch_counting<int64_t>(off, adj, deg, odeg, oadj, n, item_off, order, work, lsh_T,
-                                      max_od, deferred, work + 3, tcnt, nullptr, twin, status, s));
+      GS_TRY(launch_counting<int64_t>(off, adj, deg, odeg, oadj, okey, odp, n, item_off, order,
+                                      work, lsh_T, max_od, deferred, work + 3, tcnt, nullptr, twin,
+                                      status, s));
     }
   }
   GS_CUDA(cudaEventRecord(e1, s));
   if (n > 0 && m > 0) {
-    int64_t* odp = item_off;  // reused: exclusive prefix of the out-degrees
-    GS_TRY(exclusive_scan_i32_to_i64(odeg, odp, n, pool, s));
-    const int64_t edges = m / 2;
-    const int64_t ch = (int64_t)EXPAND_T * EXPAND_ITEMS;
-    k_expand<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((edges + ch - 1) / ch, 152 * 32)),
-               EXPAND_T, 0, s>>>(kind, off, deg, odp, oadj, opos, tcnt, tc16, twin, n, lsh_T, sim_csr,
-                                 status);
+    k_expand<<<egrid, EXPAND_T, 0, s>>>(kind, off, deg, odp, oadj, opos, tcnt, tc16, twin, n,
+                                        lsh_T, sim_csr, status);
     GS_LAUNCH();
   }
   if (count_ms) {
@@ -783,6 +866,9 @@ int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* a
   pool.put(start);
   pool.put(item_off);
   pool.put(work);
+  pool.put(odp);
+  pool.put(okey);
+  pool.put(oval);
   return SCAN_OK;
 }
 
