@@ -444,6 +444,33 @@ def bench_lsh(gs, off_d, adj_d, g, stream):
     return out
 
 
+def build_roofline(alg: dict, step_ms: float, peak: float) -> dict:
+    """Whole-build bytes (B_csr + B_touch + B_out) and the B_min-only bytes
+    (B_csr + B_out, what any build must move) over the build time, against
+    the measured copy bandwidth and against the nominal 8 TB/s."""
+    full = alg["touch"] + alg["csr"] + alg["out"]
+    bmin = alg["csr"] + alg["out"]
+    gbs = full / (step_ms / 1000.0) / 1e9
+    mgbs = bmin / (step_ms / 1000.0) / 1e9
+    return {"bytes": full, "achieved_gbs": gbs, "frac": gbs / peak, "frac_of_8tbs": gbs / 8000.0,
+            "bmin_bytes": bmin, "bmin_gbs": mgbs, "bmin_frac": mgbs / peak}
+
+
+def host_cpu() -> dict:
+    """CPU model and core count of the host the oracle runs on."""
+    import platform
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part", "hardware")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"model": model, "machine": platform.machine(), "nproc": os.cpu_count()}
+
+
 def cpu_baseline(edgefactor: int, seed: int, kind: int, repeats: int = 2):
     import graphgen
     import oracle
@@ -456,7 +483,8 @@ def cpu_baseline(edgefactor: int, seed: int, kind: int, repeats: int = 2):
     t = statistics.median(ts)
     return {"value": g.edges / t, "unit": "edges/s", "cores": 1, "kind": "oracle",
             "sample": f"full oracle index build (counts, similarities, NO, CO) of R-MAT scale 18 "
-                      f"edge factor {edgefactor} ({g.edges} edges), median of {repeats}, single thread"}
+                      f"edge factor {edgefactor} ({g.edges} edges), median of {repeats}, single thread",
+            "host": host_cpu()}
 
 
 def run_reference(args):
@@ -484,7 +512,7 @@ def run_reference(args):
         "config": {"workload": f"exact {args.kind} SCAN index build, R-MAT scale {args.scale} "
                                f"edge factor {args.edgefactor} (oracle runs a scale-18 sample)"},
         "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "host": host_cpu()},
         "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
     return 0
@@ -643,9 +671,7 @@ def main():
                      "algorithmic_bytes_per_launch": alg["touch"],
                      "hash_probe_bytes_per_launch": alg["hash_probe"],
                      "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"},
-        "build_roofline": {"bytes": alg["touch"] + alg["csr"] + alg["out"],
-                           "achieved_gbs": (alg["touch"] + alg["csr"] + alg["out"])
-                           / (statistics.mean(step_ms) / 1000.0) / 1e9},
+        "build_roofline": build_roofline(alg, statistics.mean(step_ms), peak),
         "query": qres,
         "sweep": sweep,
         "e2e": e2e,

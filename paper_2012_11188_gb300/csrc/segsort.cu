@@ -364,9 +364,16 @@ __global__ void k_long_tiles(const int64_t* __restrict__ seg_off, const int64_t*
   }
 }
 
+#ifndef GS_MERGE_ITEMS
+#define GS_MERGE_ITEMS 4  // outputs per thread of a merge pass
+#endif
 constexpr int MERGE_T = 256;
-constexpr int MERGE_ITEMS = 4;  // MERGE_CHUNK = 1024 divides 2 * TILE
+constexpr int MERGE_ITEMS = GS_MERGE_ITEMS;
 constexpr int MERGE_CHUNK = MERGE_T * MERGE_ITEMS;  // output elements per CTA per pass
+static_assert((2 * TILE) % MERGE_CHUNK == 0, "a chunk must not straddle two run pairs");
+// shared memory of a merge pass: two input buffers and the padded output staging
+constexpr size_t MERGE_SMEM = (size_t)2 * MERGE_CHUNK * 12 +
+                              (size_t)(MERGE_CHUNK + MERGE_CHUNK / MERGE_ITEMS) * 12;
 
 // Number of elements of A (length la) among the first d of merge(A, B).
 __device__ __forceinline__ int64_t merge_path(const uint64_t* ka, const int32_t* va, int64_t la,
@@ -469,12 +476,15 @@ __global__ void __launch_bounds__(MERGE_T)
 k_merge_pass(uint64_t* __restrict__ key, int32_t* __restrict__ val, uint64_t* __restrict__ tk,
              int32_t* __restrict__ tv, const int64_t* __restrict__ chunk_prefix, int64_t nlong,
              const MergeDesc* __restrict__ desc) {
-  __shared__ uint64_t ink[2][MERGE_CHUNK];
-  __shared__ int32_t inv[2][MERGE_CHUNK];
-  // output staging, one pad slot per MERGE_ITEMS (a thread's consecutive
-  // outputs) so that the lanes of a warp write distinct banks
-  __shared__ uint64_t ok_[MERGE_CHUNK + MERGE_CHUNK / MERGE_ITEMS];
-  __shared__ int32_t ov_[MERGE_CHUNK + MERGE_CHUNK / MERGE_ITEMS];
+  // two input buffers, then the output staging with one pad slot per
+  // MERGE_ITEMS (a thread's consecutive outputs) so that the lanes of a warp
+  // write distinct banks
+  extern __shared__ uint64_t msm[];
+  uint64_t (*ink)[MERGE_CHUNK] = reinterpret_cast<uint64_t (*)[MERGE_CHUNK]>(msm);
+  uint64_t* ok_ = msm + 2 * MERGE_CHUNK;
+  int32_t (*inv)[MERGE_CHUNK] =
+      reinterpret_cast<int32_t (*)[MERGE_CHUNK]>(ok_ + MERGE_CHUNK + MERGE_CHUNK / MERGE_ITEMS);
+  int32_t* ov_ = reinterpret_cast<int32_t*>(inv + 2);
   const int64_t total = chunk_prefix[nlong];
   const int t = threadIdx.x;
   auto po = [](int i) { return i + i / MERGE_ITEMS; };
@@ -581,6 +591,8 @@ int segmented_sort_desc(uint64_t* key, int32_t* val, const int64_t* seg_off, int
                                                                 counts + 1);
     GS_LAUNCH();
   }
+  GS_CUDA(cudaFuncSetAttribute(k_merge_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)MERGE_SMEM));
   GS_CUDA(cudaFuncSetAttribute(k_sort_tile<T4K_T, T4K_RI, true>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)tile_smem_bytes<T4K_T, T4K_RI>()));
@@ -629,8 +641,9 @@ int segmented_sort_desc(uint64_t* key, int32_t* val, const int64_t* seg_off, int
       k_merge_partition<<<grid_of(total_chunks_ub, 256), 256, 0, s>>>(
           key, val, tk, tv, seg_off, llist, chunk_prefix, nlong, L, pass, desc);
       GS_LAUNCH();
-      k_merge_pass<<<grid_of(total_chunks_ub, 1), MERGE_T, 0, s>>>(key, val, tk, tv, chunk_prefix,
-                                                                  nlong, desc);
+      k_merge_pass<<<grid_of(total_chunks_ub, 1), MERGE_T, MERGE_SMEM, s>>>(key, val, tk, tv,
+                                                                           chunk_prefix, nlong,
+                                                                           desc);
       GS_LAUNCH();
     }
     pool.put(desc);
