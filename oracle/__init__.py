@@ -54,6 +54,7 @@ def bind(lib):
         "orc_closed_counts": (i32, [i64, P, P, P]),
         "orc_count_pairs": (i32, [i64, P, P, i64, P, P, P]),
         "orc_similarities": (i32, [i32, i64, P, P, P, P]),
+        "orc_weighted_similarities": (i32, [i64, P, P, P, P]),
         "orc_neighbor_order": (i32, [i64, P, P, P, P, P]),
         "orc_core_order": (i32, [i64, P, P, i64, P, P, P]),
         "orc_query_index": (i32, [i64, P, P, P, P, i64, P, P, P, i32, f64, i32, P]),
@@ -115,6 +116,17 @@ def similarities(g, cnt: np.ndarray, kind: int = COSINE) -> np.ndarray:
     cnt = np.ascontiguousarray(cnt, dtype=np.int32)
     sim = np.zeros(g.arcs, dtype=np.float64)
     _check(_load().orc_similarities(kind, g.n, _p(off), _p(adj), _p(cnt), _p(sim)), "similarities")
+    return sim
+
+
+def weighted_similarities(g, w: np.ndarray) -> np.ndarray:
+    """Weighted cosine similarity of every arc (Section 3.1, w(x, x) = 1)."""
+    off, adj = _csr(g)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    assert w.shape[0] == g.arcs
+    sim = np.zeros(g.arcs, dtype=np.float64)
+    _check(_load().orc_weighted_similarities(g.n, _p(off), _p(adj), _p(w), _p(sim)),
+           "weighted_similarities")
     return sim
 
 

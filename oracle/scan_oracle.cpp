@@ -283,6 +283,62 @@ int orc_query_definition(int64_t n, const int64_t* off, const int32_t* adj, cons
   return 0;
 }
 
+// Weighted cosine similarity of every arc (Section 3.1, WeightedCosineSim of
+// the closed neighbourhoods with w(x, x) = 1 for every vertex x):
+//   sigma(u,v) = sum_{x in N̄(u) ∩ N̄(v)} w(u,x) w(v,x)
+//                / ( sqrt(sum_{x in N̄(u)} w(u,x)^2) * sqrt(sum_{x in N̄(v)} w(v,x)^2) ).
+// w[i] is the weight of arc i (w(u, adj[i]) for i in u's row); the graph's
+// weights must be symmetric. The numerator walks the two closed lists (each
+// in id order, the vertex itself with weight 1) with two pointers; the
+// norms and the final division are plain double arithmetic.
+int orc_weighted_similarities(int64_t n, const int64_t* off, const int32_t* adj, const double* w,
+                              double* sim) {
+  // closed list of x with weights, in id order
+  auto closed_w = [&](int64_t x, std::vector<int32_t>& ids, std::vector<double>& ws) {
+    ids.clear();
+    ws.clear();
+    bool self_done = false;
+    for (int64_t i = off[x]; i < off[x + 1]; ++i) {
+      if (!self_done && adj[i] > x) {
+        ids.push_back((int32_t)x);
+        ws.push_back(1.0);
+        self_done = true;
+      }
+      ids.push_back(adj[i]);
+      ws.push_back(w[i]);
+    }
+    if (!self_done) {
+      ids.push_back((int32_t)x);
+      ws.push_back(1.0);
+    }
+  };
+  std::vector<double> norm((size_t)n);
+  std::vector<int32_t> ia, ib;
+  std::vector<double> wa, wb;
+  for (int64_t x = 0; x < n; ++x) {
+    closed_w(x, ia, wa);
+    double s2 = 0.0;
+    for (double y : wa) s2 += y * y;
+    norm[x] = std::sqrt(s2);
+  }
+  for (int64_t u = 0; u < n; ++u) {
+    closed_w(u, ia, wa);
+    for (int64_t i = off[u]; i < off[u + 1]; ++i) {
+      const int64_t v = adj[i];
+      closed_w(v, ib, wb);
+      double num = 0.0;
+      size_t a = 0, b = 0;
+      while (a < ia.size() && b < ib.size()) {
+        if (ia[a] < ib[b]) ++a;
+        else if (ia[a] > ib[b]) ++b;
+        else { num += wa[a] * wb[b]; ++a; ++b; }
+      }
+      sim[i] = num / (norm[u] * norm[v]);
+    }
+  }
+  return 0;
+}
+
 // Similarities of all arcs of one vertex v (sampled checks on large graphs):
 // out[j] = sigma(v, adj[off[v]+j]), counting members of each N̄(u) among the
 // flagged N̄(v).

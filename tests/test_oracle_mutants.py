@@ -14,6 +14,7 @@ import pytest
 
 import oracle
 import test_oracle_pins as pins
+import test_oracle_weighted_pins as wpins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "scan_oracle.cpp")
 LSH = os.path.join(os.path.dirname(oracle.__file__), "lsh_oracle.cpp")
@@ -35,6 +36,11 @@ MUTANTS = {
                                        "if (a > b) p[b] = a; else p[a] = b;"),
     "hub with a single neighbouring cluster": ("else if (l != first) { hub = true; break; }",
                                                "else { hub = true; break; }"),
+    "weighted norm without the square (the listing's garble)": (
+        "for (double y : wa) s2 += y * y;", "for (double y : wa) s2 += y;"),
+    "weighted closed list without the vertex itself": (
+        "    if (!self_done) {\n      ids.push_back((int32_t)x);\n      ws.push_back(1.0);\n    }",
+        "    (void)self_done;"),
     "neighbour order ascending": (
         "return a.first > b.first;\n                     });\n    for (size_t j",
         "return a.first < b.first;\n                     });\n    for (size_t j"),
@@ -53,6 +59,9 @@ PINS = [
     pins.test_figure_captions,
     lambda: pins.test_order_invariants(oracle.COSINE),
     pins.test_exhaustive_five_vertices,
+    lambda: wpins.test_weighted_equals_matrix_identity(30, 0.2, 1),
+    wpins.test_unit_weights_reduce_to_cosine,
+    wpins.test_weighted_triangle_closed_form,
 ]
 
 
