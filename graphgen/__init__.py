@@ -132,7 +132,8 @@ def sbm(n: int, blocks: int, p_in: float, p_out: float, seed: int = 1) -> CSR:
 
 def from_edges(n: int, edges) -> CSR:
     """Clean an explicit edge list (any order, duplicates and self-loops allowed)."""
-    e = np.asarray(list(edges), dtype=np.int64).reshape(-1, 2)
+    e = np.asarray(edges if isinstance(edges, np.ndarray) else list(edges),
+                   dtype=np.int64).reshape(-1, 2)
     src = np.ascontiguousarray(e[:, 0].astype(np.int32))
     dst = np.ascontiguousarray(e[:, 1].astype(np.int32))
     return _take(_load().gg_clean_pairs(n, src.shape[0], src.ctypes.data, dst.ctypes.data))
@@ -143,6 +144,34 @@ def from_dense(A: np.ndarray) -> CSR:
     n = A.shape[0]
     iu, ju = np.nonzero(np.triu(A, 1))
     return from_edges(n, zip(iu.tolist(), ju.tolist()))
+
+
+def _mix64(x: np.ndarray) -> np.ndarray:
+    """SplitMix64 finaliser (Steele, Lea and Flood 2014), elementwise on uint64."""
+    x = (x ^ (x >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+    x = (x ^ (x >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    return x ^ (x >> np.uint64(31))
+
+
+def edge_weights(g: CSR, seed: int = 1, dist: str = "uniform") -> np.ndarray:
+    """Symmetric per-arc weights, aligned with g.adj: both arcs of an edge
+    {a, b} carry the value drawn from the hash of (min, max, seed).
+
+    dist: "uniform" (U[0.05, 3)), "int" (1, 2, 3 or 4) or "exp" (0.01 plus an
+    exponential of mean 1, a heavier tail)."""
+    src = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.off))
+    dst = g.adj.astype(np.int64)
+    lo, hi = np.minimum(src, dst).astype(np.uint64), np.maximum(src, dst).astype(np.uint64)
+    with np.errstate(over="ignore"):
+        k = lo * np.uint64(0x9E3779B97F4A7C15) ^ (hi + np.uint64(seed) * np.uint64(0xD1B54A32D192ED03))
+        u = (_mix64(_mix64(k)) >> np.uint64(11)).astype(np.float64) * (1.0 / 2**53)
+    if dist == "uniform":
+        return 0.05 + 2.95 * u
+    if dist == "int":
+        return 1.0 + np.floor(4.0 * u)
+    if dist == "exp":
+        return 0.01 - np.log1p(-u)
+    raise ValueError(dist)
 
 
 def permutation(n: int, seed: int) -> np.ndarray:

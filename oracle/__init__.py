@@ -55,6 +55,7 @@ def bind(lib):
         "orc_count_pairs": (i32, [i64, P, P, i64, P, P, P]),
         "orc_similarities": (i32, [i32, i64, P, P, P, P]),
         "orc_weighted_similarities": (i32, [i64, P, P, P, P]),
+        "orc_weighted_vertex_similarities": (i32, [i64, P, P, P, i32, P]),
         "orc_neighbor_order": (i32, [i64, P, P, P, P, P]),
         "orc_core_order": (i32, [i64, P, P, i64, P, P, P]),
         "orc_query_index": (i32, [i64, P, P, P, P, i64, P, P, P, i32, f64, i32, P]),
@@ -68,6 +69,7 @@ def bind(lib):
         sig.update({
             "orc_lsh_select": (i64, [i64, P, P, i64, P]),
             "orc_simhash_sketch": (i32, [i64, P, P, P, i64, i32, u64, P]),
+            "orc_simhash_sketch_weighted": (i32, [i64, P, P, P, P, i64, i32, u64, P]),
             "orc_minhash_sketch": (i32, [i64, P, P, P, i64, i32, i32, u64, P]),
             "orc_lsh_similarities": (i32, [i32, i64, P, P, P, P, P, i32, i32, i32, P]),
             "orc_simhash_table": (i32, [i32, P]),
@@ -128,6 +130,18 @@ def weighted_similarities(g, w: np.ndarray) -> np.ndarray:
     _check(_load().orc_weighted_similarities(g.n, _p(off), _p(adj), _p(w), _p(sim)),
            "weighted_similarities")
     return sim
+
+
+def weighted_vertex_similarities(g, w: np.ndarray, v: int) -> np.ndarray:
+    """Weighted cosine similarities of the arcs of vertex v (Section 3.1)."""
+    off, adj = _csr(g)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    assert w.shape[0] == g.arcs
+    d = int(off[v + 1] - off[v])
+    out = np.zeros(d, dtype=np.float64)
+    _check(_load().orc_weighted_vertex_similarities(g.n, _p(off), _p(adj), _p(w), v, _p(out)),
+           "weighted_vertex_similarities")
+    return out
 
 
 def neighbor_order(g, sim: np.ndarray):
@@ -231,12 +245,20 @@ def lsh_select(g, T: int = 128):
     return row, nH
 
 
-def simhash_sketch(g, row, nH: int, k: int, seed: int) -> np.ndarray:
+def simhash_sketch(g, row, nH: int, k: int, seed: int, weights=None) -> np.ndarray:
+    """SimHash sketches of the sketched vertices; weights (per arc) selects the
+    weighted closed neighbourhood."""
     off, adj = _csr(g)
     row = np.ascontiguousarray(row, dtype=np.int32)
     sig = np.zeros((max(nH, 0), k // 64), dtype=np.uint64)
-    _check(_load().orc_simhash_sketch(g.n, _p(off), _p(adj), _p(row), nH, k, seed, _p(sig)),
-           "simhash_sketch")
+    if weights is None:
+        _check(_load().orc_simhash_sketch(g.n, _p(off), _p(adj), _p(row), nH, k, seed, _p(sig)),
+               "simhash_sketch")
+    else:
+        w = np.ascontiguousarray(weights, dtype=np.float64)
+        assert w.shape[0] == g.arcs
+        _check(_load().orc_simhash_sketch_weighted(g.n, _p(off), _p(adj), _p(w), _p(row), nH, k,
+                                                   seed, _p(sig)), "simhash_sketch_weighted")
     return sig
 
 
@@ -277,11 +299,17 @@ class LSHIndex(Index):
     """Oracle index in LSH mode: SimHash for cosine, MinHash for Jaccard (Section 5)."""
 
     def __init__(self, g, kind: int, k: int, T: int = 128, seed: int = 1,
-                 kpartition: bool = True, exact_sim=None):
-        exact = similarities(g, closed_counts(g), kind) if exact_sim is None else exact_sim
+                 kpartition: bool = True, exact_sim=None, weights=None):
+        assert weights is None or kind == COSINE
+        if exact_sim is not None:
+            exact = exact_sim
+        elif weights is not None:
+            exact = weighted_similarities(g, weights)
+        else:
+            exact = similarities(g, closed_counts(g), kind)
         self.row, self.nH = lsh_select(g, T)
         if kind == COSINE:
-            self.sketch = simhash_sketch(g, self.row, self.nH, k, seed)
+            self.sketch = simhash_sketch(g, self.row, self.nH, k, seed, weights)
             sim = lsh_similarities(g, SIMHASH, self.row, self.sketch, exact, k)
         else:
             self.sketch = minhash_sketch(g, self.row, self.nH, k, seed, kpartition)

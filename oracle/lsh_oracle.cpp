@@ -18,6 +18,8 @@
 //    Estimate: h = Hamming distance of the two k-bit sketches, theta = pi h / k,
 //    sigma~ = max(0, cos(theta)) (the clamp keeps the estimate inside the range
 //    of the exact measure).
+//  * Weighted SimHash: the same hyperplanes applied to the weighted closed
+//    neighbourhood (w(v,v) = 1), double-precision sums in a fixed order.
 //  * k-partition MinHash (one-permutation hashing, Li, Owen, Zhang 2012;
 //    Section 6.3): k a power of two, L = log2 k, h(x) = low 32 bits of
 //    R(key_m, x), key_m = mix(seed ^ 0x4D494E48). Bin = top L bits of h(x),
@@ -106,6 +108,40 @@ int orc_simhash_sketch(int64_t n, const int64_t* off, const int32_t* adj, const 
     for (int w = 0; w < W; ++w) out[w] = 0;
     for (int j = 0; j < k; ++j)
       if (s[j] >= 0.0f) out[j / 64] |= 1ULL << (j % 64);
+  }
+  return 0;
+}
+
+// SimHash of the weighted closed neighbourhood (Section 3.1 with w(v,v) = 1;
+// the paper's LSH bound covers SimHash on weighted graphs, Section 5):
+// s_j(v) = sum over x in N̄(v) of rho_j(x) w(v,x), bit j = [s_j(v) >= 0].
+// rho_j(x) w(v,x) is +-w exactly; the sum is taken in double precision in the
+// order v (weight 1), then N(v) in id order, so any implementation that adds
+// the same terms in the same order takes every sign decision identically.
+// w[i] is the weight of arc i.
+int orc_simhash_sketch_weighted(int64_t n, const int64_t* off, const int32_t* adj,
+                                const double* w, const int32_t* row, int64_t nH, int k,
+                                uint64_t seed, uint64_t* sig) {
+  if (k <= 0 || k % 64 != 0 || k > 65536) return -1;
+  const uint64_t key = simhash_key(seed);
+  const int W = k / 64;
+  std::vector<double> s((size_t)k);
+  for (int64_t v = 0; v < n; ++v) {
+    if (row[v] < 0) continue;
+    if (row[v] >= nH) return -1;
+    for (int j = 0; j < k; ++j) s[j] = 0.0;
+    for (int64_t i = off[v] - 1; i < off[v + 1]; ++i) {
+      const int64_t x = i < off[v] ? v : adj[i];
+      const double wx = i < off[v] ? 1.0 : w[i];
+      for (int j = 0; j < k; ++j) {
+        const uint64_t bits = R(key, (uint64_t)x * 1024u + (uint64_t)(j / 64));
+        s[j] += ((bits >> (j % 64)) & 1u) ? wx : -wx;
+      }
+    }
+    uint64_t* out = sig + (size_t)row[v] * W;
+    for (int q = 0; q < W; ++q) out[q] = 0;
+    for (int j = 0; j < k; ++j)
+      if (s[j] >= 0.0) out[j / 64] |= 1ULL << (j % 64);
   }
   return 0;
 }

@@ -339,6 +339,56 @@ int orc_weighted_similarities(int64_t n, const int64_t* off, const int32_t* adj,
   return 0;
 }
 
+// Weighted cosine similarities of the arcs of one vertex v (sampled checks on
+// graphs too large for the all-arcs routine): out[j] = sigma(v, adj[off[v]+j])
+// by the same definition (Section 3.1). w(v, .) is spread over a dense
+// vector; each neighbour u's closed list is walked in id order, so the terms
+// of a numerator are added in the same order as by the two-pointer walk of
+// orc_weighted_similarities and the results are the same doubles.
+int orc_weighted_vertex_similarities(int64_t n, const int64_t* off, const int32_t* adj,
+                                     const double* w, int32_t v, double* out) {
+  if (v < 0 || v >= n) return -1;
+  std::vector<double> wv((size_t)n, 0.0);
+  std::vector<char> in_v((size_t)n, 0);
+  wv[v] = 1.0;
+  in_v[v] = 1;
+  for (int64_t i = off[v]; i < off[v + 1]; ++i) {
+    wv[adj[i]] = w[i];
+    in_v[adj[i]] = 1;
+  }
+  // sqrt of the sum of squares over the closed list of x, in id order
+  auto norm_of = [&](int64_t x) {
+    double s2 = 0.0;
+    bool self_done = false;
+    for (int64_t i = off[x]; i < off[x + 1]; ++i) {
+      if (!self_done && adj[i] > x) {
+        s2 += 1.0;
+        self_done = true;
+      }
+      s2 += w[i] * w[i];
+    }
+    if (!self_done) s2 += 1.0;
+    return std::sqrt(s2);
+  };
+  const double norm_v = norm_of(v);
+  for (int64_t j = off[v]; j < off[v + 1]; ++j) {
+    const int64_t u = adj[j];
+    double num = 0.0;
+    bool self_done = false;
+    for (int64_t i = off[u]; i < off[u + 1]; ++i) {
+      const int64_t x = adj[i];
+      if (!self_done && x > u) {
+        if (in_v[u]) num += 1.0 * wv[u];  // x = u, w(u,u) = 1
+        self_done = true;
+      }
+      if (in_v[x]) num += w[i] * wv[x];
+    }
+    if (!self_done && in_v[u]) num += 1.0 * wv[u];
+    out[j - off[v]] = num / (norm_of(u) * norm_v);
+  }
+  return 0;
+}
+
 // Similarities of all arcs of one vertex v (sampled checks on large graphs):
 // out[j] = sigma(v, adj[off[v]+j]), counting members of each N̄(u) among the
 // flagged N̄(v).

@@ -133,3 +133,62 @@ def test_simhash_tracks_cosine():
     theta_hat = np.arccos(np.clip(est[m], 0, 1))
     assert abs((theta_hat - theta).mean()) < 0.02
     assert np.abs(theta_hat - theta).mean() < 0.1
+
+
+def test_weighted_simhash_unit_weights_equal_unweighted():
+    g = dense_sbm()
+    row, nH = oracle.lsh_select(g, 128)
+    a = oracle.simhash_sketch(g, row, nH, 128, seed=5)
+    b = oracle.simhash_sketch(g, row, nH, 128, seed=5, weights=np.ones(g.arcs))
+    assert np.array_equal(a, b)
+
+
+def test_weighted_simhash_brute_force_definition():
+    """s_j(v) = sum over N̄(v) of rho_j(x) w(v,x) with w(v,v) = 1, written
+    out with numpy from the SplitMix64 stream (pinned to its published
+    vectors); integer weights make every sum exact, so the bits must agree."""
+    g = graphgen.sbm(120, 2, 0.3, 0.05, seed=8)
+    w = graphgen.edge_weights(g, 4, "int")
+    row, nH = oracle.lsh_select(g, 10)
+    assert nH > 20
+    k, seed = 128, 13
+    sig = oracle.simhash_sketch(g, row, nH, k, seed, weights=w)
+    # key_s = mix(seed ^ "SIMH"); output 0 of SplitMix64 started at state
+    # z - gamma is mix(z)
+    gamma = 0x9E3779B97F4A7C15
+    key = oracle.splitmix64(((seed ^ 0x53494D48) - gamma) % 2**64, 0)
+
+    def rho(x):
+        words = [oracle.splitmix64(key, x * 1024 + q) for q in range(k // 64)]
+        return np.array([1.0 if (words[j // 64] >> (j % 64)) & 1 else -1.0 for j in range(k)])
+
+    for v in np.flatnonzero(row >= 0)[:25]:
+        s = rho(int(v)) * 1.0
+        for i in range(g.off[v], g.off[v + 1]):
+            s = s + rho(int(g.adj[i])) * w[i]
+        bits = np.zeros(k // 64, dtype=np.uint64)
+        for j in range(k):
+            if s[j] >= 0:
+                bits[j // 64] |= np.uint64(1) << np.uint64(j % 64)
+        assert np.array_equal(sig[row[v]], bits), v
+
+
+def test_weighted_simhash_tracks_weighted_cosine():
+    g = dense_sbm()
+    w = graphgen.edge_weights(g, 6, "exp")
+    exact = oracle.weighted_similarities(g, w)
+    row, nH = oracle.lsh_select(g, 128)
+    k = 256
+    sig = oracle.simhash_sketch(g, row, nH, k, seed=9, weights=w)
+    est = oracle.lsh_similarities(g, oracle.SIMHASH, row, sig, exact, k)
+    m = approx_arcs(g, row)
+    theta = np.arccos(np.clip(exact[m], 0, 1))
+    theta_hat = np.arccos(np.clip(est[m], 0, 1))
+    assert abs((theta_hat - theta).mean()) < 0.03
+    assert np.abs(theta_hat - theta).mean() < 0.12
+    # the unweighted sketch of the same graph is a worse estimate of the
+    # weighted cosine: the weights are used
+    sig_u = oracle.simhash_sketch(g, row, nH, k, seed=9)
+    est_u = oracle.lsh_similarities(g, oracle.SIMHASH, row, sig_u, exact, k)
+    theta_u = np.arccos(np.clip(est_u[m], 0, 1))
+    assert np.abs(theta_hat - theta).mean() < np.abs(theta_u - theta).mean()

@@ -71,3 +71,49 @@ def test_weighted_triangle_closed_form():
     i01 = int(np.flatnonzero((src == 0) & (g.adj == 1))[0])
     want = (2 * a + b * c) / (math.sqrt(1 + a * a + b * b) * math.sqrt(1 + a * a + c * c))
     assert abs(sim[i01] - want) <= 1e-15 * want
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_vertex_routine_equals_matrix_identity_and_all_arcs(seed):
+    """The per-vertex routine (sampled checks on large graphs) against the
+    matrix identity, and bit for bit against the all-arcs routine, whose
+    numerators add the same terms in the same (id) order."""
+    g = graphgen.sbm(80, 2, 0.3, 0.05, seed=seed)
+    w = graphgen.edge_weights(g, seed, "exp")
+    W = np.eye(g.n)
+    src = np.repeat(np.arange(g.n), np.diff(g.off))
+    W[src, g.adj] = w
+    W2 = W @ W
+    full = oracle.weighted_similarities(g, w)
+    for v in range(g.n):
+        row = slice(g.off[v], g.off[v + 1])
+        got = oracle.weighted_vertex_similarities(g, w, v)
+        nb = g.adj[row]
+        want = W2[v, nb] / np.sqrt(W2[v, v] * np.diag(W2)[nb])
+        assert np.allclose(got, want, rtol=1e-13, atol=0)
+        assert np.array_equal(got, full[row])
+
+
+def test_weighted_bipartite_closed_form():
+    """K_{a,b} with one weight c on every edge has no triangles: the common
+    closed neighbourhood of an edge is its two ends, so
+    sigma = 2c / (sqrt(1 + b c^2) sqrt(1 + a c^2))."""
+    a, b, c = 5, 7, 1.75
+    g = graphgen.from_edges(a + b, [(i, a + j) for i in range(a) for j in range(b)])
+    w = np.full(g.arcs, c)
+    want = 2 * c / (math.sqrt(1 + b * c * c) * math.sqrt(1 + a * c * c))
+    sim = oracle.weighted_similarities(g, w)
+    assert np.allclose(sim, want, rtol=1e-15, atol=0)
+    assert np.allclose(oracle.weighted_vertex_similarities(g, w, 0), want, rtol=1e-15, atol=0)
+
+
+def test_edge_weights_are_symmetric_and_in_range():
+    g = graphgen.rmat(10, 8, seed=3)
+    src = np.repeat(np.arange(g.n), np.diff(g.off))
+    order = np.lexsort((g.adj, src))
+    rev = np.lexsort((src, g.adj))  # arc (b, a) at the place of (a, b)
+    for dist, lo, hi in (("uniform", 0.05, 3.0), ("int", 1.0, 4.0), ("exp", 0.01, 50.0)):
+        w = graphgen.edge_weights(g, 9, dist)
+        assert np.array_equal(w[order], w[rev])
+        assert w.min() >= lo and w.max() <= hi
+    assert set(np.unique(graphgen.edge_weights(g, 9, "int"))) <= {1.0, 2.0, 3.0, 4.0}
