@@ -50,6 +50,10 @@ def parse():
     p.add_argument("--no-lsh", action="store_true", help="skip the LSH build and quality gate")
     p.add_argument("--no-sweep", action="store_true", help="skip the modularity sweep over Sigma")
     p.add_argument("--no-dense", action="store_true", help="skip the dense-graph builds")
+    p.add_argument("--no-weighted", action="store_true", help="skip the weighted-cosine builds")
+    p.add_argument("--weighted-only", type=int, default=0, metavar="SCALE",
+                   help="only the weighted section, on R-MAT of this scale (a profiling case); "
+                        "prints that section, not the benchmark line")
     p.add_argument("--batch-graphs", type=int, default=2048)
     p.add_argument("--serve-queries", type=int, default=20000)
     return p.parse_args()
@@ -427,6 +431,58 @@ def bench_dense(gs, kind: int, seed: int, stream):
     return out
 
 
+def bench_weighted(gs, seed: int, stream, rmat_scale: int = 22, blood_vessel: bool = True):
+    """Weighted cosine index (Section 3.1) on synthetic weights: an
+    Erdos-Renyi graph shaped like the paper's weighted blood vessel graph
+    (n = 25,825, average degree 5.4K; the paper's weights are not
+    available, so each edge draws U[0.05, 3)), and R-MAT s22 weighted against
+    the same graph unweighted (parity with the oracle is the tests' job)."""
+    import graphgen
+    import torch
+
+    def timed_builds(off, adj, reps, **kw):
+        ix = gs.ScanIndex.build((off, adj), gs.COSINE, stream=stream, **kw)  # warm-up
+        ts, cnt = [], []
+        for _ in range(reps):
+            ix.free()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ix = gs.ScanIndex.build((off, adj), gs.COSINE, stream=stream, **kw)
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+            cnt.append(gs.last_build_timings().count_ms)
+        return ix, statistics.median(ts), statistics.median(cnt)
+
+    out = {}
+    cases = [("rmat_s%d" % rmat_scale, lambda: graphgen.rmat(rmat_scale, 16, seed=seed))]
+    if blood_vessel:
+        cases.insert(0, ("blood_vessel_like", lambda: graphgen.sbm(25825, 1, 5400 / 25824,
+                                                                    5400 / 25824, seed=seed)))
+    for name, make in cases:
+        g = make()
+        w = graphgen.edge_weights(g, seed, "uniform")
+        off = torch.from_numpy(g.off).to("cuda")
+        adj = torch.from_numpy(g.adj).to("cuda")
+        wd = torch.from_numpy(w).to("cuda")
+        ix, ms, cms = timed_builds(off, adj, 2, weights=wd)
+        rec = {"n": g.n, "edges": g.edges, "weights": "U[0.05, 3) per edge",
+               "weighted": {"build_ms": round(ms, 2), "count_ms": round(cms, 2),
+                            "edges_per_s": g.edges / (ms / 1000.0)}}
+        ix.free()
+        if name.startswith("rmat"):
+            uix, ums, ucms = timed_builds(off, adj, 2, counts=gs.COUNTS_SPARSE)
+            uix.free()
+            rec["unweighted"] = {"build_ms": round(ums, 2), "count_ms": round(ucms, 2),
+                                 "edges_per_s": g.edges / (ums / 1000.0)}
+            rec["weighted_over_unweighted_time"] = round(ms / ums, 2)
+        del off, adj, wd, g, w
+        torch.cuda.empty_cache()
+        out[name] = rec
+    return out
+
+
 def bench_lsh(gs, off_d, adj_d, g, stream):
     """LSH quality on the benchmark graph (timed builds), and on a dense SBM
     whose in-block edges are all approximated, so that the exact clustering
@@ -532,6 +588,10 @@ def main():
     import graphgen
     import paper_2012_11188_gb300 as gs
 
+    if args.weighted_only:
+        print(json.dumps(bench_weighted(gs, args.seed, torch.cuda.current_stream(),
+                                        rmat_scale=args.weighted_only, blood_vessel=False)))
+        return 0
     kind = gs.COSINE if args.kind == "cosine" else gs.JACCARD
     t_gen = time.perf_counter()
     g = graphgen.rmat(args.scale, args.edgefactor, seed=args.seed)
@@ -687,6 +747,8 @@ def main():
         out["serving"] = bench_serving(gs, kind, args.serve_queries, args.seed, stream)
     if not args.no_dense:
         out["dense"] = bench_dense(gs, kind, args.seed, stream)
+    if not args.no_weighted:
+        out["weighted"] = bench_weighted(gs, args.seed, stream)
     if ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.edgefactor, args.seed,
                                            0 if args.kind == "cosine" else 1)

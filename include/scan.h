@@ -124,6 +124,31 @@ int scan_index_build(const scan_csr* csr, scan_sim_kind kind, const scan_lsh_par
 int scan_index_build_ex(const scan_csr* csr, scan_sim_kind kind, const scan_lsh_params* lsh,
                         int counts, uintptr_t stream, scan_index** out);
 
+/* Build the index of a weighted graph with the weighted cosine similarity
+ * (Section 3.1): with w(x,x) = 1 and N̄ the closed neighbourhood,
+ *   sigma(u,v) = sum over x in N̄(u) ∩ N̄(v) of w(u,x) w(v,x)
+ *                / ( sqrt(sum over N̄(u) of w(u,x)^2) sqrt(sum over N̄(v) of w(v,x)^2) ),
+ * i.e. (2 w(u,v) + sum over common neighbours x of w(u,x) w(v,x)) divided by
+ * sqrt(1 + sum of w(u,x)^2) sqrt(1 + sum of w(v,x)^2) for an edge (u,v).
+ * weights: num_arcs doubles aligned with csr->adj (weights[i] belongs to the
+ * arc stored at adj[i]), on the device when csr->on_device, else on the
+ * host; borrowed. Every weight must be finite and >= 0 and the two arcs of an
+ * edge must carry the same weight, else SCAN_EINVAL (a graph that is not
+ * simple and undirected returns SCAN_EBADGRAPH). The result is a cosine
+ * index: queries, exports, modularity and the sweep work on it unchanged.
+ * Counts are always sparse. lsh: NULL or disabled for the exact index, else
+ * SimHash (simhash_bits, degree_threshold, seed as for scan_index_build) of
+ * the weighted closed neighbourhoods: hyperplane j sums +-w(v,x) over N̄(v)
+ * in double precision, v first, then N(v) in id order, and bit j is
+ * [sum >= 0] (Sections 2.1.2 and 5).
+ * Exact similarities are sums of floating-point products in an unspecified
+ * order: each lies within (2 (d_u + d_v) + 16) units of 2^-53, relative,
+ * of the value summed in id order without fused multiply-adds (and is not
+ * bit-identical run to run for edges on many triangles); with integer
+ * weights every sum is exact and so is the result. */
+int scan_index_build_weighted(const scan_csr* csr, const double* weights,
+                              const scan_lsh_params* lsh, uintptr_t stream, scan_index** out);
+
 /* Build `count` independent indexes (one per graph) in one batched pass:
  * the graphs are packed into one device arena and every step runs once over
  * all of them; each handle then behaves exactly like one from

@@ -18,6 +18,8 @@
 //    of R(km ^ ((j+1) * golden), x), min per j; estimate = equal / k.
 #include <cmath>
 
+#include <type_traits>
+
 #include "scan_internal.cuh"
 
 namespace gscan {
@@ -62,30 +64,37 @@ __global__ void k_select_rows(const int32_t* __restrict__ flag, const int64_t* _
 
 // One CTA per sketched vertex. Elements of N̄(v) in chunks of SH_T; each thread
 // hashes one element into W words, then hyperplane j adds +-1 over the chunk.
+// Weighted graphs (WTD): hyperplane j adds +-w(v,x) (w(v,v) = 1) in double
+// precision; each thread adds its hyperplanes' terms in the order v, then
+// N(v) in id order, a fixed order that decides every sign reproducibly.
 constexpr int SH_T = 256;
 constexpr int SH_WMAX = 64;  // k <= 4096
 
+template <bool WTD>
 __global__ void __launch_bounds__(SH_T)
 k_simhash(const int64_t* __restrict__ off, const int32_t* __restrict__ adj, int64_t n,
           const int32_t* __restrict__ hlist, int64_t nH, int W, uint64_t key,
-          uint64_t* __restrict__ sig) {
+          const double* __restrict__ wcsr, uint64_t* __restrict__ sig) {
+  using acc_t = typename std::conditional<WTD, double, float>::type;
   extern __shared__ uint64_t bits[];  // [SH_T][W]
   __shared__ unsigned ballots[SH_WMAX * 2];
+  __shared__ double wel[WTD ? SH_T : 1];
   const int k = 64 * W;
   const int per = (k + SH_T - 1) / SH_T;  // hyperplanes per thread (<= 16)
-  float s[16];
+  acc_t s[16];
   for (int64_t h = blockIdx.x; h < nH; h += gridDim.x) {
     const int32_t v = hlist[h];
     const int64_t b = off[v], e = off[v + 1];
     const int64_t cnt = e - b + 1;  // N̄(v)
 #pragma unroll
-    for (int t = 0; t < 16; ++t) s[t] = 0.0f;
+    for (int t = 0; t < 16; ++t) s[t] = (acc_t)0;
     for (int64_t c0 = 0; c0 < cnt; c0 += SH_T) {
       const int64_t c = c0 + threadIdx.x;
       if (c < cnt) {
         const int64_t x = c == 0 ? (int64_t)v : (int64_t)adj[b + c - 1];
         for (int w = 0; w < W; ++w)
           bits[threadIdx.x * W + w] = splitmix_out(key, (uint64_t)x * 1024u + (uint64_t)w);
+        if (WTD) wel[threadIdx.x] = c == 0 ? 1.0 : wcsr[b + c - 1];
       }
       __syncthreads();
       const int m = (int)min((int64_t)SH_T, cnt - c0);
@@ -95,9 +104,12 @@ k_simhash(const int64_t* __restrict__ off, const int32_t* __restrict__ adj, int6
         const int j = threadIdx.x + t * SH_T;
         if (j >= k) break;
         const int wj = j >> 6, bj = j & 63;
-        float acc = s[t];
-        for (int el = 0; el < m; ++el)
-          acc += ((bits[el * W + wj] >> bj) & 1ull) ? 1.0f : -1.0f;
+        acc_t acc = s[t];
+        for (int el = 0; el < m; ++el) {
+          const bool up = (bits[el * W + wj] >> bj) & 1ull;
+          if (WTD) acc = __dadd_rn(acc, up ? wel[el] : -wel[el]);
+          else acc += up ? 1.0f : -1.0f;
+        }
         s[t] = acc;
       }
       __syncthreads();
@@ -106,7 +118,7 @@ k_simhash(const int64_t* __restrict__ off, const int32_t* __restrict__ adj, int6
     const int lane = threadIdx.x & 31;
     for (int t = 0; t < per; ++t) {
       const int j = threadIdx.x + t * SH_T;
-      const unsigned bal = __ballot_sync(0xffffffffu, j < k && s[t] >= 0.0f);
+      const unsigned bal = __ballot_sync(0xffffffffu, j < k && s[t] >= (acc_t)0);
       if (lane == 0 && j < k) ballots[j >> 5] = bal;
     }
     __syncthreads();
@@ -224,7 +236,7 @@ int lsh_select(const int64_t* off, const int32_t* adj, const int32_t* deg, int64
 
 int lsh_apply(const scan_lsh_params& p, int kind, const int64_t* off, const int32_t* adj,
               const int32_t* deg, int64_t n, int64_t arcs, const int32_t* row, int64_t nH,
-              double* sim_csr, Pool& pool, cudaStream_t s) {
+              double* sim_csr, Pool& pool, cudaStream_t s, const double* wcsr) {
   (void)deg;
   (void)arcs;
   if (nH <= 0) return SCAN_OK;
@@ -247,11 +259,18 @@ int lsh_apply(const scan_lsh_params& p, int kind, const int64_t* off, const int3
     }
     GS_CUDA(cudaMemcpyAsync(tab, htab.data(), sizeof(double) * (k + 1), cudaMemcpyHostToDevice, s));
     const size_t smem = (size_t)SH_T * W * sizeof(uint64_t);
-    GS_CUDA(cudaFuncSetAttribute(k_simhash, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(SH_T * SH_WMAX * sizeof(uint64_t) > 200 * 1024
-                                           ? 200 * 1024
-                                           : SH_T * SH_WMAX * sizeof(uint64_t))));
-    k_simhash<<<gh, SH_T, smem, s>>>(off, adj, n, hlist, nH, W, key, sig);
+    const int smem_max = (int)(SH_T * SH_WMAX * sizeof(uint64_t) > 200 * 1024
+                                   ? 200 * 1024
+                                   : SH_T * SH_WMAX * sizeof(uint64_t));
+    if (wcsr) {
+      GS_CUDA(cudaFuncSetAttribute(k_simhash<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   smem_max));
+      k_simhash<true><<<gh, SH_T, smem, s>>>(off, adj, n, hlist, nH, W, key, wcsr, sig);
+    } else {
+      GS_CUDA(cudaFuncSetAttribute(k_simhash<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   smem_max));
+      k_simhash<false><<<gh, SH_T, smem, s>>>(off, adj, n, hlist, nH, W, key, nullptr, sig);
+    }
     GS_LAUNCH();
     k_lsh_sims<<<gw, 256, 0, s>>>(0, off, adj, row, hlist, nH, k, 0, sig, nullptr, tab, sim_csr);
     GS_LAUNCH();

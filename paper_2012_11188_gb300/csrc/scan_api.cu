@@ -141,7 +141,7 @@ int validate_lsh(const scan_lsh_params* p, int kind) {
 // ix holds n, arcs, off (absolute, int64), adj and allocated deg, no_id,
 // no_sim and an 8-word status block; on return ix->maxdeg is set.
 int run_pipeline(IndexData* ix, int kind, const scan_lsh_params* lsh, Pool& pool, cudaStream_t s,
-                 Events& ev, float* count_ms, int counts_mode) {
+                 Events& ev, float* count_ms, int counts_mode, const double* wcsr = nullptr) {
   const int64_t n = ix->n, arcs = ix->arcs;
   const bool use_lsh = lsh && lsh->enabled;
   unsigned* scalars = ix->status;  // [0] status, [1] maxdeg, [2] max out-degree
@@ -151,7 +151,8 @@ int run_pipeline(IndexData* ix, int kind, const scan_lsh_params* lsh, Pool& pool
   GS_CUDA(cudaStreamSynchronize(s));
   if (hs[0] & DEV_BADGRAPH) return SCAN_EBADGRAPH;
   ix->maxdeg = (int32_t)hs[1];
-  const bool dense = arcs > 0 && (counts_mode == SCAN_COUNTS_DENSE ||
+  // weighted similarities take the sparse enumeration only
+  const bool dense = arcs > 0 && !wcsr && (counts_mode == SCAN_COUNTS_DENSE ||
                                   (counts_mode == SCAN_COUNTS_AUTO && dense_counts_pay(n, arcs)));
   if (dense) {
     // closed counts of every arc from one matrix product (Section 4.1.1)
@@ -209,17 +210,19 @@ int run_pipeline(IndexData* ix, int kind, const scan_lsh_params* lsh, Pool& pool
     GS_CUDA(cudaMemcpyAsync(ix->no_id, ix->adj, arcs * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
     GS_TRY(launch_closed_counts_and_sims(kind, ix->off, ix->adj, ix->deg, n, arcs, od, oadj, opos,
                                          ix->maxdeg, max_od, use_lsh ? lsh->degree_threshold : -1,
-                                         ix->no_sim, scalars, pool, s, count_ms));
+                                         wcsr, ix->no_sim, scalars, pool, s, count_ms));
     GS_CUDA(cudaMemcpyAsync(hs, scalars, sizeof(hs), cudaMemcpyDeviceToHost, s));
     GS_CUDA(cudaStreamSynchronize(s));
     if (hs[0] & DEV_BADGRAPH) return SCAN_EBADGRAPH;
+    if (hs[0] & DEV_BADWEIGHT) return SCAN_EINVAL;
     pool.put(od);
     pool.put(oadj);
     pool.put(opos);
   }
   GS_TRY(ev.mark(s));
   if (use_lsh && nH > 0)
-    GS_TRY(lsh_apply(*lsh, kind, ix->off, ix->adj, ix->deg, n, arcs, row, nH, ix->no_sim, pool, s));
+    GS_TRY(lsh_apply(*lsh, kind, ix->off, ix->adj, ix->deg, n, arcs, row, nH, ix->no_sim, pool, s,
+                     wcsr));
   if (row) pool.put(row);
   GS_TRY(ev.mark(s));
   // ---- neighbour order (Algorithm 2)
@@ -259,11 +262,12 @@ int check_csr_args(const scan_csr* csr) {
 
 // Build one index into ix; on error every block is released by the pool.
 int build_one(const scan_csr* csr, int kind, const scan_lsh_params* lsh, cudaStream_t s,
-              IndexData* ix, int counts_mode = SCAN_COUNTS_AUTO) {
+              IndexData* ix, int counts_mode = SCAN_COUNTS_AUTO, const double* weights = nullptr) {
   if (counts_mode < SCAN_COUNTS_AUTO || counts_mode > SCAN_COUNTS_DENSE) return SCAN_EINVAL;
   GS_TRY(check_csr_args(csr));
   if (kind != SCAN_COSINE && kind != SCAN_JACCARD) return SCAN_EINVAL;
   GS_TRY(validate_lsh(lsh, kind));
+  if (weights && (kind != SCAN_COSINE || counts_mode == SCAN_COUNTS_DENSE)) return SCAN_EINVAL;
   const int64_t n = csr->n, arcs = csr->num_arcs;
   Pool pool(s);
   Events ev;
@@ -300,13 +304,20 @@ int build_one(const scan_csr* csr, int kind, const scan_lsh_params* lsh, cudaStr
                             cudaMemcpyHostToDevice, s));
   }
   if (arcs > 0) GS_CUDA(cudaMemcpyAsync(ix->adj, csr->adj, arcs * sizeof(int32_t), k_in, s));
+  double* wcsr = nullptr;  // arc weights, released with the build's scratch
+  if (weights && arcs > 0) {
+    wcsr = pool.get<double>(arcs);
+    if (!wcsr) return SCAN_ENOMEM;
+    GS_CUDA(cudaMemcpyAsync(wcsr, weights, arcs * sizeof(double), k_in, s));
+  }
   int64_t ends[2] = {0, 0};
   GS_CUDA(cudaMemcpyAsync(&ends[0], ix->off, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   GS_CUDA(cudaMemcpyAsync(&ends[1], ix->off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   GS_CUDA(cudaStreamSynchronize(s));
   if (ends[0] != 0 || ends[1] != arcs) return SCAN_EBADGRAPH;
   float count_ms = 0;
-  GS_TRY(run_pipeline(ix, kind, lsh, pool, s, ev, &count_ms, counts_mode));
+  GS_TRY(run_pipeline(ix, kind, lsh, pool, s, ev, &count_ms, counts_mode, wcsr));
+  if (wcsr) pool.put(wcsr);
   // ---- core order (Algorithm 2)
   GS_TRY(build_core_order(*ix, pool, s));
   GS_TRY(ev.mark(s));
@@ -619,6 +630,11 @@ int query_impl(scan_index* index, int q, const int* mu, const double* eps, int32
 
 using namespace gscan;
 
+namespace {
+// stands in for the weight array of a graph without arcs (never read)
+const double k_no_weight = 0.0;
+}  // namespace
+
 extern "C" {
 
 int scan_set_allocator(scan_alloc_fn alloc, scan_free_fn release, void* ctx) {
@@ -645,6 +661,24 @@ int scan_index_build_ex(const scan_csr* csr, scan_sim_kind kind, const scan_lsh_
   if (rc != SCAN_OK) {
     cudaStreamSynchronize((cudaStream_t)stream);
     delete h;  // the build's pool already released every block
+    return rc;
+  }
+  *out = h;
+  return SCAN_OK;
+}
+
+int scan_index_build_weighted(const scan_csr* csr, const double* weights,
+                              const scan_lsh_params* lsh, uintptr_t stream, scan_index** out) {
+  if (!out) return SCAN_EINVAL;
+  *out = nullptr;
+  if (!csr || (csr->num_arcs > 0 && !weights)) return SCAN_EINVAL;
+  scan_index* h = new (std::nothrow) scan_index();
+  if (!h) return SCAN_ENOMEM;
+  const int rc = build_one(csr, SCAN_COSINE, lsh, (cudaStream_t)stream, &h->d,
+                           SCAN_COUNTS_SPARSE, weights ? weights : &k_no_weight);
+  if (rc != SCAN_OK) {
+    cudaStreamSynchronize((cudaStream_t)stream);
+    delete h;
     return rc;
   }
   *out = h;

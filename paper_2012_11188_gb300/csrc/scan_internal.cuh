@@ -45,6 +45,7 @@ enum : unsigned {
   DEV_BADGRAPH = 1u,   // unsorted / duplicate / self-loop / out-of-range / asymmetric
   DEV_LIMIT = 2u,      // a bounded loop gave up
   DEV_OVERFLOW = 4u,   // a fixed-capacity structure would overflow
+  DEV_BADWEIGHT = 8u,  // a weight negative, not finite, or not symmetric
 };
 
 // ------------------------------------------------------------ device memory
@@ -132,8 +133,8 @@ int launch_orient(const int64_t* off, const int32_t* adj, const int32_t* deg, in
 int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* adj,
                                   const int32_t* deg, int64_t n, int64_t arcs, const int32_t* od,
                                   int32_t* oadj, int32_t* opos, int32_t maxdeg,
-                                  int32_t max_od, int lsh_T, double* sim_csr, unsigned* status,
-                                  Pool& pool, cudaStream_t s, float* count_ms);
+                                  int32_t max_od, int lsh_T, const double* wcsr, double* sim_csr,
+                                  unsigned* status, Pool& pool, cudaStream_t s, float* count_ms);
 
 // Sort every segment [seg_off[i], seg_off[i+1]) of (key, val) pairs by key
 // descending, then val ascending. Keys are non-negative doubles viewed as
@@ -190,7 +191,8 @@ bool is_device_ptr(const void* p);
 // LSH mode: overwrite the similarities of approximated arcs.
 int lsh_apply(const scan_lsh_params& p, int kind, const int64_t* off, const int32_t* adj,
               const int32_t* deg, int64_t n, int64_t arcs, const int32_t* row, int64_t nH,
-              double* no_sim, Pool& pool, cudaStream_t s);
+              double* no_sim, Pool& pool, cudaStream_t s,
+              const double* wcsr = nullptr);
 int lsh_select(const int64_t* off, const int32_t* adj, const int32_t* deg, int64_t n,
                int threshold, int32_t* row, int64_t* nH_host, Pool& pool, cudaStream_t s);
 

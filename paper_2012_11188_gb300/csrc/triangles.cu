@@ -27,6 +27,12 @@ namespace {
 #ifndef GS_TRI_FAST_ROUNDS
 #define GS_TRI_FAST_ROUNDS 12  // the same for out-lists streamed one at a time
 #endif
+#ifndef GS_WT_SHARED_SUMS
+// weighted mode: 1 = (v,w) and (u,v) sums in shared memory (double atomics
+// there), 0 = every sum a global double reduction (done in L2, off the SM's
+// FP64 pipe, which on this GPU issues two lanes per clock)
+#define GS_WT_SHARED_SUMS 0
+#endif
 #ifndef GS_TRI_LONG_LIST
 #define GS_TRI_LONG_LIST 64  // suffixes at least this long are streamed one at a time
 #endif
@@ -245,7 +251,8 @@ __device__ __forceinline__ OutTable table_build(uint32_t* t0, int hcap, uint32_t
       if (t0[h0 >> shift] == h0) p0[h0 >> shift] = (uint16_t)j;
       else p1[((uint32_t)list[j] * c1) >> shift] = (uint16_t)j;
     }
-  for (int i = tid; i < od; i += nthreads) vcnt[i] = 0;
+  if (vcnt)
+    for (int i = tid; i < od; i += nthreads) vcnt[i] = 0;
   sync();
   return OutTable{t0, hcap, shift, c0, c1, gkey, deg, od, failed};
 }
@@ -275,6 +282,34 @@ __device__ __forceinline__ bool probe(const OutTable& tab, int32_t x, IT j, int6
   return true;
 }
 
+// Weighted cosine (Section 3.1, w(x,x) = 1): a triangle u < v < w adds
+// w(u,w) w(v,w) to the numerator of (u,v), w(u,v) w(u,w) to that of (v,w)
+// and w(u,v) w(v,w) to that of (u,w). ow[j] is the weight of out-arc j; the
+// (v,w) sums go to vsum (shared) or tsum at ob + q, the (u,w) sums to tsum
+// at j, and on a hit the (u,v) term is added to uv. A miss does no
+// floating-point work.
+template <bool BIG, typename IT>
+__device__ __forceinline__ bool probe_w(const OutTable& tab, int32_t x, IT j, int64_t ob,
+                                        double w_uv, const double* __restrict__ ow,
+                                        double* vsum, double* __restrict__ tsum, double& uv) {
+  const int q = table_lookup<BIG>(tab, x);
+  if (q < 0) return false;
+  const double w_uw = ow[j], w_vw = ow[ob + q];
+  if (!BIG && GS_WT_SHARED_SUMS) atomicAdd(&vsum[q], w_uv * w_uw);
+  else atomicAdd(&tsum[ob + q], w_uv * w_uw);
+  atomicAdd(&tsum[j], w_uv * w_vw);
+  uv += w_uw * w_vw;
+  return true;
+}
+
+// Weighted-mode state of a counting kernel (all null when unweighted).
+struct Weights {
+  const double* ow;  // weight of every out-arc, at its position
+  double* vsum;      // (v,w) sums of the current middle vertex (shared)
+  double* tsum;      // numerator sums of every out-arc (global)
+  double* acc;       // per-warp (u,v) sums of the slice's in-neighbours (shared)
+};
+
 // One warp: triangles u < v < w for the in-neighbours u of v among the CSR
 // positions [p0, min(p0+32, p_end)) of N(v). The in-neighbours are compacted
 // to lanes 0..k-1, and each lane finds v in out(u) (ascending rank) by a
@@ -286,7 +321,7 @@ __device__ __forceinline__ bool probe(const OutTable& tab, int32_t x, IT j, int6
 // flight), the owner of an element coming from the suffix starts that fall
 // in its round (ballot / or-reduce / popc). Hits on (u,v) are counted per
 // list.
-template <bool BIG, typename IT>
+template <bool BIG, typename IT, bool WT>
 __device__ __forceinline__ void process_slice(
     int64_t p0, int64_t p_end, int64_t rb, int32_t v, int32_t dv, int32_t od, int64_t ob,
     const int32_t* __restrict__ adj, const int32_t* __restrict__ deg,
@@ -294,7 +329,7 @@ __device__ __forceinline__ void process_slice(
     const int32_t* __restrict__ oadj, const uint64_t* __restrict__ okey,
     const int64_t* __restrict__ odp, int lsh_T, const OutTable& tab, uint32_t* vcnt,
     const SliceSmem& sm, uint32_t* __restrict__ tcnt, uint32_t* __restrict__ tc16,
-    int32_t* __restrict__ twin_rel, unsigned& bad) {
+    int32_t* __restrict__ twin_rel, unsigned& bad, const Weights& wt) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int64_t p = p0 + lane;
@@ -342,6 +377,11 @@ __device__ __forceinline__ void process_slice(
     return;
   }
   sm.acc[lane] = 0;
+  double w_uv = 0.0;  // weighted mode: w(u,v) of this lane's in-neighbour
+  if (WT) {
+    if (GS_WT_SHARED_SUMS) wt.acc[lane] = 0.0;
+    if (found) w_uv = wt.ow[jv];
+  }
   __syncwarp();
 
   // 1. long suffixes, one at a time
@@ -352,7 +392,11 @@ __device__ __forceinline__ void process_slice(
     lm &= lm - 1;
     const IT ub = __shfl_sync(FULL, cub, i);
     const int32_t len = __shfl_sync(FULL, clen, i);
+    const double wi = WT ? __shfl_sync(FULL, w_uv, i) : 0.0;
+    const IT jvi = WT ? __shfl_sync(FULL, jv, i) : (IT)0;  // the arc u->v of list i
     unsigned hits = 0;  // this lane's hits on the list
+    double hsum = 0.0;  // weighted mode: this lane's (u,v) terms
+    bool any_hit = false;
     for (int32_t t0 = 0; t0 < len; t0 += 32 * RF) {
       int32_t xs[RF];
 #pragma unroll
@@ -364,11 +408,23 @@ __device__ __forceinline__ void process_slice(
       for (int rr = 0; rr < RF; ++rr) {
         if (t0 + 32 * rr >= len) break;
         const IT j = ub + (IT)(t0 + 32 * rr + lane);
-        hits += probe<BIG, IT>(tab, xs[rr], j, ob, vcnt, tcnt, tc16) ? 1u : 0u;
+        if (WT) any_hit |= probe_w<BIG, IT>(tab, xs[rr], j, ob, wi, wt.ow, wt.vsum, wt.tsum, hsum);
+        else hits += probe<BIG, IT>(tab, xs[rr], j, ob, vcnt, tcnt, tc16) ? 1u : 0u;
       }
     }
-    hits = __reduce_add_sync(FULL, hits);
-    if (lane == 0) sm.acc[i] += hits;
+    if (WT) {
+      if (GS_WT_SHARED_SUMS) {
+        if (__any_sync(FULL, any_hit)) {
+          for (int o = 16; o; o >>= 1) hsum += __shfl_xor_sync(FULL, hsum, o);
+          if (lane == 0) wt.acc[i] += hsum;
+        }
+      } else if (any_hit) {
+        atomicAdd(&wt.tsum[jvi], hsum);
+      }
+    } else {
+      hits = __reduce_add_sync(FULL, hits);
+      if (lane == 0) sm.acc[i] += hits;
+    }
   }
 
   // 2. short non-empty suffixes, concatenated: lane r takes the r-th of them
@@ -414,20 +470,36 @@ __device__ __forceinline__ void process_slice(
 #pragma unroll
       for (int rr = 0; rr < R; ++rr) {
         const int own = owns[rr];
-        const bool hit = probe<BIG, IT>(tab, xs[rr], js[rr], ob, vcnt, tcnt, tc16);
-        const unsigned hm = __ballot_sync(FULL, hit);
-        if (hm) {
-          // lanes of one owner are contiguous; its first lane adds
-          const unsigned peers = __match_any_sync(FULL, own);
-          if ((hm & peers) && lane == __ffs(peers) - 1) sm.acc[own] += __popc(hm & peers);
+        if (WT) {
+          // the owner's w(u,v) and arc u->v are held by lane `own`; its (u,v)
+          // term goes to the owner's sum
+          const double wo = __shfl_sync(FULL, w_uv, own);
+          const IT jo = __shfl_sync(FULL, jv, own);
+          double pv = 0.0;
+          if (probe_w<BIG, IT>(tab, xs[rr], js[rr], ob, wo, wt.ow, wt.vsum, wt.tsum, pv)) {
+            if (GS_WT_SHARED_SUMS) atomicAdd(&wt.acc[own], pv);
+            else atomicAdd(&wt.tsum[jo], pv);
+          }
+        } else {
+          const bool hit = probe<BIG, IT>(tab, xs[rr], js[rr], ob, vcnt, tcnt, tc16);
+          const unsigned hm = __ballot_sync(FULL, hit);
+          if (hm) {
+            // lanes of one owner are contiguous; its first lane adds
+            const unsigned peers = __match_any_sync(FULL, own);
+            if ((hm & peers) && lane == __ffs(peers) - 1) sm.acc[own] += __popc(hm & peers);
+          }
         }
       }
     }
   }
   __syncwarp();
   if (found) {
-    const uint32_t acc = sm.acc[lane];
-    if (acc) atomicAdd(&tcnt[jv], acc);
+    if (WT) {
+      if (GS_WT_SHARED_SUMS) atomicAdd(&wt.tsum[jv], wt.acc[lane]);
+    } else {
+      const uint32_t acc = sm.acc[lane];
+      if (acc) atomicAdd(&tcnt[jv], acc);
+    }
     twin_rel[jv] = cp;  // position of u in N(v)
   }
   __syncwarp();
@@ -438,7 +510,7 @@ __device__ __forceinline__ void process_slice(
 // BIG = out(v) too long for the shared table (binary search, global counters);
 // the BIG kernel also takes the items listed in `deferred`, whose shared
 // table could not be built (no cuckoo placement).
-template <bool BIG, typename IT>
+template <bool BIG, typename IT, bool WT>
 __global__ void __launch_bounds__(TRI_THREADS, 3)
 k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
             const int32_t* __restrict__ deg, const int32_t* __restrict__ odeg,
@@ -447,8 +519,8 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
             const int32_t* __restrict__ order, unsigned long long* __restrict__ work, int lsh_T,
             int od_cap, int64_t* __restrict__ deferred, unsigned long long* __restrict__ n_deferred,
             bool deferred_only, uint32_t* __restrict__ tcnt, uint32_t* __restrict__ tc16,
-            int32_t* __restrict__ twin_rel,
-            unsigned* status) {
+            int32_t* __restrict__ twin_rel, unsigned* status, const double* __restrict__ ow,
+            double* __restrict__ tsum) {
   // shared layout for od_cap (a power of two >= every od handled here) and
   // hcap = 2^table_log2(od_cap): the table (t0, t1, p0, p1; 12 bytes per
   // hcap), then vcnt[od_cap]
@@ -458,6 +530,7 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
   __shared__ int32_t s_u[TRI_WARPS][32];
   __shared__ int32_t s_p[TRI_WARPS][32];
   __shared__ uint32_t s_acc[TRI_WARPS][32];
+  __shared__ double s_accd[WT ? TRI_WARPS : 1][32];
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   // BIG: first the items whose out-list is too long for the shared table
@@ -466,7 +539,9 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
   const int64_t total = BIG ? total_items + (int64_t)*n_deferred : total_items;
   const int hcap = 1 << table_log2(od_cap);
   uint32_t* t0 = reinterpret_cast<uint32_t*>(smem4);
-  uint32_t* vcnt = t0 + 3 * hcap;
+  uint32_t* vcnt = t0 + 3 * hcap;  // weighted mode: double vsum[od_cap] in its place
+  double* vsum = reinterpret_cast<double*>(vcnt);
+  const Weights wt{ow, WT ? vsum : nullptr, tsum, WT ? s_accd[wid] : nullptr};
   const SliceSmem sm{s_u[wid], s_p[wid], s_acc[wid]};
   unsigned bad = 0;
 
@@ -490,13 +565,17 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
     if (skip_item) { __syncthreads(); continue; }
     OutTable tab{nullptr, 0, 27, 0u, 0u, okey + odp[v], deg, od, true};
     if (!BIG && od > 0) {
-      tab = table_build(t0, hcap, vcnt, oadj + ob, okey + odp[v], deg, od, threadIdx.x,
-                        TRI_THREADS,
+      tab = table_build(t0, hcap, WT ? nullptr : vcnt, oadj + ob, okey + odp[v], deg, od,
+                        threadIdx.x, TRI_THREADS,
                         [] { __syncthreads(); }, [](bool b) { return __syncthreads_or(b) != 0; });
       if (tab.bsearch) {  // hand the item to the BIG kernel
         if (threadIdx.x == 0) deferred[atomicAdd(n_deferred, 1ull)] = item;
         __syncthreads();
         continue;
+      }
+      if (WT && GS_WT_SHARED_SUMS) {
+        for (int i = threadIdx.x; i < od; i += TRI_THREADS) vsum[i] = 0.0;
+        __syncthreads();
       }
     }
     const int64_t rb = off[v];
@@ -509,14 +588,20 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
       slice = __shfl_sync(FULL, slice, 0);
       const int64_t pos0 = p_begin + slice;
       if (pos0 >= p_end) break;
-      process_slice<BIG, IT>(pos0, p_end, rb, (int32_t)v, dv, od, ob, adj, deg, off, odeg, oadj,
-                             okey, odp, lsh_T, tab, vcnt, sm, tcnt, tc16, twin_rel, bad);
+      process_slice<BIG, IT, WT>(pos0, p_end, rb, (int32_t)v, dv, od, ob, adj, deg, off, odeg,
+                                 oadj, okey, odp, lsh_T, tab, vcnt, sm, tcnt, tc16, twin_rel, bad,
+                                 wt);
     }
     __syncthreads();
-    if (!BIG)
+    if (!BIG && !(WT && !GS_WT_SHARED_SUMS))
       for (int j = threadIdx.x; j < od; j += TRI_THREADS) {
-        const uint32_t c = vcnt[j];
-        if (c) atomicAdd(&tcnt[ob + j], c);
+        if (WT) {
+          const double c = vsum[j];
+          if (__double_as_longlong(c) != 0) atomicAdd(&tsum[ob + j], c);
+        } else {
+          const uint32_t c = vcnt[j];
+          if (c) atomicAdd(&tcnt[ob + j], c);
+        }
       }
     __syncthreads();
   }
@@ -527,23 +612,28 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
 // most SMALL_OD entries: each warp owns one
 // vertex at a time, with its own table of out(v) (no CTA barrier). Warps take
 // 32 vertices per atomic fetch.
-template <typename IT>
+template <typename IT, bool WT>
 __global__ void __launch_bounds__(SW_WARPS * 32, 8)
 k_tri_small(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
             const int32_t* __restrict__ deg, const int32_t* __restrict__ odeg,
             const int32_t* __restrict__ oadj, const uint64_t* __restrict__ okey,
             const int64_t* __restrict__ odp, int64_t n, unsigned long long* __restrict__ work,
             int lsh_T, uint32_t* __restrict__ tcnt, uint32_t* __restrict__ tc16,
-            int32_t* __restrict__ twin_rel,
-            unsigned* status) {
+            int32_t* __restrict__ twin_rel, unsigned* status, const double* __restrict__ ow,
+            double* __restrict__ tsum) {
   __shared__ __align__(16) uint32_t s_tab[SW_WARPS][3 * SW_SLOTS];  // t0 | t1 | p0 p1
-  __shared__ uint32_t s_cnt[SW_WARPS][SMALL_OD];
+  __shared__ uint32_t s_cnt[WT ? 1 : SW_WARPS][SMALL_OD];
+  __shared__ double s_sum[WT && GS_WT_SHARED_SUMS ? SW_WARPS : 1]
+                        [WT && GS_WT_SHARED_SUMS ? SMALL_OD : 1];
+  __shared__ double s_accd[WT ? SW_WARPS : 1][32];
   __shared__ int32_t s_u[SW_WARPS][32];
   __shared__ int32_t s_p[SW_WARPS][32];
   __shared__ uint32_t s_acc[SW_WARPS][32];
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  uint32_t* vcnt = s_cnt[wid];
+  uint32_t* vcnt = WT ? nullptr : s_cnt[wid];
+  double* vsum = WT ? s_sum[wid] : nullptr;
+  const Weights wt{ow, vsum, tsum, WT ? s_accd[wid] : nullptr};
   const SliceSmem sm{s_u[wid], s_p[wid], s_acc[wid]};
   unsigned bad = 0;
   for (;;) {
@@ -559,27 +649,37 @@ k_tri_small(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
       if (!warp_vertex(dv, od) || dv - od == 0) continue;  // CTA kernel, or no in-neighbours
       const int64_t ob = off[vv];
       OutTable tab{nullptr, 0, 27, 0u, 0u, okey + odp[vv], deg, od, true};
-      if (od > 0)
+      if (od > 0) {
         tab = table_build(s_tab[wid], SW_SLOTS, vcnt, oadj + ob, okey + odp[vv], deg, od, lane, 32,
                           [] { __syncwarp(); },
                           [](bool b) { __syncwarp(); return __any_sync(0xffffffffu, b) != 0; });
+        if (WT && GS_WT_SHARED_SUMS) {
+          for (int i = lane; i < od; i += 32) vsum[i] = 0.0;
+          __syncwarp();
+        }
+      }
       const bool use_table = !tab.bsearch;
       const int64_t rb = off[vv];
       for (int64_t pos0 = 0; pos0 < dv; pos0 += 32) {
         if (use_table)
-          process_slice<false, IT>(pos0, dv, rb, (int32_t)vv, dv, od, ob, adj, deg, off, odeg,
-                                   oadj, okey, odp, lsh_T, tab, vcnt, sm, tcnt, tc16, twin_rel,
-                                   bad);
+          process_slice<false, IT, WT>(pos0, dv, rb, (int32_t)vv, dv, od, ob, adj, deg, off, odeg,
+                                       oadj, okey, odp, lsh_T, tab, vcnt, sm, tcnt, tc16,
+                                       twin_rel, bad, wt);
         else
-          process_slice<true, IT>(pos0, dv, rb, (int32_t)vv, dv, od, ob, adj, deg, off, odeg,
-                                  oadj, okey, odp, lsh_T, tab, vcnt, sm, tcnt, tc16, twin_rel,
-                                  bad);
+          process_slice<true, IT, WT>(pos0, dv, rb, (int32_t)vv, dv, od, ob, adj, deg, off, odeg,
+                                      oadj, okey, odp, lsh_T, tab, vcnt, sm, tcnt, tc16,
+                                      twin_rel, bad, wt);
       }
       __syncwarp();
-      if (use_table)
+      if (use_table && !(WT && !GS_WT_SHARED_SUMS))
         for (int j = lane; j < od; j += 32) {
-          const uint32_t c = vcnt[j];
-          if (c) atomicAdd(&tcnt[ob + j], c);
+          if (WT) {
+            const double c = vsum[j];
+            if (__double_as_longlong(c) != 0) atomicAdd(&tsum[ob + j], c);
+          } else {
+            const uint32_t c = vcnt[j];
+            if (c) atomicAdd(&tcnt[ob + j], c);
+          }
         }
       __syncwarp();
     }
@@ -711,6 +811,129 @@ k_rank_scatter(const int64_t* __restrict__ off, const int64_t* __restrict__ odp,
   }
 }
 
+// Weighted mode: ow[j] = weight of out-arc j (read at its row position);
+// a weight that is negative or not finite marks the build DEV_BADWEIGHT.
+__global__ void __launch_bounds__(EXPAND_T)
+k_out_weights(const int64_t* __restrict__ off, const int64_t* __restrict__ odp, int64_t n,
+              const int32_t* __restrict__ opos, const double* __restrict__ wcsr,
+              double* __restrict__ ow, unsigned* status) {
+  __shared__ int64_t s_bracket[2];
+  const int64_t m = odp[n];
+  constexpr int64_t CH = (int64_t)EXPAND_T * EXPAND_ITEMS;
+  bool bad = false;
+  for (int64_t k0 = (int64_t)blockIdx.x * CH; k0 < m; k0 += (int64_t)gridDim.x * CH) {
+    const int64_t k1 = min(m, k0 + CH);
+    if (threadIdx.x == 0) s_bracket[0] = row_of(odp, 0, n + 1, k0);
+    if (threadIdx.x == 1) s_bracket[1] = row_of(odp, 0, n + 1, k1 - 1) + 1;
+    __syncthreads();
+    const int64_t lo = s_bracket[0], hi = s_bracket[1];
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += EXPAND_T) {
+      const int64_t a = row_of(odp, lo, hi, k);
+      const int64_t j = off[a] + (k - odp[a]);
+      const double w = wcsr[off[a] + opos[j]];
+      // integer tests (off the FP64 pipe): negative non-zero, or inf / NaN
+      const long long bits = __double_as_longlong(w);
+      if ((bits < 0 && bits != (long long)0x8000000000000000ull) || ((bits >> 52) & 0x7ff) == 0x7ff)
+        bad = true;
+      ow[j] = w;
+    }
+    __syncthreads();
+  }
+  if (bad) atomicOr(status, (unsigned)DEV_BADWEIGHT);
+}
+
+// norm[x] = sqrt(1 + sum of w(x,y)^2 over N(x)): the closed neighbourhood
+// with w(x,x) = 1 (Section 3.1). FP64 instructions are issued for a whole
+// warp at a time, so rows of at most 32 entries are summed by one thread each
+// (32 vertices per instruction); longer rows by the whole warp.
+__global__ void k_wnorm(const int64_t* __restrict__ off, const double* __restrict__ wcsr, int64_t n,
+                        double* __restrict__ norm) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; base < n;
+       base += stride) {
+    const int64_t x = base + lane;
+    int64_t b = 0, e = 0;
+    if (x < n) {
+      b = off[x];
+      e = off[x + 1];
+    }
+    const bool long_row = e - b > 32;
+    if (x < n && !long_row) {
+      double s2 = 0.0;
+      for (int64_t i = b; i < e; ++i) s2 += wcsr[i] * wcsr[i];
+      norm[x] = sqrt(1.0 + s2);
+    }
+    unsigned lm = __ballot_sync(FULL, long_row);
+    while (lm) {
+      const int src = __ffs(lm) - 1;
+      lm &= lm - 1;
+      const int64_t bb = __shfl_sync(FULL, b, src), ee = __shfl_sync(FULL, e, src);
+      double s2 = 0.0;
+      for (int64_t i = bb + lane; i < ee; i += 32) s2 += wcsr[i] * wcsr[i];
+      for (int o = 16; o; o >>= 1) s2 += __shfl_xor_sync(FULL, s2, o);
+      if (lane == 0) norm[base + src] = sqrt(1.0 + s2);
+    }
+  }
+}
+
+// Weighted cosine of every oriented edge a->b, written to both CSR arcs:
+// (2 w(a,b) + triangle terms) / (norm[a] norm[b]) (Section 3.1); the weights
+// of the two arcs must agree (else DEV_BADWEIGHT).
+__global__ void __launch_bounds__(EXPAND_T)
+k_expand_w(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+           const int64_t* __restrict__ odp, const int32_t* __restrict__ oadj,
+           const int32_t* __restrict__ opos,
+           const double* __restrict__ ow, const double* __restrict__ tsum,
+           const int32_t* __restrict__ twin_rel, const double* __restrict__ wcsr,
+           const double* __restrict__ norm, const int32_t* __restrict__ deg, int64_t n,
+           int lsh_T, double* __restrict__ sim_csr, unsigned* status) {
+  __shared__ int64_t s_bracket[2];
+  const int64_t m = odp[n];
+  constexpr int64_t CH = (int64_t)EXPAND_T * EXPAND_ITEMS;
+  unsigned bad = 0;
+  for (int64_t k0 = (int64_t)blockIdx.x * CH; k0 < m; k0 += (int64_t)gridDim.x * CH) {
+    const int64_t k1 = min(m, k0 + CH);
+    if (threadIdx.x == 0) s_bracket[0] = row_of(odp, 0, n + 1, k0);
+    if (threadIdx.x == 1) s_bracket[1] = row_of(odp, 0, n + 1, k1 - 1) + 1;
+    __syncthreads();
+    const int64_t lo = s_bracket[0], hi = s_bracket[1];
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += EXPAND_T) {
+      const int64_t a = row_of(odp, lo, hi, k);
+      const int64_t ra = off[a];
+      const int64_t j = ra + (k - odp[a]);
+      const int32_t b = oadj[j];
+      const double w = ow[j];
+      if (lsh_T >= 0 && deg[a] > lsh_T && deg[b] > lsh_T) {
+        // LSH mode: the estimate pass writes the similarity of an
+        // approximated edge, and the counting kernels skipped its twin: find
+        // a in N(b) to check the weights
+        int64_t lo2 = off[b], hi2 = off[b + 1];
+        while (lo2 < hi2) {
+          const int64_t mid = (lo2 + hi2) >> 1;
+          if (adj[mid] < a) lo2 = mid + 1;
+          else hi2 = mid;
+        }
+        if (lo2 == off[b + 1] || adj[lo2] != a) bad |= DEV_BADGRAPH;
+        else if (wcsr[lo2] != w) bad |= DEV_BADWEIGHT;
+        continue;
+      }
+      const double sv = __ddiv_rn(__dadd_rn(2.0 * w, tsum[j]), __dmul_rn(norm[a], norm[b]));
+      sim_csr[ra + opos[j]] = sv;
+      const int32_t tr = twin_rel[j];
+      if (tr < 0) {
+        bad |= DEV_BADGRAPH;
+      } else {
+        if (wcsr[off[b] + tr] != w) bad |= DEV_BADWEIGHT;
+        sim_csr[off[b] + tr] = sv;
+      }
+    }
+    __syncthreads();
+  }
+  if (bad) atomicOr(status, bad);
+}
+
 __global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -720,48 +943,47 @@ __global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v) {
 }  // namespace
 
 // The three counting kernels; IT indexes elements of the CSR (32-bit when the
-// graph has fewer than 2^31 arcs, which halves the index arithmetic).
-template <typename IT>
+// graph has fewer than 2^31 arcs, which halves the index arithmetic); WT
+// accumulates weighted-cosine numerators (ow, tsum) instead of counts.
+template <typename IT, bool WT>
 int launch_counting(const int64_t* off, const int32_t* adj, const int32_t* deg, const int32_t* odeg,
                     const int32_t* oadj, const uint64_t* okey, const int64_t* odp, int64_t n,
                     const int64_t* item_off, const int32_t* order,
                     unsigned long long* work, int lsh_T, int32_t max_od, int64_t* deferred,
                     unsigned long long* n_deferred, uint32_t* tcnt, uint32_t* tc16, int32_t* twin,
-                    unsigned* status, cudaStream_t s) {
+                    unsigned* status, const double* ow, double* tsum, cudaStream_t s) {
   int od_cap = 16;
   while (od_cap < max_od && od_cap < SMEM_OD_MAX) od_cap <<= 1;
-  // the table (12 bytes per slot, 2 * od_cap slots) and the counters
-  const size_t smem = (size_t)28 * od_cap;
-  const size_t smem_max = (size_t)28 * SMEM_OD_MAX;
-  GS_CUDA(cudaFuncSetAttribute(k_triangles<false, IT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem_max));
+  // the table (12 bytes per slot, 2 * od_cap slots) and the counters (4 or 8 bytes)
+  const size_t per_od = (WT && GS_WT_SHARED_SUMS) ? 32 : 28;
+  const size_t smem = per_od * od_cap;
+  const size_t smem_max = per_od * SMEM_OD_MAX;
+  GS_CUDA(cudaFuncSetAttribute(k_triangles<false, IT, WT>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
   int dev = 0, sms = 152, per_sm = 1;
   GS_CUDA(cudaGetDevice(&dev));
   GS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  GS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_triangles<false, IT>,
+  GS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_triangles<false, IT, WT>,
                                                         TRI_THREADS, smem));
   if (per_sm < 1) per_sm = 1;
-  k_triangles<false, IT><<<sms * per_sm, TRI_THREADS, smem, s>>>(
+  k_triangles<false, IT, WT><<<sms * per_sm, TRI_THREADS, smem, s>>>(
       off, adj, deg, odeg, oadj, okey, odp, n, item_off, order, work, lsh_T, od_cap, deferred,
-      n_deferred,
-      false, tcnt, tc16, twin, status);
+      n_deferred, false, tcnt, tc16, twin, status, ow, tsum);
   GS_LAUNCH();
   int small_per_sm = 1;
-  GS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&small_per_sm, k_tri_small<IT>,
+  GS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&small_per_sm, k_tri_small<IT, WT>,
                                                         SW_WARPS * 32, 0));
   if (small_per_sm < 1) small_per_sm = 1;
-  k_tri_small<IT><<<sms * small_per_sm, SW_WARPS * 32, 0, s>>>(off, adj, deg, odeg, oadj, okey,
-                                                               odp, n,
-                                                               work + 2, lsh_T, tcnt, tc16, twin,
-                                                               status);
+  k_tri_small<IT, WT><<<sms * small_per_sm, SW_WARPS * 32, 0, s>>>(
+      off, adj, deg, odeg, oadj, okey, odp, n, work + 2, lsh_T, tcnt, tc16, twin, status, ow,
+      tsum);
   GS_LAUNCH();
   // items with out-lists too long for the shared table, and items deferred
   // by the CTA kernel (normally none: the launch then ends at once)
   const bool deferred_only = max_od <= SMEM_OD_MAX;
-  k_triangles<true, IT><<<deferred_only ? sms : sms * 4, TRI_THREADS, 0, s>>>(
+  k_triangles<true, IT, WT><<<deferred_only ? sms : sms * 4, TRI_THREADS, 0, s>>>(
       off, adj, deg, odeg, oadj, okey, odp, n, item_off, order, work + 1, lsh_T, 0, deferred,
-      n_deferred,
-      deferred_only, tcnt, tc16, twin, status);
+      n_deferred, deferred_only, tcnt, tc16, twin, status, ow, tsum);
   GS_LAUNCH();
   return SCAN_OK;
 }
@@ -769,14 +991,20 @@ int launch_counting(const int64_t* off, const int32_t* adj, const int32_t* deg, 
 int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* adj,
                                   const int32_t* deg, int64_t n, int64_t arcs, const int32_t* odeg,
                                   int32_t* oadj, int32_t* opos, int32_t maxdeg,
-                                  int32_t max_od, int lsh_T, double* sim_csr, unsigned* status,
-                                  Pool& pool, cudaStream_t s, float* count_ms) {
+                                  int32_t max_od, int lsh_T, const double* wcsr, double* sim_csr,
+                                  unsigned* status, Pool& pool, cudaStream_t s, float* count_ms) {
+  const bool weighted = wcsr != nullptr;
   const int64_t m = arcs;  // out-lists live in CSR slots: counts and twins are indexed by arc
   const int64_t edges = m / 2;  // oriented edges (the orientation checked sum od = arcs / 2)
   int64_t* odp = pool.get<int64_t>(n + 1);
   uint64_t* okey = pool.get<uint64_t>(edges > 0 ? edges : 1);
   int32_t* oval = pool.get<int32_t>(edges > 0 ? edges : 1);
   if (!odp || !okey || !oval) return SCAN_ENOMEM;
+  double* ow = weighted ? pool.get<double>(m) : nullptr;     // weight of every out-arc
+  double* tsum = weighted ? pool.get<double>(m) : nullptr;   // numerator sums per out-arc
+  double* norm = weighted ? pool.get<double>(n > 0 ? n : 1) : nullptr;
+  if (weighted && (!ow || !tsum || !norm)) return SCAN_ENOMEM;
+  if (weighted) GS_CUDA(cudaMemsetAsync(tsum, 0, m * sizeof(double), s));
   const int64_t nbins = (int64_t)maxdeg + 1;
   uint32_t* tcnt = pool.get<uint32_t>(m);
   // 16-bit (u,w) counters, two per word, when positions fit in 32 bits
@@ -833,20 +1061,40 @@ int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* a
     GS_TRY(segmented_sort_desc(okey, oval, odp, n, edges, max_od, pool, s));
     k_rank_scatter<<<egrid, EXPAND_T, 0, s>>>(off, odp, n, okey, oval, oadj, opos);
     GS_LAUNCH();
-    if (narrow) {
-      GS_TRY(launch_counting<int32_t>(off, adj, deg, odeg, oadj, okey, odp, n, item_off, order,
-                                      work, lsh_T, max_od, deferred, work + 3, tcnt, tc16, twin,
-                                      status, s));
+    if (weighted) {
+      k_out_weights<<<egrid, EXPAND_T, 0, s>>>(off, odp, n, opos, wcsr, ow, status);
+      GS_LAUNCH();
+      if (narrow) {
+        GS_TRY((launch_counting<int32_t, true>(off, adj, deg, odeg, oadj, okey, odp, n, item_off,
+                                               order, work, lsh_T, max_od, deferred, work + 3,
+                                               tcnt, tc16, twin, status, ow, tsum, s)));
+      } else {
+        GS_TRY((launch_counting<int64_t, true>(off, adj, deg, odeg, oadj, okey, odp, n, item_off,
+                                               order, work, lsh_T, max_od, deferred, work + 3,
+                                               tcnt, nullptr, twin, status, ow, tsum, s)));
+      }
+    } else if (narrow) {
+      GS_TRY((launch_counting<int32_t, false>(off, adj, deg, odeg, oadj, okey, odp, n, item_off,
+                                              order, work, lsh_T, max_od, deferred, work + 3, tcnt,
+                                              tc16, twin, status, nullptr, nullptr, s)));
     } else {
-      GS_TRY(launch_counting<int64_t>(off, adj, deg, odeg, oadj, okey, odp, n, item_off, order,
-                                      work, lsh_T, max_od, deferred, work + 3, tcnt, nullptr, twin,
-                                      status, s));
+      GS_TRY((launch_counting<int64_t, false>(off, adj, deg, odeg, oadj, okey, odp, n, item_off,
+                                              order, work, lsh_T, max_od, deferred, work + 3, tcnt,
+                                              nullptr, twin, status, nullptr, nullptr, s)));
     }
   }
   GS_CUDA(cudaEventRecord(e1, s));
   if (n > 0 && m > 0) {
-    k_expand<<<egrid, EXPAND_T, 0, s>>>(kind, off, deg, odp, oadj, opos, tcnt, tc16, twin, n,
-                                        lsh_T, sim_csr, status);
+    if (weighted) {
+      k_wnorm<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, s>>>(off, wcsr, n,
+                                                                                      norm);
+      GS_LAUNCH();
+      k_expand_w<<<egrid, EXPAND_T, 0, s>>>(off, adj, odp, oadj, opos, ow, tsum, twin, wcsr, norm,
+                                            deg, n, lsh_T, sim_csr, status);
+    } else {
+      k_expand<<<egrid, EXPAND_T, 0, s>>>(kind, off, deg, odp, oadj, opos, tcnt, tc16, twin, n,
+                                          lsh_T, sim_csr, status);
+    }
     GS_LAUNCH();
   }
   if (count_ms) {
@@ -869,6 +1117,9 @@ int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* a
   pool.put(odp);
   pool.put(okey);
   pool.put(oval);
+  if (ow) pool.put(ow);
+  if (tsum) pool.put(tsum);
+  if (norm) pool.put(norm);
   return SCAN_OK;
 }
 

@@ -63,6 +63,7 @@ def load():
         "scan_index_build": (i32, [P, i32, P, ctypes.c_size_t, P]),
         "scan_index_build_batch": (i32, [P, i32, i32, P, ctypes.c_size_t, P]),
         "scan_index_build_ex": (i32, [P, i32, P, i32, ctypes.c_size_t, P]),
+        "scan_index_build_weighted": (i32, [P, P, P, ctypes.c_size_t, P]),
         "scan_query": (i32, [P, i32, f64, P, i32, ctypes.c_size_t]),
         "scan_query_batch": (i32, [P, i32, P, P, P, i32, ctypes.c_size_t]),
         "scan_index_export": (i32, [P, P, P, P, P, P, P]),
@@ -232,15 +233,36 @@ class ScanIndex:
 
     @classmethod
     def build(cls, g, kind: int = COSINE, lsh=None, stream=None, device: bool = False,
-              counts: int = None) -> "ScanIndex":
+              counts: int = None, weights=None) -> "ScanIndex":
         """Build from a CSR (graphgen.CSR, or (offsets, adj) numpy/torch).
 
         device=True uploads numpy inputs with torch first; torch CUDA tensors are
         passed as device pointers; numpy arrays are copied in by the library.
-        counts: COUNTS_AUTO (default), COUNTS_SPARSE or COUNTS_DENSE."""
+        counts: COUNTS_AUTO (default), COUNTS_SPARSE or COUNTS_DENSE.
+        weights: float64 per arc, aligned with adj, for the weighted cosine
+        index (Section 3.1); cosine only (SimHash for lsh), sparse counts."""
         lib = load()
         c, keep = _csr_struct(g, device)
         h = ctypes.c_void_p()
+        if weights is not None:
+            if kind != COSINE or counts not in (None, COUNTS_AUTO, COUNTS_SPARSE):
+                raise ScanError(-1, "weighted builds are cosine and sparse")
+            if c.on_device:
+                import torch
+                w = weights if _is_torch(weights) else torch.from_numpy(np.asarray(weights))
+                w = w.to(device="cuda", dtype=torch.float64).contiguous()
+            else:
+                if _is_torch(weights):
+                    weights = weights.cpu().numpy()
+                w = np.ascontiguousarray(weights, dtype=np.float64)
+            if int(w.shape[0]) != c.num_arcs:
+                raise ValueError("one weight per arc is needed")
+            rc = lib.scan_index_build_weighted(ctypes.byref(c), _ptr(w),
+                                               ctypes.byref(lsh) if lsh else None,
+                                               _stream_handle(stream), ctypes.byref(h))
+            del keep, w
+            _check(rc, "scan_index_build_weighted")
+            return cls(h.value)
         rc = lib.scan_index_build_ex(ctypes.byref(c), kind, ctypes.byref(lsh) if lsh else None,
                                      COUNTS_AUTO if counts is None else int(counts),
                                      _stream_handle(stream), ctypes.byref(h))
