@@ -432,7 +432,7 @@ def bench_dense(gs, kind: int, seed: int, stream):
 
 
 def bench_weighted(gs, seed: int, stream, rmat_scale: int = 22, blood_vessel: bool = True):
-    """Weighted cosine index (Section 3.1) on synthetic weights: an
+    """Weighted cosine index (Section 4.1.1) on synthetic weights: an
     Erdos-Renyi graph shaped like the paper's weighted blood vessel graph
     (n = 25,825, average degree 5.4K; the paper's weights are not
     available, so each edge draws U[0.05, 3)), and R-MAT s22 weighted against

@@ -125,7 +125,8 @@ int scan_index_build_ex(const scan_csr* csr, scan_sim_kind kind, const scan_lsh_
                         int counts, uintptr_t stream, scan_index** out);
 
 /* Build the index of a weighted graph with the weighted cosine similarity
- * (Section 3.1): with w(x,x) = 1 and N̄ the closed neighbourhood,
+ * (Section 4.1.1; WeightedCosineSim of Section 2.1.1): with w(x,x) = 1 and N̄
+ * the closed neighbourhood,
  *   sigma(u,v) = sum over x in N̄(u) ∩ N̄(v) of w(u,x) w(v,x)
  *                / ( sqrt(sum over N̄(u) of w(u,x)^2) sqrt(sum over N̄(v) of w(v,x)^2) ),
  * i.e. (2 w(u,v) + sum over common neighbours x of w(u,x) w(v,x)) divided by

@@ -122,7 +122,7 @@ def similarities(g, cnt: np.ndarray, kind: int = COSINE) -> np.ndarray:
 
 
 def weighted_similarities(g, w: np.ndarray) -> np.ndarray:
-    """Weighted cosine similarity of every arc (Section 3.1, w(x, x) = 1)."""
+    """Weighted cosine similarity of every arc (Section 4.1.1, w(x, x) = 1)."""
     off, adj = _csr(g)
     w = np.ascontiguousarray(w, dtype=np.float64)
     assert w.shape[0] == g.arcs
@@ -133,7 +133,7 @@ def weighted_similarities(g, w: np.ndarray) -> np.ndarray:
 
 
 def weighted_vertex_similarities(g, w: np.ndarray, v: int) -> np.ndarray:
-    """Weighted cosine similarities of the arcs of vertex v (Section 3.1)."""
+    """Weighted cosine similarities of the arcs of vertex v (Section 4.1.1)."""
     off, adj = _csr(g)
     w = np.ascontiguousarray(w, dtype=np.float64)
     assert w.shape[0] == g.arcs

@@ -112,7 +112,7 @@ int orc_simhash_sketch(int64_t n, const int64_t* off, const int32_t* adj, const 
   return 0;
 }
 
-// SimHash of the weighted closed neighbourhood (Section 3.1 with w(v,v) = 1;
+// SimHash of the weighted closed neighbourhood (Section 4.1.1 with w(v,v) = 1;
 // the paper's LSH bound covers SimHash on weighted graphs, Section 5):
 // s_j(v) = sum over x in N̄(v) of rho_j(x) w(v,x), bit j = [s_j(v) >= 0].
 // rho_j(x) w(v,x) is +-w exactly; the sum is taken in double precision in the

@@ -283,7 +283,7 @@ int orc_query_definition(int64_t n, const int64_t* off, const int32_t* adj, cons
   return 0;
 }
 
-// Weighted cosine similarity of every arc (Section 3.1, WeightedCosineSim of
+// Weighted cosine similarity of every arc (Section 4.1.1: WeightedCosineSim, Section 2.1.1, of
 // the closed neighbourhoods with w(x, x) = 1 for every vertex x):
 //   sigma(u,v) = sum_{x in N̄(u) ∩ N̄(v)} w(u,x) w(v,x)
 //                / ( sqrt(sum_{x in N̄(u)} w(u,x)^2) * sqrt(sum_{x in N̄(v)} w(v,x)^2) ).
@@ -341,7 +341,7 @@ int orc_weighted_similarities(int64_t n, const int64_t* off, const int32_t* adj,
 
 // Weighted cosine similarities of the arcs of one vertex v (sampled checks on
 // graphs too large for the all-arcs routine): out[j] = sigma(v, adj[off[v]+j])
-// by the same definition (Section 3.1). w(v, .) is spread over a dense
+// by the same definition (Section 4.1.1). w(v, .) is spread over a dense
 // vector; each neighbour u's closed list is walked in id order, so the terms
 // of a numerator are added in the same order as by the two-pointer walk of
 // orc_weighted_similarities and the results are the same doubles.

@@ -282,7 +282,7 @@ __device__ __forceinline__ bool probe(const OutTable& tab, int32_t x, IT j, int6
   return true;
 }
 
-// Weighted cosine (Section 3.1, w(x,x) = 1): a triangle u < v < w adds
+// Weighted cosine (Section 4.1.1, w(x,x) = 1): a triangle u < v < w adds
 // w(u,w) w(v,w) to the numerator of (u,v), w(u,v) w(u,w) to that of (v,w)
 // and w(u,v) w(v,w) to that of (u,w). ow[j] is the weight of out-arc j; the
 // (v,w) sums go to vsum (shared) or tsum at ob + q, the (u,w) sums to tsum
@@ -843,7 +843,7 @@ k_out_weights(const int64_t* __restrict__ off, const int64_t* __restrict__ odp, 
 }
 
 // norm[x] = sqrt(1 + sum of w(x,y)^2 over N(x)): the closed neighbourhood
-// with w(x,x) = 1 (Section 3.1). FP64 instructions are issued for a whole
+// with w(x,x) = 1 (Section 4.1.1). FP64 instructions are issued for a whole
 // warp at a time, so rows of at most 32 entries are summed by one thread each
 // (32 vertices per instruction); longer rows by the whole warp.
 __global__ void k_wnorm(const int64_t* __restrict__ off, const double* __restrict__ wcsr, int64_t n,
@@ -879,7 +879,7 @@ __global__ void k_wnorm(const int64_t* __restrict__ off, const double* __restric
 }
 
 // Weighted cosine of every oriented edge a->b, written to both CSR arcs:
-// (2 w(a,b) + triangle terms) / (norm[a] norm[b]) (Section 3.1); the weights
+// (2 w(a,b) + triangle terms) / (norm[a] norm[b]) (Section 4.1.1); the weights
 // of the two arcs must agree (else DEV_BADWEIGHT).
 __global__ void __launch_bounds__(EXPAND_T)
 k_expand_w(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,

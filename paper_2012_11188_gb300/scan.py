@@ -240,7 +240,7 @@ class ScanIndex:
         passed as device pointers; numpy arrays are copied in by the library.
         counts: COUNTS_AUTO (default), COUNTS_SPARSE or COUNTS_DENSE.
         weights: float64 per arc, aligned with adj, for the weighted cosine
-        index (Section 3.1); cosine only (SimHash for lsh), sparse counts."""
+        index (Section 4.1.1); cosine only (SimHash for lsh), sparse counts."""
         lib = load()
         c, keep = _csr_struct(g, device)
         h = ctypes.c_void_p()

@@ -1,4 +1,4 @@
-"""GPU parity of the weighted cosine index (Section 3.1, w(x, x) = 1) against
+"""GPU parity of the weighted cosine index (Section 4.1.1, w(x, x) = 1) against
 the oracle.
 
 The GPU adds a numerator's triangle terms with atomics, in no fixed order,

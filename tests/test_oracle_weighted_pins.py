@@ -1,4 +1,4 @@
-"""Pins of the oracle's weighted cosine similarity (Section 3.1,
+"""Pins of the oracle's weighted cosine similarity (Section 4.1.1,
 WeightedCosineSim of closed neighbourhoods with w(x, x) = 1).
 
 The oracle walks the two closed lists with two pointers; the pins reach the
