@@ -27,12 +27,6 @@ namespace {
 #ifndef GS_TRI_FAST_ROUNDS
 #define GS_TRI_FAST_ROUNDS 12  // the same for out-lists streamed one at a time
 #endif
-#ifndef GS_WT_SHARED_SUMS
-// weighted mode: 1 = (v,w) and (u,v) sums in shared memory (double atomics
-// there), 0 = every sum a global double reduction (done in L2, off the SM's
-// FP64 pipe, which on this GPU issues two lanes per clock)
-#define GS_WT_SHARED_SUMS 0
-#endif
 #ifndef GS_TRI_LONG_LIST
 #define GS_TRI_LONG_LIST 64  // suffixes at least this long are streamed one at a time
 #endif
@@ -284,31 +278,63 @@ __device__ __forceinline__ bool probe(const OutTable& tab, int32_t x, IT j, int6
 
 // Weighted cosine (Section 4.1.1, w(x,x) = 1): a triangle u < v < w adds
 // w(u,w) w(v,w) to the numerator of (u,v), w(u,v) w(u,w) to that of (v,w)
-// and w(u,v) w(v,w) to that of (u,w). ow[j] is the weight of out-arc j; the
-// (v,w) sums go to vsum (shared) or tsum at ob + q, the (u,w) sums to tsum
-// at j, and on a hit the (u,v) term is added to uv. A miss does no
-// floating-point work.
-template <bool BIG, typename IT>
-__device__ __forceinline__ bool probe_w(const OutTable& tab, int32_t x, IT j, int64_t ob,
-                                        double w_uv, const double* __restrict__ ow,
-                                        double* vsum, double* __restrict__ tsum, double& uv) {
-  const int q = table_lookup<BIG>(tab, x);
-  if (q < 0) return false;
-  const double w_uw = ow[j], w_vw = ow[ob + q];
-  if (!BIG && GS_WT_SHARED_SUMS) atomicAdd(&vsum[q], w_uv * w_uw);
-  else atomicAdd(&tsum[ob + q], w_uv * w_uw);
-  atomicAdd(&tsum[j], w_uv * w_vw);
-  uv += w_uw * w_vw;
-  return true;
+// and w(u,v) w(v,w) to that of (u,w). ow[i] is the weight of out-arc i and
+// tsum[i] its numerator sum. A hit is named by three out-arc slots: j
+// (u->w), vq (v->w) and jo (u->v). FP64 instructions are issued for a whole
+// warp at a time on a pipe of two lanes per clock, so hits are not summed
+// where they are found: each warp appends them to a buffer in shared memory
+// and applies 32 at a time, three products and three global double
+// reductions per hit (executed in L2, off the FP64 pipe).
+constexpr int WT_BUF = 64;  // entries per warp: 32 to apply + up to 31 waiting
+
+struct Weights {
+  const double* ow;  // weight of every out-arc, at its slot
+  double* tsum;      // numerator sums of every out-arc (global)
+  void* buf;         // this warp's hit buffer: IT j[WT_BUF], vq[WT_BUF], jo[WT_BUF]
+};
+
+template <typename IT>
+__device__ __forceinline__ void wt_apply(IT j, IT vq, IT jo, const Weights& wt) {
+  const double w_uw = wt.ow[j], w_vw = wt.ow[vq], w_uv = wt.ow[jo];
+  atomicAdd(&wt.tsum[vq], w_uv * w_uw);
+  atomicAdd(&wt.tsum[j], w_uv * w_vw);
+  atomicAdd(&wt.tsum[jo], w_uw * w_vw);
 }
 
-// Weighted-mode state of a counting kernel (all null when unweighted).
-struct Weights {
-  const double* ow;  // weight of every out-arc, at its position
-  double* vsum;      // (v,w) sums of the current middle vertex (shared)
-  double* tsum;      // numerator sums of every out-arc (global)
-  double* acc;       // per-warp (u,v) sums of the slice's in-neighbours (shared)
-};
+// Warp-wide (all lanes): append this lane's hit, if any; apply the newest 32
+// entries once the buffer holds at least 32.
+template <typename IT>
+__device__ __forceinline__ void wt_push(bool hit, IT j, IT vq, IT jo, int& cnt, const Weights& wt) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const unsigned m = __ballot_sync(FULL, hit);
+  if (!m) return;
+  IT* b = static_cast<IT*>(wt.buf);
+  if (hit) {
+    const int pos = cnt + __popc(m & ((1u << lane) - 1u));
+    b[pos] = j;
+    b[WT_BUF + pos] = vq;
+    b[2 * WT_BUF + pos] = jo;
+  }
+  cnt += __popc(m);
+  if (cnt >= 32) {
+    __syncwarp();
+    const int e = cnt - 32 + lane;
+    wt_apply<IT>(b[e], b[WT_BUF + e], b[2 * WT_BUF + e], wt);
+    cnt -= 32;
+    __syncwarp();
+  }
+}
+
+// Warp-wide: apply what is left in the buffer.
+template <typename IT>
+__device__ __forceinline__ void wt_drain(int cnt, const Weights& wt) {
+  const int lane = threadIdx.x & 31;
+  const IT* b = static_cast<const IT*>(wt.buf);
+  __syncwarp();
+  if (lane < cnt) wt_apply<IT>(b[lane], b[WT_BUF + lane], b[2 * WT_BUF + lane], wt);
+  __syncwarp();
+}
 
 // One warp: triangles u < v < w for the in-neighbours u of v among the CSR
 // positions [p0, min(p0+32, p_end)) of N(v). The in-neighbours are compacted
@@ -320,7 +346,7 @@ struct Weights {
 // ones are concatenated and walked 32 elements per round (R rounds in
 // flight), the owner of an element coming from the suffix starts that fall
 // in its round (ballot / or-reduce / popc). Hits on (u,v) are counted per
-// list.
+// list; weighted hits go to the warp's hit buffer.
 template <bool BIG, typename IT, bool WT>
 __device__ __forceinline__ void process_slice(
     int64_t p0, int64_t p_end, int64_t rb, int32_t v, int32_t dv, int32_t od, int64_t ob,
@@ -377,11 +403,7 @@ __device__ __forceinline__ void process_slice(
     return;
   }
   sm.acc[lane] = 0;
-  double w_uv = 0.0;  // weighted mode: w(u,v) of this lane's in-neighbour
-  if (WT) {
-    if (GS_WT_SHARED_SUMS) wt.acc[lane] = 0.0;
-    if (found) w_uv = wt.ow[jv];
-  }
+  int wcnt = 0;  // weighted mode: entries in this warp's hit buffer
   __syncwarp();
 
   // 1. long suffixes, one at a time
@@ -392,11 +414,8 @@ __device__ __forceinline__ void process_slice(
     lm &= lm - 1;
     const IT ub = __shfl_sync(FULL, cub, i);
     const int32_t len = __shfl_sync(FULL, clen, i);
-    const double wi = WT ? __shfl_sync(FULL, w_uv, i) : 0.0;
     const IT jvi = WT ? __shfl_sync(FULL, jv, i) : (IT)0;  // the arc u->v of list i
     unsigned hits = 0;  // this lane's hits on the list
-    double hsum = 0.0;  // weighted mode: this lane's (u,v) terms
-    bool any_hit = false;
     for (int32_t t0 = 0; t0 < len; t0 += 32 * RF) {
       int32_t xs[RF];
 #pragma unroll
@@ -408,20 +427,15 @@ __device__ __forceinline__ void process_slice(
       for (int rr = 0; rr < RF; ++rr) {
         if (t0 + 32 * rr >= len) break;
         const IT j = ub + (IT)(t0 + 32 * rr + lane);
-        if (WT) any_hit |= probe_w<BIG, IT>(tab, xs[rr], j, ob, wi, wt.ow, wt.vsum, wt.tsum, hsum);
-        else hits += probe<BIG, IT>(tab, xs[rr], j, ob, vcnt, tcnt, tc16) ? 1u : 0u;
+        if (WT) {
+          const int q = table_lookup<BIG>(tab, xs[rr]);
+          wt_push<IT>(q >= 0, j, (IT)(ob + q), jvi, wcnt, wt);
+        } else {
+          hits += probe<BIG, IT>(tab, xs[rr], j, ob, vcnt, tcnt, tc16) ? 1u : 0u;
+        }
       }
     }
-    if (WT) {
-      if (GS_WT_SHARED_SUMS) {
-        if (__any_sync(FULL, any_hit)) {
-          for (int o = 16; o; o >>= 1) hsum += __shfl_xor_sync(FULL, hsum, o);
-          if (lane == 0) wt.acc[i] += hsum;
-        }
-      } else if (any_hit) {
-        atomicAdd(&wt.tsum[jvi], hsum);
-      }
-    } else {
+    if (!WT) {
       hits = __reduce_add_sync(FULL, hits);
       if (lane == 0) sm.acc[i] += hits;
     }
@@ -471,15 +485,10 @@ __device__ __forceinline__ void process_slice(
       for (int rr = 0; rr < R; ++rr) {
         const int own = owns[rr];
         if (WT) {
-          // the owner's w(u,v) and arc u->v are held by lane `own`; its (u,v)
-          // term goes to the owner's sum
-          const double wo = __shfl_sync(FULL, w_uv, own);
+          // the owner's arc u->v is held by lane `own`
           const IT jo = __shfl_sync(FULL, jv, own);
-          double pv = 0.0;
-          if (probe_w<BIG, IT>(tab, xs[rr], js[rr], ob, wo, wt.ow, wt.vsum, wt.tsum, pv)) {
-            if (GS_WT_SHARED_SUMS) atomicAdd(&wt.acc[own], pv);
-            else atomicAdd(&wt.tsum[jo], pv);
-          }
+          const int q = table_lookup<BIG>(tab, xs[rr]);
+          wt_push<IT>(q >= 0, js[rr], (IT)(ob + q), jo, wcnt, wt);
         } else {
           const bool hit = probe<BIG, IT>(tab, xs[rr], js[rr], ob, vcnt, tcnt, tc16);
           const unsigned hm = __ballot_sync(FULL, hit);
@@ -493,10 +502,9 @@ __device__ __forceinline__ void process_slice(
     }
   }
   __syncwarp();
+  if (WT) wt_drain<IT>(wcnt, wt);
   if (found) {
-    if (WT) {
-      if (GS_WT_SHARED_SUMS) atomicAdd(&wt.tsum[jv], wt.acc[lane]);
-    } else {
+    if (!WT) {
       const uint32_t acc = sm.acc[lane];
       if (acc) atomicAdd(&tcnt[jv], acc);
     }
@@ -530,7 +538,7 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
   __shared__ int32_t s_u[TRI_WARPS][32];
   __shared__ int32_t s_p[TRI_WARPS][32];
   __shared__ uint32_t s_acc[TRI_WARPS][32];
-  __shared__ double s_accd[WT ? TRI_WARPS : 1][32];
+  __shared__ IT s_hb[WT ? TRI_WARPS : 1][WT ? 3 * WT_BUF : 1];  // weighted mode: hit buffers
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   // BIG: first the items whose out-list is too long for the shared table
@@ -539,9 +547,8 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
   const int64_t total = BIG ? total_items + (int64_t)*n_deferred : total_items;
   const int hcap = 1 << table_log2(od_cap);
   uint32_t* t0 = reinterpret_cast<uint32_t*>(smem4);
-  uint32_t* vcnt = t0 + 3 * hcap;  // weighted mode: double vsum[od_cap] in its place
-  double* vsum = reinterpret_cast<double*>(vcnt);
-  const Weights wt{ow, WT ? vsum : nullptr, tsum, WT ? s_accd[wid] : nullptr};
+  uint32_t* vcnt = t0 + 3 * hcap;  // (unweighted mode only)
+  const Weights wt{ow, tsum, WT ? (void*)s_hb[wid] : nullptr};
   const SliceSmem sm{s_u[wid], s_p[wid], s_acc[wid]};
   unsigned bad = 0;
 
@@ -573,10 +580,6 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
         __syncthreads();
         continue;
       }
-      if (WT && GS_WT_SHARED_SUMS) {
-        for (int i = threadIdx.x; i < od; i += TRI_THREADS) vsum[i] = 0.0;
-        __syncthreads();
-      }
     }
     const int64_t rb = off[v];
     const int64_t p_begin = chunk * CHUNK;
@@ -593,15 +596,10 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
                                  wt);
     }
     __syncthreads();
-    if (!BIG && !(WT && !GS_WT_SHARED_SUMS))
+    if (!BIG && !WT)
       for (int j = threadIdx.x; j < od; j += TRI_THREADS) {
-        if (WT) {
-          const double c = vsum[j];
-          if (__double_as_longlong(c) != 0) atomicAdd(&tsum[ob + j], c);
-        } else {
-          const uint32_t c = vcnt[j];
-          if (c) atomicAdd(&tcnt[ob + j], c);
-        }
+        const uint32_t c = vcnt[j];
+        if (c) atomicAdd(&tcnt[ob + j], c);
       }
     __syncthreads();
   }
@@ -623,17 +621,14 @@ k_tri_small(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
             double* __restrict__ tsum) {
   __shared__ __align__(16) uint32_t s_tab[SW_WARPS][3 * SW_SLOTS];  // t0 | t1 | p0 p1
   __shared__ uint32_t s_cnt[WT ? 1 : SW_WARPS][SMALL_OD];
-  __shared__ double s_sum[WT && GS_WT_SHARED_SUMS ? SW_WARPS : 1]
-                        [WT && GS_WT_SHARED_SUMS ? SMALL_OD : 1];
-  __shared__ double s_accd[WT ? SW_WARPS : 1][32];
+  __shared__ IT s_hb[WT ? SW_WARPS : 1][WT ? 3 * WT_BUF : 1];  // weighted mode: hit buffers
   __shared__ int32_t s_u[SW_WARPS][32];
   __shared__ int32_t s_p[SW_WARPS][32];
   __shared__ uint32_t s_acc[SW_WARPS][32];
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   uint32_t* vcnt = WT ? nullptr : s_cnt[wid];
-  double* vsum = WT ? s_sum[wid] : nullptr;
-  const Weights wt{ow, vsum, tsum, WT ? s_accd[wid] : nullptr};
+  const Weights wt{ow, tsum, WT ? (void*)s_hb[wid] : nullptr};
   const SliceSmem sm{s_u[wid], s_p[wid], s_acc[wid]};
   unsigned bad = 0;
   for (;;) {
@@ -653,10 +648,6 @@ k_tri_small(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
         tab = table_build(s_tab[wid], SW_SLOTS, vcnt, oadj + ob, okey + odp[vv], deg, od, lane, 32,
                           [] { __syncwarp(); },
                           [](bool b) { __syncwarp(); return __any_sync(0xffffffffu, b) != 0; });
-        if (WT && GS_WT_SHARED_SUMS) {
-          for (int i = lane; i < od; i += 32) vsum[i] = 0.0;
-          __syncwarp();
-        }
       }
       const bool use_table = !tab.bsearch;
       const int64_t rb = off[vv];
@@ -671,15 +662,10 @@ k_tri_small(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
                                       twin_rel, bad, wt);
       }
       __syncwarp();
-      if (use_table && !(WT && !GS_WT_SHARED_SUMS))
+      if (use_table && !WT)
         for (int j = lane; j < od; j += 32) {
-          if (WT) {
-            const double c = vsum[j];
-            if (__double_as_longlong(c) != 0) atomicAdd(&tsum[ob + j], c);
-          } else {
-            const uint32_t c = vcnt[j];
-            if (c) atomicAdd(&tcnt[ob + j], c);
-          }
+          const uint32_t c = vcnt[j];
+          if (c) atomicAdd(&tcnt[ob + j], c);
         }
       __syncwarp();
     }
@@ -954,8 +940,8 @@ int launch_counting(const int64_t* off, const int32_t* adj, const int32_t* deg, 
                     unsigned* status, const double* ow, double* tsum, cudaStream_t s) {
   int od_cap = 16;
   while (od_cap < max_od && od_cap < SMEM_OD_MAX) od_cap <<= 1;
-  // the table (12 bytes per slot, 2 * od_cap slots) and the counters (4 or 8 bytes)
-  const size_t per_od = (WT && GS_WT_SHARED_SUMS) ? 32 : 28;
+  // the table (12 bytes per slot, 2 * od_cap slots) and the counters (4 bytes)
+  const size_t per_od = WT ? 24 : 28;  // weighted mode: no counters
   const size_t smem = per_od * od_cap;
   const size_t smem_max = per_od * SMEM_OD_MAX;
   GS_CUDA(cudaFuncSetAttribute(k_triangles<false, IT, WT>,
