@@ -2,8 +2,8 @@
 
 Each case copies the oracle source, plants one mistake in the copy (a dropped
 term, a wrong comparison, a wrong index, a wrong tie rule), compiles it on the
-CPU and runs the pins of test_oracle_pins.py against it: at least one pin must
-fail. The real oracle is restored afterwards.
+CPU and runs the pins of test_oracle_pins.py, test_oracle_weighted_pins.py and
+test_oracle_lsh_pins.py against it: at least one pin must fail. The real oracle is restored afterwards.
 """
 import ctypes
 import os
@@ -13,6 +13,7 @@ import subprocess
 import pytest
 
 import oracle
+import test_oracle_lsh_pins as lpins
 import test_oracle_pins as pins
 import test_oracle_weighted_pins as wpins
 
@@ -41,6 +42,17 @@ MUTANTS = {
     "weighted closed list without the vertex itself": (
         "    if (!self_done) {\n      ids.push_back((int32_t)x);\n      ws.push_back(1.0);\n    }",
         "    (void)self_done;"),
+    "weighted per-vertex norm without the square": (
+        "s2 += w[i] * w[i];", "s2 += w[i];"),
+    "weighted per-vertex numerator without the x = u term": (
+        "if (in_v[u]) num += 1.0 * wv[u];  // x = u, w(u,u) = 1", "(void)0;"),
+    # mistakes in lsh_oracle.cpp
+    "weighted SimHash ignores the weights": (
+        "lsh", "s[j] += ((bits >> (j % 64)) & 1u) ? wx : -wx;",
+        "s[j] += ((bits >> (j % 64)) & 1u) ? 1.0 : -1.0;"),
+    "weighted SimHash without the vertex itself": (
+        "lsh", "const double wx = i < off[v] ? 1.0 : w[i];", "const double wx = i < off[v] ? 0.0 : w[i];"),
+    "weighted SimHash strict sign": ("lsh", "if (s[j] >= 0.0) out", "if (s[j] > 0.0) out"),
     "neighbour order ascending": (
         "return a.first > b.first;\n                     });\n    for (size_t j",
         "return a.first < b.first;\n                     });\n    for (size_t j"),
@@ -62,17 +74,24 @@ PINS = [
     lambda: wpins.test_weighted_equals_matrix_identity(30, 0.2, 1),
     wpins.test_unit_weights_reduce_to_cosine,
     wpins.test_weighted_triangle_closed_form,
+    lambda: wpins.test_vertex_routine_equals_matrix_identity_and_all_arcs(1),
+    wpins.test_weighted_bipartite_closed_form,
+    lpins.test_weighted_simhash_unit_weights_equal_unweighted,
+    lpins.test_weighted_simhash_brute_force_definition,
+    lpins.test_weighted_simhash_tracks_weighted_cosine,
 ]
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
 def test_pins_catch_mutant(name, tmp_path):
-    old, new = MUTANTS[name]
-    text = open(SRC).read()
+    spec = MUTANTS[name]
+    which, old, new = spec if len(spec) == 3 else ("scan", *spec)
+    target, other = (SRC, LSH) if which == "scan" else (LSH, SRC)
+    text = open(target).read()
     assert text.count(old) == 1, name
+    (tmp_path / os.path.basename(target)).write_text(text.replace(old, new))
+    shutil.copy(other, tmp_path / os.path.basename(other))
     mutated = tmp_path / "scan_oracle.cpp"
-    mutated.write_text(text.replace(old, new))
-    shutil.copy(LSH, tmp_path / "lsh_oracle.cpp")
     so = tmp_path / "libmutant.so"
     subprocess.run(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", str(mutated),
                     str(tmp_path / "lsh_oracle.cpp"), "-o", str(so)], check=True)
@@ -85,6 +104,7 @@ def test_pins_catch_mutant(name, tmp_path):
                 pin()
             except (AssertionError, RuntimeError, ValueError, IndexError):
                 caught.append(pin)
+                break
     finally:
         oracle._lib = saved
     assert caught, f"no pin caught the mutant '{name}'"
