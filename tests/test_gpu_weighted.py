@@ -229,3 +229,37 @@ def test_weighted_argument_errors():
     with pytest.raises(gs.ScanError) as e:
         gs.ScanIndex.build(graphgen.CSR(off, adj), gs.COSINE, weights=w)
     assert e.value.status == -3
+
+
+@pytest.mark.parametrize("name", ["rmat_s22", "blood_vessel_like"])
+def test_weighted_bench_sizes_sampled(name):
+    """The weighted workloads bench.py times (R-MAT s22 and the blood-vessel
+    shape, n = 25,825 with average degree 5.4K; weights U[0.05, 3)), built
+    from device-resident inputs as there. Sampled rows (random vertices and
+    the three of highest degree) are within the tolerance of the oracle's
+    per-vertex routine; their neighbour order is the order of the GPU's own
+    similarities; the core order has its properties at several mu."""
+    from test_gpu_fullsize import check_core_order, device_csr
+    if name == "rmat_s22":
+        g = graphgen.rmat(22, 16, seed=1)
+    else:
+        g = graphgen.sbm(25825, 1, 5400 / 25824, 5400 / 25824, seed=1)
+    w = graphgen.edge_weights(g, 1, "uniform")
+    import torch
+    deg = np.diff(g.off)
+    with gs.ScanIndex.build(device_csr(g), gs.COSINE, weights=torch.from_numpy(w).cuda()) as ix:
+        ex = ix.export()
+    rng = np.random.default_rng(22)
+    nz = np.nonzero(deg)[0]
+    sample = list(rng.choice(nz, 12, replace=False)) + list(np.argsort(deg)[-3:])
+    for v in sample:
+        s = slice(g.off[v], g.off[v + 1])
+        want = oracle.weighted_vertex_similarities(g, w, int(v))
+        got = ex["sim"][s]
+        tol = 2.0 * (deg[v] + deg[g.adj[s]] + 8) * U * want
+        assert np.all(np.abs(got - want) <= tol), v
+        order = np.lexsort((g.adj[s], -got))
+        assert np.array_equal(ex["no_id"][s], g.adj[s][order]), v
+        assert np.array_equal(ex["no_sim"][s], got[order]), v
+    md = int(deg.max())
+    check_core_order(g, ex, [2, 3, 5, 17, 128, md + 1])
