@@ -57,3 +57,27 @@ def test_strerror_and_argument_checks_without_gpu():
 def test_build_script_targets_sm103a():
     from paper_2012_11188_gb300 import _build
     assert "arch=compute_103a,code=sm_103a" in " ".join(_build.NVCC_FLAGS)
+
+
+def test_weighted_argument_checks_without_gpu():
+    """The weighted entry point rejects missing arguments before any device
+    work, and the binding rejects weights of the wrong length or with a
+    similarity or counting mode that weighted builds do not have."""
+    import numpy as np
+
+    import graphgen
+    lib = gs.load()
+    h = ctypes.c_void_p()
+    assert lib.scan_index_build_weighted(None, None, None, 0, ctypes.byref(h)) == -1
+    assert lib.scan_index_build_weighted(None, None, None, 0, None) == -1
+    g = graphgen.from_edges(4, [(0, 1), (1, 2), (2, 3)])
+    c, keep = gs.scan._csr_struct(g, False)
+    # arcs but no weights
+    assert lib.scan_index_build_weighted(ctypes.byref(c), None, None, 0, ctypes.byref(h)) == -1
+    w = np.ones(g.arcs)
+    with pytest.raises(ValueError):
+        gs.ScanIndex.build(g, gs.COSINE, weights=w[:-1])
+    with pytest.raises(gs.ScanError):
+        gs.ScanIndex.build(g, gs.JACCARD, weights=w)
+    with pytest.raises(gs.ScanError):
+        gs.ScanIndex.build(g, gs.COSINE, counts=gs.COUNTS_DENSE, weights=w)
