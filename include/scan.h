@@ -236,6 +236,14 @@ const char* scan_strerror(int status);
  * Also the duration of the dominant (counting) kernel. */
 int scan_last_build_timings(double* ms7);
 
+/* Test hook for the index width of the counting kernels. Graphs with at
+ * least 2^31 arcs are counted with 64-bit element indices and 32-bit (u,w)
+ * counters; smaller ones with 32-bit indices and 16-bit counters. With
+ * on != 0, every later build (process-wide) takes the 64-bit path, so that
+ * path can be checked against the oracle on small graphs; the results are
+ * identical either way. Returns SCAN_OK. */
+int scan_set_wide_index(int on);
+
 /* Number of CUDA kernels this library has launched in this process so far
  * (all threads); a benchmark reads it before and after a timed region. */
 int scan_kernel_launches(uint64_t* count);

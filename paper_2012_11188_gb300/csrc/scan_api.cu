@@ -11,6 +11,9 @@
 namespace gscan {
 
 std::atomic<unsigned long long> g_kernel_launches{0};
+std::atomic<int> g_force_wide{0};  // scan_set_wide_index
+
+bool force_wide_index() { return g_force_wide.load(std::memory_order_relaxed) != 0; }
 
 // ------------------------------------------------------------ allocator hooks
 namespace {
@@ -760,6 +763,11 @@ const char* scan_strerror(int status) {
     case SCAN_EBUSY: return "admission refused";
     default: return "unknown status";
   }
+}
+
+int scan_set_wide_index(int on) {
+  g_force_wide.store(on ? 1 : 0, std::memory_order_relaxed);
+  return SCAN_OK;
 }
 
 int scan_kernel_launches(uint64_t* count) {

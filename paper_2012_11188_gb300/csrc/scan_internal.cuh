@@ -204,6 +204,9 @@ int exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, Pool& 
 // Per-thread record of the last build's phase timings.
 void record_timings(const double* ms7);
 
+// scan_set_wide_index: counting with 64-bit element indices at any size.
+bool force_wide_index();
+
 }  // namespace gscan
 
 struct scan_index {

@@ -994,7 +994,7 @@ int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* a
   const int64_t nbins = (int64_t)maxdeg + 1;
   uint32_t* tcnt = pool.get<uint32_t>(m);
   // 16-bit (u,w) counters, two per word, when positions fit in 32 bits
-  const bool narrow = m < ((int64_t)1 << 31) - 1;
+  const bool narrow = m < ((int64_t)1 << 31) - 1 && !force_wide_index();
   uint32_t* tc16 = narrow ? pool.get<uint32_t>(m / 2 + 1) : nullptr;
   int32_t* twin = pool.get<int32_t>(m);
   int32_t* items = pool.get<int32_t>(n);

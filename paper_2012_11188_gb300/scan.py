@@ -74,6 +74,7 @@ def load():
         "scan_strerror": (ctypes.c_char_p, [i32]),
         "scan_last_build_timings": (i32, [P]),
         "scan_kernel_launches": (i32, [P]),
+        "scan_set_wide_index": (i32, [i32]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -212,6 +213,12 @@ def kernel_launches() -> int:
     c = ctypes.c_uint64()
     _check(load().scan_kernel_launches(ctypes.byref(c)), "scan_kernel_launches")
     return c.value
+
+
+def set_wide_index(on: bool) -> None:
+    """Test hook: count with 64-bit element indices (the path of graphs with
+    at least 2**31 arcs) at every size, process-wide."""
+    _check(load().scan_set_wide_index(1 if on else 0), "scan_set_wide_index")
 
 
 def last_build_timings() -> BuildTimings:

@@ -227,3 +227,40 @@ def test_lsh_threshold_zero_and_huge():
     ox = oracle.LSHIndex(g, oracle.COSINE, 64, T=0, seed=1)
     with build(g, gs.COSINE, lsh=gs.make_lsh(gs.COSINE, 64, 0, seed=1)) as ix:
         assert_index_equal(ix, ox)
+
+
+@pytest.fixture
+def wide_index():
+    """Count with 64-bit element indices, the path of graphs with 2^31 arcs or
+    more, on small graphs (process-wide switch, restored afterwards)."""
+    gs.set_wide_index(True)
+    yield
+    gs.set_wide_index(False)
+
+
+@pytest.mark.parametrize("kind", [gs.COSINE, gs.JACCARD])
+def test_wide_index_path_matches_oracle(wide_index, kind):
+    g = graphgen.rmat(14, 16, seed=3)  # rows for the warp and the CTA kernels
+    ox = oracle.Index(g, kind)
+    with build(g, kind, counts=gs.COUNTS_SPARSE) as ix:
+        assert_index_equal(ix, ox)
+        assert_queries_equal(ix, ox, [2, 5, 16], [0.2, 0.5, 0.8])
+
+
+def test_wide_index_big_out_degree_and_weights(wide_index):
+    # out-degree > 4096 (the global-memory kernel): the closed form of K_{a,b}
+    a, b = 4200, 4300
+    n = a + b
+    off = np.zeros(n + 1, np.int64)
+    off[1:a + 1] = b
+    off[a + 1:] = a
+    off = np.cumsum(off)
+    adj = np.concatenate([np.tile(np.arange(a, n), a), np.tile(np.arange(a), b)]).astype(np.int32)
+    with build(graphgen.CSR(off, adj)) as ix:
+        assert np.all(ix.export()["sim"] == 2.0 / math.sqrt((a + 1) * (b + 1)))
+    # weighted, integer weights: bit exact
+    g = graphgen.sbm(3000, 6, 0.08, 0.004, seed=12)
+    w = graphgen.edge_weights(g, 3, "int")
+    ox = oracle.Index(g, oracle.COSINE, sim=oracle.weighted_similarities(g, w))
+    with build(g, weights=w) as ix:
+        assert_index_equal(ix, ox)
