@@ -33,7 +33,8 @@
  *  - Similarities are IEEE double. Cosine is c / sqrt((d_u+1)(d_v+1)) with
  *    one correctly rounded square root of the exact integer product and one
  *    correctly rounded division; Jaccard is c / (d_u + d_v + 2 - c); c is
- *    |N̄(u) ∩ N̄(v)|. The results are therefore bit-reproducible.
+ *    |N̄(u) ∩ N̄(v)|. The results are therefore bit-reproducible (weighted
+ *    similarities are sums of products: see scan_index_build_weighted).
  */
 #ifndef GB300_SCAN_H
 #define GB300_SCAN_H
