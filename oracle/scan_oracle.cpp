@@ -35,6 +35,11 @@
 //    whose neighbours (any edge) carry >= 2 distinct cluster labels is a hub
 //    (-2), else an outlier (-1) (Section 4.3).
 //  * mu > maxdeg+1 means no cores (Algorithm 3).
+//  * Weighted cosine (Section 4.1.1, WeightedCosineSim of Section 2.1.1):
+//    sum over N̄(u) ∩ N̄(v) of w(u,x) w(v,x), divided by the two norms
+//    sqrt(sum over N̄ of w^2), with w(x,x) = 1; terms added in id order.
+//  * Modularity (Section 7.2), unclustered vertices as singletons.
+// No entry point is unpinned: each has pins in the tests.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
