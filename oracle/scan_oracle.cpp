@@ -193,15 +193,23 @@ int orc_neighbor_order(int64_t n, const int64_t* off, const int32_t* adj, const 
 
 // CO (Algorithm 2, MakeCoreOrder). co_off has maxdeg+1 entries:
 // CO[mu] = co_id[co_off[mu-2] .. co_off[mu-1]), mu = 2..maxdeg+1.
+// The members of CO[mu] are the vertices with d_v + 1 >= mu. They are kept in
+// one ascending-id list that loses the vertices with d_v + 1 < mu as mu grows,
+// so building every CO[mu] reads each member once (sum over mu of |CO[mu]| =
+// the number of arcs) instead of scanning all n vertices for every mu.
 int orc_core_order(int64_t n, const int64_t* off, const double* no_sim, int64_t maxdeg,
                    int64_t* co_off, int32_t* co_id, double* co_thr) {
   std::vector<std::pair<double, int32_t>> row;
+  std::vector<int32_t> members;  // {v : d_v + 1 >= mu}, ascending id
+  for (int64_t v = 0; v < n; ++v) members.push_back((int32_t)v);
   int64_t w = 0;
   co_off[0] = 0;
   for (int64_t mu = 2; mu <= maxdeg + 1; ++mu) {
+    members.erase(std::remove_if(members.begin(), members.end(),
+                                 [&](int32_t v) { return deg_of(off, v) + 1 < mu; }),
+                  members.end());
     row.clear();
-    for (int64_t v = 0; v < n; ++v)
-      if (deg_of(off, v) + 1 >= mu) row.emplace_back(no_sim[off[v] + mu - 2], (int32_t)v);
+    for (int32_t v : members) row.emplace_back(no_sim[off[v] + mu - 2], v);
     std::stable_sort(row.begin(), row.end(),
                      [](const std::pair<double, int32_t>& a, const std::pair<double, int32_t>& b) {
                        return a.first > b.first;

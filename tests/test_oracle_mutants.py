@@ -28,8 +28,8 @@ MUTANTS = {
     "count misses v itself": ("int64_t c = mark[v];  // v itself is in N̄(v)",
                               "int64_t c = 0;"),
     "strict eps in the core test": ("ne += sim[i] >= eps;", "ne += sim[i] > eps;"),
-    "core order membership off by one": ("if (deg_of(off, v) + 1 >= mu) row.emplace_back",
-                                         "if (deg_of(off, v) >= mu) row.emplace_back"),
+    "core order membership off by one": ("[&](int32_t v) { return deg_of(off, v) + 1 < mu; }",
+                                         "[&](int32_t v) { return deg_of(off, v) < mu; }"),
     "border takes the least similar core": (
         "if (core[no_id[i]]) { labels[v] = dsu.find(no_id[i]); break; }",
         "if (core[no_id[i]]) { labels[v] = dsu.find(no_id[i]); }"),
