@@ -221,3 +221,21 @@ def batch_sbm_params(count: int, seed: int = 1, n_lo: int = 100, n_hi: int = 200
         gseed = draw(k, 4 * i + 3) & 0x7FFFFFFFFFFFFFFF
         out.append(SBMParams(n, nb, p_in, p_in / out_ratio, gseed))
     return out
+
+
+def batch_queries(count: int, per_graph: int = 8, seed: int = 1, mu_lo: int = 2, mu_hi: int = 16,
+                  k_lo: int = 2, k_hi: int = 18):
+    """(mu, eps) queries for a batch of graphs: per graph `per_graph` pairs with mu
+    uniform in {mu_lo..mu_hi} and eps = k / 20 for k uniform in {k_lo..k_hi} (the
+    0.05 grid, each value the correctly rounded double of the decimal).
+
+    Returns (mus int32[count, per_graph], epss float64[count, per_graph])."""
+    k = key(seed, 0x7175657279)  # "query"
+    mus = np.empty((count, per_graph), dtype=np.int32)
+    epss = np.empty((count, per_graph), dtype=np.float64)
+    for i in range(count):
+        for j in range(per_graph):
+            c = 2 * (i * per_graph + j)
+            mus[i, j] = mu_lo + draw(k, c) % (mu_hi - mu_lo + 1)
+            epss[i, j] = (k_lo + draw(k, c + 1) % (k_hi - k_lo + 1)) / 20.0
+    return mus, epss
