@@ -185,12 +185,16 @@ int scan_query_batch(scan_index* index, int q, const int* mu, const double* eps,
  *    index returns SCAN_EINVAL;
  *  - labels must be device memory (n int32); host memory returns SCAN_EINVAL;
  *  - the first call on a device looks up the scratch address for that device
- *    (cudaGetSymbolAddress, with the device current); make that first call
- *    before any stream capture;
+ *    (cudaGetSymbolAddress, with the device current) and keeps it for the
+ *    life of the process; make that first call before any stream capture.
+ *    Do not reset the device (cudaDeviceReset) while the library is loaded:
+ *    a new context may place the array elsewhere, and the kept address would
+ *    then be stale;
+ *  - each call copies mu and eps from host memory to the scratch and
+ *    synchronises `stream` before it returns;
  *  - every call on a device shares the same scratch, and the scratch keeps
  *    the last call's contents: calls whose work overlaps on the GPU race and
- *    give wrong labels, so issue them one after another (this function
- *    synchronises `stream` before it returns).
+ *    give wrong labels, so issue them one after another.
  * Other arguments and results are those of scan_query. */
 #define SCAN_NOALLOC_MAX_VERTICES 4194304
 int scan_query_noalloc(scan_index* index, int mu, double eps, int32_t* labels, int flags,

@@ -67,13 +67,27 @@ int scan_serve_reset_stats(scan_server* srv);
 /* Open-loop replay of a request trace, driven by a C++ thread so the arrival
  * times do not depend on the caller's language runtime. Query i is submitted
  * at q_arrival_s[i] seconds after the start, build j at b_arrival_s[j].
- * latency_ms[i] receives the query's submit-to-completion latency; labels
- * (nq * n int32, host or device, may be NULL to discard) receives its labels.
- * Returns after every request completed or after timeout_ms. */
+ *
+ * Label rows (each n int32): query i writes row i % R of `labels`, host or
+ * device. A row is handed to a new query only after the query that used it
+ * before has completed, so every query in flight owns its row; when the row
+ * of the next arrival is still busy, the replay waits for it, and that wait
+ * counts in the query's latency.
+ *   labels != NULL, label_rows = R > 0: a caller-owned ring of R rows;
+ *   labels != NULL, label_rows = 0: nq rows, one per query;
+ *   labels == NULL: the library allocates a device ring of label_rows rows
+ *     (0 = max(2 * max_batch, 128), capped at nq) for the call and releases
+ *     it before returning.
+ * latency_ms[i] receives the time from query i's scheduled arrival to its
+ * completion (-1 if it did not complete). Returns after every request
+ * completed or after timeout_ms (SCAN_ETIMEOUT). label_rows < 0: SCAN_EINVAL.
+ * (No counterpart in the paper: a serving harness for the query path of
+ * Algorithms 3-5.) */
 int scan_serve_replay(scan_server* srv, scan_index* index, int64_t nq, const double* q_arrival_s,
                       const int* q_mu, const double* q_eps, int flags, int32_t* labels,
-                      double* latency_ms, int64_t nb, const double* b_arrival_s,
-                      const scan_csr* b_graphs, scan_sim_kind b_kind, int timeout_ms);
+                      int64_t label_rows, double* latency_ms, int64_t nb,
+                      const double* b_arrival_s, const scan_csr* b_graphs, scan_sim_kind b_kind,
+                      int timeout_ms);
 
 /* Stop the threads, finish queued work and release the server. */
 void scan_serve_destroy(scan_server* srv);

@@ -10,7 +10,8 @@
 //  - the build worker admits build requests in arrival order when their
 //    footprint fits the memory budget and the device's free memory, and builds
 //    them on its own stream, overlapping with the query batches.
-// Latencies are measured on the host from submit to completion.
+// Latencies are measured on the host from submit to completion (the trace
+// replay measures from each query's scheduled arrival instead).
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -387,28 +388,41 @@ int scan_serve_reset_stats(scan_server* s) {
 
 int scan_serve_replay(scan_server* s, scan_index* index, int64_t nq, const double* q_arrival_s,
                       const int* q_mu, const double* q_eps, int flags, int32_t* labels,
-                      double* latency_ms, int64_t nb, const double* b_arrival_s,
-                      const scan_csr* b_graphs, scan_sim_kind b_kind, int timeout_ms) {
-  if (!s || !index || nq < 0 || nb < 0) return SCAN_EINVAL;
+                      int64_t label_rows, double* latency_ms, int64_t nb,
+                      const double* b_arrival_s, const scan_csr* b_graphs, scan_sim_kind b_kind,
+                      int timeout_ms) {
+  if (!s || !index || nq < 0 || nb < 0 || label_rows < 0) return SCAN_EINVAL;
   if (nq > 0 && (!q_arrival_s || !q_mu || !q_eps)) return SCAN_EINVAL;
   if (nb > 0 && (!b_arrival_s || !b_graphs)) return SCAN_EINVAL;
   const int64_t n = index->d.n;
-  // per-query label destinations: caller's rows, or one device scratch row set
-  gscan::Pool pool(0);
-  int32_t* scratch = nullptr;
-  if (!labels && n > 0) {
-    scratch = pool.get<int32_t>((size_t)n);
-    if (!scratch) return SCAN_ENOMEM;
+  const int max_batch = s->p.max_batch > 0 ? s->p.max_batch : 64;
+  // Label rows: query i writes row i % rows. A row is handed to a new query
+  // only after the query that used it before has completed, so every query in
+  // flight has a row of its own.
+  int64_t rows = label_rows;
+  if (labels && rows == 0) rows = std::max<int64_t>(nq, 1);  // one row per query
+  if (!labels && rows == 0) rows = std::max<int64_t>(2 * (int64_t)max_batch, 128);
+  gscan::Pool pool(s->qs);
+  int32_t* ring = labels;
+  if (!labels && n > 0 && nq > 0) {
+    rows = std::min(rows, nq);
+    ring = pool.get<int32_t>((size_t)rows * (size_t)n);
+    if (!ring) return SCAN_ENOMEM;
+    GS_CUDA(cudaStreamSynchronize(s->qs));
   }
   std::vector<uint64_t> qt((size_t)nq, 0), bt((size_t)nb, 0);
-  std::vector<int> qrc((size_t)nq, SCAN_OK);
+  std::vector<Request*> qr((size_t)nq, nullptr);
+  std::vector<Clock::time_point> q_sched((size_t)nq);
   int rc_all = SCAN_OK;
   const auto t0 = Clock::now();
+  const auto deadline = t0 + std::chrono::milliseconds(timeout_ms < 0 ? 1LL << 40 : timeout_ms);
+  auto at_time = [&](double sec) {
+    return t0 + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(sec));
+  };
   int64_t i = 0, j = 0;
   while (i < nq || j < nb) {
     const bool take_q = j >= nb || (i < nq && q_arrival_s[i] <= b_arrival_s[j]);
-    const double at = take_q ? q_arrival_s[i] : b_arrival_s[j];
-    const auto when = t0 + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(at));
+    const auto when = at_time(take_q ? q_arrival_s[i] : b_arrival_s[j]);
     // sleep until shortly before the arrival, then spin
     auto now = Clock::now();
     if (when - now > std::chrono::microseconds(300))
@@ -417,9 +431,25 @@ int scan_serve_replay(scan_server* s, scan_index* index, int64_t nq, const doubl
     }
     int rc;
     if (take_q) {
-      int32_t* dst = labels ? labels + (size_t)i * n : scratch;
-      rc = scan_serve_submit_query(s, index, q_mu[i], q_eps[i], dst, flags, &qt[i]);
-      if (rc != SCAN_OK) qrc[i] = rc;
+      q_sched[i] = when;
+      const int64_t slot = i % rows;
+      if (i >= rows && qr[i - rows]) {
+        // the row's previous query must have completed (bounded by the deadline)
+        Request* prev = qr[i - rows];
+        std::unique_lock<std::mutex> lk(s->mu);
+        if (!s->cv_done.wait_until(lk, deadline, [&] { return prev->done; })) {
+          lk.unlock();
+          if (rc_all == SCAN_OK) rc_all = SCAN_ETIMEOUT;
+          break;
+        }
+      }
+      rc = scan_serve_submit_query(s, index, q_mu[i], q_eps[i], ring ? ring + (size_t)slot * n : nullptr,
+                                   flags, &qt[i]);
+      if (rc == SCAN_OK) {
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->reqs.find(qt[i]);
+        qr[i] = it != s->reqs.end() ? it->second : nullptr;
+      }
       ++i;
     } else {
       rc = scan_serve_submit_build(s, &b_graphs[j], b_kind, nullptr, &bt[j]);
@@ -427,25 +457,19 @@ int scan_serve_replay(scan_server* s, scan_index* index, int64_t nq, const doubl
     }
     if (rc != SCAN_OK && rc_all == SCAN_OK) rc_all = rc;
   }
-  // collect
-  const auto deadline = t0 + std::chrono::milliseconds(timeout_ms < 0 ? 1LL << 40 : timeout_ms);
+  // collect: latency runs from the scheduled arrival to the completion, so a
+  // submission delayed by a busy row still counts its wait
   for (int64_t k = 0; k < nq; ++k) {
+    if (latency_ms) latency_ms[k] = -1;
     if (!qt[k]) continue;
-    Request* r = nullptr;
-    {
-      std::lock_guard<std::mutex> lk(s->mu);
-      auto it = s->reqs.find(qt[k]);
-      if (it != s->reqs.end()) r = it->second;
-    }
-    const int left = (int)std::max<int64_t>(
-        0, std::chrono::duration_cast<std::chrono::milliseconds>(deadline - Clock::now()).count());
+    Request* r = qr[k];
     double lat = -1;
     {
       std::unique_lock<std::mutex> lk(s->mu);
-      if (r && s->cv_done.wait_for(lk, std::chrono::milliseconds(left), [&] { return r->done; }))
-        lat = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+      if (r && s->cv_done.wait_until(lk, deadline, [&] { return r->done; }))
+        lat = std::chrono::duration<double, std::milli>(r->t_done - q_sched[k]).count();
     }
-    const int rc = scan_serve_wait(s, qt[k], 0, nullptr);
+    const int rc = lat >= 0 ? scan_serve_wait(s, qt[k], 0, nullptr) : SCAN_ETIMEOUT;
     if (latency_ms) latency_ms[k] = lat;
     if (rc != SCAN_OK && rc_all == SCAN_OK) rc_all = rc;
   }
@@ -456,7 +480,20 @@ int scan_serve_replay(scan_server* s, scan_index* index, int64_t nq, const doubl
     const int rc = scan_serve_wait(s, bt[k], left, nullptr);
     if (rc != SCAN_OK && rc_all == SCAN_OK) rc_all = rc;
   }
-  cudaDeviceSynchronize();
+  if (rc_all == SCAN_ETIMEOUT && ring != labels) {
+    // queries still queued may write the internal ring: wait (bounded) for
+    // them; if some are still pending, leave the ring allocated
+    const auto grace = Clock::now() + std::chrono::seconds(60);
+    bool all_done = true;
+    for (int64_t k = 0; k < nq && all_done; ++k) {
+      if (!qt[k] || !qr[k]) continue;
+      std::unique_lock<std::mutex> lk(s->mu);
+      if (s->reqs.count(qt[k]) && !s->cv_done.wait_until(lk, grace, [&] { return qr[k]->done; }))
+        all_done = false;
+    }
+    if (!all_done) pool.detach();
+  }
+  cudaStreamSynchronize(s->qs);
   return rc_all;
 }
 

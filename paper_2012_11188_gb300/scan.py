@@ -378,7 +378,7 @@ def _load_serve():
         "scan_serve_wait": (i32, [P, u64, i32, P]),
         "scan_serve_stats": (i32, [P, P, P, P, P]),
         "scan_serve_reset_stats": (i32, [P]),
-        "scan_serve_replay": (i32, [P, P, i64, P, P, P, i32, P, P, i64, P, P, i32, i32]),
+        "scan_serve_replay": (i32, [P, P, i64, P, P, P, i32, P, i64, P, i64, P, P, i32, i32]),
         "scan_serve_destroy": (None, [P]),
     }
     for name, (res, args) in sigs.items():
@@ -436,9 +436,15 @@ class Server:
         _check(_load_serve().scan_serve_reset_stats(self._h), "scan_serve_reset_stats")
 
     def replay(self, index: "ScanIndex", arrivals, mus, epss, hubs: bool = False, labels=None,
-               build_arrivals=None, build_graphs=None, build_kind: int = COSINE,
-               timeout_ms: int = 600000):
-        """Open-loop trace replay driven by a C++ thread; returns per-query latencies (ms)."""
+               label_rows: int = 0, build_arrivals=None, build_graphs=None,
+               build_kind: int = COSINE, timeout_ms: int = 600000):
+        """Open-loop trace replay driven by a C++ thread; returns per-query
+        latencies (ms, scheduled arrival to completion).
+
+        labels: None (a device ring of `label_rows` rows owned by the library
+        for the call; 0 = its default), or a host/device buffer of rows of n
+        int32 of which query i writes row i % label_rows (label_rows = 0: one
+        row per query). Each query in flight has its own row."""
         arrivals = np.ascontiguousarray(arrivals, dtype=np.float64)
         mus = np.ascontiguousarray(mus, dtype=np.int32)
         epss = np.ascontiguousarray(epss, dtype=np.float64)
@@ -457,7 +463,7 @@ class Server:
             bstructs = (scan_csr * nb)(*structs)
         rc = _load_serve().scan_serve_replay(
             self._h, index._h, nq, arrivals.ctypes.data, mus.ctypes.data, epss.ctypes.data,
-            Q_HUBS if hubs else 0, _ptr(labels), lat.ctypes.data, nb,
+            Q_HUBS if hubs else 0, _ptr(labels), int(label_rows), lat.ctypes.data, nb,
             barr.ctypes.data if barr is not None else None, bstructs, build_kind, timeout_ms)
         _check(rc, "scan_serve_replay")
         return lat

@@ -76,6 +76,45 @@ def test_replay_trace_matches_direct_queries(index):
     assert np.array_equal(lab, direct)
 
 
+@pytest.mark.parametrize("where", ["device", "host"])
+def test_replay_ring_of_label_rows(index, where):
+    """A ring of 16 label rows under a trace of 400 queries arriving faster
+    than one batch completes: rows are reused only after their previous query
+    completed, so the last 16 queries' rows hold exactly their own labels."""
+    import torch
+    g, ix = index
+    mus, epss = random_queries(400, 5)
+    rng = np.random.default_rng(6)
+    arrivals = np.cumsum(rng.exponential(1.0 / 50000.0, mus.shape[0]))
+    R = 16
+    if where == "device":
+        ring = torch.full((R, g.n), -7, dtype=torch.int32, device="cuda")
+    else:
+        ring = torch.full((R, g.n), -7, dtype=torch.int32).pin_memory()
+    with gs.Server(max_batch=8) as srv:
+        lat = srv.replay(ix, arrivals, mus, epss, hubs=True, labels=ring, label_rows=R)
+    assert np.all(lat > 0)
+    direct = ix.query_batch(mus[-R:], epss[-R:], hubs=True)
+    got = ring.cpu().numpy()
+    for q in range(mus.shape[0] - R, mus.shape[0]):
+        assert np.array_equal(got[q % R], direct[q - (mus.shape[0] - R)]), q
+
+
+def test_replay_library_ring(index):
+    """labels=None: the library's own device ring; every query completes."""
+    g, ix = index
+    mus, epss = random_queries(500, 7)
+    arrivals = np.arange(mus.shape[0]) * 2e-5
+    with gs.Server(max_batch=64) as srv:
+        lat = srv.replay(ix, arrivals, mus, epss, label_rows=4)
+        lat2 = srv.replay(ix, arrivals, mus, epss)
+    assert np.all(lat > 0) and np.all(lat2 > 0)
+    with gs.Server(max_batch=4) as srv:
+        with pytest.raises(gs.ScanError) as e:
+            srv.replay(ix, arrivals[:3], mus[:3], epss[:3], label_rows=-1)
+        assert e.value.status == -1
+
+
 def test_admission_and_arguments(index):
     g, ix = index
     with gs.Server(memory_budget=1 << 20, max_batch=8) as srv:
