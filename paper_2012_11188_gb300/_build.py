@@ -64,7 +64,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
             objs = list(ex.map(compile_one, sources()))
         fd, tmp = tempfile.mkstemp(suffix=".so", dir=LIBDIR)
         os.close(fd)
-        cmd = [exe, "-shared", *ARCH, "-o", tmp, *objs, "-lcublas", "-lpthread"]
+        cmd = [exe, "-shared", *ARCH, "-o", tmp, *objs, "-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")

@@ -168,7 +168,7 @@ k_co_scatter(const int32_t* __restrict__ perm, const int32_t* __restrict__ deg,
 
 inline unsigned grid1(int64_t work, int per = 256) {
   int64_t g = (work + per - 1) / per;
-  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 16));
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, sm_count() * 16));
 }
 
 }  // namespace
@@ -227,7 +227,7 @@ int build_core_order_multi(int64_t N, int64_t A, const int64_t* off, const int32
   k_rtiles<<<grid1(Tub), 256, 0, s>>>(perm, deg, m, qtb, rt);
   GS_LAUNCH();
   GS_TRY(exclusive_scan_i64(rt, rt_prefix, Tub, pool, s));
-  k_co_scatter<<<152 * 16, 256, 0, s>>>(perm, deg, off, no_key, m, qtb, co_off_all, rt_prefix, Tub,
+  k_co_scatter<<<sm_count() * 16, 256, 0, s>>>(perm, deg, off, no_key, m, qtb, co_off_all, rt_prefix, Tub,
                                         co_key, co_id);
   GS_LAUNCH();
   GS_TRY(segmented_sort_desc(co_key, co_id, co_off_all, S, A, max_n, pool, s));

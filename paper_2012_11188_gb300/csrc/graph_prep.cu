@@ -237,7 +237,7 @@ k_orient_long(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
   }
 }
 
-inline unsigned grid_for(int64_t work, int per_block, int cap = 152 * 32) {
+inline unsigned grid_for(int64_t work, int per_block, int cap = sm_count() * 32) {
   int64_t g = (work + per_block - 1) / per_block;
   if (g < 1) g = 1;
   if (g > cap) g = cap;
@@ -280,7 +280,7 @@ int launch_orient(const int64_t* off, const int32_t* adj, const int32_t* deg, in
     k_orient_inplace<<<grid_for(n, 8), 256, 0, s>>>(off, adj, deg, n, od, oadj, opos, max_od_dev,
                                                     sum_od_dev, long_rows, n_long);
     GS_LAUNCH();
-    k_orient_long<<<(unsigned)std::min<int64_t>(max_long, 152 * 2), LONG_T, 0, s>>>(
+    k_orient_long<<<(unsigned)std::min<int64_t>(max_long, sm_count() * 2), LONG_T, 0, s>>>(
         off, adj, deg, long_rows, n_long, od, oadj, opos, max_od_dev, sum_od_dev);
     GS_LAUNCH();
   }

@@ -217,13 +217,13 @@ int lsh_select(const int64_t* off, const int32_t* adj, const int32_t* deg, int64
   int64_t* pre = pool.get<int64_t>(n + 1);
   if (!flag || !pre) return SCAN_ENOMEM;
   if (n > 0) {
-    k_select_flags<<<(unsigned)std::min<int64_t>((n + 7) / 8, 152 * 32), 256, 0, s>>>(off, adj, deg,
+    k_select_flags<<<(unsigned)std::min<int64_t>((n + 7) / 8, sm_count() * 32), 256, 0, s>>>(off, adj, deg,
                                                                                      n, T, flag);
     GS_LAUNCH();
   }
   GS_TRY(exclusive_scan_i32_to_i64(flag, pre, n, pool, s));
   if (n > 0) {
-    k_select_rows<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 32), 256, 0, s>>>(flag, pre,
+    k_select_rows<<<(unsigned)std::min<int64_t>((n + 255) / 256, sm_count() * 32), 256, 0, s>>>(flag, pre,
                                                                                        n, row);
     GS_LAUNCH();
   }
@@ -242,10 +242,10 @@ int lsh_apply(const scan_lsh_params& p, int kind, const int64_t* off, const int3
   if (nH <= 0) return SCAN_OK;
   int32_t* hlist = pool.get<int32_t>(nH);
   if (!hlist) return SCAN_ENOMEM;
-  k_hlist<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 32), 256, 0, s>>>(row, n, hlist);
+  k_hlist<<<(unsigned)std::min<int64_t>((n + 255) / 256, sm_count() * 32), 256, 0, s>>>(row, n, hlist);
   GS_LAUNCH();
-  const unsigned gh = (unsigned)std::min<int64_t>(nH, 152 * 16);
-  const unsigned gw = (unsigned)std::min<int64_t>((nH + 7) / 8, 152 * 32);
+  const unsigned gh = (unsigned)std::min<int64_t>(nH, sm_count() * 16);
+  const unsigned gw = (unsigned)std::min<int64_t>((nH + 7) / 8, sm_count() * 32);
   if (kind == SCAN_COSINE) {
     const int k = p.simhash_bits, W = k / 64;
     const uint64_t key = mix64(p.seed ^ 0x53494D48ULL);  // "SIMH"

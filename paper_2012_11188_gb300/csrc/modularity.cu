@@ -91,7 +91,7 @@ __global__ void k_deg_sq(const int32_t* __restrict__ deg, int64_t n,
 unsigned grid_of(int64_t work, int per_block) {
   int64_t g = (work + per_block - 1) / per_block;
   if (g < 1) g = 1;
-  if (g > 152 * 16) g = 152 * 16;
+  if (g > sm_count() * 16) g = sm_count() * 16;
   return (unsigned)g;
 }
 

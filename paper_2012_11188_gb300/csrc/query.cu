@@ -243,8 +243,8 @@ int launch_query_batch(const IndexData& ix, int Q, const int* mu, const double* 
   // nc holds 2Q+1 words: Q core counts, then their Q+1 prefix sums
   QArgs a{ix.off, ix.deg, ix.adj, ix.no_id, ix.no_sim, ix.co_off, ix.co_id, ix.co_thr,
           n, ix.maxdeg, mu, eps, nc, nc + Q, Q, parent, labels, lab_ptrs, status_dev};
-  const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8 / std::min(Q, 8) + 1));
-  const unsigned gw = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 7) / 8, 152 * 16 / std::min(Q, 16) + 1));
+  const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, sm_count() * 8 / std::min(Q, 8) + 1));
+  const unsigned gw = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 7) / 8, sm_count() * 16 / std::min(Q, 16) + 1));
   if (lab_ptrs) {
     k_init_labels<<<dim3(gx, Q), 256, 0, s>>>(a);
     GS_LAUNCH();
@@ -256,13 +256,13 @@ int launch_query_batch(const IndexData& ix, int Q, const int* mu, const double* 
   k_core_prefix<<<1, 32, 0, s>>>(a);
   GS_LAUNCH();
   // the (query, core) items of the whole batch share one grid
-  k_mark_cores<<<152 * 8, 256, 0, s>>>(a);
+  k_mark_cores<<<sm_count() * 8, 256, 0, s>>>(a);
   GS_LAUNCH();
-  k_union<<<152 * 16, 256, 0, s>>>(a);
+  k_union<<<sm_count() * 16, 256, 0, s>>>(a);
   GS_LAUNCH();
-  k_core_labels<<<152 * 8, 256, 0, s>>>(a);
+  k_core_labels<<<sm_count() * 8, 256, 0, s>>>(a);
   GS_LAUNCH();
-  k_borders<<<152 * 16, 256, 0, s>>>(a);
+  k_borders<<<sm_count() * 16, 256, 0, s>>>(a);
   GS_LAUNCH();
   if (flags & SCAN_Q_HUBS) {
     k_hubs<<<dim3(gw, Q), 256, 0, s>>>(a);

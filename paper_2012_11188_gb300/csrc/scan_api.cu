@@ -15,6 +15,21 @@ std::atomic<int> g_force_wide{0};  // scan_set_wide_index
 
 bool force_wide_index() { return g_force_wide.load(std::memory_order_relaxed) != 0; }
 
+int sm_count() {
+  static std::atomic<int> cached[64];  // zero until looked up
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+  int c = cached[dev].load(std::memory_order_relaxed);
+  if (c == 0) {
+    if (cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || c < 1) {
+      cudaGetLastError();
+      return 1;
+    }
+    cached[dev].store(c, std::memory_order_relaxed);
+  }
+  return c;
+}
+
 // ------------------------------------------------------------ allocator hooks
 namespace {
 scan_alloc_fn g_alloc = nullptr;
@@ -476,9 +491,9 @@ int build_batch(const scan_csr* graphs, int G, int kind, const scan_lsh_params* 
     }
     if (c.num_arcs > 0) GS_CUDA(cudaMemcpyAsync(u.adj + ab[g], c.adj, c.num_arcs * 4, k, s));
   }
-  const unsigned gN = (unsigned)std::max<int64_t>(1, std::min<int64_t>((N + 256) / 256, 152 * 16));
-  const unsigned gA = (unsigned)std::max<int64_t>(1, std::min<int64_t>((A + 255) / 256, 152 * 16));
-  const unsigned gG = (unsigned)std::max<int64_t>(1, std::min<int64_t>((G + 255) / 256, 152 * 16));
+  const unsigned gN = (unsigned)std::max<int64_t>(1, std::min<int64_t>((N + 256) / 256, sm_count() * 16));
+  const unsigned gA = (unsigned)std::max<int64_t>(1, std::min<int64_t>((A + 255) / 256, sm_count() * 16));
+  const unsigned gG = (unsigned)std::max<int64_t>(1, std::min<int64_t>((G + 255) / 256, sm_count() * 16));
   k_check_ends<<<gG, 256, 0, s>>>(raw, d_vb, d_ab, G, u.status);
   GS_LAUNCH();
   k_pack_offsets<<<gN, 256, 0, s>>>(raw, d_vb, d_ab, G, N, u.off, u.status);
@@ -533,7 +548,7 @@ int build_batch(const scan_csr* graphs, int G, int kind, const scan_lsh_params* 
   }
   k_rebase_offsets<<<gN, 256, 0, s>>>(u.off, meta2 + (G + 1), meta2, d_ab, G, N + G, off_rel);
   GS_LAUNCH();
-  const unsigned gS = (unsigned)std::max<int64_t>(1, std::min<int64_t>((S + G + 255) / 256, 152 * 16));
+  const unsigned gS = (unsigned)std::max<int64_t>(1, std::min<int64_t>((S + G + 255) / 256, sm_count() * 16));
   k_rebase_offsets<<<gS, 256, 0, s>>>(co_off_all, meta2 + 3 * (G + 1), meta2 + 2 * (G + 1), d_ab, G,
                                       S + G, co_off_rel);
   GS_LAUNCH();
@@ -726,7 +741,7 @@ int scan_index_export(scan_index* index, double* sim, int32_t* no_id, double* no
     const bool dev = is_device_ptr(sim);
     double* tmp = dev ? sim : pool.get<double>(A);
     if (!tmp) return SCAN_ENOMEM;
-    k_no_to_csr<<<(unsigned)std::min<int64_t>((ix.n + 7) / 8, 152 * 32), 256, 0, s>>>(
+    k_no_to_csr<<<(unsigned)std::min<int64_t>((ix.n + 7) / 8, sm_count() * 32), 256, 0, s>>>(
         ix.off, ix.adj, ix.no_id, ix.no_sim, ix.n, tmp);
     GS_LAUNCH();
     if (!dev) GS_CUDA(cudaMemcpyAsync(sim, tmp, A * 8, cudaMemcpyDeviceToHost, s));

@@ -152,9 +152,11 @@ int build_core_order_multi(int64_t N, int64_t A, const int64_t* off, const int32
                            int32_t* co_id, uint64_t* co_key, Pool& pool, cudaStream_t s);
 
 // Dense path (dense.cu): closed counts of every arc as ((A+I)^2)[u][v] by one
-// bf16 GEMM with fp32 accumulation, then the similarities; for graphs of at
-// most DENSE_MAX_N vertices.
+// hand-written tcgen05 bf16 GEMM with fp32 accumulation, the similarities
+// written by its epilogue; for graphs of at most DENSE_MAX_N vertices, and
+// chosen automatically from DENSE_MIN_N vertices on.
 constexpr int64_t DENSE_MAX_N = 65536;
+constexpr int64_t DENSE_MIN_N = 4096;
 bool dense_counts_pay(int64_t n, int64_t arcs);
 int dense_counts_and_sims(int kind, const int64_t* off, const int32_t* adj, const int32_t* deg,
                           int64_t n, int lsh_T, double* sim_csr, unsigned* status, Pool& pool,
@@ -200,6 +202,10 @@ int lsh_select(const int64_t* off, const int32_t* adj, const int32_t* deg, int64
 int exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, Pool& pool, cudaStream_t s);
 int exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, Pool& pool,
                               cudaStream_t s);
+
+// Streaming multiprocessors of the current device (looked up once per
+// device); grids are sized in multiples of it.
+int sm_count();
 
 // Per-thread record of the last build's phase timings.
 void record_timings(const double* ms7);

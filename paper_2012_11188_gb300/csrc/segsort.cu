@@ -560,7 +560,7 @@ int segmented_sort_desc(uint64_t* key, int32_t* val, const int64_t* seg_off, int
   unsigned long long* counts = pool.get<unsigned long long>(2 * (NCLASS + 1));
   if (!counts) return SCAN_ENOMEM;
   GS_CUDA(cudaMemsetAsync(counts, 0, 2 * (NCLASS + 1) * sizeof(unsigned long long), s));
-  const unsigned g_seg = (unsigned)std::min<int64_t>((nseg + 255) / 256, 152 * 16);
+  const unsigned g_seg = (unsigned)std::min<int64_t>((nseg + 255) / 256, sm_count() * 16);
   k_classify_count<<<g_seg, 256, 0, s>>>(seg_off, nseg, counts);
   GS_LAUNCH();
   unsigned long long hc[NCLASS + 1];
@@ -579,7 +579,7 @@ int segmented_sort_desc(uint64_t* key, int32_t* val, const int64_t* seg_off, int
   // per-class counts on the device for the grid-stride kernels: counts[c]
   auto grid_of = [](int64_t units, int per) {
     int64_t g = (units + per - 1) / per;
-    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 32));
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, sm_count() * 32));
   };
   if (hc[0]) {
     k_sort_warp<<<grid_of((int64_t)hc[0], 8), 256, 0, s>>>(key, val, seg_off, list + base[0],

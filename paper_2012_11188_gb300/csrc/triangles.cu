@@ -946,9 +946,8 @@ int launch_counting(const int64_t* off, const int32_t* adj, const int32_t* deg, 
   const size_t smem_max = per_od * SMEM_OD_MAX;
   GS_CUDA(cudaFuncSetAttribute(k_triangles<false, IT, WT>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
-  int dev = 0, sms = 152, per_sm = 1;
-  GS_CUDA(cudaGetDevice(&dev));
-  GS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int sms = sm_count();
+  int per_sm = 1;
   GS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_triangles<false, IT, WT>,
                                                         TRI_THREADS, smem));
   if (per_sm < 1) per_sm = 1;
@@ -1019,7 +1018,7 @@ int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* a
     GS_LAUNCH();
   }
   if (n > 0) {
-    const unsigned g = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 64);
+    const unsigned g = (unsigned)std::min<int64_t>((n + 255) / 256, sm_count() * 64);
     k_item_counts<<<g, 256, 0, s>>>(odeg, deg, n, items);
     GS_LAUNCH();
     k_item_hist<<<g, 256, 0, s>>>(items, deg, n, maxdeg, hist);
@@ -1037,7 +1036,7 @@ int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* a
   GS_CUDA(cudaEventRecord(e0, s));
   const int64_t ch = (int64_t)EXPAND_T * EXPAND_ITEMS;
   const unsigned egrid =
-      (unsigned)std::max<int64_t>(1, std::min<int64_t>((edges + ch - 1) / ch, 152 * 32));
+      (unsigned)std::max<int64_t>(1, std::min<int64_t>((edges + ch - 1) / ch, sm_count() * 32));
   if (n > 0 && m > 0) {
     // out-lists in ascending degree order, with their rank keys kept for the
     // searches of the counting kernels
@@ -1072,7 +1071,7 @@ int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* a
   GS_CUDA(cudaEventRecord(e1, s));
   if (n > 0 && m > 0) {
     if (weighted) {
-      k_wnorm<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, s>>>(off, wcsr, n,
+      k_wnorm<<<(unsigned)std::min<int64_t>((n + 255) / 256, sm_count() * 16), 256, 0, s>>>(off, wcsr, n,
                                                                                       norm);
       GS_LAUNCH();
       k_expand_w<<<egrid, EXPAND_T, 0, s>>>(off, adj, odp, oadj, opos, ow, tsum, twin, wcsr, norm,

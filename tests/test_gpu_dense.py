@@ -54,6 +54,41 @@ def test_dense_equals_sparse_and_auto():
         assert export_equal(auto, sp)
 
 
+@pytest.mark.parametrize("kind", [gs.COSINE, gs.JACCARD])
+def test_dense_many_tiles_per_cta(kind):
+    """n = 5000 pads to 5120: 420 upper tiles of 128 x 256 over at most one
+    CTA per SM, so every CTA runs several tiles and both TMEM accumulators;
+    rows of both a dense and a sparse block, and isolated vertices."""
+    rng = np.random.default_rng(11)
+    n = 5000
+    a = graphgen.sbm(3000, 1, 0.3, 0.3, seed=5)
+    src = np.repeat(np.arange(3000), np.diff(a.off))
+    edges = np.stack([src, a.adj], 1)
+    edges = edges[edges[:, 0] < edges[:, 1]]
+    extra = rng.integers(0, 4900, (40000, 2))  # vertices 4900.. stay isolated
+    g = graphgen.from_edges(n, np.concatenate([edges, extra]))
+    ox = oracle.Index(g, kind)
+    with gs.ScanIndex.build(g, kind, counts=gs.COUNTS_DENSE) as ix:
+        assert_index_equal(ix, ox)
+        assert np.array_equal(ix.query(4, 0.4, hubs=True), ox.query(4, 0.4, hubs=True))
+
+
+def test_auto_takes_the_sparse_path_below_the_size_threshold():
+    """A small dense graph (n < 4096) goes through the sparse enumeration
+    under the automatic choice: its launches are those of the sparse path."""
+    g = graphgen.sbm(1500, 1, 0.3, 0.3, seed=2)
+
+    def launches(mode):
+        k0 = gs.kernel_launches()
+        with gs.ScanIndex.build(g, gs.COSINE, counts=mode):
+            pass
+        return gs.kernel_launches() - k0
+
+    sparse, dense, auto = (launches(m) for m in (gs.COUNTS_SPARSE, gs.COUNTS_DENSE,
+                                                 gs.COUNTS_AUTO))
+    assert auto == sparse and dense != sparse
+
+
 def test_dense_with_lsh_equals_sparse_with_lsh():
     g = graphgen.sbm(3000, 4, 0.2, 0.02, seed=8)  # degrees ~ 180: most edges approximated
     lsh = gs.make_lsh(gs.COSINE, 64, 128, seed=3)
