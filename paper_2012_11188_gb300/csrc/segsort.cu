@@ -10,9 +10,11 @@
 //
 // Segments are bucketed by length: <= 32 (one warp, one element per lane),
 // <= 256 (one warp, bitonic network on up to 8 elements per lane in
-// registers), longer (256-element tiles sorted the same way, then merge-path
-// passes that double the run length, ping-ponging between the data and a
-// scratch buffer; a pass costs about one read and one write of the data).
+// registers), <= 4096 (one CTA: 8-element register sorts, then merge-path
+// levels in shared memory), longer (8192-element tiles sorted by one CTA the
+// same way, then merge-path passes over global memory that double the run
+// length, ping-ponging between the data and a scratch buffer; a pass costs
+// about one read and one write of the data).
 #include "scan_internal.cuh"
 
 namespace gscan {
@@ -20,7 +22,7 @@ namespace gscan {
 namespace {
 
 constexpr int WTILE = 256;   // one warp sorts up to this many elements in registers
-constexpr int TILE = 4096;   // one CTA sorts a tile of this many (16 warp sorts + 4 merges)
+constexpr int TILE = 8192;   // tiles of long segments (one CTA of 1024 threads each)
 constexpr int NCLASS = 5;    // <=32, <=256, <=1024, <=4096, >4096
 
 struct KV {
@@ -36,7 +38,7 @@ __device__ __forceinline__ bool before(uint64_t ka, int32_t va, uint64_t kb, int
 constexpr int32_t SENT_V = 0x7fffffff;  // sorts after every real element (key 0, val max)
 
 __device__ __forceinline__ int seg_class(int64_t len) {
-  return len <= 32 ? 0 : len <= WTILE ? 1 : len <= 1024 ? 2 : len <= TILE ? 3 : 4;
+  return len <= 32 ? 0 : len <= WTILE ? 1 : len <= 1024 ? 2 : len <= 4096 ? 3 : 4;
 }
 
 // Count segments per class and number of tiles of long segments.
@@ -234,35 +236,79 @@ __device__ __forceinline__ int smem_merge_path_p(const uint64_t* k, const int32_
   return lo;
 }
 
-#ifndef GS_SORT_TILE_RI
-#define GS_SORT_TILE_RI 8  // elements per lane of the warp sorts inside a 4096-element tile
-#endif
+// Compare-and-swap of a register pair: afterwards (ka, va) comes first.
+__device__ __forceinline__ void cas(uint64_t& ka, int32_t& va, uint64_t& kb, int32_t& vb) {
+  if (before(kb, vb, ka, va)) {
+    const uint64_t tk = ka; ka = kb; kb = tk;
+    const int32_t tv = va; va = vb; vb = tv;
+  }
+}
 
-// One CTA of TT threads sorts a tile of up to TT*RI elements at the next
-// power of two SE >= max(len, 32*RI): SE/(32*RI) warps sort 32*RI elements
-// each in registers (RI per lane), then merge-path levels in shared memory
-// double the runs up to SE, each thread writing RI outputs. Tiles are whole
-// segments (TILED = false) or TILE-element pieces of longer segments
-// (TILED = true, TT*RI = TILE).
-// A tiled segment that takes an odd number of merge passes has its tiles
-// written to the scratch buffer (tk, tv), so that its last pass ends in
-// (key, val).
-template <int TT, int RI, bool TILED>
-__global__ void __launch_bounds__(TT, RI >= 16 ? 2 : 1024 / TT)
+// Sorts 8 register elements with Batcher's odd-even merge network (19
+// compare-and-swaps).
+__device__ __forceinline__ void sort8(uint64_t (&K)[8], int32_t (&V)[8]) {
+#define GS_CAS(i, j) cas(K[i], V[i], K[j], V[j])
+  GS_CAS(0, 1); GS_CAS(2, 3); GS_CAS(4, 5); GS_CAS(6, 7);
+  GS_CAS(0, 2); GS_CAS(1, 3); GS_CAS(4, 6); GS_CAS(5, 7);
+  GS_CAS(1, 2); GS_CAS(5, 6);
+  GS_CAS(0, 4); GS_CAS(1, 5); GS_CAS(2, 6); GS_CAS(3, 7);
+  GS_CAS(2, 4); GS_CAS(3, 5);
+  GS_CAS(1, 2); GS_CAS(3, 4); GS_CAS(5, 6);
+#undef GS_CAS
+}
+
+// Merges RI outputs starting at diagonal d of the runs A = src[a0, a0+la)
+// and B = src[b0, b0+lb) (padded shared layout), writing dst slots o..o+RI-1.
+// The current head of each run is kept in registers, so each output costs
+// one dependent shared load.
+template <int R, int RI>
+__device__ __forceinline__ void merge_out(const uint64_t* ks, const int32_t* vs, int a0, int la,
+                                          int b0, int lb, int d, uint64_t* kd, int32_t* vd, int o) {
+  int ia = smem_merge_path_p<R>(ks, vs, a0, la, b0, lb, d);
+  int ib = d - ia;
+  uint64_t ka = 0, kb = 0;
+  int32_t va = SENT_V, vb = SENT_V;
+  if (ia < la) { const int p = pslot<R>(a0 + ia); ka = ks[p]; va = vs[p]; }
+  if (ib < lb) { const int p = pslot<R>(b0 + ib); kb = ks[p]; vb = vs[p]; }
+#pragma unroll
+  for (int q = 0; q < RI; ++q) {
+    const bool take_a = ib >= lb || (ia < la && !before(kb, vb, ka, va));
+    const int po = pslot<R>(o + q);
+    if (take_a) {
+      kd[po] = ka; vd[po] = va;
+      if (++ia < la) { const int p = pslot<R>(a0 + ia); ka = ks[p]; va = vs[p]; }
+    } else {
+      kd[po] = kb; vd[po] = vb;
+      if (++ib < lb) { const int p = pslot<R>(b0 + ib); kb = ks[p]; vb = vs[p]; }
+    }
+  }
+}
+
+// One CTA of TT threads sorts a tile of up to TT*8 elements at the next power
+// of two SE >= max(len, 8): the tile is loaded into shared memory with
+// coalesced reads (padded with sentinels that sort last), each thread sorts
+// 8 consecutive elements in registers, then merge-path levels double the
+// sorted runs up to SE, each thread writing 8 outputs per level. Tiles are
+// whole segments (TILED = false) or TILE-element pieces of longer segments
+// (TILED = true, TT*8 = TILE). A tiled segment that takes an odd number of
+// merge passes has its tiles written to the scratch buffer (tk, tv), so
+// that its last pass ends in (key, val).
+template <int TT, bool TILED>
+__global__ void __launch_bounds__(TT, TT >= 1024 ? 1 : 1024 / TT)
 k_sort_tile(uint64_t* __restrict__ key, int32_t* __restrict__ val,
             const int64_t* __restrict__ seg_off, const int64_t* __restrict__ list,
             const unsigned long long* __restrict__ count_ptr,
             const int64_t* __restrict__ tile_prefix, int64_t nlong, uint64_t* __restrict__ tk,
             int32_t* __restrict__ tv) {
+  constexpr int RI = 8;
   constexpr int CAP = TT * RI;
-  constexpr int RUN = 32 * RI;          // elements sorted by one warp in registers
   constexpr int PCAP = CAP + CAP / RI;  // padded slots per buffer
   extern __shared__ uint64_t tsm[];
   uint64_t* k0 = tsm;
   uint64_t* k1 = tsm + PCAP;
   int32_t* v0 = (int32_t*)(tsm + 2 * PCAP);
   int32_t* v1 = v0 + PCAP;
-  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  const int t = threadIdx.x;
   const int64_t cnt = (int64_t)*count_ptr;
   for (int64_t u = blockIdx.x; u < cnt; u += gridDim.x) {
     int64_t b, len;
@@ -283,53 +329,38 @@ k_sort_tile(uint64_t* __restrict__ key, int32_t* __restrict__ val,
       len = min((int64_t)CAP, seg_off[sg + 1] - b);
       if (passes_for(seg_off[sg + 1] - seg_off[sg]) & 1) { ok = tk; ov = tv; }
     }
-    int se = RUN;
+    int se = RI;
     while (se < len) se <<= 1;
-    // 1. the first se/RUN warps sort RUN elements each in registers
-    if (wid * RUN < se) {
+    // 1. coalesced load, sentinels past the end
+    for (int i = t; i < se; i += TT) {
+      const int p = pslot<RI>(i);
+      if (i < len) { k0[p] = key[b + i]; v0[p] = val[b + i]; }
+      else { k0[p] = 0; v0[p] = SENT_V; }
+    }
+    __syncthreads();
+    // 2. each thread sorts its 8 consecutive elements in registers
+    if (RI * t < se) {
       uint64_t K[RI];
       int32_t V[RI];
 #pragma unroll
-      for (int r = 0; r < RI; ++r) {
-        const int64_t i = (int64_t)wid * RUN + RI * lane + r;
-        if (i < len) { K[r] = key[b + i]; V[r] = val[b + i]; }
-        else { K[r] = 0; V[r] = SENT_V; }
-      }
-      warp_sort_reg<RI>(K, V, lane);
+      for (int r = 0; r < RI; ++r) { const int p = pslot<RI>(RI * t + r); K[r] = k0[p]; V[r] = v0[p]; }
+      sort8(K, V);
 #pragma unroll
-      for (int r = 0; r < RI; ++r) {
-        const int i = pslot<RI>(wid * RUN + RI * lane + r);
-        k0[i] = K[r];
-        v0[i] = V[r];
-      }
+      for (int r = 0; r < RI; ++r) { const int p = pslot<RI>(RI * t + r); k0[p] = K[r]; v0[p] = V[r]; }
     }
     __syncthreads();
-    // 2. merge levels in shared memory: runs of w -> 2w, ping-pong k0/v0 <-> k1/v1
+    // 3. merge levels in shared memory: runs of w -> 2w, ping-pong k0/v0 <-> k1/v1
     uint64_t *ks = k0, *kd = k1;
     int32_t *vs = v0, *vd = v1;
-    for (int w = RUN; w < se; w <<= 1) {
+    for (int w = RI; w < se; w <<= 1) {
       const int o = RI * t;  // first output of this thread
       if (o < se) {
         const int a0 = (o / (2 * w)) * (2 * w);
-        const int b0 = a0 + w;
-        const int d = o - a0;
-        int ia = smem_merge_path_p<RI>(ks, vs, a0, w, b0, w, d);
-        int ib = d - ia;
-#pragma unroll
-        for (int q = 0; q < RI; ++q) {
-          bool take_a;
-          const int pa = pslot<RI>(a0 + ia), pb = pslot<RI>(b0 + ib);
-          if (ia >= w) take_a = false;
-          else if (ib >= w) take_a = true;
-          else take_a = !before(ks[pb], vs[pb], ks[pa], vs[pa]);
-          const int po = pslot<RI>(o + q);
-          if (take_a) { kd[po] = ks[pa]; vd[po] = vs[pa]; ++ia; }
-          else { kd[po] = ks[pb]; vd[po] = vs[pb]; ++ib; }
-        }
+        merge_out<RI, RI>(ks, vs, a0, w, a0 + w, w, o - a0, kd, vd, o);
       }
       __syncthreads();
-      uint64_t* tk = ks; ks = kd; kd = tk;
-      int32_t* tv = vs; vs = vd; vd = tv;
+      uint64_t* tk2 = ks; ks = kd; kd = tk2;
+      int32_t* tv2 = vs; vs = vd; vd = tv2;
     }
     for (int i = t; i < len; i += TT) {
       const int pi = pslot<RI>(i);
@@ -340,14 +371,15 @@ k_sort_tile(uint64_t* __restrict__ key, int32_t* __restrict__ val,
   }
 }
 
-template <int TT, int RI>
+template <int TT>
 constexpr size_t tile_smem_bytes() {
-  return (size_t)(TT * RI + TT) * (2 * sizeof(uint64_t) + 2 * sizeof(int32_t));
+  return (size_t)(TT * 8 + TT) * (2 * sizeof(uint64_t) + 2 * sizeof(int32_t));
 }
 
-// the 4096-element tile kernel: 512 threads x 8, or 256 threads x 16
-constexpr int T4K_RI = GS_SORT_TILE_RI;
-constexpr int T4K_T = TILE / T4K_RI;
+// whole segments of 1025..4096 elements: 512 threads x 8; tiles of long
+// segments: TILE elements, 1024 threads x 8 (one CTA per SM)
+constexpr int T4K_T = 512;
+constexpr int TLONG_T = TILE / 8;
 
 // Tiles per long segment (prefix computed by the caller).
 __global__ void k_long_tiles(const int64_t* __restrict__ seg_off, const int64_t* __restrict__ list,
@@ -526,14 +558,23 @@ k_merge_pass(uint64_t* __restrict__ key, int32_t* __restrict__ val, uint64_t* __
           else lo2 = i + 1;
         }
         int ia = lo2, ib = d - lo2;
-        for (int q = 0; q < MERGE_ITEMS && d + q < nout; ++q) {
-          bool take_a;
-          if (ia >= na) take_a = false;
-          else if (ib >= nb) take_a = true;
-          else take_a = !before(shk[na + ib], shv[na + ib], shk[ia], shv[ia]);
+        // run heads in registers: one dependent shared load per output
+        uint64_t ka = 0, kb = 0;
+        int32_t va = SENT_V, vb = SENT_V;
+        if (ia < na) { ka = shk[ia]; va = shv[ia]; }
+        if (ib < nb) { kb = shk[na + ib]; vb = shv[na + ib]; }
+#pragma unroll
+        for (int q = 0; q < MERGE_ITEMS; ++q) {
+          if (d + q >= nout) break;
+          const bool take_a = ib >= nb || (ia < na && !before(kb, vb, ka, va));
           const int pq = po(d + q);
-          if (take_a) { ok_[pq] = shk[ia]; ov_[pq] = shv[ia]; ++ia; }
-          else { ok_[pq] = shk[na + ib]; ov_[pq] = shv[na + ib]; ++ib; }
+          if (take_a) {
+            ok_[pq] = ka; ov_[pq] = va;
+            if (++ia < na) { ka = shk[ia]; va = shv[ia]; }
+          } else {
+            ok_[pq] = kb; ov_[pq] = vb;
+            if (++ib < nb) { kb = shk[na + ib]; vb = shv[na + ib]; }
+          }
         }
       }
       __syncthreads();
@@ -593,20 +634,19 @@ int segmented_sort_desc(uint64_t* key, int32_t* val, const int64_t* seg_off, int
   }
   GS_CUDA(cudaFuncSetAttribute(k_merge_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)MERGE_SMEM));
-  GS_CUDA(cudaFuncSetAttribute(k_sort_tile<T4K_T, T4K_RI, true>,
+  GS_CUDA(cudaFuncSetAttribute(k_sort_tile<TLONG_T, true>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)tile_smem_bytes<T4K_T, T4K_RI>()));
-  GS_CUDA(cudaFuncSetAttribute(k_sort_tile<T4K_T, T4K_RI, false>,
+                               (int)tile_smem_bytes<TLONG_T>()));
+  GS_CUDA(cudaFuncSetAttribute(k_sort_tile<T4K_T, false>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)tile_smem_bytes<T4K_T, T4K_RI>()));
+                               (int)tile_smem_bytes<T4K_T>()));
   if (hc[2]) {
-    k_sort_tile<128, 8, false><<<grid_of((int64_t)hc[2], 1), 128, tile_smem_bytes<128, 8>(), s>>>(
+    k_sort_tile<128, false><<<grid_of((int64_t)hc[2], 1), 128, tile_smem_bytes<128>(), s>>>(
         key, val, seg_off, list + base[2], counts + 2, nullptr, 0, nullptr, nullptr);
     GS_LAUNCH();
   }
   if (hc[3]) {
-    k_sort_tile<T4K_T, T4K_RI, false><<<grid_of((int64_t)hc[3], 1), T4K_T,
-                                        tile_smem_bytes<T4K_T, T4K_RI>(), s>>>(
+    k_sort_tile<T4K_T, false><<<grid_of((int64_t)hc[3], 1), T4K_T, tile_smem_bytes<T4K_T>(), s>>>(
         key, val, seg_off, list + base[3], counts + 3, nullptr, 0, nullptr, nullptr);
     GS_LAUNCH();
   }
@@ -627,9 +667,8 @@ int segmented_sort_desc(uint64_t* key, int32_t* val, const int64_t* seg_off, int
     GS_TRY(exclusive_scan_i64(chunks, chunk_prefix, nlong, pool, s));
     const int64_t ntiles = (int64_t)hc[NCLASS];
     // tile sort (count = ntiles, read from counts[NCLASS])
-    k_sort_tile<T4K_T, T4K_RI, true><<<grid_of(ntiles, 1), T4K_T, tile_smem_bytes<T4K_T, T4K_RI>(),
-                                       s>>>(key, val, seg_off, llist, counts + NCLASS, tile_prefix,
-                                            nlong, tk, tv);
+    k_sort_tile<TLONG_T, true><<<grid_of(ntiles, 1), TLONG_T, tile_smem_bytes<TLONG_T>(), s>>>(
+        key, val, seg_off, llist, counts + NCLASS, tile_prefix, nlong, tk, tv);
     GS_LAUNCH();
     const int64_t total_chunks_ub = (total + MERGE_CHUNK - 1) / MERGE_CHUNK + nlong;
     MergeDesc* desc = pool.get<MergeDesc>((size_t)total_chunks_ub);
