@@ -205,7 +205,10 @@ def algorithmic_bytes(off_t, adj_t):
 def bench_batched(gs, kind: int, count: int, seed: int, stream):
     """2048 independent SBM graphs (n log-uniform in [100, 20000], 2-64 blocks,
     p_in uniform in [.02, .2], p_out = p_in/50) indexed by one batched build from
-    device-resident CSRs, then 8 (mu, eps) queries per graph."""
+    device-resident CSRs, then 8 (mu, eps) queries per graph. The counting
+    strategy per degree bucket is first autotuned on the batch (coordinate
+    search, the winner recorded for the batch's degree class); the batched
+    build is timed with the tuned choice and with the fixed defaults."""
     import numpy as np
     import torch
     import graphgen
@@ -219,34 +222,54 @@ def bench_batched(gs, kind: int, count: int, seed: int, stream):
         for h in gs.ScanIndex.build_batch(dev, kind, stream=stream):
             h.free()
     torch.cuda.synchronize()
-    ts = []
-    for _ in range(3):
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        hs = gs.ScanIndex.build_batch(dev, kind, stream=stream)
-        b.record(stream)
-        b.synchronize()
-        ts.append(a.elapsed_time(b))
-        if len(ts) < 3:
-            for h in hs:
-                h.free()
-    rng = np.random.default_rng(seed)
+    gs.tuning_clear()
+    t0 = time.perf_counter()
+    tune = gs.autotune_batch(dev, kind, reps=1, stream=stream)
+    tune_s = time.perf_counter() - t0
+
+    def timed(reps=3):
+        ts, cnt = [], []
+        hs = None
+        for _ in range(reps):
+            if hs is not None:
+                for h in hs:
+                    h.free()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            hs = gs.ScanIndex.build_batch(dev, kind, stream=stream)
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+            cnt.append(gs.last_build_timings().count_ms)
+        return hs, statistics.median(ts), statistics.median(cnt)
+
+    defaults = dict(gs.DEFAULT_COUNT_CONFIG)
+    gs.set_count_config(defaults)
+    hs, ms_default, cnt_default = timed()
+    gs.set_count_config(None)
+    for h in hs:
+        h.free()
+    hs, ms, cnt_ms = timed()  # the tuning table's choice for this batch
+    mus, epss = graphgen.batch_queries(count, 8, seed=seed)
     t0 = time.perf_counter()
     nq = 0
-    for h in hs:
-        mus = rng.integers(2, 17, 8).astype(np.int32)
-        epss = np.round(rng.integers(2, 19, 8) * 0.05, 2)
+    for i, h in enumerate(hs):
         lab = torch.empty((8, max(h.n, 1)), dtype=torch.int32, device="cuda")
-        h.query_batch(mus, epss, out=lab, stream=stream)
+        h.query_batch(mus[i], epss[i], out=lab, stream=stream)
         nq += 8
     torch.cuda.synchronize()
     q_s = time.perf_counter() - t0
     for h in hs:
         h.free()
-    ms = statistics.median(ts)
     return {"workload": f"{count} SBM graphs, sum n = {sum(g.n for g in gl)}, sum m = {edges}",
             "build_ms": round(ms, 2), "edges_per_s": edges / (ms / 1000.0),
+            "count_ms": round(cnt_ms, 2),
+            "fixed_defaults": {"config": defaults, "build_ms": round(ms_default, 2),
+                               "count_ms": round(cnt_default, 2)},
+            "autotune": {"chosen": tune["best"], "build_ms_tuned": round(tune["best_ms"], 2),
+                         "build_ms_defaults": round(tune["default_ms"], 2),
+                         "search_s": round(tune_s, 1)},
             "queries": nq, "query_s": round(q_s, 3), "generation_s": round(gen_s, 1)}
 
 

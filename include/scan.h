@@ -253,6 +253,79 @@ int scan_set_wide_index(int on);
  * (all threads); a benchmark reads it before and after a timed region. */
 int scan_kernel_launches(uint64_t* count);
 
+/* ---- Counting strategy per degree bucket, and its autotuner ----
+ * No counterpart in the paper, which runs one merge-based intersection on a
+ * multicore host (Section 6.1). Here the closed counts of every edge
+ * (Section 3.1) come either from one tcgen05 matrix product for a dense
+ * graph ((A+I)^2, Section 4.1.1) or from oriented triangle enumeration with
+ * a hash table of the middle vertex's out-list, and how each graph and each
+ * vertex is handled depends on its degree bucket:
+ *   dense_div, dense_min_n  a graph of at least dense_min_n vertices with
+ *              dense_div * arcs >= n^2 takes the dense path under the
+ *              automatic choice (dense_div = 0: never; 0..1024,
+ *              dense_min_n 2..65536);
+ *   warp_deg   rows of at most this many positions whose out-list has at
+ *              most 256 entries are handled by one warp with its own table;
+ *              the others by a CTA sharing one table (32..4096);
+ *   cta_chunk  CSR positions of a row per CTA work item (256..65536, a
+ *              multiple of 32);
+ *   long_list  suffixes of an out-list at least this long are streamed one
+ *              at a time by a whole warp, shorter ones are concatenated
+ *              (1..2^20);
+ *   rounds     32-element rounds of loads in flight for the concatenated
+ *              suffixes (4 or 8).
+ * Every configuration gives bit-identical results; only the speed differs.
+ * A build uses, in this order: the configuration set by
+ * scan_set_count_config, the tuning table's entry for its class (the bit
+ * length of the vertex count of its largest graph and of its average
+ * degree, both known before any device work), or the defaults
+ * {512, 4096, 64, 4, 16, 4096}. In a batched build the members that the
+ * dense rule selects are built one by one on the dense path, the others
+ * together. */
+typedef struct scan_count_config {
+  int warp_deg;
+  int cta_chunk;
+  int long_list;
+  int rounds;
+  int dense_div;
+  int dense_min_n;
+} scan_count_config;
+
+/* Set (cfg) or clear (NULL) a process-wide configuration for every later
+ * build; SCAN_EINVAL if a field is out of range. */
+int scan_set_count_config(const scan_count_config* cfg);
+
+/* Autotuner of the batched build: builds the `count` graphs with
+ * scan_index_build_batch repeatedly (each configuration `reps` times, the
+ * fastest counted), timing the whole build with CUDA events on `stream`,
+ * and searches the configurations one parameter at a time (dense_div in
+ * {0, 8, 16, 32, 64}, dense_min_n in {2048, 4096, 8192}, warp_deg in
+ * {128, 256, 512, 1024, 2048}, cta_chunk in {1024, 2048, 4096, 8192},
+ * long_list in {32, 64, 128, 256}, rounds in {4, 8}), keeping each change
+ * that is faster. The winner is stored in the in-process tuning table under
+ * the class of the batch, so later builds of that class use it. *best
+ * receives it, *best_ms its build time, *default_ms that of the defaults
+ * (any of the three may be NULL). Builds run on the calling thread; the
+ * graphs follow the rules of scan_index_build_batch. */
+int scan_autotune_batch(const scan_csr* graphs, int count, scan_sim_kind kind, int reps,
+                        uintptr_t stream, scan_count_config* best, double* best_ms,
+                        double* default_ms);
+
+/* The configuration a build would use (see above): a single graph has
+ * max_n = total_n = its vertex count; SCAN_EINVAL if total_n < max_n or a
+ * size is negative. */
+int scan_count_config_for(int64_t max_n, int64_t total_n, int64_t num_arcs,
+                          scan_count_config* cfg);
+
+/* Persist the tuning table as text (one line per class: vertex-count bits,
+ * average-degree bits, warp_deg, cta_chunk, long_list, rounds, dense_div,
+ * dense_min_n), load such a file (entries are added or replaced; a
+ * malformed file changes nothing and returns SCAN_EINVAL), or empty the
+ * table. */
+int scan_tuning_save(const char* path);
+int scan_tuning_load(const char* path);
+int scan_tuning_clear(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -451,12 +451,13 @@ std::vector<uint32_t> upper_tiles(int64_t np) {
 
 }  // namespace
 
-bool dense_counts_pay(int64_t n, int64_t arcs) {
+bool dense_counts_pay(int64_t n, int64_t arcs, const CountCfg& cfg) {
   // the product costs ~n^3 flops (half of the tiles); the sparse enumeration
   // ~ n (d/2)^2 probes at about 1000 flop-times each: dense wins from an
-  // average degree of about n/16 on, for graphs large enough that a GEMM
-  // beats the enumeration's launch and table costs
-  return n >= DENSE_MIN_N && n <= DENSE_MAX_N && 16 * arcs >= n * n;
+  // average degree of about n/16 on (dense_div = 16), for graphs large
+  // enough that a GEMM beats the enumeration's launch and table costs
+  return cfg.dense_div > 0 && n >= cfg.dense_min_n && n <= DENSE_MAX_N &&
+         (int64_t)cfg.dense_div * arcs >= n * n;
 }
 
 int dense_counts_and_sims(int kind, const int64_t* off, const int32_t* adj, const int32_t* deg,

@@ -1,7 +1,9 @@
 // C ABI of libscan.so: index lifecycle, build orchestration, queries, export.
 // Declarations and argument conventions: include/scan.h.
 #include <cmath>
+#include <cstdio>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <vector>
@@ -14,6 +16,36 @@ std::atomic<unsigned long long> g_kernel_launches{0};
 std::atomic<int> g_force_wide{0};  // scan_set_wide_index
 
 bool force_wide_index() { return g_force_wide.load(std::memory_order_relaxed) != 0; }
+
+// ------------------------------------------------------------ counting configuration
+// Class of a build: (bit length of the vertex count of its largest graph,
+// bit length of its average degree), both known before any device work. The
+// tuning table maps a class to the configuration the autotuner found fastest
+// for it.
+namespace {
+int bit_length(int64_t x) {
+  int b = 0;
+  while (x > 0) { ++b; x >>= 1; }
+  return b;
+}
+std::pair<int, int> degree_class(int64_t n_max, int64_t n_total, int64_t arcs) {
+  return {bit_length(n_max), bit_length(n_total > 0 ? arcs / n_total : 0)};
+}
+std::mutex g_tune_mu;
+std::map<std::pair<int, int>, CountCfg> g_tune_table;
+bool g_cfg_global_set = false;
+CountCfg g_cfg_global;
+thread_local bool t_cfg_set = false;  // the autotuner's override on its own thread
+thread_local CountCfg t_cfg;
+}  // namespace
+
+CountCfg count_config_for(int64_t n_max, int64_t n_total, int64_t arcs) {
+  if (t_cfg_set) return t_cfg;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (g_cfg_global_set) return g_cfg_global;
+  auto it = g_tune_table.find(degree_class(n_max, n_total, arcs));
+  return it != g_tune_table.end() ? it->second : CountCfg{};
+}
 
 int sm_count() {
   static std::atomic<int> cached[64];  // zero until looked up
@@ -159,7 +191,8 @@ int validate_lsh(const scan_lsh_params* p, int kind) {
 // ix holds n, arcs, off (absolute, int64), adj and allocated deg, no_id,
 // no_sim and an 8-word status block; on return ix->maxdeg is set.
 int run_pipeline(IndexData* ix, int kind, const scan_lsh_params* lsh, Pool& pool, cudaStream_t s,
-                 Events& ev, float* count_ms, int counts_mode, const double* wcsr = nullptr) {
+                 Events& ev, float* count_ms, int counts_mode, const CountCfg& cfg,
+                 const double* wcsr = nullptr) {
   const int64_t n = ix->n, arcs = ix->arcs;
   const bool use_lsh = lsh && lsh->enabled;
   unsigned* scalars = ix->status;  // [0] status, [1] maxdeg, [2] max out-degree
@@ -171,7 +204,7 @@ int run_pipeline(IndexData* ix, int kind, const scan_lsh_params* lsh, Pool& pool
   ix->maxdeg = (int32_t)hs[1];
   // weighted similarities take the sparse enumeration only
   const bool dense = arcs > 0 && !wcsr && (counts_mode == SCAN_COUNTS_DENSE ||
-                                  (counts_mode == SCAN_COUNTS_AUTO && dense_counts_pay(n, arcs)));
+                                  (counts_mode == SCAN_COUNTS_AUTO && dense_counts_pay(n, arcs, cfg)));
   if (dense) {
     // closed counts of every arc from one matrix product (Section 4.1.1)
     if (n > DENSE_MAX_N) return SCAN_EINVAL;
@@ -228,7 +261,7 @@ int run_pipeline(IndexData* ix, int kind, const scan_lsh_params* lsh, Pool& pool
     GS_CUDA(cudaMemcpyAsync(ix->no_id, ix->adj, arcs * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
     GS_TRY(launch_closed_counts_and_sims(kind, ix->off, ix->adj, ix->deg, n, arcs, od, oadj, opos,
                                          ix->maxdeg, max_od, use_lsh ? lsh->degree_threshold : -1,
-                                         wcsr, ix->no_sim, scalars, pool, s, count_ms));
+                                         wcsr, ix->no_sim, scalars, pool, s, count_ms, cfg));
     GS_CUDA(cudaMemcpyAsync(hs, scalars, sizeof(hs), cudaMemcpyDeviceToHost, s));
     GS_CUDA(cudaStreamSynchronize(s));
     if (hs[0] & DEV_BADGRAPH) return SCAN_EBADGRAPH;
@@ -280,7 +313,8 @@ int check_csr_args(const scan_csr* csr) {
 
 // Build one index into ix; on error every block is released by the pool.
 int build_one(const scan_csr* csr, int kind, const scan_lsh_params* lsh, cudaStream_t s,
-              IndexData* ix, int counts_mode = SCAN_COUNTS_AUTO, const double* weights = nullptr) {
+              IndexData* ix, int counts_mode = SCAN_COUNTS_AUTO, const double* weights = nullptr,
+              const CountCfg* cfg_in = nullptr) {
   if (counts_mode < SCAN_COUNTS_AUTO || counts_mode > SCAN_COUNTS_DENSE) return SCAN_EINVAL;
   GS_TRY(check_csr_args(csr));
   if (kind != SCAN_COSINE && kind != SCAN_JACCARD) return SCAN_EINVAL;
@@ -334,7 +368,8 @@ int build_one(const scan_csr* csr, int kind, const scan_lsh_params* lsh, cudaStr
   GS_CUDA(cudaStreamSynchronize(s));
   if (ends[0] != 0 || ends[1] != arcs) return SCAN_EBADGRAPH;
   float count_ms = 0;
-  GS_TRY(run_pipeline(ix, kind, lsh, pool, s, ev, &count_ms, counts_mode, wcsr));
+  const CountCfg cfg = cfg_in ? *cfg_in : count_config_for(n, n, arcs);
+  GS_TRY(run_pipeline(ix, kind, lsh, pool, s, ev, &count_ms, counts_mode, cfg, wcsr));
   if (wcsr) pool.put(wcsr);
   // ---- core order (Algorithm 2)
   GS_TRY(build_core_order(*ix, pool, s));
@@ -435,10 +470,10 @@ struct Arena {
   }
 };
 
-int build_batch(const scan_csr* graphs, int G, int kind, const scan_lsh_params* lsh,
-                cudaStream_t s, scan_index** out) {
-  if (kind != SCAN_COSINE && kind != SCAN_JACCARD) return SCAN_EINVAL;
-  GS_TRY(validate_lsh(lsh, kind));
+// The G graphs packed into one union CSR and built by one pass of the
+// pipeline; the per-graph indexes are views into one shared arena.
+int build_union(const scan_csr* graphs, int G, int kind, const scan_lsh_params* lsh,
+                cudaStream_t s, const CountCfg& cfg, scan_index** out) {
   std::vector<int64_t> vb(G + 1, 0), ab(G + 1, 0);
   for (int g = 0; g < G; ++g) {
     GS_TRY(check_csr_args(&graphs[g]));
@@ -507,7 +542,7 @@ int build_batch(const scan_csr* graphs, int G, int kind, const scan_lsh_params* 
   pool.put(raw);
   // ---- the shared pipeline over the union (every step is local to a vertex)
   float count_ms = 0;
-  GS_TRY(run_pipeline(&u, kind, lsh, pool, s, ev, &count_ms, SCAN_COUNTS_SPARSE));
+  GS_TRY(run_pipeline(&u, kind, lsh, pool, s, ev, &count_ms, SCAN_COUNTS_SPARSE, cfg));
   // ---- per-graph core orders
   int32_t* md_dev = pool.get<int32_t>(G);
   if (!md_dev) return SCAN_ENOMEM;
@@ -591,6 +626,64 @@ int build_batch(const scan_csr* graphs, int G, int kind, const scan_lsh_params* 
     d.bytes = A > 0 ? (size_t)((double)total_bytes * (double)d.arcs / (double)A) : 0;
     out[g] = hs[g];
   }
+  return SCAN_OK;
+}
+
+// Batched build: the members that the counting configuration sends to the
+// dense path (one tcgen05 GEMM each) are built one by one, the others packed
+// into one union build. The handles come back in the callers' order; the
+// phase timings recorded are the sums over the builds.
+int build_batch(const scan_csr* graphs, int G, int kind, const scan_lsh_params* lsh,
+                cudaStream_t s, scan_index** out) {
+  if (kind != SCAN_COSINE && kind != SCAN_JACCARD) return SCAN_EINVAL;
+  GS_TRY(validate_lsh(lsh, kind));
+  int64_t N = 0, A = 0, nmax = 0;
+  for (int g = 0; g < G; ++g) {
+    GS_TRY(check_csr_args(&graphs[g]));
+    N += graphs[g].n;
+    A += graphs[g].num_arcs;
+    nmax = std::max<int64_t>(nmax, graphs[g].n);
+  }
+  const CountCfg cfg = count_config_for(nmax, N, A);
+  std::vector<int> dense_ids, sparse_ids;
+  for (int g = 0; g < G; ++g)
+    (graphs[g].num_arcs > 0 && dense_counts_pay(graphs[g].n, graphs[g].num_arcs, cfg)
+         ? dense_ids : sparse_ids).push_back(g);
+  if (dense_ids.empty()) return build_union(graphs, G, kind, lsh, s, cfg, out);
+  double tsum[7] = {0, 0, 0, 0, 0, 0, 0};
+  auto add_timings = [&] {
+    for (int i = 0; i < 7; ++i) tsum[i] += g_timings[i];
+  };
+  std::vector<scan_index*> built;  // released if a later build fails
+  auto fail = [&](int rc) {
+    for (scan_index* h : built) scan_index_free(h);
+    return rc;
+  };
+  if (!sparse_ids.empty()) {
+    std::vector<scan_csr> sp;
+    for (int g : sparse_ids) sp.push_back(graphs[g]);
+    std::vector<scan_index*> sp_out(sp.size(), nullptr);
+    const int rc = build_union(sp.data(), (int)sp.size(), kind, lsh, s, cfg, sp_out.data());
+    if (rc != SCAN_OK) return rc;
+    add_timings();
+    for (size_t i = 0; i < sp.size(); ++i) {
+      out[sparse_ids[i]] = sp_out[i];
+      built.push_back(sp_out[i]);
+    }
+  }
+  for (int g : dense_ids) {
+    scan_index* h = new (std::nothrow) scan_index();
+    if (!h) return fail(SCAN_ENOMEM);
+    const int rc = build_one(&graphs[g], kind, lsh, s, &h->d, SCAN_COUNTS_DENSE, nullptr, &cfg);
+    if (rc != SCAN_OK) {
+      delete h;
+      return fail(rc);
+    }
+    add_timings();
+    out[g] = h;
+    built.push_back(h);
+  }
+  record_timings(tsum);
   return SCAN_OK;
 }
 
@@ -794,6 +887,159 @@ int scan_kernel_launches(uint64_t* count) {
 int scan_last_build_timings(double* ms7) {
   if (!ms7) return SCAN_EINVAL;
   for (int i = 0; i < 7; ++i) ms7[i] = g_timings[i];
+  return SCAN_OK;
+}
+
+namespace {
+bool valid_cfg(const scan_count_config& c) {
+  return c.warp_deg >= 32 && c.warp_deg <= 4096 && c.cta_chunk >= 256 && c.cta_chunk <= 65536 &&
+         c.cta_chunk % 32 == 0 && c.long_list >= 1 && c.long_list <= (1 << 20) &&
+         (c.rounds == 4 || c.rounds == 8) && c.dense_div >= 0 && c.dense_div <= 1024 &&
+         c.dense_min_n >= 2 && c.dense_min_n <= gscan::DENSE_MAX_N;
+}
+gscan::CountCfg to_cfg(const scan_count_config& c) {
+  gscan::CountCfg g;
+  g.warp_deg = c.warp_deg;
+  g.cta_chunk = c.cta_chunk;
+  g.long_list = c.long_list;
+  g.rounds = c.rounds;
+  g.dense_div = c.dense_div;
+  g.dense_min_n = c.dense_min_n;
+  return g;
+}
+scan_count_config from_cfg(const gscan::CountCfg& g) {
+  return scan_count_config{g.warp_deg, g.cta_chunk, g.long_list, g.rounds, g.dense_div,
+                           g.dense_min_n};
+}
+}  // namespace
+
+int scan_set_count_config(const scan_count_config* cfg) {
+  if (cfg && !valid_cfg(*cfg)) return SCAN_EINVAL;
+  std::lock_guard<std::mutex> lk(gscan::g_tune_mu);
+  gscan::g_cfg_global_set = cfg != nullptr;
+  if (cfg) gscan::g_cfg_global = to_cfg(*cfg);
+  return SCAN_OK;
+}
+
+int scan_autotune_batch(const scan_csr* graphs, int count, scan_sim_kind kind, int reps,
+                        uintptr_t stream, scan_count_config* best, double* best_ms,
+                        double* default_ms) {
+  if (!graphs || count <= 0 || reps <= 0) return SCAN_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<scan_index*> hs((size_t)count, nullptr);
+  int64_t N = 0, A = 0, nmax = 0;
+  for (int g = 0; g < count; ++g) {
+    N += graphs[g].n;
+    A += graphs[g].num_arcs;
+    nmax = std::max<int64_t>(nmax, graphs[g].n);
+  }
+  // the fastest of `reps` batched builds (whole build, CUDA events)
+  auto measure = [&](const gscan::CountCfg& c, double* ms) -> int {
+    gscan::t_cfg_set = true;
+    gscan::t_cfg = c;
+    double best_t = 1e300;
+    int rc = SCAN_OK;
+    for (int r = 0; r < reps && rc == SCAN_OK; ++r) {
+      rc = gscan::build_batch(graphs, count, kind, nullptr, s, hs.data());
+      if (rc != SCAN_OK) break;
+      best_t = std::min(best_t, gscan::g_timings[6]);
+      for (int g = 0; g < count; ++g) scan_index_free(hs[g]);
+    }
+    gscan::t_cfg_set = false;
+    *ms = best_t;
+    return rc;
+  };
+  gscan::CountCfg cur;
+  double cur_ms = 0;
+  GS_TRY(measure(cur, &cur_ms));
+  if (default_ms) *default_ms = cur_ms;
+  // coordinate search: one parameter at a time, keeping any improvement
+  const int dense_divs[] = {0, 8, 16, 32, 64};
+  const int dense_min_ns[] = {2048, 4096, 8192};
+  const int warp_degs[] = {128, 256, 512, 1024, 2048};
+  const int chunks[] = {1024, 2048, 4096, 8192};
+  const int longs[] = {32, 64, 128, 256};
+  const int rounds[] = {4, 8};
+  auto try_value = [&](int gscan::CountCfg::*field, int v) -> int {
+    if (cur.*field == v) return SCAN_OK;
+    gscan::CountCfg c = cur;
+    c.*field = v;
+    double t = 0;
+    GS_TRY(measure(c, &t));
+    if (t < cur_ms) {
+      cur = c;
+      cur_ms = t;
+    }
+    return SCAN_OK;
+  };
+  for (int v : dense_divs) GS_TRY(try_value(&gscan::CountCfg::dense_div, v));
+  if (cur.dense_div > 0)
+    for (int v : dense_min_ns) GS_TRY(try_value(&gscan::CountCfg::dense_min_n, v));
+  for (int v : warp_degs) GS_TRY(try_value(&gscan::CountCfg::warp_deg, v));
+  for (int v : chunks) GS_TRY(try_value(&gscan::CountCfg::cta_chunk, v));
+  for (int v : longs) GS_TRY(try_value(&gscan::CountCfg::long_list, v));
+  for (int v : rounds) GS_TRY(try_value(&gscan::CountCfg::rounds, v));
+  {
+    std::lock_guard<std::mutex> lk(gscan::g_tune_mu);
+    gscan::g_tune_table[gscan::degree_class(nmax, N, A)] = cur;
+  }
+  if (best) *best = from_cfg(cur);
+  if (best_ms) *best_ms = cur_ms;
+  return SCAN_OK;
+}
+
+int scan_count_config_for(int64_t max_n, int64_t total_n, int64_t num_arcs,
+                          scan_count_config* cfg) {
+  if (!cfg || max_n < 0 || total_n < max_n || num_arcs < 0) return SCAN_EINVAL;
+  *cfg = from_cfg(gscan::count_config_for(max_n, total_n, num_arcs));
+  return SCAN_OK;
+}
+
+int scan_tuning_save(const char* path) {
+  if (!path) return SCAN_EINVAL;
+  FILE* f = std::fopen(path, "w");
+  if (!f) return SCAN_EINVAL;
+  std::fprintf(f, "# max_n_bits avg_degree_bits warp_deg cta_chunk long_list rounds dense_div "
+                 "dense_min_n\n");
+  {
+    std::lock_guard<std::mutex> lk(gscan::g_tune_mu);
+    for (const auto& kv : gscan::g_tune_table)
+      std::fprintf(f, "%d %d %d %d %d %d %d %d\n", kv.first.first, kv.first.second,
+                   kv.second.warp_deg, kv.second.cta_chunk, kv.second.long_list, kv.second.rounds,
+                   kv.second.dense_div, kv.second.dense_min_n);
+  }
+  return std::fclose(f) == 0 ? SCAN_OK : SCAN_EINVAL;
+}
+
+int scan_tuning_load(const char* path) {
+  if (!path) return SCAN_EINVAL;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return SCAN_EINVAL;
+  std::map<std::pair<int, int>, gscan::CountCfg> table;
+  char line[256];
+  int rc = SCAN_OK;
+  while (std::fgets(line, sizeof(line), f)) {
+    if (line[0] == '#' || line[0] == '\n') continue;
+    int a, b;
+    scan_count_config c;
+    if (std::sscanf(line, "%d %d %d %d %d %d %d %d", &a, &b, &c.warp_deg, &c.cta_chunk,
+                    &c.long_list, &c.rounds, &c.dense_div, &c.dense_min_n) != 8 ||
+        !valid_cfg(c)) {
+      rc = SCAN_EINVAL;
+      break;
+    }
+    table[{a, b}] = to_cfg(c);
+  }
+  std::fclose(f);
+  if (rc != SCAN_OK) return rc;
+  std::lock_guard<std::mutex> lk(gscan::g_tune_mu);
+  for (const auto& kv : table) gscan::g_tune_table[kv.first] = kv.second;
+  return SCAN_OK;
+}
+
+int scan_tuning_clear(void) {
+  std::lock_guard<std::mutex> lk(gscan::g_tune_mu);
+  gscan::g_tune_table.clear();
   return SCAN_OK;
 }
 

@@ -126,6 +126,27 @@ int launch_orient(const int64_t* off, const int32_t* adj, const int32_t* deg, in
                   int64_t arcs, Pool& pool, int32_t** od, int32_t** oadj, int32_t** opos,
                   int32_t* max_od_dev, unsigned long long* sum_od_dev, cudaStream_t s);
 
+// Counting strategy per degree bucket (a tuning point): a graph of at least
+// dense_min_n vertices with dense_div * arcs >= n^2 takes the dense GEMM
+// path (dense_div = 0: never); otherwise, rows of at most warp_deg positions
+// with out-lists of at most 256 entries go to the warp kernel, the others to
+// the CTA kernel in items of cta_chunk CSR positions; suffixes of at least
+// long_list entries are streamed one at a time; rounds (4 or 8) of 32-element
+// loads stay in flight for the short ones.
+constexpr int64_t DENSE_MIN_N = 4096;
+struct CountCfg {
+  int warp_deg = 512;
+  int cta_chunk = 4096;
+  int long_list = 64;
+  int rounds = 4;
+  int dense_div = 16;
+  int dense_min_n = (int)DENSE_MIN_N;
+};
+// The configuration of a build (a batch: its largest graph has n_max
+// vertices, all of them n_total vertices and arcs arcs): a process or thread
+// override, else the tuning table's entry for its class, else the defaults.
+CountCfg count_config_for(int64_t n_max, int64_t n_total, int64_t arcs);
+
 // Closed counts of every edge by oriented triangle enumeration, then the
 // similarity of every CSR arc written to sim_csr (the unsorted NO). With
 // lsh_T >= 0, edges whose endpoints both have degree > lsh_T are left for the
@@ -134,7 +155,8 @@ int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* a
                                   const int32_t* deg, int64_t n, int64_t arcs, const int32_t* od,
                                   int32_t* oadj, int32_t* opos, int32_t maxdeg,
                                   int32_t max_od, int lsh_T, const double* wcsr, double* sim_csr,
-                                  unsigned* status, Pool& pool, cudaStream_t s, float* count_ms);
+                                  unsigned* status, Pool& pool, cudaStream_t s, float* count_ms,
+                                  const CountCfg& cfg);
 
 // Sort every segment [seg_off[i], seg_off[i+1]) of (key, val) pairs by key
 // descending, then val ascending. Keys are non-negative doubles viewed as
@@ -154,10 +176,9 @@ int build_core_order_multi(int64_t N, int64_t A, const int64_t* off, const int32
 // Dense path (dense.cu): closed counts of every arc as ((A+I)^2)[u][v] by one
 // hand-written tcgen05 bf16 GEMM with fp32 accumulation, the similarities
 // written by its epilogue; for graphs of at most DENSE_MAX_N vertices, and
-// chosen automatically from DENSE_MIN_N vertices on.
+// chosen automatically by the rule of the counting configuration.
 constexpr int64_t DENSE_MAX_N = 65536;
-constexpr int64_t DENSE_MIN_N = 4096;
-bool dense_counts_pay(int64_t n, int64_t arcs);
+bool dense_counts_pay(int64_t n, int64_t arcs, const CountCfg& cfg);
 int dense_counts_and_sims(int kind, const int64_t* off, const int32_t* adj, const int32_t* deg,
                           int64_t n, int lsh_T, double* sim_csr, unsigned* status, Pool& pool,
                           cudaStream_t s, float* count_ms);

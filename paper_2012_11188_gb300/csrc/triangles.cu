@@ -21,20 +21,12 @@ namespace gscan {
 
 namespace {
 
-#ifndef GS_TRI_ROUNDS
-#define GS_TRI_ROUNDS 4  // 32-element rounds of loads in flight per warp in the counting loop
-#endif
 #ifndef GS_TRI_FAST_ROUNDS
-#define GS_TRI_FAST_ROUNDS 12  // the same for out-lists streamed one at a time
+#define GS_TRI_FAST_ROUNDS 12  // 32-element rounds in flight for out-lists streamed one at a time
 #endif
-#ifndef GS_TRI_LONG_LIST
-#define GS_TRI_LONG_LIST 64  // suffixes at least this long are streamed one at a time
-#endif
-constexpr int LONG_LIST = GS_TRI_LONG_LIST;
 
 constexpr int TRI_THREADS = 512;
 constexpr int TRI_WARPS = TRI_THREADS / 32;
-constexpr int CHUNK = 4096;          // CSR positions of N(v) per work item
 constexpr int SMEM_OD_MAX = 4096;    // out(v) sizes handled by the shared-memory table
 
 __device__ __forceinline__ bool lower(int32_t du, int32_t u, int32_t dv, int32_t v) {
@@ -56,33 +48,30 @@ __device__ __forceinline__ int key_search(const uint64_t* __restrict__ kb, int l
   return (lo < len && kb[lo] == kv) ? lo : -1;
 }
 
-#ifndef GS_TRI_WARP_DEG
-#define GS_TRI_WARP_DEG 512
-#endif
-// A vertex whose row has at most WARP_DEG positions and whose out-list has at
-// most SMALL_OD entries is handled by one warp with its own table; the rest
-// by the CTA kernel.
-constexpr int WARP_DEG = GS_TRI_WARP_DEG;
+// A vertex whose row has at most cfg.warp_deg positions and whose out-list
+// has at most SMALL_OD entries is handled by one warp with its own table;
+// the rest by the CTA kernel (the strategy per degree bucket, a tuning
+// parameter).
 constexpr int SMALL_OD = 256;
 constexpr int SW_SLOTS = 2 * SMALL_OD;  // 2^table_log2(SMALL_OD) slots per table
 
-__host__ __device__ __forceinline__ bool warp_vertex(int64_t d, int64_t od) {
-  return d <= WARP_DEG && od <= SMALL_OD;
+__host__ __device__ __forceinline__ bool warp_vertex(int64_t d, int64_t od, int warp_deg) {
+  return d <= warp_deg && od <= SMALL_OD;
 }
 constexpr int SW_WARPS = 4;
 
 // Work items of the CTA kernel: a vertex v not handled by a warp contributes
-// ceil(deg/CHUNK) items when it has in-neighbours (every in-arc needs the
+// ceil(deg/chunk) items when it has in-neighbours (every in-arc needs the
 // position of its source in N(v), even when out(v) is empty and no triangle
 // has v in the middle). items[v] -> prefix -> item index maps to (v, chunk).
 __global__ void k_item_counts(const int32_t* __restrict__ odeg, const int32_t* __restrict__ deg,
-                              int64_t n, int32_t* __restrict__ items) {
+                              int64_t n, int warp_deg, int chunk, int32_t* __restrict__ items) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
        v += (int64_t)gridDim.x * blockDim.x) {
     const int64_t od = odeg[v];
     const int32_t d = deg[v];
     int c = 0;
-    if (!warp_vertex(d, od) && d - od > 0) c = (int)((d + CHUNK - 1) / CHUNK);
+    if (!warp_vertex(d, od, warp_deg) && d - od > 0) c = (int)((d + chunk - 1) / chunk);
     items[v] = c;
   }
 }
@@ -341,15 +330,16 @@ __device__ __forceinline__ void wt_drain(int cnt, const Weights& wt) {
 // to lanes 0..k-1, and each lane finds v in out(u) (ascending rank) by a
 // binary search of its rank key: that gives the twin position of the arc
 // u->v, and the possible third vertices w > v are the entries after it.
-// Suffixes of at least LONG_LIST entries are streamed one at a time, lane l
+// Suffixes of at least long_list entries are streamed one at a time, lane l
 // taking elements l, l+32, ... (RF rounds of loads in flight); the shorter
 // ones are concatenated and walked 32 elements per round (R rounds in
 // flight), the owner of an element coming from the suffix starts that fall
 // in its round (ballot / or-reduce / popc). Hits on (u,v) are counted per
 // list; weighted hits go to the warp's hit buffer.
-template <bool BIG, typename IT, bool WT>
+template <bool BIG, typename IT, bool WT, int R>
 __device__ __forceinline__ void process_slice(
     int64_t p0, int64_t p_end, int64_t rb, int32_t v, int32_t dv, int32_t od, int64_t ob,
+    int long_list,
     const int32_t* __restrict__ adj, const int32_t* __restrict__ deg,
     const int64_t* __restrict__ off, const int32_t* __restrict__ odeg,
     const int32_t* __restrict__ oadj, const uint64_t* __restrict__ okey,
@@ -408,7 +398,7 @@ __device__ __forceinline__ void process_slice(
 
   // 1. long suffixes, one at a time
   constexpr int RF = GS_TRI_FAST_ROUNDS;
-  unsigned lm = __ballot_sync(FULL, lane < k && clen >= LONG_LIST);
+  unsigned lm = __ballot_sync(FULL, lane < k && clen >= long_list);
   while (lm) {
     const int i = __ffs(lm) - 1;
     lm &= lm - 1;
@@ -442,7 +432,7 @@ __device__ __forceinline__ void process_slice(
   }
 
   // 2. short non-empty suffixes, concatenated: lane r takes the r-th of them
-  const bool is_short = lane < k && clen > 0 && clen < LONG_LIST;
+  const bool is_short = lane < k && clen > 0 && clen < long_list;
   const unsigned shm = __ballot_sync(FULL, is_short);
   if (shm) {
     const int k2 = __popc(shm);
@@ -460,7 +450,6 @@ __device__ __forceinline__ void process_slice(
     }
     const int32_t cstart = incl - slen;
     const int32_t W = __shfl_sync(FULL, incl, 31);
-    constexpr int R = GS_TRI_ROUNDS;
     for (int32_t rbase = 0; rbase < W; rbase += 32 * R) {
       int32_t xs[R];
       IT js[R];
@@ -518,13 +507,14 @@ __device__ __forceinline__ void process_slice(
 // BIG = out(v) too long for the shared table (binary search, global counters);
 // the BIG kernel also takes the items listed in `deferred`, whose shared
 // table could not be built (no cuckoo placement).
-template <bool BIG, typename IT, bool WT>
+template <bool BIG, typename IT, bool WT, int R>
 __global__ void __launch_bounds__(TRI_THREADS, 3)
 k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
             const int32_t* __restrict__ deg, const int32_t* __restrict__ odeg,
             const int32_t* __restrict__ oadj, const uint64_t* __restrict__ okey,
             const int64_t* __restrict__ odp, int64_t n, const int64_t* __restrict__ item_off,
             const int32_t* __restrict__ order, unsigned long long* __restrict__ work, int lsh_T,
+            int item_chunk, int long_list,
             int od_cap, int64_t* __restrict__ deferred, unsigned long long* __restrict__ n_deferred,
             bool deferred_only, uint32_t* __restrict__ tcnt, uint32_t* __restrict__ tc16,
             int32_t* __restrict__ twin_rel, unsigned* status, const double* __restrict__ ow,
@@ -582,8 +572,8 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
       }
     }
     const int64_t rb = off[v];
-    const int64_t p_begin = chunk * CHUNK;
-    const int64_t p_end = min((int64_t)dv, p_begin + CHUNK);
+    const int64_t p_begin = chunk * item_chunk;
+    const int64_t p_end = min((int64_t)dv, p_begin + item_chunk);
     for (;;) {
       // warps pull 32-position slices until the item's range is exhausted
       int slice = 0;
@@ -591,9 +581,9 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
       slice = __shfl_sync(FULL, slice, 0);
       const int64_t pos0 = p_begin + slice;
       if (pos0 >= p_end) break;
-      process_slice<BIG, IT, WT>(pos0, p_end, rb, (int32_t)v, dv, od, ob, adj, deg, off, odeg,
-                                 oadj, okey, odp, lsh_T, tab, vcnt, sm, tcnt, tc16, twin_rel, bad,
-                                 wt);
+      process_slice<BIG, IT, WT, R>(pos0, p_end, rb, (int32_t)v, dv, od, ob, long_list, adj, deg,
+                                    off, odeg, oadj, okey, odp, lsh_T, tab, vcnt, sm, tcnt, tc16,
+                                    twin_rel, bad, wt);
     }
     __syncthreads();
     if (!BIG && !WT)
@@ -606,17 +596,18 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
   if (bad) atomicOr(status, (unsigned)DEV_BADGRAPH);
 }
 
-// Warp kernel for rows of at most WARP_DEG positions with out-lists of at
+// Warp kernel for rows of at most warp_deg positions with out-lists of at
 // most SMALL_OD entries: each warp owns one
 // vertex at a time, with its own table of out(v) (no CTA barrier). Warps take
 // 32 vertices per atomic fetch.
-template <typename IT, bool WT>
+template <typename IT, bool WT, int R>
 __global__ void __launch_bounds__(SW_WARPS * 32, 8)
 k_tri_small(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
             const int32_t* __restrict__ deg, const int32_t* __restrict__ odeg,
             const int32_t* __restrict__ oadj, const uint64_t* __restrict__ okey,
             const int64_t* __restrict__ odp, int64_t n, unsigned long long* __restrict__ work,
-            int lsh_T, uint32_t* __restrict__ tcnt, uint32_t* __restrict__ tc16,
+            int lsh_T, int warp_deg, int long_list, uint32_t* __restrict__ tcnt,
+            uint32_t* __restrict__ tc16,
             int32_t* __restrict__ twin_rel, unsigned* status, const double* __restrict__ ow,
             double* __restrict__ tsum) {
   __shared__ __align__(16) uint32_t s_tab[SW_WARPS][3 * SW_SLOTS];  // t0 | t1 | p0 p1
@@ -641,7 +632,7 @@ k_tri_small(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
       const int32_t dv = deg[vv];
       if (dv == 0) continue;
       const int32_t od = odeg[vv];
-      if (!warp_vertex(dv, od) || dv - od == 0) continue;  // CTA kernel, or no in-neighbours
+      if (!warp_vertex(dv, od, warp_deg) || dv - od == 0) continue;  // CTA kernel, or no in-neighbours
       const int64_t ob = off[vv];
       OutTable tab{nullptr, 0, 27, 0u, 0u, okey + odp[vv], deg, od, true};
       if (od > 0) {
@@ -653,13 +644,13 @@ k_tri_small(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
       const int64_t rb = off[vv];
       for (int64_t pos0 = 0; pos0 < dv; pos0 += 32) {
         if (use_table)
-          process_slice<false, IT, WT>(pos0, dv, rb, (int32_t)vv, dv, od, ob, adj, deg, off, odeg,
-                                       oadj, okey, odp, lsh_T, tab, vcnt, sm, tcnt, tc16,
-                                       twin_rel, bad, wt);
+          process_slice<false, IT, WT, R>(pos0, dv, rb, (int32_t)vv, dv, od, ob, long_list, adj,
+                                          deg, off, odeg, oadj, okey, odp, lsh_T, tab, vcnt, sm,
+                                          tcnt, tc16, twin_rel, bad, wt);
         else
-          process_slice<true, IT, WT>(pos0, dv, rb, (int32_t)vv, dv, od, ob, adj, deg, off, odeg,
-                                      oadj, okey, odp, lsh_T, tab, vcnt, sm, tcnt, tc16,
-                                      twin_rel, bad, wt);
+          process_slice<true, IT, WT, R>(pos0, dv, rb, (int32_t)vv, dv, od, ob, long_list, adj,
+                                         deg, off, odeg, oadj, okey, odp, lsh_T, tab, vcnt, sm,
+                                         tcnt, tc16, twin_rel, bad, wt);
       }
       __syncwarp();
       if (use_table && !WT)
@@ -930,54 +921,77 @@ __global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v) {
 
 // The three counting kernels; IT indexes elements of the CSR (32-bit when the
 // graph has fewer than 2^31 arcs, which halves the index arithmetic); WT
-// accumulates weighted-cosine numerators (ow, tsum) instead of counts.
-template <typename IT, bool WT>
+// accumulates weighted-cosine numerators (ow, tsum) instead of counts; R is
+// the number of 32-element rounds of loads in flight for the concatenated
+// short suffixes (a tuning parameter: 4 or 8).
+template <typename IT, bool WT, int R>
 int launch_counting(const int64_t* off, const int32_t* adj, const int32_t* deg, const int32_t* odeg,
                     const int32_t* oadj, const uint64_t* okey, const int64_t* odp, int64_t n,
                     const int64_t* item_off, const int32_t* order,
                     unsigned long long* work, int lsh_T, int32_t max_od, int64_t* deferred,
                     unsigned long long* n_deferred, uint32_t* tcnt, uint32_t* tc16, int32_t* twin,
-                    unsigned* status, const double* ow, double* tsum, cudaStream_t s) {
+                    unsigned* status, const double* ow, double* tsum, const CountCfg& cfg,
+                    cudaStream_t s) {
   int od_cap = 16;
   while (od_cap < max_od && od_cap < SMEM_OD_MAX) od_cap <<= 1;
   // the table (12 bytes per slot, 2 * od_cap slots) and the counters (4 bytes)
   const size_t per_od = WT ? 24 : 28;  // weighted mode: no counters
   const size_t smem = per_od * od_cap;
   const size_t smem_max = per_od * SMEM_OD_MAX;
-  GS_CUDA(cudaFuncSetAttribute(k_triangles<false, IT, WT>,
+  GS_CUDA(cudaFuncSetAttribute(k_triangles<false, IT, WT, R>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
   const int sms = sm_count();
   int per_sm = 1;
-  GS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_triangles<false, IT, WT>,
+  GS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_triangles<false, IT, WT, R>,
                                                         TRI_THREADS, smem));
   if (per_sm < 1) per_sm = 1;
-  k_triangles<false, IT, WT><<<sms * per_sm, TRI_THREADS, smem, s>>>(
-      off, adj, deg, odeg, oadj, okey, odp, n, item_off, order, work, lsh_T, od_cap, deferred,
-      n_deferred, false, tcnt, tc16, twin, status, ow, tsum);
+  k_triangles<false, IT, WT, R><<<sms * per_sm, TRI_THREADS, smem, s>>>(
+      off, adj, deg, odeg, oadj, okey, odp, n, item_off, order, work, lsh_T, cfg.cta_chunk,
+      cfg.long_list, od_cap, deferred, n_deferred, false, tcnt, tc16, twin, status, ow, tsum);
   GS_LAUNCH();
   int small_per_sm = 1;
-  GS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&small_per_sm, k_tri_small<IT, WT>,
+  GS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&small_per_sm, k_tri_small<IT, WT, R>,
                                                         SW_WARPS * 32, 0));
   if (small_per_sm < 1) small_per_sm = 1;
-  k_tri_small<IT, WT><<<sms * small_per_sm, SW_WARPS * 32, 0, s>>>(
-      off, adj, deg, odeg, oadj, okey, odp, n, work + 2, lsh_T, tcnt, tc16, twin, status, ow,
-      tsum);
+  k_tri_small<IT, WT, R><<<sms * small_per_sm, SW_WARPS * 32, 0, s>>>(
+      off, adj, deg, odeg, oadj, okey, odp, n, work + 2, lsh_T, cfg.warp_deg, cfg.long_list, tcnt,
+      tc16, twin, status, ow, tsum);
   GS_LAUNCH();
   // items with out-lists too long for the shared table, and items deferred
   // by the CTA kernel (normally none: the launch then ends at once)
   const bool deferred_only = max_od <= SMEM_OD_MAX;
-  k_triangles<true, IT, WT><<<deferred_only ? sms : sms * 4, TRI_THREADS, 0, s>>>(
-      off, adj, deg, odeg, oadj, okey, odp, n, item_off, order, work + 1, lsh_T, 0, deferred,
-      n_deferred, deferred_only, tcnt, tc16, twin, status, ow, tsum);
+  k_triangles<true, IT, WT, R><<<deferred_only ? sms : sms * 4, TRI_THREADS, 0, s>>>(
+      off, adj, deg, odeg, oadj, okey, odp, n, item_off, order, work + 1, lsh_T, cfg.cta_chunk,
+      cfg.long_list, 0, deferred, n_deferred, deferred_only, tcnt, tc16, twin, status, ow, tsum);
   GS_LAUNCH();
   return SCAN_OK;
+}
+
+// One set of counting kernels for the configuration: rounds 8 is compiled for
+// the unweighted instances only.
+template <typename IT, bool WT>
+int launch_counting_cfg(const int64_t* off, const int32_t* adj, const int32_t* deg,
+                        const int32_t* odeg, const int32_t* oadj, const uint64_t* okey,
+                        const int64_t* odp, int64_t n, const int64_t* item_off,
+                        const int32_t* order, unsigned long long* work, int lsh_T, int32_t max_od,
+                        int64_t* deferred, unsigned long long* n_deferred, uint32_t* tcnt,
+                        uint32_t* tc16, int32_t* twin, unsigned* status, const double* ow,
+                        double* tsum, const CountCfg& cfg, cudaStream_t s) {
+  if (!WT && cfg.rounds == 8)
+    return launch_counting<IT, WT, 8>(off, adj, deg, odeg, oadj, okey, odp, n, item_off, order,
+                                      work, lsh_T, max_od, deferred, n_deferred, tcnt, tc16, twin,
+                                      status, ow, tsum, cfg, s);
+  return launch_counting<IT, WT, 4>(off, adj, deg, odeg, oadj, okey, odp, n, item_off, order,
+                                    work, lsh_T, max_od, deferred, n_deferred, tcnt, tc16, twin,
+                                    status, ow, tsum, cfg, s);
 }
 
 int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* adj,
                                   const int32_t* deg, int64_t n, int64_t arcs, const int32_t* odeg,
                                   int32_t* oadj, int32_t* opos, int32_t maxdeg,
                                   int32_t max_od, int lsh_T, const double* wcsr, double* sim_csr,
-                                  unsigned* status, Pool& pool, cudaStream_t s, float* count_ms) {
+                                  unsigned* status, Pool& pool, cudaStream_t s, float* count_ms,
+                                  const CountCfg& cfg) {
   const bool weighted = wcsr != nullptr;
   const int64_t m = arcs;  // out-lists live in CSR slots: counts and twins are indexed by arc
   const int64_t edges = m / 2;  // oriented edges (the orientation checked sum od = arcs / 2)
@@ -1003,8 +1017,8 @@ int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* a
   unsigned long long* hist = pool.get<unsigned long long>(2 * nbins);  // counts | fill cursors
   int64_t* start = pool.get<int64_t>(nbins + 1);
   unsigned long long* work = pool.get<unsigned long long>(4);  // 3 counters + deferred count
-  // items: at most one per vertex plus one per CHUNK arcs
-  int64_t* deferred = pool.get<int64_t>(n + m / CHUNK + 1);
+  // items: at most one per vertex plus one per cta_chunk arcs
+  int64_t* deferred = pool.get<int64_t>(n + m / cfg.cta_chunk + 1);
   if (!tcnt || (narrow && !tc16) || !twin || !items || !items_sorted || !order || !item_off ||
       !hist || !start ||
       !work || !deferred)
@@ -1019,7 +1033,7 @@ int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* a
   }
   if (n > 0) {
     const unsigned g = (unsigned)std::min<int64_t>((n + 255) / 256, sm_count() * 64);
-    k_item_counts<<<g, 256, 0, s>>>(odeg, deg, n, items);
+    k_item_counts<<<g, 256, 0, s>>>(odeg, deg, n, cfg.warp_deg, cfg.cta_chunk, items);
     GS_LAUNCH();
     k_item_hist<<<g, 256, 0, s>>>(items, deg, n, maxdeg, hist);
     GS_LAUNCH();
@@ -1050,22 +1064,22 @@ int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* a
       k_out_weights<<<egrid, EXPAND_T, 0, s>>>(off, odp, n, opos, wcsr, ow, status);
       GS_LAUNCH();
       if (narrow) {
-        GS_TRY((launch_counting<int32_t, true>(off, adj, deg, odeg, oadj, okey, odp, n, item_off,
+        GS_TRY((launch_counting_cfg<int32_t, true>(off, adj, deg, odeg, oadj, okey, odp, n, item_off,
                                                order, work, lsh_T, max_od, deferred, work + 3,
-                                               tcnt, tc16, twin, status, ow, tsum, s)));
+                                               tcnt, tc16, twin, status, ow, tsum, cfg, s)));
       } else {
-        GS_TRY((launch_counting<int64_t, true>(off, adj, deg, odeg, oadj, okey, odp, n, item_off,
+        GS_TRY((launch_counting_cfg<int64_t, true>(off, adj, deg, odeg, oadj, okey, odp, n, item_off,
                                                order, work, lsh_T, max_od, deferred, work + 3,
-                                               tcnt, nullptr, twin, status, ow, tsum, s)));
+                                               tcnt, nullptr, twin, status, ow, tsum, cfg, s)));
       }
     } else if (narrow) {
-      GS_TRY((launch_counting<int32_t, false>(off, adj, deg, odeg, oadj, okey, odp, n, item_off,
+      GS_TRY((launch_counting_cfg<int32_t, false>(off, adj, deg, odeg, oadj, okey, odp, n, item_off,
                                               order, work, lsh_T, max_od, deferred, work + 3, tcnt,
-                                              tc16, twin, status, nullptr, nullptr, s)));
+                                              tc16, twin, status, nullptr, nullptr, cfg, s)));
     } else {
-      GS_TRY((launch_counting<int64_t, false>(off, adj, deg, odeg, oadj, okey, odp, n, item_off,
+      GS_TRY((launch_counting_cfg<int64_t, false>(off, adj, deg, odeg, oadj, okey, odp, n, item_off,
                                               order, work, lsh_T, max_od, deferred, work + 3, tcnt,
-                                              nullptr, twin, status, nullptr, nullptr, s)));
+                                              nullptr, twin, status, nullptr, nullptr, cfg, s)));
     }
   }
   GS_CUDA(cudaEventRecord(e1, s));

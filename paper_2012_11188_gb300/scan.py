@@ -40,6 +40,15 @@ class scan_lsh_params(ctypes.Structure):
                 ("degree_threshold", ctypes.c_int), ("seed", ctypes.c_uint64)]
 
 
+class scan_count_config(ctypes.Structure):
+    _fields_ = [("warp_deg", ctypes.c_int), ("cta_chunk", ctypes.c_int),
+                ("long_list", ctypes.c_int), ("rounds", ctypes.c_int),
+                ("dense_div", ctypes.c_int), ("dense_min_n", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -75,12 +84,70 @@ def load():
         "scan_last_build_timings": (i32, [P]),
         "scan_kernel_launches": (i32, [P]),
         "scan_set_wide_index": (i32, [i32]),
+        "scan_set_count_config": (i32, [P]),
+        "scan_autotune_batch": (i32, [P, i32, i32, i32, ctypes.c_size_t, P, P, P]),
+        "scan_count_config_for": (i32, [i64, i64, i64, P]),
+        "scan_tuning_save": (i32, [ctypes.c_char_p]),
+        "scan_tuning_load": (i32, [ctypes.c_char_p]),
+        "scan_tuning_clear": (i32, []),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
         f.restype, f.argtypes = res, args
     _lib = lib
     return lib
+
+
+def set_count_config(cfg=None):
+    """Set (a dict with any of the fields of DEFAULT_COUNT_CONFIG; missing
+    ones take the default) or clear (None) the process-wide counting
+    configuration."""
+    if cfg is None:
+        _check(load().scan_set_count_config(None), "scan_set_count_config")
+        return
+    c = scan_count_config(**{**DEFAULT_COUNT_CONFIG, **cfg})
+    _check(load().scan_set_count_config(ctypes.byref(c)), "scan_set_count_config")
+
+
+def autotune_batch(graphs, kind: int = COSINE, reps: int = 2, stream=None, device: bool = False):
+    """Autotune the counting strategy per degree bucket on a batch of graphs
+    (include/scan.h); returns {"best": cfg, "best_ms": t, "default_ms": t0}."""
+    structs, keep = [], []
+    for g in graphs:
+        c, k = _csr_struct(g, device)
+        structs.append(c)
+        keep.append(k)
+    arr = (scan_csr * len(structs))(*structs)
+    best = scan_count_config()
+    bms, dms = ctypes.c_double(), ctypes.c_double()
+    _check(load().scan_autotune_batch(arr, len(structs), kind, int(reps), _stream_handle(stream),
+                                      ctypes.byref(best), ctypes.byref(bms), ctypes.byref(dms)),
+           "scan_autotune_batch")
+    return {"best": best.as_dict(), "best_ms": bms.value, "default_ms": dms.value}
+
+
+DEFAULT_COUNT_CONFIG = {"warp_deg": 512, "cta_chunk": 4096, "long_list": 64, "rounds": 4,
+                        "dense_div": 16, "dense_min_n": 4096}
+
+
+def count_config_for(max_n: int, total_n: int, arcs: int) -> dict:
+    """The configuration a build would use (a single graph: max_n = total_n = n)."""
+    c = scan_count_config()
+    _check(load().scan_count_config_for(int(max_n), int(total_n), int(arcs), ctypes.byref(c)),
+           "scan_count_config_for")
+    return c.as_dict()
+
+
+def tuning_save(path: str):
+    _check(load().scan_tuning_save(os.fsencode(path)), "scan_tuning_save")
+
+
+def tuning_load(path: str):
+    _check(load().scan_tuning_load(os.fsencode(path)), "scan_tuning_load")
+
+
+def tuning_clear():
+    _check(load().scan_tuning_clear(), "scan_tuning_clear")
 
 
 def paper_sigma():

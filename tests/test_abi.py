@@ -81,3 +81,45 @@ def test_weighted_argument_checks_without_gpu():
         gs.ScanIndex.build(g, gs.JACCARD, weights=w)
     with pytest.raises(gs.ScanError):
         gs.ScanIndex.build(g, gs.COSINE, counts=gs.COUNTS_DENSE, weights=w)
+
+
+def test_count_config_table_on_the_host(tmp_path):
+    """Counting configurations and the tuning table (host-side only)."""
+    gs.tuning_clear()
+    gs.set_count_config(None)
+    default = dict(gs.DEFAULT_COUNT_CONFIG)
+    # class of a batch whose largest graph has 1000 vertices (10 bits) and whose
+    # average degree is 20 (5 bits)
+    assert gs.count_config_for(1000, 5000, 100000) == default
+    for bad in ({"warp_deg": 8}, {"cta_chunk": 1000}, {"long_list": 0}, {"rounds": 5},
+                {"dense_div": -1}, {"dense_min_n": 1}, {"dense_min_n": 70000}):
+        with pytest.raises(gs.ScanError):
+            gs.set_count_config(bad)
+    with pytest.raises(gs.ScanError):
+        gs.count_config_for(10, 5, 100)  # total below the largest graph
+    f = tmp_path / "tune.txt"
+    f.write_text("# comment\n10 5 256 2048 128 8 0 4096\n")
+    gs.tuning_load(str(f))
+    tuned = {"warp_deg": 256, "cta_chunk": 2048, "long_list": 128, "rounds": 8, "dense_div": 0,
+             "dense_min_n": 4096}
+    assert gs.count_config_for(1000, 5000, 100000) == tuned
+    assert gs.count_config_for(1000, 5000, 200000) == default  # another class (average 40)
+    # a process-wide setting wins over the table; missing fields take the defaults
+    gs.set_count_config({"warp_deg": 1024})
+    assert gs.count_config_for(1000, 5000, 100000) == {**default, "warp_deg": 1024}
+    gs.set_count_config(None)
+    # save and reload round trip; a malformed file changes nothing
+    out = tmp_path / "saved.txt"
+    gs.tuning_save(str(out))
+    gs.tuning_clear()
+    assert gs.count_config_for(1000, 5000, 100000) == default
+    gs.tuning_load(str(out))
+    assert gs.count_config_for(1000, 5000, 100000) == tuned
+    bad = tmp_path / "bad.txt"
+    bad.write_text("10 5 256 2048 128 8\n")
+    with pytest.raises(gs.ScanError):
+        gs.tuning_load(str(bad))
+    assert gs.count_config_for(1000, 5000, 100000) == tuned
+    with pytest.raises(gs.ScanError):
+        gs.tuning_load(str(tmp_path / "missing.txt"))
+    gs.tuning_clear()
