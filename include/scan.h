@@ -326,6 +326,17 @@ int scan_tuning_save(const char* path);
 int scan_tuning_load(const char* path);
 int scan_tuning_clear(void);
 
+/* The segmented sort of the neighbour and core orders (Algorithm 2), for
+ * callers that assemble orders themselves, such as the sharded build, whose
+ * ranks sort their runs of CO[mu] and merge the runs they receive. Every
+ * segment [seg_off[i], seg_off[i+1]) of (keys, ids) is sorted in place by key
+ * descending, then id ascending. keys: non-negative doubles (similarities);
+ * ids: int32; seg_off: nseg+1 int64 offsets, seg_off[nseg] = total; max_len:
+ * an upper bound of every segment's length. All three arrays device memory
+ * (host pointers: SCAN_EINVAL). Synchronises `stream`. */
+int scan_sort_segments_desc(double* keys, int32_t* ids, const int64_t* seg_off, int64_t nseg,
+                            int64_t total, int64_t max_len, uintptr_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -7,7 +7,8 @@ from .scan import (COSINE, COUNTS_AUTO, COUNTS_DENSE, COUNTS_SPARSE, DEFAULT_COU
                    Q_HUBS, ScanError,
                    ScanIndex, Server, autotune_batch, count_config_for, kernel_launches,
                    last_build_timings, library_path, load, make_lsh, paper_sigma,
-                   set_count_config, set_wide_index, tuning_clear, tuning_load, tuning_save,
+                   set_count_config, set_wide_index, sort_segments_desc, tuning_clear, tuning_load,
+                   tuning_save,
                    use_torch_allocator)
 from ._build import build
 
@@ -15,5 +16,6 @@ __all__ = ["COSINE", "COUNTS_AUTO", "COUNTS_DENSE", "COUNTS_SPARSE", "DEFAULT_CO
            "JACCARD", "Q_HUBS",
            "ScanError", "ScanIndex", "Server", "autotune_batch", "build", "count_config_for",
            "kernel_launches", "last_build_timings", "library_path", "load", "make_lsh",
-           "paper_sigma", "set_count_config", "set_wide_index", "tuning_clear", "tuning_load",
+           "paper_sigma", "set_count_config", "set_wide_index", "sort_segments_desc",
+           "tuning_clear", "tuning_load",
            "tuning_save", "use_torch_allocator"]

@@ -1037,6 +1037,22 @@ int scan_tuning_load(const char* path) {
   return SCAN_OK;
 }
 
+int scan_sort_segments_desc(double* keys, int32_t* ids, const int64_t* seg_off, int64_t nseg,
+                            int64_t total, int64_t max_len, uintptr_t stream) {
+  if (nseg < 0 || total < 0 || max_len < 0) return SCAN_EINVAL;
+  if (nseg == 0 || total <= 1 || max_len <= 1) return SCAN_OK;
+  if (!keys || !ids || !seg_off) return SCAN_EINVAL;
+  if (!gscan::is_device_ptr(keys) || !gscan::is_device_ptr(ids) ||
+      !gscan::is_device_ptr(seg_off))
+    return SCAN_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  gscan::Pool pool(s);
+  GS_TRY(gscan::segmented_sort_desc(reinterpret_cast<uint64_t*>(keys), ids, seg_off, nseg, total,
+                                    max_len, pool, s));
+  GS_CUDA(cudaStreamSynchronize(s));
+  return SCAN_OK;
+}
+
 int scan_tuning_clear(void) {
   std::lock_guard<std::mutex> lk(gscan::g_tune_mu);
   gscan::g_tune_table.clear();

@@ -90,6 +90,7 @@ def load():
         "scan_tuning_save": (i32, [ctypes.c_char_p]),
         "scan_tuning_load": (i32, [ctypes.c_char_p]),
         "scan_tuning_clear": (i32, []),
+        "scan_sort_segments_desc": (i32, [P, P, P, i64, i64, i64, ctypes.c_size_t]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -148,6 +149,18 @@ def tuning_load(path: str):
 
 def tuning_clear():
     _check(load().scan_tuning_clear(), "scan_tuning_clear")
+
+
+def sort_segments_desc(keys, ids, seg_off, max_len: int = 0, stream=None):
+    """Sort every segment of (keys, ids) in place, key descending then id
+    ascending; CUDA tensors (float64, int32, int64 offsets)."""
+    nseg = int(seg_off.shape[0]) - 1
+    total = int(keys.shape[0])
+    if max_len <= 0:
+        max_len = int((seg_off[1:] - seg_off[:-1]).max().item()) if nseg > 0 else 0
+    _check(load().scan_sort_segments_desc(_ptr(keys), _ptr(ids), _ptr(seg_off), nseg, total,
+                                          int(max_len), _stream_handle(stream)),
+           "scan_sort_segments_desc")
 
 
 def paper_sigma():

@@ -1,0 +1,45 @@
+"""Device steps of the sharded build: the library's segmented sort sorts and
+merges CO runs exactly like a plain lexicographic sort, and the per-rank runs
+of a one-rank plan on the GPU give the oracle's core order."""
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+import paper_2012_11188_gb300 as gs
+from paper_2012_11188_gb300 import shard
+
+pytestmark = pytest.mark.gpu
+
+
+def test_sort_segments_matches_lexsort():
+    import torch
+    rng = np.random.default_rng(5)
+    lens = np.concatenate([rng.integers(0, 40, 300), [1, 0, 5000, 9000, 20000]])
+    off = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    keys = np.round(rng.random(off[-1]), 2)  # many ties
+    ids = rng.permutation(off[-1]).astype(np.int32)
+    want_k, want_i = keys.copy(), ids.copy()
+    for a, b in zip(off[:-1], off[1:]):
+        o = np.lexsort((want_i[a:b], -want_k[a:b]))
+        want_k[a:b], want_i[a:b] = want_k[a:b][o], want_i[a:b][o]
+    k = torch.from_numpy(keys).cuda()
+    v = torch.from_numpy(ids).cuda()
+    gs.sort_segments_desc(k, v, torch.from_numpy(off).cuda())
+    assert np.array_equal(k.cpu().numpy(), want_k) and np.array_equal(v.cpu().numpy(), want_i)
+    with pytest.raises(gs.ScanError):  # host arrays are refused
+        gs.load().scan_sort_segments_desc(keys.ctypes.data, ids.ctypes.data, off.ctypes.data,
+                                          len(lens), int(off[-1]), 20000, 0)
+
+
+def test_one_rank_plan_with_device_sorts_is_the_oracle_core_order():
+    g = graphgen.rmat(13, 16, seed=4)
+    ox = oracle.Index(g)
+    deg = np.diff(g.off)
+    mu_b = shard.mu_ranges(deg, 1)
+    ids, thr, dest, per_mu = shard.local_runs(g.off.astype(np.int64), ox.no_sim, deg, 0, g.n,
+                                              mu_b, shard.device_sort)
+    run_len = per_mu.reshape(-1, 1)
+    seg_off, mid, mthr = shard.merge_runs(ids, thr, run_len, shard.device_sort)
+    assert np.array_equal(mid, ox.co_id) and np.array_equal(mthr, ox.co_thr)
+    assert np.array_equal(seg_off, ox.co_off)
