@@ -357,54 +357,104 @@ def adjusted_rand_index(a, b):
 
 
 def lsh_quality(gs, off_d, adj_d, g, stream, timed: bool):
-    """LSH index mode on one graph: SimHash 64/256 bits for cosine and
-    k-partition MinHash k=64 for Jaccard, degree threshold 128; build time, and
-    ARI / misclassified-edge fraction against the exact index at mu=5,
-    eps in {.3, .5, .7}, with the number of clustered vertices on each side
-    (ARI is 0 whenever one side clusters nothing and the other something)."""
+    """LSH index mode on one graph under the paper's protocol (Section 7.3.4,
+    Fig. 9): the (mu, eps) of Sigma whose exact clustering has the highest
+    modularity is found by the sweep on the exact index, and the LSH index
+    is judged there by the adjusted Rand index of its clustering against the
+    exact one and by the fraction of edges whose side of eps changes.
+    SimHash 64/256 bits for cosine and k-partition MinHash 64 for Jaccard, at
+    the degree threshold T = 128 and at the paper's rule (T = k for cosine,
+    3k/2 for Jaccard, Section 6.3). Also mu = 5, eps in {.3, .5, .7} at
+    T = 128, and the phase times of each LSH build."""
+    import numpy as np
     import torch
     out = {}
     deg = (off_d[1:] - off_d[:-1])
     src = torch.repeat_interleave(torch.arange(g.n, device=off_d.device), deg)
-    approx = ((deg[src] > 128) & (deg[adj_d.long()] > 128))
-    out["approximated_edge_fraction"] = approx.sum().item() / g.arcs
+    ddst = deg[adj_d.long()]
+    dsrc = deg[src]
     del src
+    smu, seps = gs.paper_sigma()
+    phase_keys = ("orient_ms", "count_ms", "sims_ms", "neighbor_order_ms", "core_order_ms",
+                  "lsh_ms", "total_ms")
     for kind, name, ks in ((gs.COSINE, "simhash", (64, 256)), (gs.JACCARD, "minhash", (64,))):
         exact = gs.ScanIndex.build((off_d, adj_d), kind, stream=stream)
         ex_sim = torch.empty(g.arcs, dtype=torch.float64, device="cuda")
         gs.load().scan_index_export(exact._h, ex_sim.data_ptr(), None, None, None, None, None)
-        labs_exact = {e: exact.query(5, e) for e in (0.3, 0.5, 0.7)}
+        qs = exact.sweep(smu, seps, stream=stream)
+        bi = int(np.argmax(qs))
+        best_mu, best_eps = int(smu[bi]), float(seps[bi])
+        # the paper does not say which of several pairs of equal (maximal)
+        # modularity it takes: the first one in Sigma's order is the primary
+        # reading, the middle one of the ties a second
+        ties = np.nonzero(qs >= qs[bi] - 1e-12)[0]
+        mi = int(ties[len(ties) // 2])
+        mid_mu, mid_eps = int(smu[mi]), float(seps[mi])
+        lab_best = exact.query(best_mu, best_eps)
+        lab_mid = exact.query(mid_mu, mid_eps)
+        labs_fixed = {e: exact.query(5, e) for e in (0.3, 0.5, 0.7)}
         exact.free()
+        kname = "cosine" if kind == gs.COSINE else "jaccard"
+        out[f"best_{kname}"] = {"mu": best_mu, "eps": best_eps,
+                                "modularity": round(float(qs[bi]), 6),
+                                "clustered": int((lab_best >= 0).sum()),
+                                "tied_pairs": int(len(ties)),
+                                "middle_tie": {"mu": mid_mu, "eps": mid_eps}}
         for k in ks:
-            lsh = gs.make_lsh(kind, k, 128, seed=1)
-            ix = gs.ScanIndex.build((off_d, adj_d), kind, lsh=lsh, stream=stream)
-            rec = {}
-            if timed:
-                ts = []
-                for _ in range(3):
-                    ix.free()
-                    a = torch.cuda.Event(enable_timing=True)
-                    b = torch.cuda.Event(enable_timing=True)
-                    a.record(stream)
-                    ix = gs.ScanIndex.build((off_d, adj_d), kind, lsh=lsh, stream=stream)
-                    b.record(stream)
-                    b.synchronize()
-                    ts.append(a.elapsed_time(b))
-                rec = {"build_ms": round(statistics.median(ts), 2),
-                       "edges_per_s": g.edges / (statistics.median(ts) / 1000.0)}
-            ap_sim = torch.empty(g.arcs, dtype=torch.float64, device="cuda")
-            gs.load().scan_index_export(ix._h, ap_sim.data_ptr(), None, None, None, None, None)
-            for e in (0.3, 0.5, 0.7):
-                lab = ix.query(5, e)
-                flip = (ex_sim >= e) != (ap_sim >= e)
-                rec[f"eps{e}"] = {
-                    "ari": round(adjusted_rand_index(labs_exact[e], lab), 4),
+            paper_T = k if kind == gs.COSINE else 3 * k // 2
+            for rule, T in (("T128", 128), (f"paper_T{paper_T}", paper_T)):
+                lsh = gs.make_lsh(kind, k, T, seed=1)
+                ix = gs.ScanIndex.build((off_d, adj_d), kind, lsh=lsh, stream=stream)
+                rec = {"threshold": T}
+                if timed:
+                    ts, ph = [], []
+                    for _ in range(3):
+                        ix.free()
+                        a = torch.cuda.Event(enable_timing=True)
+                        b = torch.cuda.Event(enable_timing=True)
+                        a.record(stream)
+                        ix = gs.ScanIndex.build((off_d, adj_d), kind, lsh=lsh, stream=stream)
+                        b.record(stream)
+                        b.synchronize()
+                        ts.append(a.elapsed_time(b))
+                        ph.append(gs.last_build_timings())
+                    rec.update({"build_ms": round(statistics.median(ts), 2),
+                                "edges_per_s": g.edges / (statistics.median(ts) / 1000.0),
+                                "phases_ms": {key: round(statistics.median(getattr(p, key)
+                                                                           for p in ph), 2)
+                                              for key in phase_keys}})
+                ap_sim = torch.empty(g.arcs, dtype=torch.float64, device="cuda")
+                gs.load().scan_index_export(ix._h, ap_sim.data_ptr(), None, None, None, None,
+                                            None)
+                approx = (dsrc > T) & (ddst > T)
+                n_approx = int(approx.sum().item())
+                lab = ix.query(best_mu, best_eps)
+                flip = (ex_sim >= best_eps) != (ap_sim >= best_eps)
+                rec["at_best"] = {
+                    "ari": round(adjusted_rand_index(lab_best, lab), 4),
                     "misclassified_edge_fraction": flip.sum().item() / g.arcs,
-                    "clustered_exact": int((labs_exact[e] >= 0).sum()),
+                    "misclassified_of_approximated": (flip & approx).sum().item() / max(n_approx, 1),
+                    "clustered_exact": int((lab_best >= 0).sum()),
                     "clustered_lsh": int((lab >= 0).sum())}
-            ix.free()
-            del ap_sim
-            out[f"{name}_k{k}"] = rec
+                if len(ties) > 1:
+                    lab = ix.query(mid_mu, mid_eps)
+                    flip = (ex_sim >= mid_eps) != (ap_sim >= mid_eps)
+                    rec["at_middle_tie"] = {
+                        "ari": round(adjusted_rand_index(lab_mid, lab), 4),
+                        "misclassified_edge_fraction": flip.sum().item() / g.arcs}
+                rec["approximated_edge_fraction"] = n_approx / g.arcs
+                if rule == "T128":
+                    for e in (0.3, 0.5, 0.7):
+                        lab = ix.query(5, e)
+                        flip = (ex_sim >= e) != (ap_sim >= e)
+                        rec[f"mu5_eps{e}"] = {
+                            "ari": round(adjusted_rand_index(labs_fixed[e], lab), 4),
+                            "misclassified_edge_fraction": flip.sum().item() / g.arcs,
+                            "clustered_exact": int((labs_fixed[e] >= 0).sum()),
+                            "clustered_lsh": int((lab >= 0).sum())}
+                ix.free()
+                del ap_sim
+                out[f"{name}_k{k}_{rule}"] = rec
         del ex_sim
     return out
 
