@@ -54,6 +54,9 @@ def parse():
     p.add_argument("--weighted-only", type=int, default=0, metavar="SCALE",
                    help="only the weighted section, on R-MAT of this scale (a profiling case); "
                         "prints that section, not the benchmark line")
+    p.add_argument("--dense-only", type=int, default=0, metavar="N",
+                   help="only the dense section, on one Erdos-Renyi graph of N vertices and "
+                        "average degree N/5 (a profiling case); prints that section")
     p.add_argument("--batch-graphs", type=int, default=2048)
     p.add_argument("--serve-queries", type=int, default=100000)
     return p.parse_args()
@@ -469,7 +472,7 @@ def dense_tile_flops(n: int) -> int:
     return tiles * 2 * 128 * 256 * np_
 
 
-def bench_dense(gs, kind: int, seed: int, stream):
+def bench_dense(gs, kind: int, seed: int, stream, shapes=None):
     """Dense graphs shaped like the paper's blood vessel and cochlea graphs
     (n = 25,825, average degree 5.4K and 21.9K), as Erdos-Renyi graphs: the
     closed counts from one hand-written tcgen05 bf16 GEMM ((A+I)^2, Section
@@ -479,8 +482,8 @@ def bench_dense(gs, kind: int, seed: int, stream):
     import graphgen
     import torch
     out = {}
-    for name, avg in (("blood_vessel_like", 5400), ("cochlea_like", 21900)):
-        n = 25825
+    for name, n, avg in shapes or (("blood_vessel_like", 25825, 5400),
+                                   ("cochlea_like", 25825, 21900)):
         p = avg / (n - 1)
         t0 = time.perf_counter()
         g = graphgen.sbm(n, 1, p, p, seed=seed)
@@ -693,6 +696,11 @@ def main():
     import graphgen
     import paper_2012_11188_gb300 as gs
 
+    if args.dense_only:
+        n = args.dense_only
+        print(json.dumps(bench_dense(gs, gs.COSINE, args.seed, torch.cuda.current_stream(),
+                                     shapes=((f"er_n{n}", n, n // 5),))))
+        return 0
     if args.weighted_only:
         print(json.dumps(bench_weighted(gs, args.seed, torch.cuda.current_stream(),
                                         rmat_scale=args.weighted_only, blood_vessel=False)))

@@ -8,7 +8,8 @@
 // byte-swizzled K-slices of (A+I) into a 4-stage shared-memory ring, one
 // thread issues tcgen05.mma (bf16 x bf16 -> fp32, 128 x 256 tiles) into one
 // of two TMEM accumulators, and four epilogue warps read the other with
-// tcgen05.ld while the next tile is being multiplied. (A+I) is symmetric, so
+// tcgen05.ld while the next tile is being multiplied (two groups of four
+// epilogue warps, one per accumulator buffer). (A+I) is symmetric, so
 // the product is too, and only the tiles that hold some pair u < v are
 // computed. The epilogue never writes the n x n product: it reads, for the
 // arcs that fall in the tile, their counts and writes the similarity of both
@@ -34,12 +35,14 @@ constexpr int STAGES = 4;
 constexpr int A_BYTES = BM * BK * 2;              // 16 KB
 constexpr int B_BYTES = BN * BK * 2;              // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;    // 48 KB
-constexpr int CHUNK = 16;                         // accumulator columns per epilogue step
-constexpr int EPI_WARPS = 4;
-constexpr int THREADS = 64 + 32 * EPI_WARPS;      // producer, MMA, 4 epilogue warps
+constexpr int CHUNK = 8;                          // accumulator columns per epilogue step
+constexpr int EPI_WARPS = 4;                      // warps of one epilogue group (4 lane quadrants)
+constexpr int EPI_GROUPS = 2;                     // group g drains TMEM buffer g (tiles it % 2 == g)
+constexpr int THREADS = 64 + 32 * EPI_WARPS * EPI_GROUPS;  // producer, MMA, epilogue groups
 constexpr int CNT_PITCH = CHUNK + 1;              // padded row of the count staging
+constexpr size_t EPI_SMEM = (size_t)BM * CNT_PITCH * 4 + (size_t)BM * CHUNK * 8;  // per group
 constexpr size_t SMEM_BYTES = 1024 /* alignment slack */ + (size_t)STAGES * STAGE_BYTES +
-                              (size_t)BM * CNT_PITCH * 4 + (size_t)BM * CHUNK * 8 + 256;
+                              EPI_GROUPS * EPI_SMEM + 256;
 // The matrices are np x np with np = n rounded up to DENSE_PAD: zero rows
 // and columns leave the n x n block of the product unchanged.
 constexpr int64_t DENSE_PAD = 256;
@@ -130,21 +133,19 @@ __device__ __forceinline__ void tc_fence_before() {
 __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
-// 16 consecutive 32-bit accumulator columns of this thread's TMEM lane
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+// 8 consecutive 32-bit accumulator columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
+        "=r"(r[7])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
-// Named barrier of the epilogue warps (non-aligned form: the threads arrive
-// from divergent loops).
-__device__ __forceinline__ void epi_barrier() {
-  asm volatile("barrier.sync 1, %0;" ::"n"(32 * EPI_WARPS) : "memory");
+// Named barrier of one epilogue group (non-aligned form: the threads arrive
+// from divergent loops); group g uses barriers 1 + 2g (sync) and 2 + 2g (vote).
+__device__ __forceinline__ void epi_barrier(int id) {
+  asm volatile("barrier.sync %0, %1;" ::"r"(id), "n"(32 * EPI_WARPS) : "memory");
 }
 
 __device__ __forceinline__ double sim_from(int kind, int64_t c, int64_t du, int64_t dv) {
@@ -209,8 +210,9 @@ struct DenseArgs {
 };
 
 // Persistent GEMM + similarity epilogue. Warp 0 loads (TMA), warp 1 issues
-// the MMAs (one elected thread) and owns the TMEM allocation, warps 2-5 are
-// the epilogue; warp w reads TMEM lanes 32*(w%4) .. +31 (tile rows).
+// the MMAs (one elected thread) and owns the TMEM allocation, warps 2-5 and
+// 6-9 are two epilogue groups, each draining one of the two accumulator
+// buffers; warp w reads TMEM lanes 32*(w%4) .. +31 (tile rows).
 __global__ void __launch_bounds__(THREADS, 1)
 k_dense_mma(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
             const DenseArgs a) {
@@ -219,9 +221,8 @@ k_dense_mma(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ C
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint8_t* stage_a = smem;                                  // STAGES x A_BYTES
   uint8_t* stage_b = smem + (size_t)STAGES * A_BYTES;       // STAGES x B_BYTES
-  uint32_t* s_cnt = reinterpret_cast<uint32_t*>(smem + (size_t)STAGES * STAGE_BYTES);
-  int64_t* s_pos = reinterpret_cast<int64_t*>(s_cnt + BM * CNT_PITCH);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(s_pos + BM * CHUNK);
+  uint8_t* epi_smem = smem + (size_t)STAGES * STAGE_BYTES;   // EPI_GROUPS x EPI_SMEM
+  uint64_t* bars = reinterpret_cast<uint64_t*>(epi_smem + EPI_GROUPS * EPI_SMEM);
   uint64_t* full = bars;                 // STAGES
   uint64_t* empty = bars + STAGES;       // STAGES
   uint64_t* acc_full = bars + 2 * STAGES;      // 2
@@ -320,14 +321,20 @@ k_dense_mma(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ C
       }
     }
   } else {
-    // ---- epilogue: warp w owns TMEM lanes 32*(w%4) .. +31
+    // ---- epilogue: group g = (w-2)/4 drains TMEM buffer g, i.e. the tiles
+    // of odd or even iteration; warp w owns TMEM lanes 32*(w%4) .. +31
+    const int grp = (warp - 2) / EPI_WARPS;
     const int q = warp & 3;
-    const int r_loc = 32 * q + lane;         // row of the tile
-    const int et = threadIdx.x - 64;         // 0..127 across the epilogue warps
+    const int r_loc = 32 * q + lane;                          // row of the tile
+    const int et = threadIdx.x - 64 - 32 * EPI_WARPS * grp;   // 0..127 in the group
+    const int bar_sync = 1 + 2 * grp, bar_vote = 2 + 2 * grp;
+    uint32_t* s_cnt = reinterpret_cast<uint32_t*>(epi_smem + grp * EPI_SMEM);
+    int64_t* s_pos = reinterpret_cast<int64_t*>(s_cnt + BM * CNT_PITCH);
     int it = 0;
     bool ok = true;
     for (int64_t t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x, ++it) {
       const int buf = it & 1;
+      if (buf != grp) continue;
       const uint32_t use = (uint32_t)(it >> 1);
       const uint32_t tl = a.tiles[t];
       const int64_t bi = tl >> 16, bj = tl & 0xFFFFu;
@@ -346,18 +353,18 @@ k_dense_mma(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ C
       uint32_t all_ok;
       asm volatile(
           "{\n .reg .pred pi, po;\n setp.ne.u32 pi, %1, 0;\n"
-          " barrier.red.and.pred po, 2, %2, pi;\n selp.u32 %0, 1, 0, po;\n}\n"
+          " barrier.red.and.pred po, %2, %3, pi;\n selp.u32 %0, 1, 0, po;\n}\n"
           : "=r"(all_ok)
-          : "r"(w_ok), "n"(32 * EPI_WARPS)
+          : "r"(w_ok), "r"(bar_vote), "n"(32 * EPI_WARPS)
           : "memory");
       if (!all_ok) { ok = false; break; }
       tc_fence_after();
       const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * BN);
       for (int c = 0; c < BN / CHUNK; ++c) {
         const int64_t c0 = j0 + (int64_t)c * CHUNK;
-        uint32_t r[16];
+        uint32_t r[CHUNK];
         __syncwarp();
-        tmem_ld16(tbase + (uint32_t)(c * CHUNK), r);
+        tmem_ld8(tbase + (uint32_t)(c * CHUNK), r);
 #pragma unroll
         for (int x = 0; x < CHUNK; ++x)
           s_cnt[r_loc * CNT_PITCH + x] = (uint32_t)__uint_as_float(r[x]);
@@ -368,18 +375,18 @@ k_dense_mma(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ C
           if (j > i) s_pos[r_loc * CHUNK + (j - c0)] = cur;
           ++cur;
         }
-        epi_barrier();
+        epi_barrier(bar_sync);
         // column pass: for column j, the arcs (j, x) with x in the tile's rows
         // and x < j; each edge x < j gets its similarity once, written to both
-        // arcs. 8 threads per column.
+        // arcs. 16 threads per column.
         {
-          const int jc = et >> 3, sub = et & 7;
+          const int jc = et >> 4, sub = et & 15;
           const int64_t j = c0 + jc;
           if (j < a.n && j > i0) {
             const int64_t* bp = a.bpos + j * (a.nb + 1);
             const int64_t p0 = bp[bi], p1 = bp[bi + 1];
             const int64_t dj = a.deg[j];
-            for (int64_t p = p0 + sub; p < p1; p += 8) {
+            for (int64_t p = p0 + sub; p < p1; p += 16) {
               const int32_t x = a.adj[p];
               if (x >= j) break;
               const int xl = (int)(x - i0);
@@ -394,7 +401,7 @@ k_dense_mma(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ C
             }
           }
         }
-        epi_barrier();
+        epi_barrier(bar_sync);
       }
       tc_fence_before();
       __syncwarp();
