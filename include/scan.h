@@ -241,6 +241,13 @@ const char* scan_strerror(int status);
  * Also the duration of the dominant (counting) kernel. */
 int scan_last_build_timings(double* ms7);
 
+/* Duration (ms, CUDA events on the build's stream) of the last exact build's
+ * CTA counting kernel on this thread: the oriented triangle enumeration over
+ * the rows whose out-lists sit in a shared-memory table (Section 6.1 and the
+ * hash intersection of Algorithm 1), the bulk of the counting step; 0 if the
+ * last build did not run it. */
+int scan_last_count_kernel_ms(double* ms);
+
 /* Test hook for the index width of the counting kernels. Graphs with at
  * least 2^31 arcs are counted with 64-bit element indices and 32-bit (u,w)
  * counters; smaller ones with 32-bit indices and 16-bit counters. With

@@ -102,6 +102,8 @@ void dev_free(void* p, size_t bytes, cudaStream_t s) {
   cudaFreeAsync(p, s);
 }
 
+void record_kernel_ms(double ms) { g_timings[7] = ms; }
+
 void record_timings(const double* ms7) {
   for (int i = 0; i < 7; ++i) g_timings[i] = ms7[i];
 }
@@ -887,6 +889,12 @@ int scan_kernel_launches(uint64_t* count) {
 int scan_last_build_timings(double* ms7) {
   if (!ms7) return SCAN_EINVAL;
   for (int i = 0; i < 7; ++i) ms7[i] = g_timings[i];
+  return SCAN_OK;
+}
+
+int scan_last_count_kernel_ms(double* ms) {
+  if (!ms) return SCAN_EINVAL;
+  *ms = g_timings[7];
   return SCAN_OK;
 }
 

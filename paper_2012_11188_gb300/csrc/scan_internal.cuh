@@ -228,8 +228,10 @@ int exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, Pool& 
 // device); grids are sized in multiples of it.
 int sm_count();
 
-// Per-thread record of the last build's phase timings.
+// Per-thread record of the last build's phase timings, and of the duration
+// of its CTA counting kernel (k_triangles over the shared-table rows).
 void record_timings(const double* ms7);
+void record_kernel_ms(double ms);
 
 // scan_set_wide_index: counting with 64-bit element indices at any size.
 bool force_wide_index();

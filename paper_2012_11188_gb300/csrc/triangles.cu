@@ -931,7 +931,7 @@ int launch_counting(const int64_t* off, const int32_t* adj, const int32_t* deg, 
                     unsigned long long* work, int lsh_T, int32_t max_od, int64_t* deferred,
                     unsigned long long* n_deferred, uint32_t* tcnt, uint32_t* tc16, int32_t* twin,
                     unsigned* status, const double* ow, double* tsum, const CountCfg& cfg,
-                    cudaStream_t s) {
+                    cudaStream_t s, cudaEvent_t k0 = nullptr, cudaEvent_t k1 = nullptr) {
   int od_cap = 16;
   while (od_cap < max_od && od_cap < SMEM_OD_MAX) od_cap <<= 1;
   // the table (12 bytes per slot, 2 * od_cap slots) and the counters (4 bytes)
@@ -945,10 +945,12 @@ int launch_counting(const int64_t* off, const int32_t* adj, const int32_t* deg, 
   GS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_triangles<false, IT, WT, R>,
                                                         TRI_THREADS, smem));
   if (per_sm < 1) per_sm = 1;
+  if (k0) GS_CUDA(cudaEventRecord(k0, s));
   k_triangles<false, IT, WT, R><<<sms * per_sm, TRI_THREADS, smem, s>>>(
       off, adj, deg, odeg, oadj, okey, odp, n, item_off, order, work, lsh_T, cfg.cta_chunk,
       cfg.long_list, od_cap, deferred, n_deferred, false, tcnt, tc16, twin, status, ow, tsum);
   GS_LAUNCH();
+  if (k1) GS_CUDA(cudaEventRecord(k1, s));
   int small_per_sm = 1;
   GS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&small_per_sm, k_tri_small<IT, WT, R>,
                                                         SW_WARPS * 32, 0));
@@ -976,14 +978,15 @@ int launch_counting_cfg(const int64_t* off, const int32_t* adj, const int32_t* d
                         const int32_t* order, unsigned long long* work, int lsh_T, int32_t max_od,
                         int64_t* deferred, unsigned long long* n_deferred, uint32_t* tcnt,
                         uint32_t* tc16, int32_t* twin, unsigned* status, const double* ow,
-                        double* tsum, const CountCfg& cfg, cudaStream_t s) {
+                        double* tsum, const CountCfg& cfg, cudaStream_t s, cudaEvent_t k0,
+                        cudaEvent_t k1) {
   if (!WT && cfg.rounds == 8)
     return launch_counting<IT, WT, 8>(off, adj, deg, odeg, oadj, okey, odp, n, item_off, order,
                                       work, lsh_T, max_od, deferred, n_deferred, tcnt, tc16, twin,
-                                      status, ow, tsum, cfg, s);
+                                      status, ow, tsum, cfg, s, k0, k1);
   return launch_counting<IT, WT, 4>(off, adj, deg, odeg, oadj, okey, odp, n, item_off, order,
                                     work, lsh_T, max_od, deferred, n_deferred, tcnt, tc16, twin,
-                                    status, ow, tsum, cfg, s);
+                                    status, ow, tsum, cfg, s, k0, k1);
 }
 
 int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* adj,
@@ -1044,9 +1047,13 @@ int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* a
     GS_LAUNCH();
   }
   GS_TRY(exclusive_scan_i32_to_i64(items_sorted, item_off, n, pool, s));
-  cudaEvent_t e0, e1;
+  cudaEvent_t e0, e1, k0 = nullptr, k1 = nullptr;
   GS_CUDA(cudaEventCreate(&e0));
   GS_CUDA(cudaEventCreate(&e1));
+  if (count_ms) {  // the CTA counting kernel alone, for its roofline
+    GS_CUDA(cudaEventCreate(&k0));
+    GS_CUDA(cudaEventCreate(&k1));
+  }
   GS_CUDA(cudaEventRecord(e0, s));
   const int64_t ch = (int64_t)EXPAND_T * EXPAND_ITEMS;
   const unsigned egrid =
@@ -1066,20 +1073,20 @@ int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* a
       if (narrow) {
         GS_TRY((launch_counting_cfg<int32_t, true>(off, adj, deg, odeg, oadj, okey, odp, n, item_off,
                                                order, work, lsh_T, max_od, deferred, work + 3,
-                                               tcnt, tc16, twin, status, ow, tsum, cfg, s)));
+                                               tcnt, tc16, twin, status, ow, tsum, cfg, s, k0, k1)));
       } else {
         GS_TRY((launch_counting_cfg<int64_t, true>(off, adj, deg, odeg, oadj, okey, odp, n, item_off,
                                                order, work, lsh_T, max_od, deferred, work + 3,
-                                               tcnt, nullptr, twin, status, ow, tsum, cfg, s)));
+                                               tcnt, nullptr, twin, status, ow, tsum, cfg, s, k0, k1)));
       }
     } else if (narrow) {
       GS_TRY((launch_counting_cfg<int32_t, false>(off, adj, deg, odeg, oadj, okey, odp, n, item_off,
                                               order, work, lsh_T, max_od, deferred, work + 3, tcnt,
-                                              tc16, twin, status, nullptr, nullptr, cfg, s)));
+                                              tc16, twin, status, nullptr, nullptr, cfg, s, k0, k1)));
     } else {
       GS_TRY((launch_counting_cfg<int64_t, false>(off, adj, deg, odeg, oadj, okey, odp, n, item_off,
                                               order, work, lsh_T, max_od, deferred, work + 3, tcnt,
-                                              nullptr, twin, status, nullptr, nullptr, cfg, s)));
+                                              nullptr, twin, status, nullptr, nullptr, cfg, s, k0, k1)));
     }
   }
   GS_CUDA(cudaEventRecord(e1, s));
@@ -1099,6 +1106,14 @@ int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* a
   if (count_ms) {
     GS_CUDA(cudaEventSynchronize(e1));
     GS_CUDA(cudaEventElapsedTime(count_ms, e0, e1));
+    float kms = 0;
+    if (n > 0 && m > 0 && cudaEventElapsedTime(&kms, k0, k1) == cudaSuccess)
+      record_kernel_ms(kms);
+    else
+      record_kernel_ms(0);
+    cudaGetLastError();
+    cudaEventDestroy(k0);
+    cudaEventDestroy(k1);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -82,6 +82,7 @@ def load():
         "scan_index_free": (None, [P]),
         "scan_strerror": (ctypes.c_char_p, [i32]),
         "scan_last_build_timings": (i32, [P]),
+        "scan_last_count_kernel_ms": (i32, [P]),
         "scan_kernel_launches": (i32, [P]),
         "scan_set_wide_index": (i32, [i32]),
         "scan_set_count_config": (i32, [P]),
@@ -299,6 +300,13 @@ def set_wide_index(on: bool) -> None:
     """Test hook: count with 64-bit element indices (the path of graphs with
     at least 2**31 arcs) at every size, process-wide."""
     _check(load().scan_set_wide_index(1 if on else 0), "scan_set_wide_index")
+
+
+def last_count_kernel_ms() -> float:
+    """Duration of the last build's CTA counting kernel (CUDA events)."""
+    v = ctypes.c_double()
+    _check(load().scan_last_count_kernel_ms(ctypes.byref(v)), "scan_last_count_kernel_ms")
+    return v.value
 
 
 def last_build_timings() -> BuildTimings:
