@@ -8,10 +8,10 @@
 // does not depend on stability: equal similarities come out in ascending id,
 // the tie rule of the paper's deterministic experiments.
 //
-// Segments are bucketed by length: <= 32 (one warp, one element per lane),
-// <= 256 (one warp, bitonic network on up to 8 elements per lane in
-// registers), <= 4096 (one CTA: 8-element register sorts, then merge-path
-// levels in shared memory), longer (8192-element tiles sorted by one CTA the
+// Segments are bucketed by length: <= 32 (one warp, one element per lane,
+// bitonic network across lanes), <= 256, <= 1024 and <= 4096 (one CTA of
+// 32, 128 or 512 threads: 8-element register sorts, then merge-path levels
+// in shared memory), longer (8192-element tiles sorted by one CTA the
 // same way, then merge-path passes over global memory that double the run
 // length, ping-ponging between the data and a scratch buffer; a pass costs
 // about one read and one write of the data).
@@ -21,7 +21,7 @@ namespace gscan {
 
 namespace {
 
-constexpr int WTILE = 256;   // one warp sorts up to this many elements in registers
+constexpr int WTILE = 256;   // rows up to this length are sorted by a one-warp CTA
 constexpr int TILE = 8192;   // tiles of long segments (one CTA of 1024 threads each)
 constexpr int NCLASS = 5;    // <=32, <=256, <=1024, <=4096, >4096
 
@@ -111,99 +111,6 @@ __global__ void k_sort_warp(uint64_t* __restrict__ key, int32_t* __restrict__ va
       }
     }
     if (lane < len) { key[b + lane] = k; val[b + lane] = v; }
-  }
-}
-
-// Warp-level bitonic sort of 32*RI elements held in registers, blocked: lane l
-// holds elements RI*l .. RI*l+RI-1. Strides below RI compare inside a thread,
-// larger ones exchange with lane l ^ (stride/RI) by shuffles; no shared memory
-// and no barrier, so every warp sorts its own segment or tile.
-template <int J, int RI>
-__device__ __forceinline__ void reg_stage(uint64_t (&K)[RI], int32_t (&V)[RI], int lane, int k) {
-#pragma unroll
-  for (int r = 0; r < RI; ++r) {
-    const int rp = r ^ J;
-    if (rp > r) {
-      const bool asc = ((RI * lane + r) & k) == 0;  // r is the lower index of the pair
-      const bool swap = asc ? before(K[rp], V[rp], K[r], V[r]) : before(K[r], V[r], K[rp], V[rp]);
-      if (swap) {
-        const uint64_t tk = K[r]; K[r] = K[rp]; K[rp] = tk;
-        const int32_t tv = V[r]; V[r] = V[rp]; V[rp] = tv;
-      }
-    }
-  }
-}
-
-template <int RI>
-__device__ __forceinline__ void warp_sort_reg(uint64_t (&K)[RI], int32_t (&V)[RI], int lane) {
-  static_assert(RI == 1 || RI == 2 || RI == 4 || RI == 8 || RI == 16 || RI == 32,
-                "elements per lane: a power of two up to 32");
-  constexpr int S = 32 * RI;
-#pragma unroll
-  for (int k = 2; k <= S; k <<= 1) {
-#pragma unroll
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      if (j >= RI) {
-#pragma unroll
-        for (int r = 0; r < RI; ++r) {
-          const uint64_t pk = __shfl_xor_sync(0xffffffffu, K[r], j / RI);
-          const int32_t pv = __shfl_xor_sync(0xffffffffu, V[r], j / RI);
-          const int i = RI * lane + r;
-          const bool asc = (i & k) == 0, low = (i & j) == 0;
-          const bool partner_first = before(pk, pv, K[r], V[r]);
-          if (partner_first == (low == asc)) { K[r] = pk; V[r] = pv; }
-        }
-      } else if (j == 16) {
-        if constexpr (RI > 16) reg_stage<16, RI>(K, V, lane, k);
-      } else if (j == 8) {
-        if constexpr (RI > 8) reg_stage<8, RI>(K, V, lane, k);
-      } else if (j == 4) {
-        if constexpr (RI > 4) reg_stage<4, RI>(K, V, lane, k);
-      } else if (j == 2) {
-        if constexpr (RI > 2) reg_stage<2, RI>(K, V, lane, k);
-      } else {
-        if constexpr (RI > 1) reg_stage<1, RI>(K, V, lane, k);
-      }
-    }
-  }
-}
-
-template <int RI>
-__device__ __forceinline__ void warp_sort_range(uint64_t* __restrict__ key, int32_t* __restrict__ val,
-                                                int64_t b, int64_t len, int lane) {
-  uint64_t K[RI];
-  int32_t V[RI];
-#pragma unroll
-  for (int r = 0; r < RI; ++r) {
-    const int64_t i = RI * lane + r;
-    if (i < len) { K[r] = key[b + i]; V[r] = val[b + i]; }
-    else { K[r] = 0; V[r] = SENT_V; }
-  }
-  warp_sort_reg<RI>(K, V, lane);
-#pragma unroll
-  for (int r = 0; r < RI; ++r) {
-    const int64_t i = RI * lane + r;
-    if (i < len) { key[b + i] = K[r]; val[b + i] = V[r]; }
-  }
-}
-
-
-// One warp per segment of 33..256 elements, sorted at the next power of two.
-__global__ void __launch_bounds__(256, 4)
-k_sort_warp_reg(uint64_t* __restrict__ key, int32_t* __restrict__ val,
-                const int64_t* __restrict__ seg_off, const int64_t* __restrict__ list,
-                const unsigned long long* __restrict__ count_ptr) {
-  const int lane = threadIdx.x & 31;
-  const int64_t cnt = (int64_t)*count_ptr;
-  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t u = w0; u < cnt; u += nw) {
-    const int64_t sg = list[u];
-    const int64_t b = seg_off[sg];
-    const int64_t len = seg_off[sg + 1] - b;
-    if (len <= 64) warp_sort_range<2>(key, val, b, len, lane);
-    else if (len <= 128) warp_sort_range<4>(key, val, b, len, lane);
-    else warp_sort_range<8>(key, val, b, len, lane);
   }
 }
 
@@ -628,8 +535,11 @@ int segmented_sort_desc(uint64_t* key, int32_t* val, const int64_t* seg_off, int
     GS_LAUNCH();
   }
   if (hc[1]) {
-    k_sort_warp_reg<<<grid_of((int64_t)hc[1], 8), 256, 0, s>>>(key, val, seg_off, list + base[1],
-                                                                counts + 1);
+    // 33..256 elements: one 32-thread CTA per row (8-element register
+    // networks and merge levels: compact code, unlike fully unrolled bitonic
+    // networks, whose instruction footprint stalls the warp on fetches)
+    k_sort_tile<32, false><<<grid_of((int64_t)hc[1], 1), 32, tile_smem_bytes<32>(), s>>>(
+        key, val, seg_off, list + base[1], counts + 1, nullptr, 0, nullptr, nullptr);
     GS_LAUNCH();
   }
   GS_CUDA(cudaFuncSetAttribute(k_merge_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
