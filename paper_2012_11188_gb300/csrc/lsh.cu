@@ -166,11 +166,12 @@ k_minhash(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
   }
 }
 
-// Overwrite the similarity of every approximated arc (warp per sketched vertex).
-__global__ void k_lsh_sims(int scheme, const int64_t* __restrict__ off,
-                           const int32_t* __restrict__ adj, const int32_t* __restrict__ row,
-                           const int32_t* __restrict__ hlist, int64_t nH, int k, int kpartition,
-                           const uint64_t* __restrict__ sig, const uint32_t* __restrict__ mh,
+// SimHash estimates: overwrite the similarity of every approximated arc
+// (warp per sketched vertex, lane per arc; a signature of k/64 words is one
+// 32-byte sector at k = 256).
+__global__ void k_lsh_sims(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+                           const int32_t* __restrict__ row, const int32_t* __restrict__ hlist,
+                           int64_t nH, int k, const uint64_t* __restrict__ sig,
                            const double* __restrict__ costab, double* __restrict__ sim_csr) {
   const int lane = threadIdx.x & 31;
   const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -181,24 +182,54 @@ __global__ void k_lsh_sims(int scheme, const int64_t* __restrict__ off,
     for (int64_t j = off[u] + lane; j < off[u + 1]; j += 32) {
       const int32_t r = row[adj[j]];
       if (r < 0) continue;
-      double est;
-      if (scheme == 0) {
-        int ham = 0;
-        for (int w = 0; w < W; ++w) ham += __popcll(sig[h * W + w] ^ sig[(int64_t)r * W + w]);
-        est = costab[ham];
+      int ham = 0;
+      for (int w = 0; w < W; ++w) ham += __popcll(sig[h * W + w] ^ sig[(int64_t)r * W + w]);
+      sim_csr[j] = costab[ham];
+    }
+  }
+}
+
+// MinHash estimates, lane per arc (warp per sketched vertex): equal
+// non-empty bins and bins empty in both; a sketch row whose length is a
+// multiple of 4 is read as 16-byte vectors, so that the loads of one arc are
+// independent and in flight together.
+__device__ __forceinline__ void mh_bin(uint32_t x, uint32_t y, int& match, int& both_empty) {
+  if (x == 0xFFFFFFFFu && y == 0xFFFFFFFFu) ++both_empty;
+  else if (x == y) ++match;
+}
+
+__global__ void k_minhash_sims(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+                               const int32_t* __restrict__ row, const int32_t* __restrict__ hlist,
+                               int64_t nH, int k, int kpartition, const uint32_t* __restrict__ mh,
+                               double* __restrict__ sim_csr) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const bool vec = (k & 3) == 0;
+  for (int64_t h = w0; h < nH; h += nw) {
+    const int32_t u = hlist[h];
+    for (int64_t j = off[u] + lane; j < off[u + 1]; j += 32) {
+      const int32_t r = row[adj[j]];
+      if (r < 0) continue;
+      int match = 0, both_empty = 0;
+      if (vec) {
+        const uint4* a4 = reinterpret_cast<const uint4*>(mh + h * k);
+        const uint4* b4 = reinterpret_cast<const uint4*>(mh + (int64_t)r * k);
+#pragma unroll 16
+        for (int t = 0; t < k / 4; ++t) {
+          const uint4 x = a4[t], y = b4[t];
+          mh_bin(x.x, y.x, match, both_empty);
+          mh_bin(x.y, y.y, match, both_empty);
+          mh_bin(x.z, y.z, match, both_empty);
+          mh_bin(x.w, y.w, match, both_empty);
+        }
       } else {
-        int match = 0, both_empty = 0;
         const uint32_t* a = mh + h * k;
         const uint32_t* bb = mh + (int64_t)r * k;
-        for (int t = 0; t < k; ++t) {
-          const uint32_t x = a[t], y = bb[t];
-          if (x == 0xFFFFFFFFu && y == 0xFFFFFFFFu) ++both_empty;
-          else if (x == y) ++match;
-        }
-        const int denom = kpartition ? k - both_empty : k;
-        est = denom > 0 ? __ddiv_rn((double)match, (double)denom) : 0.0;
+        for (int t = 0; t < k; ++t) mh_bin(a[t], bb[t], match, both_empty);
       }
-      sim_csr[j] = est;
+      const int denom = kpartition ? k - both_empty : k;
+      sim_csr[j] = denom > 0 ? __ddiv_rn((double)match, (double)denom) : 0.0;
     }
   }
 }
@@ -272,7 +303,7 @@ int lsh_apply(const scan_lsh_params& p, int kind, const int64_t* off, const int3
       k_simhash<false><<<gh, SH_T, smem, s>>>(off, adj, n, hlist, nH, W, key, nullptr, sig);
     }
     GS_LAUNCH();
-    k_lsh_sims<<<gw, 256, 0, s>>>(0, off, adj, row, hlist, nH, k, 0, sig, nullptr, tab, sim_csr);
+    k_lsh_sims<<<gw, 256, 0, s>>>(off, adj, row, hlist, nH, k, sig, tab, sim_csr);
     GS_LAUNCH();
     GS_CUDA(cudaStreamSynchronize(s));  // the host table must outlive the copy
     pool.put(sig);
@@ -286,8 +317,8 @@ int lsh_apply(const scan_lsh_params& p, int kind, const int64_t* off, const int3
     if (!mh) return SCAN_ENOMEM;
     k_minhash<<<gh, 256, 0, s>>>(off, adj, hlist, nH, k, L, p.minhash_kpartition, key, mh);
     GS_LAUNCH();
-    k_lsh_sims<<<gw, 256, 0, s>>>(1, off, adj, row, hlist, nH, k, p.minhash_kpartition, nullptr,
-                                  mh, nullptr, sim_csr);
+    k_minhash_sims<<<gw, 256, 0, s>>>(off, adj, row, hlist, nH, k, p.minhash_kpartition, mh,
+                                      sim_csr);
     GS_LAUNCH();
     pool.put(mh);
   }
