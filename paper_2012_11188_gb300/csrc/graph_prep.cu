@@ -162,19 +162,25 @@ __global__ void k_orient_inplace(const int64_t* __restrict__ off, const int32_t*
       if (lane == 0) long_rows[atomicAdd(n_long, 1u)] = (int32_t)v;
       continue;
     }
-    int64_t w = b;
+    int64_t w = b, wi = 0;  // out-arcs placed from the front, in-arcs from the back
     for (int64_t i0 = b; i0 < e; i0 += 32) {
       const int64_t i = i0 + lane;
       bool up = false;
       int32_t x = 0;
       if (i < e) { x = adj[i]; up = lower(dv, (int32_t)v, deg[x], x); }
       const unsigned m = __ballot_sync(0xffffffffu, up);
+      const int before = __popc(m & ((1u << lane) - 1u));
       if (up) {
-        const int64_t dst = w + __popc(m & ((1u << lane) - 1u));
+        const int64_t dst = w + before;
+        oadj[dst] = x;
+        opos[dst] = (int32_t)(i - b);
+      } else if (i < e) {
+        const int64_t dst = e - 1 - (wi + (lane - before));
         oadj[dst] = x;
         opos[dst] = (int32_t)(i - b);
       }
       w += __popc(m);
+      wi += min((int64_t)32, e - i0) - __popc(m);
     }
     if (lane == 0) od[v] = (int32_t)(w - b);
     local_sum += (unsigned long long)(w - b);
@@ -188,7 +194,8 @@ __global__ void k_orient_inplace(const int64_t* __restrict__ off, const int32_t*
 
 // One CTA per listed long row: chunks of LONG_T positions, the out-arcs of a
 // chunk placed by a block-wide prefix count (ballots, then a scan of the 32
-// warp counts), so the out-list stays in id order.
+// warp counts), so the out-list stays in id order; the in-arcs fill the rest
+// of the row from its end.
 __global__ void __launch_bounds__(LONG_T)
 k_orient_long(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
               const int32_t* __restrict__ deg, const int32_t* __restrict__ long_rows,
@@ -202,7 +209,7 @@ k_orient_long(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
     const int32_t v = long_rows[r];
     const int64_t b = off[v], e = off[v + 1];
     const int32_t dv = deg[v];
-    int64_t w = b;
+    int64_t w = b, wi = 0;  // out-arcs placed from the front, in-arcs from the back
     for (int64_t i0 = b; i0 < e; i0 += LONG_T) {
       const int64_t i = i0 + t;
       bool up = false;
@@ -221,12 +228,18 @@ k_orient_long(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
       }
       const int before = __shfl_sync(0xffffffffu, incl - c, wid);
       const int total = __shfl_sync(0xffffffffu, incl, 31);
+      const int up_before = before + __popc(m & ((1u << lane) - 1u));
       if (up) {
-        const int64_t dst = w + before + __popc(m & ((1u << lane) - 1u));
+        const int64_t dst = w + up_before;
+        oadj[dst] = x;
+        opos[dst] = (int32_t)(i - b);
+      } else if (i < e) {
+        const int64_t dst = e - 1 - (wi + (t - up_before));
         oadj[dst] = x;
         opos[dst] = (int32_t)(i - b);
       }
       w += total;
+      wi += min((int64_t)LONG_T, e - i0) - total;
       __syncthreads();  // s_cnt is rewritten by the next chunk
     }
     if (t == 0) {

@@ -120,7 +120,9 @@ int launch_degrees(const int64_t* off, const int32_t* adj, int64_t n, int64_t ar
                    int32_t* maxdeg_dev, unsigned* status, cudaStream_t s);
 
 // Orientation by (degree, id), in place: out(v) = oadj[off[v] .. off[v]+od[v]),
-// in id order; opos = position of each out-arc inside its source's CSR row.
+// in id order; the in-neighbours of v fill the rest of its slot range,
+// oadj[off[v]+od[v] .. off[v+1]), in descending id order; opos = position of
+// each arc inside v's CSR row.
 // max_od_dev receives the largest out-degree, sum_od_dev the number of out-arcs.
 int launch_orient(const int64_t* off, const int32_t* adj, const int32_t* deg, int64_t n,
                   int64_t arcs, Pool& pool, int32_t** od, int32_t** oadj, int32_t** opos,

@@ -61,9 +61,10 @@ __host__ __device__ __forceinline__ bool warp_vertex(int64_t d, int64_t od, int 
 constexpr int SW_WARPS = 4;
 
 // Work items of the CTA kernel: a vertex v not handled by a warp contributes
-// ceil(deg/chunk) items when it has in-neighbours (every in-arc needs the
-// position of its source in N(v), even when out(v) is empty and no triangle
-// has v in the middle). items[v] -> prefix -> item index maps to (v, chunk).
+// ceil(in-degree/chunk) items when it has in-neighbours (every in-arc needs
+// the position of its source in N(v), even when out(v) is empty and no
+// triangle has v in the middle). items[v] -> prefix -> item index maps to
+// (v, chunk).
 __global__ void k_item_counts(const int32_t* __restrict__ odeg, const int32_t* __restrict__ deg,
                               int64_t n, int warp_deg, int chunk, int32_t* __restrict__ items) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
@@ -71,7 +72,7 @@ __global__ void k_item_counts(const int32_t* __restrict__ odeg, const int32_t* _
     const int64_t od = odeg[v];
     const int32_t d = deg[v];
     int c = 0;
-    if (!warp_vertex(d, od, warp_deg) && d - od > 0) c = (int)((d + chunk - 1) / chunk);
+    if (!warp_vertex(d, od, warp_deg) && d - od > 0) c = (int)((d - od + chunk - 1) / chunk);
     items[v] = c;
   }
 }
@@ -325,8 +326,9 @@ __device__ __forceinline__ void wt_drain(int cnt, const Weights& wt) {
   __syncwarp();
 }
 
-// One warp: triangles u < v < w for the in-neighbours u of v among the CSR
-// positions [p0, min(p0+32, p_end)) of N(v). The in-neighbours are compacted
+// One warp: triangles u < v < w for the in-neighbours u of v at positions
+// [p0, min(p0+32, p_end)) of v's in-arc range (oadj[rb ..], packed by the
+// orientation; in LSH mode the skipped ones are dropped). They are compacted
 // to lanes 0..k-1, and each lane finds v in out(u) (ascending rank) by a
 // binary search of its rank key: that gives the twin position of the arc
 // u->v, and the possible third vertices w > v are the entries after it.
@@ -339,7 +341,7 @@ __device__ __forceinline__ void wt_drain(int cnt, const Weights& wt) {
 template <bool BIG, typename IT, bool WT, int R>
 __device__ __forceinline__ void process_slice(
     int64_t p0, int64_t p_end, int64_t rb, int32_t v, int32_t dv, int32_t od, int64_t ob,
-    int long_list,
+    int long_list, const int32_t* __restrict__ opos,
     const int32_t* __restrict__ adj, const int32_t* __restrict__ deg,
     const int64_t* __restrict__ off, const int32_t* __restrict__ odeg,
     const int32_t* __restrict__ oadj, const uint64_t* __restrict__ okey,
@@ -352,12 +354,12 @@ __device__ __forceinline__ void process_slice(
   int32_t u = -1;
   bool is_in = false;
   if (p < p_end) {
-    u = adj[rb + p];
-    const int32_t du = deg[u];
-    is_in = lower(du, u, dv, v);
+    // v's in-neighbours are packed at the end of its slot range (orientation)
+    u = oadj[rb + p];
+    is_in = true;
     // LSH mode: if u and v are both above the threshold, every edge of
     // every triangle u < v < w is approximated, so the scan is not needed
-    if (is_in && lsh_T >= 0 && du > lsh_T) is_in = false;
+    if (lsh_T >= 0 && deg[u] > lsh_T) is_in = false;
   }
   const unsigned m = __ballot_sync(FULL, is_in);
   if (!m) return;
@@ -365,7 +367,7 @@ __device__ __forceinline__ void process_slice(
   if (is_in) {
     const int r = __popc(m & ((1u << lane) - 1u));
     sm.u[r] = u;
-    sm.p[r] = (int32_t)p;
+    sm.p[r] = opos[rb + p];  // position of u in N(v), the twin of the arc u->v
   }
   __syncwarp();
   int32_t cp = 0, clen = 0;  // suffix length after v
@@ -503,7 +505,7 @@ __device__ __forceinline__ void process_slice(
 }
 
 // CTA kernel for the other rows: the CTA shares out(v)'s table and
-// its warps pull 32-position slices of the item's CSR range.
+// its warps pull 32-position slices of the item's range of in-arcs.
 // BIG = out(v) too long for the shared table (binary search, global counters);
 // the BIG kernel also takes the items listed in `deferred`, whose shared
 // table could not be built (no cuckoo placement).
@@ -511,7 +513,8 @@ template <bool BIG, typename IT, bool WT, int R>
 __global__ void __launch_bounds__(TRI_THREADS, 3)
 k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
             const int32_t* __restrict__ deg, const int32_t* __restrict__ odeg,
-            const int32_t* __restrict__ oadj, const uint64_t* __restrict__ okey,
+            const int32_t* __restrict__ oadj, const int32_t* __restrict__ opos,
+            const uint64_t* __restrict__ okey,
             const int64_t* __restrict__ odp, int64_t n, const int64_t* __restrict__ item_off,
             const int32_t* __restrict__ order, unsigned long long* __restrict__ work, int lsh_T,
             int item_chunk, int long_list,
@@ -571,9 +574,9 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
         continue;
       }
     }
-    const int64_t rb = off[v];
+    const int64_t rb = off[v] + od;  // v's in-arcs
     const int64_t p_begin = chunk * item_chunk;
-    const int64_t p_end = min((int64_t)dv, p_begin + item_chunk);
+    const int64_t p_end = min((int64_t)(dv - od), p_begin + item_chunk);
     for (;;) {
       // warps pull 32-position slices until the item's range is exhausted
       int slice = 0;
@@ -581,7 +584,7 @@ k_triangles(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
       slice = __shfl_sync(FULL, slice, 0);
       const int64_t pos0 = p_begin + slice;
       if (pos0 >= p_end) break;
-      process_slice<BIG, IT, WT, R>(pos0, p_end, rb, (int32_t)v, dv, od, ob, long_list, adj, deg,
+      process_slice<BIG, IT, WT, R>(pos0, p_end, rb, (int32_t)v, dv, od, ob, long_list, opos, adj, deg,
                                     off, odeg, oadj, okey, odp, lsh_T, tab, vcnt, sm, tcnt, tc16,
                                     twin_rel, bad, wt);
     }
@@ -604,7 +607,8 @@ template <typename IT, bool WT, int R>
 __global__ void __launch_bounds__(SW_WARPS * 32, 8)
 k_tri_small(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
             const int32_t* __restrict__ deg, const int32_t* __restrict__ odeg,
-            const int32_t* __restrict__ oadj, const uint64_t* __restrict__ okey,
+            const int32_t* __restrict__ oadj, const int32_t* __restrict__ opos,
+            const uint64_t* __restrict__ okey,
             const int64_t* __restrict__ odp, int64_t n, unsigned long long* __restrict__ work,
             int lsh_T, int warp_deg, int long_list, uint32_t* __restrict__ tcnt,
             uint32_t* __restrict__ tc16,
@@ -641,14 +645,14 @@ k_tri_small(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
                           [](bool b) { __syncwarp(); return __any_sync(0xffffffffu, b) != 0; });
       }
       const bool use_table = !tab.bsearch;
-      const int64_t rb = off[vv];
-      for (int64_t pos0 = 0; pos0 < dv; pos0 += 32) {
+      const int64_t rb = off[vv] + od;  // vv's in-arcs
+      for (int64_t pos0 = 0; pos0 < dv - od; pos0 += 32) {
         if (use_table)
-          process_slice<false, IT, WT, R>(pos0, dv, rb, (int32_t)vv, dv, od, ob, long_list, adj,
+          process_slice<false, IT, WT, R>(pos0, dv - od, rb, (int32_t)vv, dv, od, ob, long_list, opos, adj,
                                           deg, off, odeg, oadj, okey, odp, lsh_T, tab, vcnt, sm,
                                           tcnt, tc16, twin_rel, bad, wt);
         else
-          process_slice<true, IT, WT, R>(pos0, dv, rb, (int32_t)vv, dv, od, ob, long_list, adj,
+          process_slice<true, IT, WT, R>(pos0, dv - od, rb, (int32_t)vv, dv, od, ob, long_list, opos, adj,
                                          deg, off, odeg, oadj, okey, odp, lsh_T, tab, vcnt, sm,
                                          tcnt, tc16, twin_rel, bad, wt);
       }
@@ -926,7 +930,8 @@ __global__ void k_fill_i32(int32_t* p, int64_t n, int32_t v) {
 // short suffixes (a tuning parameter: 4 or 8).
 template <typename IT, bool WT, int R>
 int launch_counting(const int64_t* off, const int32_t* adj, const int32_t* deg, const int32_t* odeg,
-                    const int32_t* oadj, const uint64_t* okey, const int64_t* odp, int64_t n,
+                    const int32_t* oadj, const int32_t* opos, const uint64_t* okey,
+                    const int64_t* odp, int64_t n,
                     const int64_t* item_off, const int32_t* order,
                     unsigned long long* work, int lsh_T, int32_t max_od, int64_t* deferred,
                     unsigned long long* n_deferred, uint32_t* tcnt, uint32_t* tc16, int32_t* twin,
@@ -947,7 +952,7 @@ int launch_counting(const int64_t* off, const int32_t* adj, const int32_t* deg, 
   if (per_sm < 1) per_sm = 1;
   if (k0) GS_CUDA(cudaEventRecord(k0, s));
   k_triangles<false, IT, WT, R><<<sms * per_sm, TRI_THREADS, smem, s>>>(
-      off, adj, deg, odeg, oadj, okey, odp, n, item_off, order, work, lsh_T, cfg.cta_chunk,
+      off, adj, deg, odeg, oadj, opos, okey, odp, n, item_off, order, work, lsh_T, cfg.cta_chunk,
       cfg.long_list, od_cap, deferred, n_deferred, false, tcnt, tc16, twin, status, ow, tsum);
   GS_LAUNCH();
   if (k1) GS_CUDA(cudaEventRecord(k1, s));
@@ -956,14 +961,15 @@ int launch_counting(const int64_t* off, const int32_t* adj, const int32_t* deg, 
                                                         SW_WARPS * 32, 0));
   if (small_per_sm < 1) small_per_sm = 1;
   k_tri_small<IT, WT, R><<<sms * small_per_sm, SW_WARPS * 32, 0, s>>>(
-      off, adj, deg, odeg, oadj, okey, odp, n, work + 2, lsh_T, cfg.warp_deg, cfg.long_list, tcnt,
+      off, adj, deg, odeg, oadj, opos, okey, odp, n, work + 2, lsh_T, cfg.warp_deg, cfg.long_list,
+      tcnt,
       tc16, twin, status, ow, tsum);
   GS_LAUNCH();
   // items with out-lists too long for the shared table, and items deferred
   // by the CTA kernel (normally none: the launch then ends at once)
   const bool deferred_only = max_od <= SMEM_OD_MAX;
   k_triangles<true, IT, WT, R><<<deferred_only ? sms : sms * 4, TRI_THREADS, 0, s>>>(
-      off, adj, deg, odeg, oadj, okey, odp, n, item_off, order, work + 1, lsh_T, cfg.cta_chunk,
+      off, adj, deg, odeg, oadj, opos, okey, odp, n, item_off, order, work + 1, lsh_T, cfg.cta_chunk,
       cfg.long_list, 0, deferred, n_deferred, deferred_only, tcnt, tc16, twin, status, ow, tsum);
   GS_LAUNCH();
   return SCAN_OK;
@@ -973,7 +979,8 @@ int launch_counting(const int64_t* off, const int32_t* adj, const int32_t* deg, 
 // the unweighted instances only.
 template <typename IT, bool WT>
 int launch_counting_cfg(const int64_t* off, const int32_t* adj, const int32_t* deg,
-                        const int32_t* odeg, const int32_t* oadj, const uint64_t* okey,
+                        const int32_t* odeg, const int32_t* oadj, const int32_t* opos,
+                        const uint64_t* okey,
                         const int64_t* odp, int64_t n, const int64_t* item_off,
                         const int32_t* order, unsigned long long* work, int lsh_T, int32_t max_od,
                         int64_t* deferred, unsigned long long* n_deferred, uint32_t* tcnt,
@@ -981,10 +988,10 @@ int launch_counting_cfg(const int64_t* off, const int32_t* adj, const int32_t* d
                         double* tsum, const CountCfg& cfg, cudaStream_t s, cudaEvent_t k0,
                         cudaEvent_t k1) {
   if (!WT && cfg.rounds == 8)
-    return launch_counting<IT, WT, 8>(off, adj, deg, odeg, oadj, okey, odp, n, item_off, order,
+    return launch_counting<IT, WT, 8>(off, adj, deg, odeg, oadj, opos, okey, odp, n, item_off, order,
                                       work, lsh_T, max_od, deferred, n_deferred, tcnt, tc16, twin,
                                       status, ow, tsum, cfg, s, k0, k1);
-  return launch_counting<IT, WT, 4>(off, adj, deg, odeg, oadj, okey, odp, n, item_off, order,
+  return launch_counting<IT, WT, 4>(off, adj, deg, odeg, oadj, opos, okey, odp, n, item_off, order,
                                     work, lsh_T, max_od, deferred, n_deferred, tcnt, tc16, twin,
                                     status, ow, tsum, cfg, s, k0, k1);
 }
@@ -1071,20 +1078,20 @@ int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* a
       k_out_weights<<<egrid, EXPAND_T, 0, s>>>(off, odp, n, opos, wcsr, ow, status);
       GS_LAUNCH();
       if (narrow) {
-        GS_TRY((launch_counting_cfg<int32_t, true>(off, adj, deg, odeg, oadj, okey, odp, n, item_off,
+        GS_TRY((launch_counting_cfg<int32_t, true>(off, adj, deg, odeg, oadj, opos, okey, odp, n, item_off,
                                                order, work, lsh_T, max_od, deferred, work + 3,
                                                tcnt, tc16, twin, status, ow, tsum, cfg, s, k0, k1)));
       } else {
-        GS_TRY((launch_counting_cfg<int64_t, true>(off, adj, deg, odeg, oadj, okey, odp, n, item_off,
+        GS_TRY((launch_counting_cfg<int64_t, true>(off, adj, deg, odeg, oadj, opos, okey, odp, n, item_off,
                                                order, work, lsh_T, max_od, deferred, work + 3,
                                                tcnt, nullptr, twin, status, ow, tsum, cfg, s, k0, k1)));
       }
     } else if (narrow) {
-      GS_TRY((launch_counting_cfg<int32_t, false>(off, adj, deg, odeg, oadj, okey, odp, n, item_off,
+      GS_TRY((launch_counting_cfg<int32_t, false>(off, adj, deg, odeg, oadj, opos, okey, odp, n, item_off,
                                               order, work, lsh_T, max_od, deferred, work + 3, tcnt,
                                               tc16, twin, status, nullptr, nullptr, cfg, s, k0, k1)));
     } else {
-      GS_TRY((launch_counting_cfg<int64_t, false>(off, adj, deg, odeg, oadj, okey, odp, n, item_off,
+      GS_TRY((launch_counting_cfg<int64_t, false>(off, adj, deg, odeg, oadj, opos, okey, odp, n, item_off,
                                               order, work, lsh_T, max_od, deferred, work + 3, tcnt,
                                               nullptr, twin, status, nullptr, nullptr, cfg, s, k0, k1)));
     }
