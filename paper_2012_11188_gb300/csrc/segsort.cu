@@ -177,17 +177,24 @@ __device__ __forceinline__ void merge_out(const uint64_t* ks, const int32_t* vs,
   int32_t va = SENT_V, vb = SENT_V;
   if (ia < la) { const int p = pslot<R>(a0 + ia); ka = ks[p]; va = vs[p]; }
   if (ib < lb) { const int p = pslot<R>(b0 + ib); kb = ks[p]; vb = vs[p]; }
+  // branch-free steps: every lane selects, advances and reloads the same way
 #pragma unroll
   for (int q = 0; q < RI; ++q) {
     const bool take_a = ib >= lb || (ia < la && !before(kb, vb, ka, va));
     const int po = pslot<R>(o + q);
-    if (take_a) {
-      kd[po] = ka; vd[po] = va;
-      if (++ia < la) { const int p = pslot<R>(a0 + ia); ka = ks[p]; va = vs[p]; }
-    } else {
-      kd[po] = kb; vd[po] = vb;
-      if (++ib < lb) { const int p = pslot<R>(b0 + ib); kb = ks[p]; vb = vs[p]; }
-    }
+    kd[po] = take_a ? ka : kb;
+    vd[po] = take_a ? va : vb;
+    ia += take_a ? 1 : 0;
+    ib += take_a ? 0 : 1;
+    const int nxt = take_a ? a0 + ia : b0 + ib;
+    const bool more = take_a ? ia < la : ib < lb;
+    uint64_t kn = 0;
+    int32_t vn = SENT_V;
+    if (more) { const int p = pslot<R>(nxt); kn = ks[p]; vn = vs[p]; }
+    ka = take_a ? kn : ka;
+    va = take_a ? vn : va;
+    kb = take_a ? kb : kn;
+    vb = take_a ? vb : vn;
   }
 }
 
@@ -475,13 +482,19 @@ k_merge_pass(uint64_t* __restrict__ key, int32_t* __restrict__ val, uint64_t* __
           if (d + q >= nout) break;
           const bool take_a = ib >= nb || (ia < na && !before(kb, vb, ka, va));
           const int pq = po(d + q);
-          if (take_a) {
-            ok_[pq] = ka; ov_[pq] = va;
-            if (++ia < na) { ka = shk[ia]; va = shv[ia]; }
-          } else {
-            ok_[pq] = kb; ov_[pq] = vb;
-            if (++ib < nb) { kb = shk[na + ib]; vb = shv[na + ib]; }
-          }
+          ok_[pq] = take_a ? ka : kb;
+          ov_[pq] = take_a ? va : vb;
+          ia += take_a ? 1 : 0;
+          ib += take_a ? 0 : 1;
+          const int nxt = take_a ? ia : na + ib;
+          const bool more = take_a ? ia < na : ib < nb;
+          uint64_t kn = 0;
+          int32_t vn = SENT_V;
+          if (more) { kn = shk[nxt]; vn = shv[nxt]; }
+          ka = take_a ? kn : ka;
+          va = take_a ? vn : va;
+          kb = take_a ? kb : kn;
+          vb = take_a ? vb : vn;
         }
       }
       __syncthreads();
