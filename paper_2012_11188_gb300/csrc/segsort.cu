@@ -151,18 +151,34 @@ __device__ __forceinline__ void cas(uint64_t& ka, int32_t& va, uint64_t& kb, int
   }
 }
 
-// Sorts 8 register elements with Batcher's odd-even merge network (19
-// compare-and-swaps).
-__device__ __forceinline__ void sort8(uint64_t (&K)[8], int32_t (&V)[8]) {
+// Sorts 8 or 16 register elements with Batcher's odd-even merge network
+// (19 or 63 compare-and-swaps).
 #define GS_CAS(i, j) cas(K[i], V[i], K[j], V[j])
+__device__ __forceinline__ void sort_regs(uint64_t (&K)[8], int32_t (&V)[8]) {
   GS_CAS(0, 1); GS_CAS(2, 3); GS_CAS(4, 5); GS_CAS(6, 7);
   GS_CAS(0, 2); GS_CAS(1, 3); GS_CAS(4, 6); GS_CAS(5, 7);
   GS_CAS(1, 2); GS_CAS(5, 6);
   GS_CAS(0, 4); GS_CAS(1, 5); GS_CAS(2, 6); GS_CAS(3, 7);
   GS_CAS(2, 4); GS_CAS(3, 5);
   GS_CAS(1, 2); GS_CAS(3, 4); GS_CAS(5, 6);
-#undef GS_CAS
 }
+__device__ __forceinline__ void sort_regs(uint64_t (&K)[16], int32_t (&V)[16]) {
+  // the two halves, then the odd-even merge of the halves
+  GS_CAS(0, 1); GS_CAS(2, 3); GS_CAS(0, 2); GS_CAS(1, 3); GS_CAS(1, 2);
+  GS_CAS(4, 5); GS_CAS(6, 7); GS_CAS(4, 6); GS_CAS(5, 7); GS_CAS(5, 6);
+  GS_CAS(0, 4); GS_CAS(2, 6); GS_CAS(2, 4); GS_CAS(1, 5); GS_CAS(3, 7); GS_CAS(3, 5);
+  GS_CAS(1, 2); GS_CAS(3, 4); GS_CAS(5, 6);
+  GS_CAS(8, 9); GS_CAS(10, 11); GS_CAS(8, 10); GS_CAS(9, 11); GS_CAS(9, 10);
+  GS_CAS(12, 13); GS_CAS(14, 15); GS_CAS(12, 14); GS_CAS(13, 15); GS_CAS(13, 14);
+  GS_CAS(8, 12); GS_CAS(10, 14); GS_CAS(10, 12); GS_CAS(9, 13); GS_CAS(11, 15); GS_CAS(11, 13);
+  GS_CAS(9, 10); GS_CAS(11, 12); GS_CAS(13, 14);
+  GS_CAS(0, 8); GS_CAS(4, 12); GS_CAS(4, 8); GS_CAS(2, 10); GS_CAS(6, 14); GS_CAS(6, 10);
+  GS_CAS(2, 4); GS_CAS(6, 8); GS_CAS(10, 12); GS_CAS(1, 9); GS_CAS(5, 13); GS_CAS(5, 9);
+  GS_CAS(3, 11); GS_CAS(7, 15); GS_CAS(7, 11); GS_CAS(3, 5); GS_CAS(7, 9); GS_CAS(11, 13);
+  GS_CAS(1, 2); GS_CAS(3, 4); GS_CAS(5, 6); GS_CAS(7, 8); GS_CAS(9, 10); GS_CAS(11, 12);
+  GS_CAS(13, 14);
+}
+#undef GS_CAS
 
 // Merges RI outputs starting at diagonal d of the runs A = src[a0, a0+la)
 // and B = src[b0, b0+lb) (padded shared layout), writing dst slots o..o+RI-1.
@@ -198,23 +214,22 @@ __device__ __forceinline__ void merge_out(const uint64_t* ks, const int32_t* vs,
   }
 }
 
-// One CTA of TT threads sorts a tile of up to TT*8 elements at the next power
-// of two SE >= max(len, 8): the tile is loaded into shared memory with
-// coalesced reads (padded with sentinels that sort last), each thread sorts
-// 8 consecutive elements in registers, then merge-path levels double the
-// sorted runs up to SE, each thread writing 8 outputs per level. Tiles are
-// whole segments (TILED = false) or TILE-element pieces of longer segments
-// (TILED = true, TT*8 = TILE). A tiled segment that takes an odd number of
-// merge passes has its tiles written to the scratch buffer (tk, tv), so
-// that its last pass ends in (key, val).
-template <int TT, bool TILED>
-__global__ void __launch_bounds__(TT, TT >= 1024 ? 1 : 1024 / TT)
+// One CTA of TT threads sorts a tile of up to TT*RI elements (RI = 8 or 16)
+// at the next power of two SE >= max(len, RI): the tile is loaded into
+// shared memory with coalesced reads (padded with sentinels that sort last),
+// each thread sorts RI consecutive elements in registers, then merge-path
+// levels double the sorted runs up to SE, each thread writing RI outputs per
+// level. Tiles are whole segments (TILED = false) or TILE-element pieces of
+// longer segments (TILED = true, TT*RI = TILE). A tiled segment that takes
+// an odd number of merge passes has its tiles written to the scratch buffer
+// (tk, tv), so that its last pass ends in (key, val).
+template <int TT, int RI, bool TILED>
+__global__ void __launch_bounds__(TT, TT * RI >= 8192 ? 1 : (TT >= 1024 ? 1 : 1024 / TT))
 k_sort_tile(uint64_t* __restrict__ key, int32_t* __restrict__ val,
             const int64_t* __restrict__ seg_off, const int64_t* __restrict__ list,
             const unsigned long long* __restrict__ count_ptr,
             const int64_t* __restrict__ tile_prefix, int64_t nlong, uint64_t* __restrict__ tk,
             int32_t* __restrict__ tv) {
-  constexpr int RI = 8;
   constexpr int CAP = TT * RI;
   constexpr int PCAP = CAP + CAP / RI;  // padded slots per buffer
   extern __shared__ uint64_t tsm[];
@@ -258,7 +273,7 @@ k_sort_tile(uint64_t* __restrict__ key, int32_t* __restrict__ val,
       int32_t V[RI];
 #pragma unroll
       for (int r = 0; r < RI; ++r) { const int p = pslot<RI>(RI * t + r); K[r] = k0[p]; V[r] = v0[p]; }
-      sort8(K, V);
+      sort_regs(K, V);
 #pragma unroll
       for (int r = 0; r < RI; ++r) { const int p = pslot<RI>(RI * t + r); k0[p] = K[r]; v0[p] = V[r]; }
     }
@@ -285,15 +300,19 @@ k_sort_tile(uint64_t* __restrict__ key, int32_t* __restrict__ val,
   }
 }
 
-template <int TT>
+template <int TT, int RI>
 constexpr size_t tile_smem_bytes() {
-  return (size_t)(TT * 8 + TT) * (2 * sizeof(uint64_t) + 2 * sizeof(int32_t));
+  return (size_t)(TT * RI + TT * RI / RI) * (2 * sizeof(uint64_t) + 2 * sizeof(int32_t));
 }
 
+#ifndef GS_SORT_LONG_RI
+#define GS_SORT_LONG_RI 8  // elements per thread in the tiles of long segments (8 or 16)
+#endif
 // whole segments of 1025..4096 elements: 512 threads x 8; tiles of long
-// segments: TILE elements, 1024 threads x 8 (one CTA per SM)
+// segments: TILE elements, TILE / GS_SORT_LONG_RI threads (one CTA per SM)
 constexpr int T4K_T = 512;
-constexpr int TLONG_T = TILE / 8;
+constexpr int TLONG_RI = GS_SORT_LONG_RI;
+constexpr int TLONG_T = TILE / TLONG_RI;
 
 // Tiles per long segment (prefix computed by the caller).
 __global__ void k_long_tiles(const int64_t* __restrict__ seg_off, const int64_t* __restrict__ list,
@@ -551,25 +570,26 @@ int segmented_sort_desc(uint64_t* key, int32_t* val, const int64_t* seg_off, int
     // 33..256 elements: one 32-thread CTA per row (8-element register
     // networks and merge levels: compact code, unlike fully unrolled bitonic
     // networks, whose instruction footprint stalls the warp on fetches)
-    k_sort_tile<32, false><<<grid_of((int64_t)hc[1], 1), 32, tile_smem_bytes<32>(), s>>>(
+    k_sort_tile<32, 8, false><<<grid_of((int64_t)hc[1], 1), 32, tile_smem_bytes<32, 8>(), s>>>(
         key, val, seg_off, list + base[1], counts + 1, nullptr, 0, nullptr, nullptr);
     GS_LAUNCH();
   }
   GS_CUDA(cudaFuncSetAttribute(k_merge_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)MERGE_SMEM));
-  GS_CUDA(cudaFuncSetAttribute(k_sort_tile<TLONG_T, true>,
+  GS_CUDA(cudaFuncSetAttribute(k_sort_tile<TLONG_T, TLONG_RI, true>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)tile_smem_bytes<TLONG_T>()));
-  GS_CUDA(cudaFuncSetAttribute(k_sort_tile<T4K_T, false>,
+                               (int)tile_smem_bytes<TLONG_T, TLONG_RI>()));
+  GS_CUDA(cudaFuncSetAttribute(k_sort_tile<T4K_T, 8, false>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)tile_smem_bytes<T4K_T>()));
+                               (int)tile_smem_bytes<T4K_T, 8>()));
   if (hc[2]) {
-    k_sort_tile<128, false><<<grid_of((int64_t)hc[2], 1), 128, tile_smem_bytes<128>(), s>>>(
+    k_sort_tile<128, 8, false><<<grid_of((int64_t)hc[2], 1), 128, tile_smem_bytes<128, 8>(), s>>>(
         key, val, seg_off, list + base[2], counts + 2, nullptr, 0, nullptr, nullptr);
     GS_LAUNCH();
   }
   if (hc[3]) {
-    k_sort_tile<T4K_T, false><<<grid_of((int64_t)hc[3], 1), T4K_T, tile_smem_bytes<T4K_T>(), s>>>(
+    k_sort_tile<T4K_T, 8, false><<<grid_of((int64_t)hc[3], 1), T4K_T, tile_smem_bytes<T4K_T, 8>(),
+                                 s>>>(
         key, val, seg_off, list + base[3], counts + 3, nullptr, 0, nullptr, nullptr);
     GS_LAUNCH();
   }
@@ -590,7 +610,8 @@ int segmented_sort_desc(uint64_t* key, int32_t* val, const int64_t* seg_off, int
     GS_TRY(exclusive_scan_i64(chunks, chunk_prefix, nlong, pool, s));
     const int64_t ntiles = (int64_t)hc[NCLASS];
     // tile sort (count = ntiles, read from counts[NCLASS])
-    k_sort_tile<TLONG_T, true><<<grid_of(ntiles, 1), TLONG_T, tile_smem_bytes<TLONG_T>(), s>>>(
+    k_sort_tile<TLONG_T, TLONG_RI, true><<<grid_of(ntiles, 1), TLONG_T,
+                                          tile_smem_bytes<TLONG_T, TLONG_RI>(), s>>>(
         key, val, seg_off, llist, counts + NCLASS, tile_prefix, nlong, tk, tv);
     GS_LAUNCH();
     const int64_t total_chunks_ub = (total + MERGE_CHUNK - 1) / MERGE_CHUNK + nlong;
