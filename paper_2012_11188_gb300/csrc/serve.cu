@@ -1,12 +1,13 @@
 // Continuous-batching request loop over resident SCAN indexes (include/scan_serve.h).
 //
-// Two worker threads own two CUDA streams:
+// Two worker threads own the CUDA streams:
 //  - the query worker takes every query queued for one (index, flags) pair, up
 //    to max_batch (default 64), and answers them with one batched pass (one
 //    launch per phase for the whole batch, labels written straight into device
-//    destinations; host destinations go through staging rows). Its scratch is
-//    kept across batches. Queries that arrive meanwhile wait in the queue and
-//    join the next batch as soon as this one completes.
+//    destinations; host destinations go through staging rows, copied out on a
+//    third stream while the next batch's kernels run; a host function on that
+//    stream completes the batch). At most two batches are in flight; queries
+//    that arrive meanwhile wait in the queue and join the next batch.
 //  - the build worker admits build requests in arrival order when their
 //    footprint fits the memory budget and the device's free memory, and builds
 //    them on its own stream, overlapping with the query batches.
@@ -56,8 +57,10 @@ struct scan_server {
   scan_serve_params p{};
   int device = 0;
   cudaStream_t qs = nullptr, bs = nullptr;
+  cudaStream_t cs = nullptr;  // copies of host-bound labels, and batch completions
   std::mutex mu;
-  std::condition_variable cv_q, cv_b, cv_done;
+  std::condition_variable cv_q, cv_b, cv_done, cv_slot;
+  int batches_in_flight = 0;  // query batches launched and not yet completed (at most 2)
   std::deque<Request*> qq, bq;
   std::unordered_map<uint64_t, Request*> reqs;
   uint64_t next_ticket = 1;
@@ -86,8 +89,10 @@ void finish(scan_server* s, Request* r, int status) {
 }
 
 // Scratch of the query worker, kept across batches and grown on demand:
-// parents (cap x n), a device table of label destinations, mu/eps/core
-// counts, a status word, and staging rows for host destinations.
+// parents (cap x n), mu/eps/core counts and the table of label destinations,
+// and two sets of what a batch in flight owns until its copies are done:
+// staging rows for host destinations, a device status word, its pinned host
+// copy and the event that marks its kernels done.
 struct QueryScratch {
   int cap = 0;
   int64_t n = 0;
@@ -96,10 +101,12 @@ struct QueryScratch {
   int* mu = nullptr;
   double* eps = nullptr;
   int64_t* nc = nullptr;
-  unsigned* status = nullptr;
-  int32_t* staging = nullptr;
-  int staging_rows = 0;
-  std::vector<std::pair<void*, size_t>> held;  // every block, for release
+  unsigned* status[2] = {nullptr, nullptr};
+  unsigned* status_host = nullptr;  // pinned, 2 words
+  int32_t* staging[2] = {nullptr, nullptr};
+  int staging_rows[2] = {0, 0};
+  cudaEvent_t kern_done[2] = {nullptr, nullptr};
+  std::vector<std::pair<void*, size_t>> held;  // every device block, for release
   template <class T>
   T* get(size_t count, cudaStream_t s) {
     const size_t b = count * sizeof(T) > 0 ? count * sizeof(T) : 16;
@@ -109,10 +116,18 @@ struct QueryScratch {
   }
   void release(cudaStream_t s) {
     for (auto& h : held) gscan::dev_free(h.first, h.second, s);
+    if (status_host) cudaFreeHost(status_host);
+    for (auto& e : kern_done)
+      if (e) cudaEventDestroy(e);
     *this = QueryScratch();
   }
-  int ensure(int c, int64_t nn, cudaStream_t s) {
+  int ensure(int c, int64_t nn, cudaStream_t s, cudaStream_t cs) {
     if (c <= cap && nn <= n) return SCAN_OK;
+    if (cap > 0) {
+      // a batch may still be in flight on the old scratch: drain both streams
+      cudaStreamSynchronize(s);
+      cudaStreamSynchronize(cs);
+    }
     release(s);
     cap = c;
     n = nn;
@@ -121,27 +136,63 @@ struct QueryScratch {
     mu = get<int>(c, s);
     eps = get<double>(c, s);
     nc = get<int64_t>(2 * (size_t)c + 1, s);
-    status = get<unsigned>(1, s);
-    if (!parent || !ptrs || !mu || !eps || !nc || !status) {
+    status[0] = get<unsigned>(1, s);
+    status[1] = get<unsigned>(1, s);
+    if (cudaHostAlloc((void**)&status_host, 2 * sizeof(unsigned), cudaHostAllocDefault) !=
+        cudaSuccess)
+      status_host = nullptr;
+    bool ev_ok = true;
+    for (auto& e : kern_done)
+      ev_ok &= cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    if (!parent || !ptrs || !mu || !eps || !nc || !status[0] || !status[1] || !status_host ||
+        !ev_ok) {
       release(s);
       return SCAN_ENOMEM;
     }
     return SCAN_OK;
   }
-  int ensure_staging(int rows, cudaStream_t s) {
-    if (rows <= staging_rows) return SCAN_OK;
-    staging = get<int32_t>((size_t)rows * (size_t)n, s);  // the smaller one is released with the rest
-    if (!staging) return SCAN_ENOMEM;
-    staging_rows = rows;
+  int ensure_staging(int set, int rows, cudaStream_t s) {
+    if (rows <= staging_rows[set]) return SCAN_OK;
+    staging[set] = get<int32_t>((size_t)rows * (size_t)n, s);  // the smaller one is released with the rest
+    if (!staging[set]) return SCAN_ENOMEM;
+    staging_rows[set] = rows;
     return SCAN_OK;
   }
 };
 
-int run_batch(scan_server* s, QueryScratch& qs, const std::vector<Request*>& batch) {
+// A launched batch, completed by a host function on the copy stream once its
+// kernels and its label copies are done.
+struct BatchDone {
+  scan_server* s;
+  std::vector<Request*> batch;
+  const unsigned* status_host;
+};
+
+void finish_batch(scan_server* s, const std::vector<Request*>& batch, int rc) {
+  for (Request* r : batch) finish(s, r, rc);
+  std::lock_guard<std::mutex> lk(s->mu);
+  --s->batches_in_flight;
+  s->cv_slot.notify_all();
+}
+
+// Host function (no CUDA calls): the batch's status word has landed.
+void CUDART_CB on_batch_done(void* p) {
+  BatchDone* d = static_cast<BatchDone*>(p);
+  const int rc = (*d->status_host & gscan::DEV_LIMIT) ? SCAN_ETIMEOUT : SCAN_OK;
+  finish_batch(d->s, d->batch, rc);
+  delete d;
+}
+
+// Launch one batch: kernels on the query stream, writing device destinations
+// directly and host destinations into the staging rows of set `set`; then,
+// on the copy stream, once the kernels are done, the staging rows go to the
+// host buffers, the status word to pinned memory, and a host function
+// completes the requests. The next batch's kernels overlap these copies; a
+// set is reused two batches later, when the copy stream has drained it.
+int launch_batch(scan_server* s, QueryScratch& qs, const std::vector<Request*>& batch, int set) {
   const gscan::IndexData& d = batch[0]->ix->d;
   const int Q = (int)batch.size();
-  if (d.n == 0) return SCAN_OK;
-  GS_TRY(qs.ensure(std::max(Q, s->p.max_batch > 0 ? s->p.max_batch : 64), d.n, s->qs));
+  GS_TRY(qs.ensure(std::max(Q, s->p.max_batch > 0 ? s->p.max_batch : 64), d.n, s->qs, s->cs));
   std::vector<int> mus(Q);
   std::vector<double> epss(Q);
   std::vector<int32_t*> dst(Q);
@@ -156,23 +207,32 @@ int run_batch(scan_server* s, QueryScratch& qs, const std::vector<Request*>& bat
       dst[i] = nullptr;
     }
   }
+  // the staging rows of this set belonged to the batch before the previous
+  // one, which has completed (at most two batches are in flight)
   if (!host_rows.empty()) {
-    GS_TRY(qs.ensure_staging((int)host_rows.size(), s->qs));
-    for (size_t r = 0; r < host_rows.size(); ++r) dst[host_rows[r]] = qs.staging + r * (size_t)d.n;
+    GS_TRY(qs.ensure_staging(set, (int)host_rows.size(), s->qs));
+    for (size_t r = 0; r < host_rows.size(); ++r)
+      dst[host_rows[r]] = qs.staging[set] + r * (size_t)d.n;
   }
   GS_CUDA(cudaMemcpyAsync(qs.mu, mus.data(), sizeof(int) * Q, cudaMemcpyHostToDevice, s->qs));
   GS_CUDA(cudaMemcpyAsync(qs.eps, epss.data(), sizeof(double) * Q, cudaMemcpyHostToDevice, s->qs));
   GS_CUDA(cudaMemcpyAsync(qs.ptrs, dst.data(), sizeof(int32_t*) * Q, cudaMemcpyHostToDevice, s->qs));
-  GS_CUDA(cudaMemsetAsync(qs.status, 0, sizeof(unsigned), s->qs));
+  GS_CUDA(cudaMemsetAsync(qs.status[set], 0, sizeof(unsigned), s->qs));
   GS_TRY(gscan::launch_query_batch(d, Q, qs.mu, qs.eps, qs.nc, qs.parent, nullptr, qs.ptrs,
-                                   batch[0]->flags, s->qs, qs.status));
+                                   batch[0]->flags, s->qs, qs.status[set]));
+  GS_CUDA(cudaEventRecord(qs.kern_done[set], s->qs));
+  GS_CUDA(cudaStreamWaitEvent(s->cs, qs.kern_done[set], 0));
   for (size_t r = 0; r < host_rows.size(); ++r)
-    GS_CUDA(cudaMemcpyAsync(batch[host_rows[r]]->labels, qs.staging + r * (size_t)d.n,
-                            sizeof(int32_t) * (size_t)d.n, cudaMemcpyDeviceToHost, s->qs));
-  unsigned hst = 0;
-  GS_CUDA(cudaMemcpyAsync(&hst, qs.status, sizeof(unsigned), cudaMemcpyDeviceToHost, s->qs));
-  GS_CUDA(cudaStreamSynchronize(s->qs));
-  if (hst & gscan::DEV_LIMIT) return SCAN_ETIMEOUT;
+    GS_CUDA(cudaMemcpyAsync(batch[host_rows[r]]->labels, qs.staging[set] + r * (size_t)d.n,
+                            sizeof(int32_t) * (size_t)d.n, cudaMemcpyDeviceToHost, s->cs));
+  GS_CUDA(cudaMemcpyAsync(qs.status_host + set, qs.status[set], sizeof(unsigned),
+                          cudaMemcpyDeviceToHost, s->cs));
+  BatchDone* done = new (std::nothrow) BatchDone{s, batch, qs.status_host + set};
+  if (!done) return SCAN_ENOMEM;
+  if (cudaLaunchHostFunc(s->cs, on_batch_done, done) != cudaSuccess) {
+    delete done;
+    return SCAN_ECUDA;
+  }
   return SCAN_OK;
 }
 
@@ -181,12 +241,16 @@ void query_worker(scan_server* s) {
   const int max_batch = s->p.max_batch > 0 ? s->p.max_batch : 64;
   QueryScratch qs;
   std::vector<Request*> batch;
+  int set = 0;
   for (;;) {
     batch.clear();
     {
       std::unique_lock<std::mutex> lk(s->mu);
       s->cv_q.wait(lk, [&] { return s->stop || !s->qq.empty(); });
       if (s->qq.empty() && s->stop) break;
+      // at most two batches in flight: the next one may overlap the copies
+      // of the previous one, and queries arriving meanwhile join it
+      s->cv_slot.wait(lk, [&] { return s->batches_in_flight < 2; });
       // everything queued for the front request's (index, flags), up to max_batch
       scan_index* ix = s->qq.front()->ix;
       const int flags = s->qq.front()->flags;
@@ -198,11 +262,23 @@ void query_worker(scan_server* s) {
           ++it;
         }
       }
+      ++s->batches_in_flight;
     }
-    const int rc = run_batch(s, qs, batch);
-    cudaStreamSynchronize(s->qs);
-    for (Request* r : batch) finish(s, r, rc);
+    if (batch[0]->ix->d.n == 0) {
+      finish_batch(s, batch, SCAN_OK);
+      continue;
+    }
+    const int rc = launch_batch(s, qs, batch, set);
+    if (rc != SCAN_OK) {
+      // nothing was handed to the copy stream for this batch: complete it now
+      cudaStreamSynchronize(s->qs);
+      cudaStreamSynchronize(s->cs);
+      finish_batch(s, batch, rc);
+    }
+    set ^= 1;
   }
+  cudaStreamSynchronize(s->qs);
+  cudaStreamSynchronize(s->cs);  // the last batches' host functions have run
   qs.release(s->qs);
   cudaStreamSynchronize(s->qs);
 }
@@ -285,8 +361,10 @@ int scan_serve_create(const scan_serve_params* params, scan_server** out) {
   s->device = s->p.device;
   if (cudaSetDevice(s->device) != cudaSuccess ||
       cudaStreamCreateWithFlags(&s->qs, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&s->bs, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaStreamCreateWithFlags(&s->bs, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking) != cudaSuccess) {
     if (s->qs) cudaStreamDestroy(s->qs);
+    if (s->bs) cudaStreamDestroy(s->bs);
     delete s;
     return SCAN_ECUDA;
   }
@@ -513,6 +591,7 @@ void scan_serve_destroy(scan_server* s) {
   }
   cudaStreamDestroy(s->qs);
   cudaStreamDestroy(s->bs);
+  cudaStreamDestroy(s->cs);
   delete s;
 }
 
