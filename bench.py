@@ -279,7 +279,7 @@ def bench_batched(gs, kind: int, count: int, seed: int, stream):
 
 
 def bench_serving(gs, kind: int, nq: int, seed: int, stream,
-                  rates=(5000, 10000, 20000, 30000, 40000, 50000),
+                  rates=(5000, 7500, 10000, 15000, 20000, 25000, 30000, 40000, 50000),
                   ring_rows: int = 128):
     """Resident exact index of R-MAT s22 ef16; Poisson query arrivals, mu uniform
     in {2..32}, eps uniform on the 0.05 grid in [0.1, 0.9], 1% of requests are
