@@ -286,7 +286,7 @@ int scan_kernel_launches(uint64_t* count);
  * scan_set_count_config, the tuning table's entry for its class (the bit
  * length of the vertex count of its largest graph and of its average
  * degree, both known before any device work), or the defaults
- * {512, 4096, 64, 4, 16, 4096}. In a batched build the members that the
+ * {512, 32768, 64, 4, 16, 4096}. In a batched build the members that the
  * dense rule selects are built one by one on the dense path, the others
  * together. */
 typedef struct scan_count_config {

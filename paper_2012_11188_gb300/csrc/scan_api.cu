@@ -965,7 +965,7 @@ int scan_autotune_batch(const scan_csr* graphs, int count, scan_sim_kind kind, i
   const int dense_divs[] = {0, 8, 16, 32, 64};
   const int dense_min_ns[] = {2048, 4096, 8192};
   const int warp_degs[] = {128, 256, 512, 1024, 2048};
-  const int chunks[] = {1024, 2048, 4096, 8192};
+  const int chunks[] = {1024, 2048, 4096, 8192, 16384, 32768, 65536};
   const int longs[] = {32, 64, 128, 256};
   const int rounds[] = {4, 8};
   auto try_value = [&](int gscan::CountCfg::*field, int v) -> int {

@@ -138,7 +138,7 @@ int launch_orient(const int64_t* off, const int32_t* adj, const int32_t* deg, in
 constexpr int64_t DENSE_MIN_N = 4096;
 struct CountCfg {
   int warp_deg = 512;
-  int cta_chunk = 4096;
+  int cta_chunk = 32768;
   int long_list = 64;
   int rounds = 4;
   int dense_div = 16;

@@ -128,7 +128,7 @@ def autotune_batch(graphs, kind: int = COSINE, reps: int = 2, stream=None, devic
     return {"best": best.as_dict(), "best_ms": bms.value, "default_ms": dms.value}
 
 
-DEFAULT_COUNT_CONFIG = {"warp_deg": 512, "cta_chunk": 4096, "long_list": 64, "rounds": 4,
+DEFAULT_COUNT_CONFIG = {"warp_deg": 512, "cta_chunk": 32768, "long_list": 64, "rounds": 4,
                         "dense_div": 16, "dense_min_n": 4096}
 
 
