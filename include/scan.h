@@ -338,9 +338,14 @@ int scan_tuning_clear(void);
  * ranks sort their runs of CO[mu] and merge the runs they receive. Every
  * segment [seg_off[i], seg_off[i+1]) of (keys, ids) is sorted in place by key
  * descending, then id ascending. keys: non-negative doubles (similarities);
- * ids: int32; seg_off: nseg+1 int64 offsets, seg_off[nseg] = total; max_len:
- * an upper bound of every segment's length. All three arrays device memory
- * (host pointers: SCAN_EINVAL). Synchronises `stream`. */
+ * ids: int32; seg_off: nseg+1 int64 offsets, non-decreasing within [0, total]
+ * (checked on the device before any element is read or written: otherwise
+ * SCAN_EINVAL and the arrays are unchanged); max_len: an upper bound of every
+ * segment's length. All three arrays device memory (host pointers:
+ * SCAN_EINVAL). Synchronises `stream`. Segments longer than 4096 are split
+ * into buckets by a sample sort (sorted random samples give the splitters,
+ * one scatter places every element in its bucket), then the buckets are
+ * sorted in shared memory. */
 int scan_sort_segments_desc(double* keys, int32_t* ids, const int64_t* seg_off, int64_t nseg,
                             int64_t total, int64_t max_len, uintptr_t stream);
 

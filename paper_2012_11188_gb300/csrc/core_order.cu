@@ -45,16 +45,32 @@ __device__ __forceinline__ int64_t cum(const Multi& m, int64_t g, int64_t d) {
   return ng - (m.Sx[m.hb[g] + d] - m.Sx[m.hb[g]]);
 }
 
-__global__ void k_hist(const int32_t* __restrict__ deg, int64_t N, Multi m,
-                       unsigned long long* __restrict__ hist) {
+// Keys below HB_SMALL (the low degrees, where most vertices fall) are
+// counted in shared memory first, one global atomic per key and CTA; the
+// others by warp-aggregated global atomics.
+constexpr int HB_SMALL = 4096;
+
+__global__ void __launch_bounds__(256)
+k_hist(const int32_t* __restrict__ deg, int64_t N, Multi m, unsigned long long* __restrict__ hist) {
+  __shared__ unsigned sh[HB_SMALL];
+  for (int i = threadIdx.x; i < HB_SMALL; i += blockDim.x) sh[i] = 0;
+  __syncthreads();
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
        v += (int64_t)gridDim.x * blockDim.x) {
     const int64_t g = m.G == 1 ? 0 : last_le(m.vb, m.G, v);
     const int64_t key = m.hb[g] + deg[v];
-    // lanes with the same key add once
-    const unsigned peers = __match_any_sync(__activemask(), (unsigned long long)key);
-    if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[key], (unsigned long long)__popc(peers));
+    if (key < HB_SMALL) {
+      atomicAdd(&sh[key], 1u);
+    } else {
+      // lanes with the same key add once
+      const unsigned peers = __match_any_sync(__activemask(), (unsigned long long)key);
+      if ((threadIdx.x & 31) == __ffs(peers) - 1)
+        atomicAdd(&hist[key], (unsigned long long)__popc(peers));
+    }
   }
+  __syncthreads();
+  for (int i = threadIdx.x; i < HB_SMALL; i += blockDim.x)
+    if (sh[i]) atomicAdd(&hist[i], (unsigned long long)sh[i]);
 }
 
 // sizes[sb_g + r] = |CO[r+2]| of graph g = cum(g, r+1)
@@ -74,27 +90,53 @@ __global__ void k_qtiles(Multi m, int64_t* __restrict__ qt) {
 }
 
 // Vertices of degree >= 1, per graph, in non-increasing degree order (the
-// order among equal degrees is arbitrary; the final sort does not depend on it).
-__global__ void k_place(const int32_t* __restrict__ deg, int64_t N, Multi m,
-                        unsigned long long* __restrict__ fill, int32_t* __restrict__ perm) {
+// order among equal degrees is arbitrary; the final sort does not depend on
+// it). Each CTA takes a contiguous vertex range: keys below HB_SMALL get one
+// global reservation per key and CTA (counted in shared memory first), the
+// others one per key and warp.
+__global__ void __launch_bounds__(256)
+k_place(const int32_t* __restrict__ deg, int64_t N, Multi m, unsigned long long* __restrict__ fill,
+        int32_t* __restrict__ perm) {
+  __shared__ unsigned long long sbase[HB_SMALL];
   const int lane = threadIdx.x & 31;
-  // uniform trip count per warp, so that the lanes can aggregate their atomics
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t first = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
-  for (int64_t v0 = first; v0 < N; v0 += stride) {
+  const int64_t per = ((N + gridDim.x - 1) / gridDim.x + 31) & ~(int64_t)31;
+  const int64_t v_lo = min(N, (int64_t)blockIdx.x * per), v_hi = min(N, v_lo + per);
+  auto key_of = [&](int64_t v, int32_t d, int64_t& g) -> unsigned long long {
+    g = (d < 1 || m.G == 1) ? 0 : last_le(m.vb, m.G, v);
+    return d >= 1 ? (unsigned long long)(m.hb[g] + d) : ~0ull;
+  };
+  // 1. counts of the small keys in this range
+  for (int i = threadIdx.x; i < HB_SMALL; i += blockDim.x) sbase[i] = 0;
+  __syncthreads();
+  for (int64_t v = v_lo + threadIdx.x; v < v_hi; v += blockDim.x) {
+    int64_t g;
+    const unsigned long long key = key_of(v, deg[v], g);
+    if (key < (unsigned long long)HB_SMALL) atomicAdd(&sbase[key], 1ull);
+  }
+  __syncthreads();
+  // 2. one reservation per small key
+  for (int i = threadIdx.x; i < HB_SMALL; i += blockDim.x) {
+    const unsigned long long c = sbase[i];
+    if (c) sbase[i] = atomicAdd(&fill[i], c);
+  }
+  __syncthreads();
+  // 3. placement (uniform trip count per warp for the aggregated atomics)
+  for (int64_t v0 = v_lo + (threadIdx.x & ~31); v0 < v_hi; v0 += blockDim.x) {
     const int64_t v = v0 + lane;
-    const int32_t d = v < N ? deg[v] : 0;
-    const bool take = d >= 1;
-    const int64_t g = (!take || m.G == 1) ? 0 : last_le(m.vb, m.G, v);
-    const unsigned long long key = take ? (unsigned long long)(m.hb[g] + d) : ~0ull;
-    // lanes with the same (graph, degree) bin take consecutive slots with one atomic
-    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const int32_t d = v < v_hi ? deg[v] : 0;
+    int64_t g;
+    const unsigned long long key = key_of(v, d, g);
+    const bool small = key < (unsigned long long)HB_SMALL;
+    const bool big = d >= 1 && !small;
+    // every lane takes part in the match and the shuffle
+    const unsigned peers = __match_any_sync(0xffffffffu, big ? key : ~0ull);
     const int leader = __ffs(peers) - 1;
-    unsigned long long slot = 0;
-    if (take && lane == leader) slot = atomicAdd(&fill[key], (unsigned long long)__popc(peers));
-    slot = __shfl_sync(0xffffffffu, slot, leader);
-    if (take) {
-      const int64_t pos = cum(m, g, d + 1) + (int64_t)slot + __popc(peers & ((1u << lane) - 1u));
+    unsigned long long gslot = 0;
+    if (big && lane == leader) gslot = atomicAdd(&fill[key], (unsigned long long)__popc(peers));
+    gslot = __shfl_sync(0xffffffffu, gslot, leader) + __popc(peers & ((1u << lane) - 1u));
+    const unsigned long long slot = small ? atomicAdd(&sbase[key], 1ull) : gslot;
+    if (d >= 1) {
+      const int64_t pos = cum(m, g, d + 1) + (int64_t)slot;
       perm[m.vb[g] + pos] = (int32_t)v;
     }
   }
@@ -126,8 +168,13 @@ k_co_scatter(const int32_t* __restrict__ perm, const int32_t* __restrict__ deg,
   __shared__ int64_t to[32];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
   const int64_t total = rt_prefix[Tub];
-  for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
-    const int64_t t = last_le(rt_prefix, Tub, tile);
+  // each CTA takes a contiguous range of tiles and walks its q-tile forward
+  // (one search per CTA instead of one dependent search per tile)
+  const int64_t per = (total + gridDim.x - 1) / gridDim.x;
+  const int64_t first = (int64_t)blockIdx.x * per, last = min(total, first + per);
+  int64_t t = first < last ? last_le(rt_prefix, Tub, first) : 0;
+  for (int64_t tile = first; tile < last; ++tile) {
+    while (rt_prefix[t + 1] <= tile) ++t;
     const int64_t r0 = (tile - rt_prefix[t]) * 32;
     const int64_t g = m.G == 1 ? 0 : last_le(qtb, m.G, t);
     const int64_t q0 = (t - qtb[g]) * 32;

@@ -98,37 +98,98 @@ int scan_impl(const T* in, int64_t* out, int64_t n, Pool& pool, cudaStream_t s) 
 }
 
 // deg[v], per-row checks, max degree. One warp per vertex row.
+// Degrees and CSR checks, 32 rows per warp: lane j reads the bounds of row
+// v0 + j, then the warp walks the group's arcs [off[v0], off[v0 + 32]) --
+// contiguous -- 32 positions at a time, each lane finding its row among the
+// group's by a five-step search over the lanes' row starts. (One warp per row
+// would leave most lanes idle on the many short rows.) Rows longer than
+// DEG_LONG are listed for k_degrees_long and jumped over (one warp would walk
+// a hub's row alone, one dependent load at a time). A group with a bad row
+// bound is not walked.
+constexpr int DEG_LONG = 4096;
+
 __global__ void k_degrees(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
                           int64_t n, int64_t arcs, int32_t* __restrict__ deg, int32_t* maxdeg,
-                          unsigned* status) {
+                          unsigned* status, int32_t* __restrict__ long_rows,
+                          unsigned* __restrict__ n_long) {
+  constexpr unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   int32_t local_max = 0;
   unsigned bad = 0;
-  for (int64_t v = warp; v < n; v += nwarps) {
-    const int64_t b = off[v], e = off[v + 1];
-    const int64_t d = e - b;
+  for (int64_t v0 = warp * 32; v0 < n; v0 += nwarps * 32) {
+    const int cnt = (int)min((int64_t)32, n - v0);  // rows in this group
+    const int64_t v = v0 + lane;
+    int64_t b = 0, e = 0;
+    if (lane < cnt) { b = off[v]; e = off[v + 1]; }
     // rows must lie inside [0, arcs] before adj is touched
-    if (b < 0 || e > arcs || d < 0 || d > 0x7fffffff) {
+    const bool row_bad = lane < cnt && (b < 0 || e > arcs || e - b < 0 || e - b > 0x7fffffff);
+    const bool is_long = !row_bad && e - b > DEG_LONG;
+    if (lane < cnt) {
+      deg[v] = row_bad ? 0 : (int32_t)(e - b);
+      if (!row_bad) local_max = max(local_max, (int32_t)(e - b));
+      if (is_long) long_rows[atomicAdd(n_long, 1u)] = (int32_t)v;
+    }
+    if (__any_sync(FULL, row_bad)) {
       bad = 1;
-      if (lane == 0) deg[v] = 0;
       continue;
     }
-    if (lane == 0) deg[v] = (int32_t)d;
-    local_max = max(local_max, (int32_t)d);
-    for (int64_t i = b + lane; i < e; i += 32) {
-      const int32_t x = adj[i];
-      if (x < 0 || x >= n || x == v) bad = 1;
-      if (i > b && adj[i - 1] >= x) bad = 1;  // strictly ascending: sorted, no duplicates
+    const int64_t gb = __shfl_sync(FULL, b, 0), ge = __shfl_sync(FULL, e, cnt - 1);
+    int32_t carry = 0;  // adj[i - 1] for lane 0
+    for (int64_t i0 = gb; i0 < ge;) {
+      const int64_t i = i0 + lane;
+      // row of position i: the last row of the group starting at or before it
+      int j = 0;
+#pragma unroll
+      for (int step = 16; step; step >>= 1) {
+        const int64_t bs = __shfl_sync(FULL, b, (j + step) & 31);
+        if (j + step < cnt && bs <= i) j += step;
+      }
+      const bool row_long = __shfl_sync(FULL, is_long, j);
+      const int j0 = __shfl_sync(FULL, j, 0);
+      if (__shfl_sync(FULL, row_long, 0)) {  // the chunk starts inside a long row: skip it
+        i0 = __shfl_sync(FULL, e, j0);
+        continue;
+      }
+      const bool act = i < ge && !row_long;
+      const int32_t x = act ? adj[i] : 0;
+      const int64_t bj = __shfl_sync(FULL, b, j);
+      int32_t prev = __shfl_up_sync(FULL, x, 1);
+      if (lane == 0) prev = carry;
+      carry = __shfl_sync(FULL, x, 31);
+      if (act) {
+        if (x < 0 || x >= n || x == v0 + j) bad = 1;
+        if (i > bj && prev >= x) bad = 1;  // strictly ascending: sorted, no duplicates
+      }
+      i0 += 32;
     }
   }
-  for (int o = 16; o; o >>= 1) local_max = max(local_max, __shfl_xor_sync(0xffffffffu, local_max, o));
-  bad = __any_sync(0xffffffffu, bad);
+  for (int o = 16; o; o >>= 1) local_max = max(local_max, __shfl_xor_sync(FULL, local_max, o));
+  bad = __any_sync(FULL, bad);
   if (lane == 0) {
     if (local_max) atomicMax(maxdeg, local_max);
     if (bad) atomicOr(status, (unsigned)DEV_BADGRAPH);
   }
+}
+
+// The CSR checks of the listed long rows, one CTA per row.
+__global__ void __launch_bounds__(1024)
+k_degrees_long(const int64_t* __restrict__ off, const int32_t* __restrict__ adj, int64_t n,
+               const int32_t* __restrict__ long_rows, const unsigned* __restrict__ n_long,
+               unsigned* status) {
+  const unsigned cnt = *n_long;
+  unsigned bad = 0;
+  for (unsigned r = blockIdx.x; r < cnt; r += gridDim.x) {
+    const int32_t v = long_rows[r];
+    const int64_t b = off[v], e = off[v + 1];
+    for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) {
+      const int32_t x = adj[i];
+      if (x < 0 || x >= n || x == v) bad = 1;
+      if (i > b && adj[i - 1] >= x) bad = 1;
+    }
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, (unsigned)DEV_BADGRAPH);
 }
 
 __device__ __forceinline__ bool lower(int32_t du, int32_t u, int32_t dv, int32_t v) {
@@ -269,10 +330,21 @@ int exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, Pool& 
 }
 
 int launch_degrees(const int64_t* off, const int32_t* adj, int64_t n, int64_t arcs, int32_t* deg,
-                   int32_t* maxdeg_dev, unsigned* status, cudaStream_t s) {
+                   int32_t* maxdeg_dev, unsigned* status, Pool& pool, cudaStream_t s) {
   if (n == 0) return SCAN_OK;
-  k_degrees<<<grid_for(n, 8), 256, 0, s>>>(off, adj, n, arcs, deg, maxdeg_dev, status);
+  const int64_t max_long = arcs / DEG_LONG + 1;
+  int32_t* long_rows = pool.get<int32_t>(max_long);
+  unsigned* n_long = pool.get<unsigned>(1);
+  if (!long_rows || !n_long) return SCAN_ENOMEM;
+  GS_CUDA(cudaMemsetAsync(n_long, 0, sizeof(unsigned), s));
+  k_degrees<<<grid_for(n, 256), 256, 0, s>>>(off, adj, n, arcs, deg, maxdeg_dev, status, long_rows,
+                                             n_long);
   GS_LAUNCH();
+  k_degrees_long<<<(unsigned)std::min<int64_t>(max_long, sm_count() * 2), 1024, 0, s>>>(
+      off, adj, n, long_rows, n_long, status);
+  GS_LAUNCH();
+  pool.put(long_rows);
+  pool.put(n_long);
   return SCAN_OK;
 }
 

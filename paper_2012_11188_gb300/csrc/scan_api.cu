@@ -198,7 +198,8 @@ int run_pipeline(IndexData* ix, int kind, const scan_lsh_params* lsh, Pool& pool
   const int64_t n = ix->n, arcs = ix->arcs;
   const bool use_lsh = lsh && lsh->enabled;
   unsigned* scalars = ix->status;  // [0] status, [1] maxdeg, [2] max out-degree
-  GS_TRY(launch_degrees(ix->off, ix->adj, n, arcs, ix->deg, (int32_t*)scalars + 1, scalars, s));
+  GS_TRY(launch_degrees(ix->off, ix->adj, n, arcs, ix->deg, (int32_t*)scalars + 1, scalars, pool,
+                        s));
   unsigned hs[4];
   GS_CUDA(cudaMemcpyAsync(hs, scalars, sizeof(hs), cudaMemcpyDeviceToHost, s));
   GS_CUDA(cudaStreamSynchronize(s));

@@ -117,7 +117,7 @@ struct IndexData {
 
 // Degrees, CSR checks (sorted, in range, no self-loops), max degree.
 int launch_degrees(const int64_t* off, const int32_t* adj, int64_t n, int64_t arcs, int32_t* deg,
-                   int32_t* maxdeg_dev, unsigned* status, cudaStream_t s);
+                   int32_t* maxdeg_dev, unsigned* status, Pool& pool, cudaStream_t s);
 
 // Orientation by (degree, id), in place: out(v) = oadj[off[v] .. off[v]+od[v]),
 // in id order; the in-neighbours of v fill the rest of its slot range,

@@ -30,9 +30,27 @@ struct KV {
   int32_t v;
 };
 
+// Segments as begin/end arrays: segment i is [b[i], e[i]). A contiguous
+// segmentation by offsets is {off, off + 1}; the buckets of long segments
+// are listed on their own, without the short segments between them.
+struct Segs {
+  const int64_t* b;
+  const int64_t* e;
+};
+
 // true iff a must come before b
 __device__ __forceinline__ bool before(uint64_t ka, int32_t va, uint64_t kb, int32_t vb) {
   return ka > kb || (ka == kb && va < vb);
+}
+
+// before() on elements i and j of one (key, val) array pair, the vals read
+// only when the keys tie: the searches are bound by shared-memory wavefronts,
+// and most probes are decided by the keys alone
+__device__ __forceinline__ bool before_at(const uint64_t* k, const int32_t* v, int64_t i,
+                                          int64_t j) {
+  const uint64_t ki = k[i], kj = k[j];
+  if (ki != kj) return ki > kj;
+  return v[i] < v[j];
 }
 
 constexpr int32_t SENT_V = 0x7fffffff;  // sorts after every real element (key 0, val max)
@@ -42,26 +60,41 @@ __device__ __forceinline__ int seg_class(int64_t len) {
 }
 
 // Count segments per class and number of tiles of long segments.
-__global__ void k_classify_count(const int64_t* __restrict__ seg_off, int64_t nseg,
-                                 unsigned long long* counts /* NCLASS + 1 (tiles) */) {
-  __shared__ unsigned long long c[NCLASS + 1];
-  if (threadIdx.x < NCLASS + 1) c[threadIdx.x] = 0;
+// counts[]: per class, tiles of the long class, the longest long segment,
+// and a flag for offsets that are not non-decreasing within [0, total]
+constexpr int NCNT = NCLASS + 3;
+
+__global__ void k_classify_count(Segs S, int64_t nseg, int64_t total,
+                                 unsigned long long* counts) {
+  __shared__ unsigned long long c[NCLASS + 2];
+  if (threadIdx.x < NCLASS + 2) c[threadIdx.x] = 0;
   __syncthreads();
+  bool bad = false;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nseg;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t len = seg_off[i + 1] - seg_off[i];
+    const int64_t b = S.b[i], e = S.e[i];
+    if (b < 0 || e < b || e > total) {
+      bad = true;
+      continue;
+    }
+    const int64_t len = e - b;
     if (len <= 1) continue;
     const int cl = seg_class(len);
     atomicAdd(&c[cl], 1ull);
-    if (cl == 4) atomicAdd(&c[NCLASS], (unsigned long long)((len + TILE - 1) / TILE));
+    if (cl == 4) {
+      atomicAdd(&c[NCLASS], (unsigned long long)((len + TILE - 1) / TILE));
+      atomicMax(&c[NCLASS + 1], (unsigned long long)len);
+    }
   }
   __syncthreads();
   if (threadIdx.x < NCLASS + 1 && c[threadIdx.x]) atomicAdd(&counts[threadIdx.x], c[threadIdx.x]);
+  if (threadIdx.x == NCLASS + 1 && c[threadIdx.x]) atomicMax(&counts[threadIdx.x], c[threadIdx.x]);
+  if (bad) atomicOr(&counts[NCLASS + 2], 1ull);
 }
 
 // Fill per-class segment lists (order irrelevant). The lanes of a warp that
 // share a class take consecutive slots with one atomic.
-__global__ void k_classify_fill(const int64_t* __restrict__ seg_off, int64_t nseg,
+__global__ void k_classify_fill(Segs S, int64_t nseg,
                                 const int64_t* __restrict__ class_base,
                                 unsigned long long* __restrict__ fill, int64_t* __restrict__ list) {
   const int lane = threadIdx.x & 31;
@@ -69,7 +102,7 @@ __global__ void k_classify_fill(const int64_t* __restrict__ seg_off, int64_t nse
   for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < nseg;
        i0 += stride) {
     const int64_t i = i0 + lane;
-    const int64_t len = i < nseg ? seg_off[i + 1] - seg_off[i] : 0;
+    const int64_t len = i < nseg ? S.e[i] - S.b[i] : 0;
     const int cl = len <= 1 ? -1 : seg_class(len);
     const unsigned peers = __match_any_sync(0xffffffffu, cl);
     const int leader = __ffs(peers) - 1;
@@ -83,7 +116,7 @@ __global__ void k_classify_fill(const int64_t* __restrict__ seg_off, int64_t nse
 
 // <= 32 elements: one warp per segment, bitonic network across lanes.
 __global__ void k_sort_warp(uint64_t* __restrict__ key, int32_t* __restrict__ val,
-                            const int64_t* __restrict__ seg_off, const int64_t* __restrict__ list,
+                            Segs S, const int64_t* __restrict__ list,
                             const unsigned long long* __restrict__ count_ptr) {
   const int lane = threadIdx.x & 31;
   const int64_t cnt = (int64_t)*count_ptr;
@@ -91,8 +124,8 @@ __global__ void k_sort_warp(uint64_t* __restrict__ key, int32_t* __restrict__ va
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t w = w0; w < cnt; w += nw) {
     const int64_t sg = list[w];
-    const int64_t b = seg_off[sg];
-    const int len = (int)(seg_off[sg + 1] - b);
+    const int64_t b = S.b[sg];
+    const int len = (int)(S.e[sg] - b);
     uint64_t k = 0;
     int32_t v = SENT_V;
     if (lane < len) { k = key[b + lane]; v = val[b + lane]; }
@@ -136,8 +169,7 @@ __device__ __forceinline__ int smem_merge_path_p(const uint64_t* k, const int32_
   int lo = max(0, d - lb), hi = min(d, la);
   while (lo < hi) {
     const int i = (lo + hi) >> 1;
-    const int pb = pslot<R>(b0 + d - 1 - i), pa = pslot<R>(a0 + i);
-    if (before(k[pb], v[pb], k[pa], v[pa])) hi = i;
+    if (before_at(k, v, pslot<R>(b0 + d - 1 - i), pslot<R>(a0 + i))) hi = i;
     else lo = i + 1;
   }
   return lo;
@@ -214,20 +246,20 @@ __device__ __forceinline__ void merge_out(const uint64_t* ks, const int32_t* vs,
   }
 }
 
-// One CTA of TT threads sorts a tile of up to TT*RI elements (RI = 8 or 16)
-// at the next power of two SE >= max(len, RI): the tile is loaded into
-// shared memory with coalesced reads (padded with sentinels that sort last),
-// each thread sorts RI consecutive elements in registers, then merge-path
-// levels double the sorted runs up to SE, each thread writing RI outputs per
-// level. Tiles are whole segments (TILED = false) or TILE-element pieces of
-// longer segments (TILED = true, TT*RI = TILE). A tiled segment that takes
-// an odd number of merge passes has its tiles written to the scratch buffer
-// (tk, tv), so that its last pass ends in (key, val).
+// One CTA of TT threads sorts a tile of up to TT*RI elements (RI = 8 or 16):
+// the tile is loaded into shared memory with coalesced reads (padded with
+// sentinels that sort last up to a multiple of RI), each thread sorts RI
+// consecutive elements in registers, then merge-path levels double the
+// sorted runs (the last pair of a level may be short), each thread writing
+// RI outputs per level. Tiles are whole segments (TILED = false) or
+// TILE-element pieces of longer segments (TILED = true, TT*RI = TILE). A
+// tiled segment that takes an odd number of merge passes has its tiles
+// written to the scratch buffer (tk, tv), so that its last pass ends in
+// (key, val).
 template <int TT, int RI, bool TILED>
 __global__ void __launch_bounds__(TT, TT * RI >= 8192 ? 1 : (TT >= 1024 ? 1 : 1024 / TT))
-k_sort_tile(uint64_t* __restrict__ key, int32_t* __restrict__ val,
-            const int64_t* __restrict__ seg_off, const int64_t* __restrict__ list,
-            const unsigned long long* __restrict__ count_ptr,
+k_sort_tile(uint64_t* __restrict__ key, int32_t* __restrict__ val, Segs S,
+            const int64_t* __restrict__ list, const unsigned long long* __restrict__ count_ptr,
             const int64_t* __restrict__ tile_prefix, int64_t nlong, uint64_t* __restrict__ tk,
             int32_t* __restrict__ tv) {
   constexpr int CAP = TT * RI;
@@ -245,8 +277,8 @@ k_sort_tile(uint64_t* __restrict__ key, int32_t* __restrict__ val,
     int32_t* ov = val;
     if (!TILED) {
       const int64_t sg = list[u];
-      b = seg_off[sg];
-      len = seg_off[sg + 1] - b;
+      b = S.b[sg];
+      len = S.e[sg] - b;
     } else {
       int64_t lo = 0, hi = nlong;
       while (hi - lo > 1) {
@@ -254,21 +286,22 @@ k_sort_tile(uint64_t* __restrict__ key, int32_t* __restrict__ val,
         if (tile_prefix[mid] <= u) lo = mid; else hi = mid;
       }
       const int64_t sg = list[lo];
-      b = seg_off[sg] + (u - tile_prefix[lo]) * CAP;
-      len = min((int64_t)CAP, seg_off[sg + 1] - b);
-      if (passes_for(seg_off[sg + 1] - seg_off[sg]) & 1) { ok = tk; ov = tv; }
+      b = S.b[sg] + (u - tile_prefix[lo]) * CAP;
+      len = min((int64_t)CAP, S.e[sg] - b);
+      if (passes_for(S.e[sg] - S.b[sg]) & 1) { ok = tk; ov = tv; }
     }
-    int se = RI;
-    while (se < len) se <<= 1;
+    // the tile is worked up to len rounded up to RI (sentinels past len); the
+    // merge levels clip their last run pair there, so the work follows len
+    const int lr = len <= RI ? RI : (int)((len + RI - 1) / RI) * RI;
     // 1. coalesced load, sentinels past the end
-    for (int i = t; i < se; i += TT) {
+    for (int i = t; i < lr; i += TT) {
       const int p = pslot<RI>(i);
       if (i < len) { k0[p] = key[b + i]; v0[p] = val[b + i]; }
       else { k0[p] = 0; v0[p] = SENT_V; }
     }
     __syncthreads();
-    // 2. each thread sorts its 8 consecutive elements in registers
-    if (RI * t < se) {
+    // 2. each thread sorts its RI consecutive elements in registers
+    if (RI * t < lr) {
       uint64_t K[RI];
       int32_t V[RI];
 #pragma unroll
@@ -281,11 +314,12 @@ k_sort_tile(uint64_t* __restrict__ key, int32_t* __restrict__ val,
     // 3. merge levels in shared memory: runs of w -> 2w, ping-pong k0/v0 <-> k1/v1
     uint64_t *ks = k0, *kd = k1;
     int32_t *vs = v0, *vd = v1;
-    for (int w = RI; w < se; w <<= 1) {
+    for (int w = RI; w < lr; w <<= 1) {
       const int o = RI * t;  // first output of this thread
-      if (o < se) {
+      if (o < lr) {
         const int a0 = (o / (2 * w)) * (2 * w);
-        merge_out<RI, RI>(ks, vs, a0, w, a0 + w, w, o - a0, kd, vd, o);
+        const int la = min(w, lr - a0), lb = max(0, min(w, lr - a0 - w));
+        merge_out<RI, RI>(ks, vs, a0, la, a0 + w, lb, o - a0, kd, vd, o);
       }
       __syncthreads();
       uint64_t* tk2 = ks; ks = kd; kd = tk2;
@@ -315,7 +349,7 @@ constexpr int TLONG_RI = GS_SORT_LONG_RI;
 constexpr int TLONG_T = TILE / TLONG_RI;
 
 // Tiles per long segment (prefix computed by the caller).
-__global__ void k_long_tiles(const int64_t* __restrict__ seg_off, const int64_t* __restrict__ list,
+__global__ void k_long_tiles(Segs S, const int64_t* __restrict__ list,
                              const unsigned long long* __restrict__ count_ptr,
                              int64_t* __restrict__ tiles, int64_t* __restrict__ outchunks,
                              int chunk) {
@@ -323,7 +357,7 @@ __global__ void k_long_tiles(const int64_t* __restrict__ seg_off, const int64_t*
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t sg = list[i];
-    const int64_t len = seg_off[sg + 1] - seg_off[sg];
+    const int64_t len = S.e[sg] - S.b[sg];
     tiles[i] = (len + TILE - 1) / TILE;
     outchunks[i] = (len + chunk - 1) / chunk;
   }
@@ -347,7 +381,8 @@ __device__ __forceinline__ int64_t merge_path(const uint64_t* ka, const int32_t*
   int64_t lo = max((int64_t)0, d - lb), hi = min(d, la);
   while (lo < hi) {
     const int64_t i = (lo + hi) >> 1;  // take i from A, d-i from B
-    if (before(kb[d - 1 - i], vb[d - 1 - i], ka[i], va[i])) hi = i;
+    const uint64_t kbi = kb[d - 1 - i], kai = ka[i];
+    if (kbi != kai ? kbi > kai : vb[d - 1 - i] < va[i]) hi = i;
     else lo = i + 1;
   }
   return lo;
@@ -379,7 +414,7 @@ struct MergeDesc {
 // odd, so that its last pass writes (key, val).
 __global__ void k_merge_partition(const uint64_t* __restrict__ key, const int32_t* __restrict__ val,
                                   const uint64_t* __restrict__ tk, const int32_t* __restrict__ tv,
-                                  const int64_t* __restrict__ seg_off,
+                                  Segs S,
                                   const int64_t* __restrict__ list,
                                   const int64_t* __restrict__ chunk_prefix, int64_t nlong, int64_t L,
                                   int pass, MergeDesc* __restrict__ desc) {
@@ -388,7 +423,7 @@ __global__ void k_merge_partition(const uint64_t* __restrict__ key, const int32_
        c += (int64_t)gridDim.x * blockDim.x) {
     const int64_t si = chunk_segment(chunk_prefix, nlong, c);
     const int64_t sg = list[si];
-    const int64_t base = seg_off[sg], len = seg_off[sg + 1] - base;
+    const int64_t base = S.b[sg], len = S.e[sg] - base;
     MergeDesc d{0, 0, 0, 0, 0, 0};
     if (len > L) {
       d.from_tmp = (passes_for(len) - pass) & 1;
@@ -487,7 +522,7 @@ k_merge_pass(uint64_t* __restrict__ key, int32_t* __restrict__ val, uint64_t* __
         int lo2 = max(0, d - nb), hi2 = min(d, na);
         while (lo2 < hi2) {
           const int i = (lo2 + hi2) >> 1;
-          if (before(shk[na + d - 1 - i], shv[na + d - 1 - i], shk[i], shv[i])) hi2 = i;
+          if (before_at(shk, shv, na + d - 1 - i, i)) hi2 = i;
           else lo2 = i + 1;
         }
         int ia = lo2, ib = d - lo2;
@@ -532,20 +567,404 @@ k_merge_pass(uint64_t* __restrict__ key, int32_t* __restrict__ val, uint64_t* __
   cp_async_wait<0>();
 }
 
+// ---------------------------------------------------------------- buckets
+// Long segments are split into buckets by sample sort before any tile is
+// sorted: every long segment draws BKT_OS random samples per bucket (one per
+// stratum of its positions, so each element is drawn with the same
+// probability), the samples are sorted (the same segmented sort, one level
+// down), and every BKT_OS-th sorted sample becomes a splitter. An element
+// goes to the bucket numbered by the splitters that come strictly before it
+// in the (key desc, val asc) order, so every element of bucket j comes
+// before every element of bucket j + 1 and sorting the buckets sorts the
+// segment. The buckets then take the place of their segment in one
+// segmentation of the whole array, sorted one level down: by the short
+// segment kernels, or, when still long, split again.
+//
+// A level splits a segment into at most BKT_FAN buckets, so that each
+// 4096-element chunk, once sorted by bucket in shared memory, leaves for
+// global memory in runs of about 4 or more elements per bucket (scattered
+// single-element stores would be bound by L2 write transactions): a segment
+// of up to BKT_FAN * BKT_TARGET elements gets buckets of about BKT_TARGET
+// elements at once, a longer one buckets of BKT_TARGET * BKT_FAN^k first.
+constexpr int BKT_TARGET = 640;   // expected final bucket length (the 1024-element class)
+constexpr int BKT_FAN = 1024;     // buckets per segment and level
+constexpr int BKT_OS = 32;        // samples per bucket
+constexpr int BKT_CH = 4096;      // elements of one segment per chunk (sorted by bucket as one)
+constexpr int BKT_G = 8;          // chunks per group: a CTA's unit, one reservation per bucket
+constexpr int BKT_T = 512;        // threads of the count and scatter CTAs
+constexpr int BKT_E = BKT_CH / BKT_T;
+constexpr int BKT_DEPTH = 3;      // levels of bucketing before the merge passes take over
+
+__host__ __device__ __forceinline__ int64_t buckets_for(int64_t len) {
+  int64_t unit = BKT_TARGET;
+  while (unit * BKT_FAN < len) unit *= BKT_FAN;
+  const int64_t b = (len + unit - 1) / unit;
+  return b < 2 ? 2 : b;
+}
+
+// MurmurHash3's 64-bit finaliser (Appleby): sample positions within strata
+__device__ __forceinline__ uint64_t fmix64(uint64_t x) {
+  x ^= x >> 33;
+  x *= 0xff51afd7ed558ccdULL;
+  x ^= x >> 33;
+  x *= 0xc4ceb9fe1a85ec53ULL;
+  x ^= x >> 33;
+  return x;
+}
+
+// Buckets, samples and count/scatter groups of every long segment.
+__global__ void k_bucket_plan(Segs S, const int64_t* __restrict__ list,
+                              int64_t nlong, int64_t* __restrict__ nb, int64_t* __restrict__ ns,
+                              int64_t* __restrict__ nch) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nlong;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t sg = list[x];
+    const int64_t len = S.e[sg] - S.b[sg];
+    const int64_t b = buckets_for(len);
+    nb[x] = b;
+    ns[x] = b * BKT_OS;
+    nch[x] = (len + (int64_t)BKT_CH * BKT_G - 1) / ((int64_t)BKT_CH * BKT_G);  // groups
+  }
+}
+
+// Sample j of long segment x: a random position of stratum j of its ns_x
+// equal strata.
+__global__ void k_take_samples(const uint64_t* __restrict__ key, const int32_t* __restrict__ val,
+                               Segs S, const int64_t* __restrict__ list,
+                               const int64_t* __restrict__ soff, int64_t nlong, int depth,
+                               uint64_t* __restrict__ skey, int32_t* __restrict__ sval) {
+  const int64_t nsamples = soff[nlong];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nsamples;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t x = chunk_segment(soff, nlong, i);
+    const int64_t j = i - soff[x], nsx = soff[x + 1] - soff[x];
+    const int64_t sg = list[x];
+    const int64_t b = S.b[sg], len = S.e[sg] - b;
+    const int64_t s0 = j * len / nsx, s1 = (j + 1) * len / nsx;
+    const uint64_t h = fmix64(((uint64_t)x << 32) ^ (uint64_t)j ^ ((uint64_t)depth << 60));
+    const int64_t p = s0 + (int64_t)(h % (uint64_t)(s1 - s0));
+    skey[i] = key[b + p];
+    sval[i] = val[b + p];
+  }
+}
+
+// Exclusive block-wide scan of h[0 .. 2 * BKT_T) in place (two entries per
+// thread).
+__device__ __forceinline__ void block_exclusive_scan(unsigned* h, unsigned* wsum) {
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const unsigned h0 = h[2 * t], h1 = h[2 * t + 1];
+  const unsigned own = h0 + h1;
+  unsigned inc = own;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) wsum[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    const unsigned ws = lane < BKT_T / 32 ? wsum[lane] : 0u;
+    unsigned wi = ws;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += y;
+    }
+    if (lane < BKT_T / 32) wsum[lane] = wi - ws;
+  }
+  __syncthreads();
+  const unsigned pre = inc - own + wsum[w];
+  h[2 * t] = pre;
+  h[2 * t + 1] = pre + h0;
+}
+
+// Bucket of every element of the long segments (binary search over the
+// segment's splitters in shared memory) and the bucket sizes (one global
+// atomic per bucket and group of BKT_G chunks). Each chunk is sorted by
+// bucket in shared memory (a counting sort; lanes of a warp that share a
+// bucket take their ranks with one shared atomic) and written to (tk, tv,
+// tb) at its own positions, so that the scatter can move whole runs.
+__global__ void __launch_bounds__(BKT_T, 2)
+k_bucket_count(const uint64_t* __restrict__ key, const int32_t* __restrict__ val, Segs S,
+               const int64_t* __restrict__ list, int64_t nlong, const int64_t* __restrict__ soff,
+               const int64_t* __restrict__ boff, const int64_t* __restrict__ gpre,
+               const uint64_t* __restrict__ skey, const int32_t* __restrict__ sval,
+               unsigned long long* __restrict__ bcount, uint64_t* __restrict__ tk,
+               int32_t* __restrict__ tv, uint16_t* __restrict__ tb) {
+  extern __shared__ uint64_t bsm[];
+  uint64_t* spk = bsm;                                           // splitter keys [BKT_FAN]
+  uint64_t* stk = spk + BKT_FAN;                                 // staged keys [BKT_CH]
+  int32_t* spv = reinterpret_cast<int32_t*>(stk + BKT_CH);       // splitter vals [BKT_FAN]
+  unsigned* hist = reinterpret_cast<unsigned*>(spv + BKT_FAN);   // chunk sizes, then starts
+  unsigned* hsum = hist + BKT_FAN;                               // group sizes [BKT_FAN]
+  int32_t* stv = reinterpret_cast<int32_t*>(hsum + BKT_FAN);     // staged vals [BKT_CH]
+  uint16_t* stb = reinterpret_cast<uint16_t*>(stv + BKT_CH);     // staged buckets [BKT_CH]
+  __shared__ unsigned wsum[32];
+  const int t = threadIdx.x, lane = t & 31;
+  const int64_t G = gpre[nlong];
+  for (int64_t g = blockIdx.x; g < G; g += gridDim.x) {
+    const int64_t x = chunk_segment(gpre, nlong, g);
+    const int64_t sg = list[x];
+    const int64_t b = S.b[sg], len = S.e[sg] - b;
+    const int nbx = (int)(boff[x + 1] - boff[x]);
+    const int64_t q0 = (g - gpre[x]) * BKT_CH * BKT_G;
+    const int64_t q1 = min(len, q0 + (int64_t)BKT_CH * BKT_G);
+    for (int j = t; j < nbx - 1; j += BKT_T) {
+      const int64_t q = soff[x] + (int64_t)(j + 1) * BKT_OS;
+      spk[j] = skey[q];
+      spv[j] = sval[q];
+    }
+    hsum[2 * t] = 0;
+    hsum[2 * t + 1] = 0;
+    for (int64_t p0 = q0; p0 < q1; p0 += BKT_CH) {
+      const int n = (int)min((int64_t)BKT_CH, q1 - p0);
+      hist[2 * t] = 0;
+      hist[2 * t + 1] = 0;
+      __syncthreads();
+      uint64_t K[BKT_E];
+      int32_t V[BKT_E];
+      unsigned B[BKT_E], R[BKT_E];
+#pragma unroll
+      for (int e = 0; e < BKT_E; ++e) {
+        const int i = t + e * BKT_T;
+        const bool act = i < n;
+        int lo = 0;
+        if (act) {
+          const uint64_t k = key[b + p0 + i];
+          const int32_t v = val[b + p0 + i];
+          int hi = nbx - 1;  // splitters strictly before (k, v)
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            const uint64_t km = spk[mid];
+            if (km > k || (km == k && spv[mid] < v)) lo = mid + 1;
+            else hi = mid;
+          }
+          K[e] = k;
+          V[e] = v;
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, act ? lo : -1);
+        const int leader = __ffs(peers) - 1;
+        unsigned r0 = 0;
+        if (act && lane == leader) r0 = atomicAdd(&hist[lo], (unsigned)__popc(peers));
+        r0 = __shfl_sync(0xffffffffu, r0, leader);
+        B[e] = (unsigned)lo;
+        R[e] = r0 + __popc(peers & ((1u << lane) - 1u));
+      }
+      __syncthreads();
+      hsum[2 * t] += hist[2 * t];
+      hsum[2 * t + 1] += hist[2 * t + 1];
+      block_exclusive_scan(hist, wsum);  // hist[j] = first slot of bucket j in the chunk
+      __syncthreads();
+#pragma unroll
+      for (int e = 0; e < BKT_E; ++e) {
+        const int i = t + e * BKT_T;
+        if (i < n) {
+          const unsigned q = hist[B[e]] + R[e];
+          stk[q] = K[e];
+          stv[q] = V[e];
+          stb[q] = (uint16_t)B[e];
+        }
+      }
+      __syncthreads();
+      for (int i = t; i < n; i += BKT_T) {
+        tk[b + p0 + i] = stk[i];
+        tv[b + p0 + i] = stv[i];
+        tb[b + p0 + i] = stb[i];
+      }
+    }
+    __syncthreads();
+    for (int j = t; j < nbx; j += BKT_T)
+      if (hsum[j]) atomicAdd(&bcount[boff[x] + j], (unsigned long long)hsum[j]);
+    __syncthreads();
+  }
+}
+
+// Every group of the long segments, its chunks sorted by bucket in (tk, tv,
+// tb), moves to its buckets in (key, val): one global reservation per bucket
+// of the group (the sizes counted from the runs' ends and starts), then each
+// chunk's run of a bucket is copied to consecutive positions. The order of
+// the runs within a bucket is arbitrary; the bucket sort removes it.
+__global__ void __launch_bounds__(BKT_T, 4)
+k_bucket_scatter(const uint64_t* __restrict__ tk, const int32_t* __restrict__ tv,
+                 const uint16_t* __restrict__ tb, Segs S, const int64_t* __restrict__ list,
+                 int64_t nlong, const int64_t* __restrict__ boff, const int64_t* __restrict__ gpre,
+                 const int64_t* __restrict__ bscan, unsigned long long* __restrict__ bfill,
+                 uint64_t* __restrict__ key, int32_t* __restrict__ val) {
+  __shared__ uint16_t sb[BKT_CH];
+  __shared__ int rs[BKT_FAN];                   // first index of each bucket's run in the chunk
+  __shared__ unsigned cnt[BKT_FAN];             // bucket sizes in the group
+  __shared__ unsigned long long gpos[BKT_FAN];  // next global position of each bucket
+  const int t = threadIdx.x;
+  const int64_t G = gpre[nlong];
+  for (int64_t g = blockIdx.x; g < G; g += gridDim.x) {
+    const int64_t x = chunk_segment(gpre, nlong, g);
+    const int64_t sg = list[x];
+    const int64_t b = S.b[sg], len = S.e[sg] - b;
+    const int nbx = (int)(boff[x + 1] - boff[x]);
+    const int64_t q0 = (g - gpre[x]) * BKT_CH * BKT_G;
+    const int64_t q1 = min(len, q0 + (int64_t)BKT_CH * BKT_G);
+    const int64_t bb0 = boff[x];
+    const int64_t base = b - bscan[bb0];  // bucket j starts at base + bscan[bb0 + j]
+    for (int j = t; j < nbx; j += BKT_T) cnt[j] = 0;
+    __syncthreads();
+    // sizes: + (end) at each run's last element, - (start) at its first
+    const int m = (int)(q1 - q0);
+    for (int i = t; i < m; i += BKT_T) {
+      const int j = tb[b + q0 + i];
+      if (i == 0 || tb[b + q0 + i - 1] != j) atomicSub(&cnt[j], (unsigned)i);
+      if (i == m - 1 || tb[b + q0 + i + 1] != j) atomicAdd(&cnt[j], (unsigned)(i + 1));
+    }
+    __syncthreads();
+    for (int j = t; j < nbx; j += BKT_T) {
+      const unsigned c = cnt[j];
+      gpos[j] = (unsigned long long)(base + bscan[bb0 + j]) +
+                (c ? atomicAdd(&bfill[bb0 + j], (unsigned long long)c) : 0ull);
+    }
+    __syncthreads();
+    for (int64_t p0 = q0; p0 < q1; p0 += BKT_CH) {
+      const int n = (int)min((int64_t)BKT_CH, q1 - p0);
+      for (int i = t; i < n; i += BKT_T) sb[i] = tb[b + p0 + i];
+      __syncthreads();
+      for (int i = t; i < n; i += BKT_T)
+        if (i == 0 || sb[i - 1] != sb[i]) rs[sb[i]] = i;
+      __syncthreads();
+      for (int i = t; i < n; i += BKT_T) {
+        const int j = sb[i];
+        const int64_t q = (int64_t)gpos[j] + (i - rs[j]);
+        key[q] = tk[b + p0 + i];
+        val[q] = tv[b + p0 + i];
+      }
+      __syncthreads();
+      for (int i = t; i < n; i += BKT_T) {
+        const int j = sb[i];
+        if (i == n - 1 || sb[i + 1] != j) gpos[j] += (unsigned long long)(i + 1 - rs[j]);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Begin and end of every bucket in (key, val); the entries past the real
+// buckets are empty segments.
+__global__ void k_bucket_bounds(Segs S, const int64_t* __restrict__ list, int64_t nlong,
+                                const int64_t* __restrict__ boff, const int64_t* __restrict__ bscan,
+                                int64_t nb_ub, int64_t* __restrict__ bb, int64_t* __restrict__ be) {
+  const int64_t B = boff[nlong];
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nb_ub;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    if (k >= B) {
+      bb[k] = be[k] = 0;
+      continue;
+    }
+    const int64_t x = chunk_segment(boff, nlong, k);
+    const int64_t start = S.b[list[x]] + bscan[k] - bscan[boff[x]];
+    bb[k] = start;
+    be[k] = start + (bscan[k + 1] - bscan[k]);
+  }
+}
+
 }  // namespace
 
-int segmented_sort_desc(uint64_t* key, int32_t* val, const int64_t* seg_off, int64_t nseg,
-                        int64_t total, int64_t max_len, Pool& pool, cudaStream_t s) {
-  if (nseg <= 0 || total <= 1 || max_len <= 1) return SCAN_OK;
-  unsigned long long* counts = pool.get<unsigned long long>(2 * (NCLASS + 1));
-  if (!counts) return SCAN_ENOMEM;
-  GS_CUDA(cudaMemsetAsync(counts, 0, 2 * (NCLASS + 1) * sizeof(unsigned long long), s));
-  const unsigned g_seg = (unsigned)std::min<int64_t>((nseg + 255) / 256, sm_count() * 16);
-  k_classify_count<<<g_seg, 256, 0, s>>>(seg_off, nseg, counts);
+namespace {
+
+unsigned grid_of(int64_t units, int per) {
+  int64_t g = (units + per - 1) / per;
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, sm_count() * 32));
+}
+
+int sort_level(uint64_t* key, int32_t* val, Segs S, int64_t nseg, int64_t total, Pool& pool,
+               cudaStream_t s, int depth);
+
+// Moves the elements of the nlong long segments (device list llist) into
+// their buckets and sorts the buckets one level down. total bounds every
+// position of the array.
+int bucket_level(uint64_t* key, int32_t* val, Segs S, int64_t total, const int64_t* llist,
+                 int64_t nlong, Pool& pool, cudaStream_t s, int depth) {
+  // bounds known on the host: every long segment has at most len / BKT_TARGET
+  // + 1 buckets and len / (BKT_CH * BKT_G) + 1 groups
+  const int64_t B_ub = std::min<int64_t>(total / BKT_TARGET + 2 * nlong, nlong * BKT_FAN);
+  const int64_t S_ub = B_ub * BKT_OS;
+  const int64_t C_ub = total / ((int64_t)BKT_CH * BKT_G) + nlong;  // groups
+  int64_t* nb = pool.get<int64_t>(nlong);
+  int64_t* ns = pool.get<int64_t>(nlong);
+  int64_t* nch = pool.get<int64_t>(nlong);
+  int64_t* boff = pool.get<int64_t>(nlong + 1);
+  int64_t* soff = pool.get<int64_t>(nlong + 1);
+  int64_t* cpre = pool.get<int64_t>(nlong + 1);
+  uint64_t* skey = pool.get<uint64_t>(S_ub);
+  int32_t* sval = pool.get<int32_t>(S_ub);
+  if (!nb || !ns || !nch || !boff || !soff || !cpre || !skey || !sval) return SCAN_ENOMEM;
+  k_bucket_plan<<<grid_of(nlong, 256), 256, 0, s>>>(S, llist, nlong, nb, ns, nch);
   GS_LAUNCH();
-  unsigned long long hc[NCLASS + 1];
+  GS_TRY(exclusive_scan_i64(nb, boff, nlong, pool, s));
+  GS_TRY(exclusive_scan_i64(ns, soff, nlong, pool, s));
+  GS_TRY(exclusive_scan_i64(nch, cpre, nlong, pool, s));
+  k_take_samples<<<grid_of(S_ub, 256), 256, 0, s>>>(key, val, S, llist, soff, nlong, depth, skey,
+                                                    sval);
+  GS_LAUNCH();
+  GS_TRY(sort_level(skey, sval, Segs{soff, soff + 1}, nlong, S_ub, pool, s, depth + 1));
+  unsigned long long* bcount = pool.get<unsigned long long>(B_ub);
+  unsigned long long* bfill = pool.get<unsigned long long>(B_ub);
+  int64_t* bscan = pool.get<int64_t>(B_ub + 1);
+  uint16_t* bid = pool.get<uint16_t>(total);
+  uint64_t* tk = pool.get<uint64_t>(total);
+  int32_t* tv = pool.get<int32_t>(total);
+  if (!bcount || !bfill || !bscan || !bid || !tk || !tv) return SCAN_ENOMEM;
+  GS_CUDA(cudaMemsetAsync(bcount, 0, B_ub * sizeof(unsigned long long), s));
+  GS_CUDA(cudaMemsetAsync(bfill, 0, B_ub * sizeof(unsigned long long), s));
+  constexpr size_t count_smem = (size_t)BKT_FAN * 20 + (size_t)BKT_CH * 14;
+  GS_CUDA(cudaFuncSetAttribute(k_bucket_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)count_smem));
+  const unsigned g_count =
+      (unsigned)std::max<int64_t>(1, std::min<int64_t>(C_ub, sm_count() * 2));
+  const unsigned g_scatter =
+      (unsigned)std::max<int64_t>(1, std::min<int64_t>(C_ub, sm_count() * 4));
+  k_bucket_count<<<g_count, BKT_T, count_smem, s>>>(key, val, S, llist, nlong, soff, boff, cpre,
+                                                    skey, sval, bcount, tk, tv, bid);
+  GS_LAUNCH();
+  GS_TRY(exclusive_scan_i64(reinterpret_cast<const int64_t*>(bcount), bscan, B_ub, pool, s));
+  k_bucket_scatter<<<g_scatter, BKT_T, 0, s>>>(tk, tv, bid, S, llist, nlong, boff, cpre, bscan,
+                                               bfill, key, val);
+  GS_LAUNCH();
+  pool.put(tk);
+  pool.put(tv);
+  pool.put(bid);
+  pool.put(skey);
+  pool.put(sval);
+  pool.put(bcount);
+  pool.put(bfill);
+  // the buckets as segments of their own
+  int64_t* bb = pool.get<int64_t>(B_ub);
+  int64_t* be = pool.get<int64_t>(B_ub);
+  if (!bb || !be) return SCAN_ENOMEM;
+  k_bucket_bounds<<<grid_of(B_ub, 256), 256, 0, s>>>(S, llist, nlong, boff, bscan, B_ub, bb, be);
+  GS_LAUNCH();
+  pool.put(bscan);
+  pool.put(nb);
+  pool.put(ns);
+  pool.put(nch);
+  pool.put(boff);
+  pool.put(soff);
+  pool.put(cpre);
+  GS_TRY(sort_level(key, val, Segs{bb, be}, B_ub, total, pool, s, depth + 1));
+  pool.put(bb);
+  pool.put(be);
+  return SCAN_OK;
+}
+
+int sort_level(uint64_t* key, int32_t* val, Segs S, int64_t nseg, int64_t total, Pool& pool,
+               cudaStream_t s, int depth) {
+  if (nseg <= 0 || total <= 1) return SCAN_OK;
+  unsigned long long* counts = pool.get<unsigned long long>(2 * NCNT);
+  if (!counts) return SCAN_ENOMEM;
+  GS_CUDA(cudaMemsetAsync(counts, 0, 2 * NCNT * sizeof(unsigned long long), s));
+  const unsigned g_seg = (unsigned)std::min<int64_t>((nseg + 255) / 256, sm_count() * 16);
+  k_classify_count<<<g_seg, 256, 0, s>>>(S, nseg, total, counts);
+  GS_LAUNCH();
+  unsigned long long hc[NCNT];
   GS_CUDA(cudaMemcpyAsync(hc, counts, sizeof(hc), cudaMemcpyDeviceToHost, s));
   GS_CUDA(cudaStreamSynchronize(s));
+  if (hc[NCLASS + 2]) return SCAN_EINVAL;  // before any element is touched
   int64_t base[NCLASS + 1];
   base[0] = 0;
   for (int c = 0; c < NCLASS; ++c) base[c + 1] = base[c] + (int64_t)hc[c];
@@ -553,16 +972,18 @@ int segmented_sort_desc(uint64_t* key, int32_t* val, const int64_t* seg_off, int
   int64_t* base_dev = pool.get<int64_t>(NCLASS + 1);
   if (!list || !base_dev) return SCAN_ENOMEM;
   GS_CUDA(cudaMemcpyAsync(base_dev, base, sizeof(base), cudaMemcpyHostToDevice, s));
-  unsigned long long* fill = counts + (NCLASS + 1);
-  k_classify_fill<<<g_seg, 256, 0, s>>>(seg_off, nseg, base_dev, fill, list);
+  unsigned long long* fill = counts + NCNT;
+  k_classify_fill<<<g_seg, 256, 0, s>>>(S, nseg, base_dev, fill, list);
   GS_LAUNCH();
+  const int64_t nlong = (int64_t)hc[4];
+  const int64_t max_long = (int64_t)hc[NCLASS + 1];
+  // long segments are split into buckets, sorted one level down; below
+  // BKT_DEPTH levels they take the tiles and merge passes
+  const bool bucketed = nlong && depth < BKT_DEPTH;
+  if (bucketed) GS_TRY(bucket_level(key, val, S, total, list + base[4], nlong, pool, s, depth));
   // per-class counts on the device for the grid-stride kernels: counts[c]
-  auto grid_of = [](int64_t units, int per) {
-    int64_t g = (units + per - 1) / per;
-    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, sm_count() * 32));
-  };
   if (hc[0]) {
-    k_sort_warp<<<grid_of((int64_t)hc[0], 8), 256, 0, s>>>(key, val, seg_off, list + base[0],
+    k_sort_warp<<<grid_of((int64_t)hc[0], 8), 256, 0, s>>>(key, val, S, list + base[0],
                                                            counts + 0);
     GS_LAUNCH();
   }
@@ -571,7 +992,7 @@ int segmented_sort_desc(uint64_t* key, int32_t* val, const int64_t* seg_off, int
     // networks and merge levels: compact code, unlike fully unrolled bitonic
     // networks, whose instruction footprint stalls the warp on fetches)
     k_sort_tile<32, 8, false><<<grid_of((int64_t)hc[1], 1), 32, tile_smem_bytes<32, 8>(), s>>>(
-        key, val, seg_off, list + base[1], counts + 1, nullptr, 0, nullptr, nullptr);
+        key, val, S, list + base[1], counts + 1, nullptr, 0, nullptr, nullptr);
     GS_LAUNCH();
   }
   GS_CUDA(cudaFuncSetAttribute(k_merge_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -584,17 +1005,16 @@ int segmented_sort_desc(uint64_t* key, int32_t* val, const int64_t* seg_off, int
                                (int)tile_smem_bytes<T4K_T, 8>()));
   if (hc[2]) {
     k_sort_tile<128, 8, false><<<grid_of((int64_t)hc[2], 1), 128, tile_smem_bytes<128, 8>(), s>>>(
-        key, val, seg_off, list + base[2], counts + 2, nullptr, 0, nullptr, nullptr);
+        key, val, S, list + base[2], counts + 2, nullptr, 0, nullptr, nullptr);
     GS_LAUNCH();
   }
   if (hc[3]) {
     k_sort_tile<T4K_T, 8, false><<<grid_of((int64_t)hc[3], 1), T4K_T, tile_smem_bytes<T4K_T, 8>(),
                                  s>>>(
-        key, val, seg_off, list + base[3], counts + 3, nullptr, 0, nullptr, nullptr);
+        key, val, S, list + base[3], counts + 3, nullptr, 0, nullptr, nullptr);
     GS_LAUNCH();
   }
-  const int64_t nlong = (int64_t)hc[4];
-  if (nlong) {
+  if (nlong && !bucketed) {
     const int64_t* llist = list + base[4];
     int64_t* tiles = pool.get<int64_t>(nlong);
     int64_t* tile_prefix = pool.get<int64_t>(nlong + 1);
@@ -603,7 +1023,7 @@ int segmented_sort_desc(uint64_t* key, int32_t* val, const int64_t* seg_off, int
     uint64_t* tk = pool.get<uint64_t>(total);
     int32_t* tv = pool.get<int32_t>(total);
     if (!tiles || !tile_prefix || !chunks || !chunk_prefix || !tk || !tv) return SCAN_ENOMEM;
-    k_long_tiles<<<grid_of(nlong, 256), 256, 0, s>>>(seg_off, llist, counts + 4, tiles, chunks,
+    k_long_tiles<<<grid_of(nlong, 256), 256, 0, s>>>(S, llist, counts + 4, tiles, chunks,
                                                      MERGE_CHUNK);
     GS_LAUNCH();
     GS_TRY(exclusive_scan_i64(tiles, tile_prefix, nlong, pool, s));
@@ -612,7 +1032,7 @@ int segmented_sort_desc(uint64_t* key, int32_t* val, const int64_t* seg_off, int
     // tile sort (count = ntiles, read from counts[NCLASS])
     k_sort_tile<TLONG_T, TLONG_RI, true><<<grid_of(ntiles, 1), TLONG_T,
                                           tile_smem_bytes<TLONG_T, TLONG_RI>(), s>>>(
-        key, val, seg_off, llist, counts + NCLASS, tile_prefix, nlong, tk, tv);
+        key, val, S, llist, counts + NCLASS, tile_prefix, nlong, tk, tv);
     GS_LAUNCH();
     const int64_t total_chunks_ub = (total + MERGE_CHUNK - 1) / MERGE_CHUNK + nlong;
     MergeDesc* desc = pool.get<MergeDesc>((size_t)total_chunks_ub);
@@ -620,9 +1040,9 @@ int segmented_sort_desc(uint64_t* key, int32_t* val, const int64_t* seg_off, int
     // every pass reads each segment from the buffer its parity says and
     // writes the other; the last pass of every segment writes (key, val)
     int pass = 0;
-    for (int64_t L = TILE; L < max_len; L <<= 1, ++pass) {
+    for (int64_t L = TILE; L < max_long; L <<= 1, ++pass) {
       k_merge_partition<<<grid_of(total_chunks_ub, 256), 256, 0, s>>>(
-          key, val, tk, tv, seg_off, llist, chunk_prefix, nlong, L, pass, desc);
+          key, val, tk, tv, S, llist, chunk_prefix, nlong, L, pass, desc);
       GS_LAUNCH();
       k_merge_pass<<<grid_of(total_chunks_ub, 1), MERGE_T, MERGE_SMEM, s>>>(key, val, tk, tv,
                                                                            chunk_prefix, nlong,
@@ -641,6 +1061,14 @@ int segmented_sort_desc(uint64_t* key, int32_t* val, const int64_t* seg_off, int
   pool.put(base_dev);
   pool.put(counts);
   return SCAN_OK;
+}
+
+}  // namespace
+
+int segmented_sort_desc(uint64_t* key, int32_t* val, const int64_t* seg_off, int64_t nseg,
+                        int64_t total, int64_t max_len, Pool& pool, cudaStream_t s) {
+  if (nseg <= 0 || total <= 1 || max_len <= 1) return SCAN_OK;
+  return sort_level(key, val, Segs{seg_off, seg_off + 1}, nseg, total, pool, s, 0);
 }
 
 }  // namespace gscan

@@ -185,6 +185,42 @@ def test_bad_graphs_rejected(kind):
     assert e.value.status == -3
 
 
+def long_row_graph(kind=None):
+    # a hub of degree 5099 (a row longer than 4096) in the middle of a group
+    # of 32 rows, and a path through the other vertices
+    n, hub = 5100, 40
+    edges = [(hub, x) for x in range(n) if x != hub]
+    edges += [(x, x + 1) for x in range(n - 1) if hub not in (x, x + 1)]
+    g = graphgen.from_edges(n, edges)
+    off, adj = g.off.copy(), g.adj.copy()
+    h0, h1 = off[hub], off[hub + 1]
+    if kind == "unsorted_hub":
+        adj[h0 + 3000], adj[h0 + 3001] = adj[h0 + 3001], adj[h0 + 3000]
+    elif kind == "selfloop_hub":
+        adj[h0 + 39] = hub  # the entry 39 sits between 38 and 41: still ascending
+    elif kind == "range_hub":
+        adj[h1 - 1] = n + 5
+    elif kind == "unsorted_after":  # the row right after the hub, same group
+        r0, r1 = off[hub + 1], off[hub + 2]
+        adj[r0:r1] = adj[r0:r1][::-1]
+    return graphgen.CSR(off, adj)
+
+
+def test_long_row_graph_builds_like_the_oracle():
+    g = long_row_graph()
+    with build(g) as ix:
+        ex = ix.export()
+    ox = oracle.Index(g)
+    assert np.array_equal(ex["sim"], ox.sim) and np.array_equal(ex["co_id"], ox.co_id)
+
+
+@pytest.mark.parametrize("kind", ["unsorted_hub", "selfloop_hub", "range_hub", "unsorted_after"])
+def test_bad_long_rows_rejected(kind):
+    with pytest.raises(gs.ScanError) as e:
+        build(long_row_graph(kind))
+    assert e.value.status == -3
+
+
 def test_bad_query_arguments():
     g = graphgen.from_edges(4, [(0, 1), (1, 2), (2, 3)])
     with build(g) as ix:
