@@ -8,13 +8,13 @@
 // does not depend on stability: equal similarities come out in ascending id,
 // the tie rule of the paper's deterministic experiments.
 //
-// Segments are bucketed by length: <= 32 (one warp, one element per lane,
-// bitonic network across lanes), <= 256, <= 1024 and <= 4096 (one CTA of
-// 32, 128 or 512 threads: 8-element register sorts, then merge-path levels
-// in shared memory), longer (8192-element tiles sorted by one CTA the
-// same way, then merge-path passes over global memory that double the run
-// length, ping-ponging between the data and a scratch buffer; a pass costs
-// about one read and one write of the data).
+// Segments are classed by length: <= 32 (one warp, one element per lane,
+// bitonic network across lanes), <= 256, 512, 1024, 2048 and 4096 (one CTA
+// of 32 to 512 threads: 8-element register sorts, then merge-path levels in
+// shared memory), longer (split into buckets by sample sort, below; past
+// three levels of splitting, 8192-element tiles sorted by one CTA the same
+// way, then merge-path passes over global memory that double the run length,
+// ping-ponging between the data and a scratch buffer).
 #include "scan_internal.cuh"
 
 namespace gscan {
@@ -23,7 +23,8 @@ namespace {
 
 constexpr int WTILE = 256;   // rows up to this length are sorted by a one-warp CTA
 constexpr int TILE = 8192;   // tiles of long segments (one CTA of 1024 threads each)
-constexpr int NCLASS = 5;    // <=32, <=256, <=1024, <=4096, >4096
+constexpr int NCLASS = 7;    // <=32, <=256, <=512, <=1024, <=2048, <=4096, >4096
+constexpr int LONGC = NCLASS - 1;  // the long class
 
 struct KV {
   uint64_t k;
@@ -55,8 +56,11 @@ __device__ __forceinline__ bool before_at(const uint64_t* k, const int32_t* v, i
 
 constexpr int32_t SENT_V = 0x7fffffff;  // sorts after every real element (key 0, val max)
 
+// The tile classes double in length and in CTA size (32 to 512 threads at 8
+// elements each), so that a segment keeps at least half of its CTA busy.
 __device__ __forceinline__ int seg_class(int64_t len) {
-  return len <= 32 ? 0 : len <= WTILE ? 1 : len <= 1024 ? 2 : len <= 4096 ? 3 : 4;
+  return len <= 32 ? 0 : len <= WTILE ? 1 : len <= 512 ? 2 : len <= 1024 ? 3 : len <= 2048 ? 4
+       : len <= 4096 ? 5 : LONGC;
 }
 
 // Count segments per class and number of tiles of long segments.
@@ -81,7 +85,7 @@ __global__ void k_classify_count(Segs S, int64_t nseg, int64_t total,
     if (len <= 1) continue;
     const int cl = seg_class(len);
     atomicAdd(&c[cl], 1ull);
-    if (cl == 4) {
+    if (cl == LONGC) {
       atomicAdd(&c[NCLASS], (unsigned long long)((len + TILE - 1) / TILE));
       atomicMax(&c[NCLASS + 1], (unsigned long long)len);
     }
@@ -716,31 +720,36 @@ k_bucket_count(const uint64_t* __restrict__ key, const int32_t* __restrict__ val
     }
     hsum[2 * t] = 0;
     hsum[2 * t + 1] = 0;
+    const int nsp = nbx - 1;                         // splitters
+    const int top = nsp > 0 ? 1 << (31 - __clz(nsp)) : 0;  // largest power of two <= nsp
     for (int64_t p0 = q0; p0 < q1; p0 += BKT_CH) {
       const int n = (int)min((int64_t)BKT_CH, q1 - p0);
       hist[2 * t] = 0;
       hist[2 * t + 1] = 0;
-      __syncthreads();
+      // the chunk's elements first: independent loads in flight
       uint64_t K[BKT_E];
       int32_t V[BKT_E];
+#pragma unroll
+      for (int e = 0; e < BKT_E; ++e) {
+        const int i = t + e * BKT_T;
+        K[e] = i < n ? key[b + p0 + i] : 0;
+        V[e] = i < n ? val[b + p0 + i] : 0;
+      }
+      __syncthreads();
       unsigned B[BKT_E], R[BKT_E];
 #pragma unroll
       for (int e = 0; e < BKT_E; ++e) {
         const int i = t + e * BKT_T;
         const bool act = i < n;
+        // splitters strictly before (K, V): binary lifting, the same number of
+        // steps in every lane
         int lo = 0;
-        if (act) {
-          const uint64_t k = key[b + p0 + i];
-          const int32_t v = val[b + p0 + i];
-          int hi = nbx - 1;  // splitters strictly before (k, v)
-          while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            const uint64_t km = spk[mid];
-            if (km > k || (km == k && spv[mid] < v)) lo = mid + 1;
-            else hi = mid;
+        for (int step = top; step > 0; step >>= 1) {
+          const int pr = lo + step;
+          if (pr <= nsp) {
+            const uint64_t km = spk[pr - 1];
+            if (km > K[e] || (km == K[e] && spv[pr - 1] < V[e])) lo = pr;
           }
-          K[e] = k;
-          V[e] = v;
         }
         const unsigned peers = __match_any_sync(0xffffffffu, act ? lo : -1);
         const int leader = __ffs(peers) - 1;
@@ -975,12 +984,13 @@ int sort_level(uint64_t* key, int32_t* val, Segs S, int64_t nseg, int64_t total,
   unsigned long long* fill = counts + NCNT;
   k_classify_fill<<<g_seg, 256, 0, s>>>(S, nseg, base_dev, fill, list);
   GS_LAUNCH();
-  const int64_t nlong = (int64_t)hc[4];
+  const int64_t nlong = (int64_t)hc[LONGC];
   const int64_t max_long = (int64_t)hc[NCLASS + 1];
   // long segments are split into buckets, sorted one level down; below
   // BKT_DEPTH levels they take the tiles and merge passes
   const bool bucketed = nlong && depth < BKT_DEPTH;
-  if (bucketed) GS_TRY(bucket_level(key, val, S, total, list + base[4], nlong, pool, s, depth));
+  if (bucketed)
+    GS_TRY(bucket_level(key, val, S, total, list + base[LONGC], nlong, pool, s, depth));
   // per-class counts on the device for the grid-stride kernels: counts[c]
   if (hc[0]) {
     k_sort_warp<<<grid_of((int64_t)hc[0], 8), 256, 0, s>>>(key, val, S, list + base[0],
@@ -1000,22 +1010,35 @@ int sort_level(uint64_t* key, int32_t* val, Segs S, int64_t nseg, int64_t total,
   GS_CUDA(cudaFuncSetAttribute(k_sort_tile<TLONG_T, TLONG_RI, true>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)tile_smem_bytes<TLONG_T, TLONG_RI>()));
+  GS_CUDA(cudaFuncSetAttribute(k_sort_tile<256, 8, false>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)tile_smem_bytes<256, 8>()));
   GS_CUDA(cudaFuncSetAttribute(k_sort_tile<T4K_T, 8, false>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)tile_smem_bytes<T4K_T, 8>()));
   if (hc[2]) {
-    k_sort_tile<128, 8, false><<<grid_of((int64_t)hc[2], 1), 128, tile_smem_bytes<128, 8>(), s>>>(
+    k_sort_tile<64, 8, false><<<grid_of((int64_t)hc[2], 1), 64, tile_smem_bytes<64, 8>(), s>>>(
         key, val, S, list + base[2], counts + 2, nullptr, 0, nullptr, nullptr);
     GS_LAUNCH();
   }
   if (hc[3]) {
-    k_sort_tile<T4K_T, 8, false><<<grid_of((int64_t)hc[3], 1), T4K_T, tile_smem_bytes<T4K_T, 8>(),
-                                 s>>>(
+    k_sort_tile<128, 8, false><<<grid_of((int64_t)hc[3], 1), 128, tile_smem_bytes<128, 8>(), s>>>(
         key, val, S, list + base[3], counts + 3, nullptr, 0, nullptr, nullptr);
     GS_LAUNCH();
   }
+  if (hc[4]) {
+    k_sort_tile<256, 8, false><<<grid_of((int64_t)hc[4], 1), 256, tile_smem_bytes<256, 8>(), s>>>(
+        key, val, S, list + base[4], counts + 4, nullptr, 0, nullptr, nullptr);
+    GS_LAUNCH();
+  }
+  if (hc[5]) {
+    k_sort_tile<T4K_T, 8, false><<<grid_of((int64_t)hc[5], 1), T4K_T, tile_smem_bytes<T4K_T, 8>(),
+                                 s>>>(
+        key, val, S, list + base[5], counts + 5, nullptr, 0, nullptr, nullptr);
+    GS_LAUNCH();
+  }
   if (nlong && !bucketed) {
-    const int64_t* llist = list + base[4];
+    const int64_t* llist = list + base[LONGC];
     int64_t* tiles = pool.get<int64_t>(nlong);
     int64_t* tile_prefix = pool.get<int64_t>(nlong + 1);
     int64_t* chunks = pool.get<int64_t>(nlong);
@@ -1023,7 +1046,7 @@ int sort_level(uint64_t* key, int32_t* val, Segs S, int64_t nseg, int64_t total,
     uint64_t* tk = pool.get<uint64_t>(total);
     int32_t* tv = pool.get<int32_t>(total);
     if (!tiles || !tile_prefix || !chunks || !chunk_prefix || !tk || !tv) return SCAN_ENOMEM;
-    k_long_tiles<<<grid_of(nlong, 256), 256, 0, s>>>(S, llist, counts + 4, tiles, chunks,
+    k_long_tiles<<<grid_of(nlong, 256), 256, 0, s>>>(S, llist, counts + LONGC, tiles, chunks,
                                                      MERGE_CHUNK);
     GS_LAUNCH();
     GS_TRY(exclusive_scan_i64(tiles, tile_prefix, nlong, pool, s));
