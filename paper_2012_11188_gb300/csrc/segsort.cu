@@ -118,8 +118,9 @@ __global__ void k_classify_fill(Segs S, int64_t nseg,
   }
 }
 
-// <= 32 elements: one warp per segment, bitonic network across lanes.
-__global__ void k_sort_warp(uint64_t* __restrict__ key, int32_t* __restrict__ val,
+// <= 32 elements: one warp per segment, bitonic network across lanes; read
+// from (ik, iv), written to (key, val) (the same arrays, or a copy).
+__global__ void k_sort_warp(const uint64_t* ik, const int32_t* iv, uint64_t* key, int32_t* val,
                             Segs S, const int64_t* __restrict__ list,
                             const unsigned long long* __restrict__ count_ptr) {
   const int lane = threadIdx.x & 31;
@@ -132,7 +133,7 @@ __global__ void k_sort_warp(uint64_t* __restrict__ key, int32_t* __restrict__ va
     const int len = (int)(S.e[sg] - b);
     uint64_t k = 0;
     int32_t v = SENT_V;
-    if (lane < len) { k = key[b + lane]; v = val[b + lane]; }
+    if (lane < len) { k = ik[b + lane]; v = iv[b + lane]; }
 #pragma unroll
     for (int size = 2; size <= 32; size <<= 1) {
 #pragma unroll
@@ -255,14 +256,15 @@ __device__ __forceinline__ void merge_out(const uint64_t* ks, const int32_t* vs,
 // sentinels that sort last up to a multiple of RI), each thread sorts RI
 // consecutive elements in registers, then merge-path levels double the
 // sorted runs (the last pair of a level may be short), each thread writing
-// RI outputs per level. Tiles are whole segments (TILED = false) or
-// TILE-element pieces of longer segments (TILED = true, TT*RI = TILE). A
-// tiled segment that takes an odd number of merge passes has its tiles
-// written to the scratch buffer (tk, tv), so that its last pass ends in
-// (key, val).
+// RI outputs per level. The tile is read from (ik, iv) and written to (key,
+// val) (the same arrays, or a copy). Tiles are whole segments (TILED =
+// false) or TILE-element pieces of longer segments (TILED = true, TT*RI =
+// TILE, ik = key). A tiled segment that takes an odd number of merge passes
+// has its tiles written to the scratch buffer (tk, tv), so that its last
+// pass ends in (key, val).
 template <int TT, int RI, bool TILED>
 __global__ void __launch_bounds__(TT, TT * RI >= 8192 ? 1 : (TT >= 1024 ? 1 : 1024 / TT))
-k_sort_tile(uint64_t* __restrict__ key, int32_t* __restrict__ val, Segs S,
+k_sort_tile(const uint64_t* ik, const int32_t* iv, uint64_t* key, int32_t* val, Segs S,
             const int64_t* __restrict__ list, const unsigned long long* __restrict__ count_ptr,
             const int64_t* __restrict__ tile_prefix, int64_t nlong, uint64_t* __restrict__ tk,
             int32_t* __restrict__ tv) {
@@ -300,7 +302,7 @@ k_sort_tile(uint64_t* __restrict__ key, int32_t* __restrict__ val, Segs S,
     // 1. coalesced load, sentinels past the end
     for (int i = t; i < lr; i += TT) {
       const int p = pslot<RI>(i);
-      if (i < len) { k0[p] = key[b + i]; v0[p] = val[b + i]; }
+      if (i < len) { k0[p] = ik[b + i]; v0[p] = iv[b + i]; }
       else { k0[p] = 0; v0[p] = SENT_V; }
     }
     __syncthreads();
@@ -682,27 +684,106 @@ __device__ __forceinline__ void block_exclusive_scan(unsigned* h, unsigned* wsum
   h[2 * t + 1] = pre + h0;
 }
 
-// Bucket of every element of the long segments (binary search over the
-// segment's splitters in shared memory) and the bucket sizes (one global
-// atomic per bucket and group of BKT_G chunks). Each chunk is sorted by
-// bucket in shared memory (a counting sort; lanes of a warp that share a
-// bucket take their ranks with one shared atomic) and written to (tk, tv,
-// tb) at its own positions, so that the scatter can move whole runs.
+// Bucket of every element of the long segments, written to bid, and the
+// bucket sizes per group of BKT_G chunks (ghist) and per segment (one global
+// atomic per bucket and group). The segment's splitters are held in shared
+// memory as a complete binary search tree in breadth-first order (node i's
+// children are 2i and 2i + 1; padded with entries that no element follows),
+// so that every lane descends the same number of levels without branches.
 __global__ void __launch_bounds__(BKT_T, 2)
-k_bucket_count(const uint64_t* __restrict__ key, const int32_t* __restrict__ val, Segs S,
+k_bucket_count(const uint64_t* __restrict__ ck, const int32_t* __restrict__ cv, Segs S,
                const int64_t* __restrict__ list, int64_t nlong, const int64_t* __restrict__ soff,
                const int64_t* __restrict__ boff, const int64_t* __restrict__ gpre,
                const uint64_t* __restrict__ skey, const int32_t* __restrict__ sval,
-               unsigned long long* __restrict__ bcount, uint64_t* __restrict__ tk,
-               int32_t* __restrict__ tv, uint16_t* __restrict__ tb) {
+               unsigned long long* __restrict__ bcount, unsigned* __restrict__ ghist,
+               uint16_t* __restrict__ bid) {
+  __shared__ uint64_t tkey[BKT_FAN];
+  __shared__ int32_t tval[BKT_FAN];
+  __shared__ unsigned hsum[BKT_FAN];
+  constexpr int U = 8;  // elements per thread in flight
+  const int t = threadIdx.x, lane = t & 31;
+  const int64_t G = gpre[nlong];
+  for (int64_t g = blockIdx.x; g < G; g += gridDim.x) {
+    const int64_t x = chunk_segment(gpre, nlong, g);
+    const int64_t sg = list[x];
+    const int64_t b = S.b[sg], len = S.e[sg] - b;
+    const int nbx = (int)(boff[x + 1] - boff[x]);
+    const int nsp = nbx - 1;
+    const int L = 32 - __clz(nsp);  // levels: 2^L - 1 >= nsp nodes
+    const int64_t q0 = (g - gpre[x]) * BKT_CH * BKT_G;
+    const int m = (int)(min(len, q0 + (int64_t)BKT_CH * BKT_G) - q0);
+    for (int i = t + 1; i < (1 << L); i += BKT_T) {
+      const int l = 31 - __clz(i), p = i - (1 << l);
+      const int r = ((2 * p + 1) << (L - 1 - l)) - 1;  // in-order rank of node i
+      if (r < nsp) {
+        const int64_t q = soff[x] + (int64_t)(r + 1) * BKT_OS;
+        tkey[i] = skey[q];
+        tval[i] = sval[q];
+      } else {
+        tkey[i] = 0;  // sorts after every element
+        tval[i] = SENT_V;
+      }
+    }
+    for (int j = t; j < nbx; j += BKT_T) hsum[j] = 0;
+    __syncthreads();
+    const uint64_t* kc = ck + b + q0;
+    const int32_t* vc = cv + b + q0;
+    uint16_t* bc = bid + b + q0;
+    for (int i0 = 0; i0 < m; i0 += BKT_T * U) {
+      uint64_t K[U];
+      int32_t V[U];
+#pragma unroll
+      for (int e = 0; e < U; ++e) {
+        const int i = i0 + t + e * BKT_T;
+        K[e] = i < m ? kc[i] : 0;
+        V[e] = i < m ? vc[i] : 0;
+      }
+#pragma unroll
+      for (int e = 0; e < U; ++e) {
+        const int i = i0 + t + e * BKT_T;
+        int j = 1;
+        for (int l = 0; l < L; ++l) {
+          const uint64_t tk = tkey[j];
+          const bool right = tk > K[e] || (tk == K[e] && tval[j] < V[e]);
+          j = 2 * j + (right ? 1 : 0);
+        }
+        const int bk = j - (1 << L);  // splitters before (K, V)
+        const bool act = i < m;
+        if (act) bc[i] = (uint16_t)bk;
+        const unsigned peers = __match_any_sync(0xffffffffu, act ? bk : -1);
+        if (act && lane == __ffs(peers) - 1) atomicAdd(&hsum[bk], (unsigned)__popc(peers));
+      }
+    }
+    __syncthreads();
+    for (int j = t; j < nbx; j += BKT_T) {
+      const unsigned c = hsum[j];
+      ghist[g * BKT_FAN + j] = c;
+      if (c) atomicAdd(&bcount[boff[x] + j], (unsigned long long)c);
+    }
+    __syncthreads();
+  }
+}
+
+// Every group of the long segments moves from (ck, cv) to its buckets in
+// (ok, ov): one global reservation per bucket of the group (its size from
+// ghist), then each chunk is sorted by bucket in shared memory (a counting
+// sort; lanes of a warp that share a bucket take their ranks with one shared
+// atomic) and leaves in runs, one run per bucket, at the bucket's next free
+// positions. The order of the runs within a bucket is arbitrary; the bucket
+// sort removes it.
+__global__ void __launch_bounds__(BKT_T, 2)
+k_bucket_scatter(const uint64_t* __restrict__ ck, const int32_t* __restrict__ cv,
+                 const uint16_t* __restrict__ bid, const unsigned* __restrict__ ghist, Segs S,
+                 const int64_t* __restrict__ list, int64_t nlong, const int64_t* __restrict__ boff,
+                 const int64_t* __restrict__ gpre, const int64_t* __restrict__ bscan,
+                 unsigned long long* __restrict__ bfill, uint64_t* __restrict__ ok,
+                 int32_t* __restrict__ ov) {
   extern __shared__ uint64_t bsm[];
-  uint64_t* spk = bsm;                                           // splitter keys [BKT_FAN]
-  uint64_t* stk = spk + BKT_FAN;                                 // staged keys [BKT_CH]
-  int32_t* spv = reinterpret_cast<int32_t*>(stk + BKT_CH);       // splitter vals [BKT_FAN]
-  unsigned* hist = reinterpret_cast<unsigned*>(spv + BKT_FAN);   // chunk sizes, then starts
-  unsigned* hsum = hist + BKT_FAN;                               // group sizes [BKT_FAN]
-  int32_t* stv = reinterpret_cast<int32_t*>(hsum + BKT_FAN);     // staged vals [BKT_CH]
-  uint16_t* stb = reinterpret_cast<uint16_t*>(stv + BKT_CH);     // staged buckets [BKT_CH]
+  uint64_t* stk = bsm;                                            // staged keys [BKT_CH]
+  unsigned long long* gpos = reinterpret_cast<unsigned long long*>(stk + BKT_CH);  // [BKT_FAN]
+  int32_t* stv = reinterpret_cast<int32_t*>(gpos + BKT_FAN);      // staged vals [BKT_CH]
+  unsigned* hist = reinterpret_cast<unsigned*>(stv + BKT_CH);     // chunk sizes, then starts
+  uint16_t* stb = reinterpret_cast<uint16_t*>(hist + BKT_FAN);    // staged buckets [BKT_CH]
   __shared__ unsigned wsum[32];
   const int t = threadIdx.x, lane = t & 31;
   const int64_t G = gpre[nlong];
@@ -713,61 +794,47 @@ k_bucket_count(const uint64_t* __restrict__ key, const int32_t* __restrict__ val
     const int nbx = (int)(boff[x + 1] - boff[x]);
     const int64_t q0 = (g - gpre[x]) * BKT_CH * BKT_G;
     const int64_t q1 = min(len, q0 + (int64_t)BKT_CH * BKT_G);
-    for (int j = t; j < nbx - 1; j += BKT_T) {
-      const int64_t q = soff[x] + (int64_t)(j + 1) * BKT_OS;
-      spk[j] = skey[q];
-      spv[j] = sval[q];
+    const int64_t bb0 = boff[x];
+    const int64_t base = b - bscan[bb0];  // bucket j starts at base + bscan[bb0 + j]
+    for (int j = t; j < nbx; j += BKT_T) {
+      const unsigned c = ghist[g * BKT_FAN + j];
+      gpos[j] = (unsigned long long)(base + bscan[bb0 + j]) +
+                (c ? atomicAdd(&bfill[bb0 + j], (unsigned long long)c) : 0ull);
     }
-    hsum[2 * t] = 0;
-    hsum[2 * t + 1] = 0;
-    const int nsp = nbx - 1;                         // splitters
-    const int top = nsp > 0 ? 1 << (31 - __clz(nsp)) : 0;  // largest power of two <= nsp
     for (int64_t p0 = q0; p0 < q1; p0 += BKT_CH) {
       const int n = (int)min((int64_t)BKT_CH, q1 - p0);
+      const uint64_t* kc = ck + b + p0;
+      const int32_t* vc = cv + b + p0;
+      const uint16_t* bc = bid + b + p0;
       hist[2 * t] = 0;
       hist[2 * t + 1] = 0;
-      // the chunk's elements first: independent loads in flight
       uint64_t K[BKT_E];
       int32_t V[BKT_E];
-#pragma unroll
-      for (int e = 0; e < BKT_E; ++e) {
-        const int i = t + e * BKT_T;
-        K[e] = i < n ? key[b + p0 + i] : 0;
-        V[e] = i < n ? val[b + p0 + i] : 0;
-      }
-      __syncthreads();
       unsigned B[BKT_E], R[BKT_E];
 #pragma unroll
       for (int e = 0; e < BKT_E; ++e) {
         const int i = t + e * BKT_T;
-        const bool act = i < n;
-        // splitters strictly before (K, V): binary lifting, the same number of
-        // steps in every lane
-        int lo = 0;
-        for (int step = top; step > 0; step >>= 1) {
-          const int pr = lo + step;
-          if (pr <= nsp) {
-            const uint64_t km = spk[pr - 1];
-            if (km > K[e] || (km == K[e] && spv[pr - 1] < V[e])) lo = pr;
-          }
-        }
-        const unsigned peers = __match_any_sync(0xffffffffu, act ? lo : -1);
+        K[e] = i < n ? kc[i] : 0;
+        V[e] = i < n ? vc[i] : 0;
+        B[e] = i < n ? bc[i] : 0u;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int e = 0; e < BKT_E; ++e) {
+        const bool act = t + e * BKT_T < n;
+        const unsigned peers = __match_any_sync(0xffffffffu, act ? (int)B[e] : -1);
         const int leader = __ffs(peers) - 1;
         unsigned r0 = 0;
-        if (act && lane == leader) r0 = atomicAdd(&hist[lo], (unsigned)__popc(peers));
+        if (act && lane == leader) r0 = atomicAdd(&hist[B[e]], (unsigned)__popc(peers));
         r0 = __shfl_sync(0xffffffffu, r0, leader);
-        B[e] = (unsigned)lo;
         R[e] = r0 + __popc(peers & ((1u << lane) - 1u));
       }
       __syncthreads();
-      hsum[2 * t] += hist[2 * t];
-      hsum[2 * t + 1] += hist[2 * t + 1];
       block_exclusive_scan(hist, wsum);  // hist[j] = first slot of bucket j in the chunk
       __syncthreads();
 #pragma unroll
       for (int e = 0; e < BKT_E; ++e) {
-        const int i = t + e * BKT_T;
-        if (i < n) {
+        if (t + e * BKT_T < n) {
           const unsigned q = hist[B[e]] + R[e];
           stk[q] = K[e];
           stv[q] = V[e];
@@ -776,79 +843,30 @@ k_bucket_count(const uint64_t* __restrict__ key, const int32_t* __restrict__ val
       }
       __syncthreads();
       for (int i = t; i < n; i += BKT_T) {
-        tk[b + p0 + i] = stk[i];
-        tv[b + p0 + i] = stv[i];
-        tb[b + p0 + i] = stb[i];
+        const int j = stb[i];
+        const int64_t q = (int64_t)gpos[j] + (i - (int)hist[j]);
+        ok[q] = stk[i];
+        ov[q] = stv[i];
       }
+      __syncthreads();
+      for (int i = t; i < n; i += BKT_T) {
+        const int j = stb[i];
+        if (i == n - 1 || stb[i + 1] != j) gpos[j] += (unsigned long long)(i + 1 - (int)hist[j]);
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    for (int j = t; j < nbx; j += BKT_T)
-      if (hsum[j]) atomicAdd(&bcount[boff[x] + j], (unsigned long long)hsum[j]);
-    __syncthreads();
   }
 }
 
-// Every group of the long segments, its chunks sorted by bucket in (tk, tv,
-// tb), moves to its buckets in (key, val): one global reservation per bucket
-// of the group (the sizes counted from the runs' ends and starts), then each
-// chunk's run of a bucket is copied to consecutive positions. The order of
-// the runs within a bucket is arbitrary; the bucket sort removes it.
-__global__ void __launch_bounds__(BKT_T, 4)
-k_bucket_scatter(const uint64_t* __restrict__ tk, const int32_t* __restrict__ tv,
-                 const uint16_t* __restrict__ tb, Segs S, const int64_t* __restrict__ list,
-                 int64_t nlong, const int64_t* __restrict__ boff, const int64_t* __restrict__ gpre,
-                 const int64_t* __restrict__ bscan, unsigned long long* __restrict__ bfill,
-                 uint64_t* __restrict__ key, int32_t* __restrict__ val) {
-  __shared__ uint16_t sb[BKT_CH];
-  __shared__ int rs[BKT_FAN];                   // first index of each bucket's run in the chunk
-  __shared__ unsigned cnt[BKT_FAN];             // bucket sizes in the group
-  __shared__ unsigned long long gpos[BKT_FAN];  // next global position of each bucket
-  const int t = threadIdx.x;
-  const int64_t G = gpre[nlong];
-  for (int64_t g = blockIdx.x; g < G; g += gridDim.x) {
-    const int64_t x = chunk_segment(gpre, nlong, g);
+// Copies the listed segments from (sk, sv) to (dk, dv), one CTA per segment.
+__global__ void k_copy_segments(const uint64_t* __restrict__ sk, const int32_t* __restrict__ sv,
+                                uint64_t* __restrict__ dk, int32_t* __restrict__ dv, Segs S,
+                                const int64_t* __restrict__ list, int64_t nlist) {
+  for (int64_t x = blockIdx.x; x < nlist; x += gridDim.x) {
     const int64_t sg = list[x];
-    const int64_t b = S.b[sg], len = S.e[sg] - b;
-    const int nbx = (int)(boff[x + 1] - boff[x]);
-    const int64_t q0 = (g - gpre[x]) * BKT_CH * BKT_G;
-    const int64_t q1 = min(len, q0 + (int64_t)BKT_CH * BKT_G);
-    const int64_t bb0 = boff[x];
-    const int64_t base = b - bscan[bb0];  // bucket j starts at base + bscan[bb0 + j]
-    for (int j = t; j < nbx; j += BKT_T) cnt[j] = 0;
-    __syncthreads();
-    // sizes: + (end) at each run's last element, - (start) at its first
-    const int m = (int)(q1 - q0);
-    for (int i = t; i < m; i += BKT_T) {
-      const int j = tb[b + q0 + i];
-      if (i == 0 || tb[b + q0 + i - 1] != j) atomicSub(&cnt[j], (unsigned)i);
-      if (i == m - 1 || tb[b + q0 + i + 1] != j) atomicAdd(&cnt[j], (unsigned)(i + 1));
-    }
-    __syncthreads();
-    for (int j = t; j < nbx; j += BKT_T) {
-      const unsigned c = cnt[j];
-      gpos[j] = (unsigned long long)(base + bscan[bb0 + j]) +
-                (c ? atomicAdd(&bfill[bb0 + j], (unsigned long long)c) : 0ull);
-    }
-    __syncthreads();
-    for (int64_t p0 = q0; p0 < q1; p0 += BKT_CH) {
-      const int n = (int)min((int64_t)BKT_CH, q1 - p0);
-      for (int i = t; i < n; i += BKT_T) sb[i] = tb[b + p0 + i];
-      __syncthreads();
-      for (int i = t; i < n; i += BKT_T)
-        if (i == 0 || sb[i - 1] != sb[i]) rs[sb[i]] = i;
-      __syncthreads();
-      for (int i = t; i < n; i += BKT_T) {
-        const int j = sb[i];
-        const int64_t q = (int64_t)gpos[j] + (i - rs[j]);
-        key[q] = tk[b + p0 + i];
-        val[q] = tv[b + p0 + i];
-      }
-      __syncthreads();
-      for (int i = t; i < n; i += BKT_T) {
-        const int j = sb[i];
-        if (i == n - 1 || sb[i + 1] != j) gpos[j] += (unsigned long long)(i + 1 - rs[j]);
-      }
-      __syncthreads();
+    for (int64_t i = S.b[sg] + threadIdx.x; i < S.e[sg]; i += blockDim.x) {
+      dk[i] = sk[i];
+      dv[i] = sv[i];
     }
   }
 }
@@ -881,63 +899,74 @@ unsigned grid_of(int64_t units, int per) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, sm_count() * 32));
 }
 
-int sort_level(uint64_t* key, int32_t* val, Segs S, int64_t nseg, int64_t total, Pool& pool,
-               cudaStream_t s, int depth);
+// Sorts every segment of S into (key, val). The data is in (key, val), or
+// in the copy (alt_k, alt_v) when in_alt; alt_k may be null until a level
+// needs it (it then holds total elements).
+int sort_level(uint64_t* key, int32_t* val, uint64_t* alt_k, int32_t* alt_v, Segs S, int64_t nseg,
+               int64_t total, bool in_alt, Pool& pool, cudaStream_t s, int depth);
 
 // Moves the elements of the nlong long segments (device list llist) into
-// their buckets and sorts the buckets one level down. total bounds every
-// position of the array.
-int bucket_level(uint64_t* key, int32_t* val, Segs S, int64_t total, const int64_t* llist,
-                 int64_t nlong, Pool& pool, cudaStream_t s, int depth) {
+// their buckets in the other array pair and sorts the buckets, as segments of
+// their own, one level down. total bounds every position of the array.
+int bucket_level(uint64_t* key, int32_t* val, uint64_t* alt_k, int32_t* alt_v, Segs S,
+                 int64_t total, const int64_t* llist, int64_t nlong, bool in_alt, Pool& pool,
+                 cudaStream_t s, int depth) {
+  const bool own_alt = alt_k == nullptr;
+  if (own_alt) {
+    alt_k = pool.get<uint64_t>(total);
+    alt_v = pool.get<int32_t>(total);
+    if (!alt_k || !alt_v) return SCAN_ENOMEM;
+  }
+  const uint64_t* ck = in_alt ? alt_k : key;  // where the data is
+  const int32_t* cv = in_alt ? alt_v : val;
+  uint64_t* ok = in_alt ? key : alt_k;        // where the buckets go
+  int32_t* ov = in_alt ? val : alt_v;
   // bounds known on the host: every long segment has at most len / BKT_TARGET
   // + 1 buckets and len / (BKT_CH * BKT_G) + 1 groups
   const int64_t B_ub = std::min<int64_t>(total / BKT_TARGET + 2 * nlong, nlong * BKT_FAN);
   const int64_t S_ub = B_ub * BKT_OS;
-  const int64_t C_ub = total / ((int64_t)BKT_CH * BKT_G) + nlong;  // groups
+  const int64_t G_ub = total / ((int64_t)BKT_CH * BKT_G) + nlong;
   int64_t* nb = pool.get<int64_t>(nlong);
   int64_t* ns = pool.get<int64_t>(nlong);
-  int64_t* nch = pool.get<int64_t>(nlong);
+  int64_t* ngr = pool.get<int64_t>(nlong);
   int64_t* boff = pool.get<int64_t>(nlong + 1);
   int64_t* soff = pool.get<int64_t>(nlong + 1);
-  int64_t* cpre = pool.get<int64_t>(nlong + 1);
+  int64_t* gpre = pool.get<int64_t>(nlong + 1);
   uint64_t* skey = pool.get<uint64_t>(S_ub);
   int32_t* sval = pool.get<int32_t>(S_ub);
-  if (!nb || !ns || !nch || !boff || !soff || !cpre || !skey || !sval) return SCAN_ENOMEM;
-  k_bucket_plan<<<grid_of(nlong, 256), 256, 0, s>>>(S, llist, nlong, nb, ns, nch);
+  if (!nb || !ns || !ngr || !boff || !soff || !gpre || !skey || !sval) return SCAN_ENOMEM;
+  k_bucket_plan<<<grid_of(nlong, 256), 256, 0, s>>>(S, llist, nlong, nb, ns, ngr);
   GS_LAUNCH();
   GS_TRY(exclusive_scan_i64(nb, boff, nlong, pool, s));
   GS_TRY(exclusive_scan_i64(ns, soff, nlong, pool, s));
-  GS_TRY(exclusive_scan_i64(nch, cpre, nlong, pool, s));
-  k_take_samples<<<grid_of(S_ub, 256), 256, 0, s>>>(key, val, S, llist, soff, nlong, depth, skey,
+  GS_TRY(exclusive_scan_i64(ngr, gpre, nlong, pool, s));
+  k_take_samples<<<grid_of(S_ub, 256), 256, 0, s>>>(ck, cv, S, llist, soff, nlong, depth, skey,
                                                     sval);
   GS_LAUNCH();
-  GS_TRY(sort_level(skey, sval, Segs{soff, soff + 1}, nlong, S_ub, pool, s, depth + 1));
+  GS_TRY(sort_level(skey, sval, nullptr, nullptr, Segs{soff, soff + 1}, nlong, S_ub, false, pool, s,
+                    depth + 1));
   unsigned long long* bcount = pool.get<unsigned long long>(B_ub);
   unsigned long long* bfill = pool.get<unsigned long long>(B_ub);
   int64_t* bscan = pool.get<int64_t>(B_ub + 1);
   uint16_t* bid = pool.get<uint16_t>(total);
-  uint64_t* tk = pool.get<uint64_t>(total);
-  int32_t* tv = pool.get<int32_t>(total);
-  if (!bcount || !bfill || !bscan || !bid || !tk || !tv) return SCAN_ENOMEM;
+  unsigned* ghist = pool.get<unsigned>((size_t)G_ub * BKT_FAN);
+  if (!bcount || !bfill || !bscan || !bid || !ghist) return SCAN_ENOMEM;
   GS_CUDA(cudaMemsetAsync(bcount, 0, B_ub * sizeof(unsigned long long), s));
   GS_CUDA(cudaMemsetAsync(bfill, 0, B_ub * sizeof(unsigned long long), s));
-  constexpr size_t count_smem = (size_t)BKT_FAN * 20 + (size_t)BKT_CH * 14;
-  GS_CUDA(cudaFuncSetAttribute(k_bucket_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)count_smem));
-  const unsigned g_count =
-      (unsigned)std::max<int64_t>(1, std::min<int64_t>(C_ub, sm_count() * 2));
-  const unsigned g_scatter =
-      (unsigned)std::max<int64_t>(1, std::min<int64_t>(C_ub, sm_count() * 4));
-  k_bucket_count<<<g_count, BKT_T, count_smem, s>>>(key, val, S, llist, nlong, soff, boff, cpre,
-                                                    skey, sval, bcount, tk, tv, bid);
+  constexpr size_t scatter_smem = (size_t)BKT_FAN * 12 + (size_t)BKT_CH * 14;
+  GS_CUDA(cudaFuncSetAttribute(k_bucket_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)scatter_smem));
+  const unsigned g_groups =
+      (unsigned)std::max<int64_t>(1, std::min<int64_t>(G_ub, sm_count() * 2));
+  k_bucket_count<<<g_groups, BKT_T, 0, s>>>(ck, cv, S, llist, nlong, soff, boff, gpre, skey, sval,
+                                            bcount, ghist, bid);
   GS_LAUNCH();
   GS_TRY(exclusive_scan_i64(reinterpret_cast<const int64_t*>(bcount), bscan, B_ub, pool, s));
-  k_bucket_scatter<<<g_scatter, BKT_T, 0, s>>>(tk, tv, bid, S, llist, nlong, boff, cpre, bscan,
-                                               bfill, key, val);
+  k_bucket_scatter<<<g_groups, BKT_T, scatter_smem, s>>>(ck, cv, bid, ghist, S, llist, nlong, boff,
+                                                         gpre, bscan, bfill, ok, ov);
   GS_LAUNCH();
-  pool.put(tk);
-  pool.put(tv);
   pool.put(bid);
+  pool.put(ghist);
   pool.put(skey);
   pool.put(sval);
   pool.put(bcount);
@@ -951,18 +980,23 @@ int bucket_level(uint64_t* key, int32_t* val, Segs S, int64_t total, const int64
   pool.put(bscan);
   pool.put(nb);
   pool.put(ns);
-  pool.put(nch);
+  pool.put(ngr);
   pool.put(boff);
   pool.put(soff);
-  pool.put(cpre);
-  GS_TRY(sort_level(key, val, Segs{bb, be}, B_ub, total, pool, s, depth + 1));
+  pool.put(gpre);
+  GS_TRY(sort_level(key, val, alt_k, alt_v, Segs{bb, be}, B_ub, total, !in_alt, pool, s,
+                    depth + 1));
   pool.put(bb);
   pool.put(be);
+  if (own_alt) {
+    pool.put(alt_k);
+    pool.put(alt_v);
+  }
   return SCAN_OK;
 }
 
-int sort_level(uint64_t* key, int32_t* val, Segs S, int64_t nseg, int64_t total, Pool& pool,
-               cudaStream_t s, int depth) {
+int sort_level(uint64_t* key, int32_t* val, uint64_t* alt_k, int32_t* alt_v, Segs S, int64_t nseg,
+               int64_t total, bool in_alt, Pool& pool, cudaStream_t s, int depth) {
   if (nseg <= 0 || total <= 1) return SCAN_OK;
   unsigned long long* counts = pool.get<unsigned long long>(2 * NCNT);
   if (!counts) return SCAN_ENOMEM;
@@ -981,6 +1015,8 @@ int sort_level(uint64_t* key, int32_t* val, Segs S, int64_t nseg, int64_t total,
   int64_t* base_dev = pool.get<int64_t>(NCLASS + 1);
   if (!list || !base_dev) return SCAN_ENOMEM;
   GS_CUDA(cudaMemcpyAsync(base_dev, base, sizeof(base), cudaMemcpyHostToDevice, s));
+  const uint64_t* ik = in_alt ? alt_k : key;  // where the data is
+  const int32_t* iv = in_alt ? alt_v : val;
   unsigned long long* fill = counts + NCNT;
   k_classify_fill<<<g_seg, 256, 0, s>>>(S, nseg, base_dev, fill, list);
   GS_LAUNCH();
@@ -990,10 +1026,11 @@ int sort_level(uint64_t* key, int32_t* val, Segs S, int64_t nseg, int64_t total,
   // BKT_DEPTH levels they take the tiles and merge passes
   const bool bucketed = nlong && depth < BKT_DEPTH;
   if (bucketed)
-    GS_TRY(bucket_level(key, val, S, total, list + base[LONGC], nlong, pool, s, depth));
+    GS_TRY(bucket_level(key, val, alt_k, alt_v, S, total, list + base[LONGC], nlong, in_alt, pool,
+                        s, depth));
   // per-class counts on the device for the grid-stride kernels: counts[c]
   if (hc[0]) {
-    k_sort_warp<<<grid_of((int64_t)hc[0], 8), 256, 0, s>>>(key, val, S, list + base[0],
+    k_sort_warp<<<grid_of((int64_t)hc[0], 8), 256, 0, s>>>(ik, iv, key, val, S, list + base[0],
                                                            counts + 0);
     GS_LAUNCH();
   }
@@ -1002,7 +1039,7 @@ int sort_level(uint64_t* key, int32_t* val, Segs S, int64_t nseg, int64_t total,
     // networks and merge levels: compact code, unlike fully unrolled bitonic
     // networks, whose instruction footprint stalls the warp on fetches)
     k_sort_tile<32, 8, false><<<grid_of((int64_t)hc[1], 1), 32, tile_smem_bytes<32, 8>(), s>>>(
-        key, val, S, list + base[1], counts + 1, nullptr, 0, nullptr, nullptr);
+        ik, iv, key, val, S, list + base[1], counts + 1, nullptr, 0, nullptr, nullptr);
     GS_LAUNCH();
   }
   GS_CUDA(cudaFuncSetAttribute(k_merge_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1018,27 +1055,31 @@ int sort_level(uint64_t* key, int32_t* val, Segs S, int64_t nseg, int64_t total,
                                (int)tile_smem_bytes<T4K_T, 8>()));
   if (hc[2]) {
     k_sort_tile<64, 8, false><<<grid_of((int64_t)hc[2], 1), 64, tile_smem_bytes<64, 8>(), s>>>(
-        key, val, S, list + base[2], counts + 2, nullptr, 0, nullptr, nullptr);
+        ik, iv, key, val, S, list + base[2], counts + 2, nullptr, 0, nullptr, nullptr);
     GS_LAUNCH();
   }
   if (hc[3]) {
     k_sort_tile<128, 8, false><<<grid_of((int64_t)hc[3], 1), 128, tile_smem_bytes<128, 8>(), s>>>(
-        key, val, S, list + base[3], counts + 3, nullptr, 0, nullptr, nullptr);
+        ik, iv, key, val, S, list + base[3], counts + 3, nullptr, 0, nullptr, nullptr);
     GS_LAUNCH();
   }
   if (hc[4]) {
     k_sort_tile<256, 8, false><<<grid_of((int64_t)hc[4], 1), 256, tile_smem_bytes<256, 8>(), s>>>(
-        key, val, S, list + base[4], counts + 4, nullptr, 0, nullptr, nullptr);
+        ik, iv, key, val, S, list + base[4], counts + 4, nullptr, 0, nullptr, nullptr);
     GS_LAUNCH();
   }
   if (hc[5]) {
     k_sort_tile<T4K_T, 8, false><<<grid_of((int64_t)hc[5], 1), T4K_T, tile_smem_bytes<T4K_T, 8>(),
                                  s>>>(
-        key, val, S, list + base[5], counts + 5, nullptr, 0, nullptr, nullptr);
+        ik, iv, key, val, S, list + base[5], counts + 5, nullptr, 0, nullptr, nullptr);
     GS_LAUNCH();
   }
   if (nlong && !bucketed) {
     const int64_t* llist = list + base[LONGC];
+    if (in_alt) {  // the tiles and merge passes work in (key, val)
+      k_copy_segments<<<grid_of(nlong, 1), 256, 0, s>>>(alt_k, alt_v, key, val, S, llist, nlong);
+      GS_LAUNCH();
+    }
     int64_t* tiles = pool.get<int64_t>(nlong);
     int64_t* tile_prefix = pool.get<int64_t>(nlong + 1);
     int64_t* chunks = pool.get<int64_t>(nlong);
@@ -1055,7 +1096,7 @@ int sort_level(uint64_t* key, int32_t* val, Segs S, int64_t nseg, int64_t total,
     // tile sort (count = ntiles, read from counts[NCLASS])
     k_sort_tile<TLONG_T, TLONG_RI, true><<<grid_of(ntiles, 1), TLONG_T,
                                           tile_smem_bytes<TLONG_T, TLONG_RI>(), s>>>(
-        key, val, S, llist, counts + NCLASS, tile_prefix, nlong, tk, tv);
+        key, val, key, val, S, llist, counts + NCLASS, tile_prefix, nlong, tk, tv);
     GS_LAUNCH();
     const int64_t total_chunks_ub = (total + MERGE_CHUNK - 1) / MERGE_CHUNK + nlong;
     MergeDesc* desc = pool.get<MergeDesc>((size_t)total_chunks_ub);
@@ -1091,7 +1132,8 @@ int sort_level(uint64_t* key, int32_t* val, Segs S, int64_t nseg, int64_t total,
 int segmented_sort_desc(uint64_t* key, int32_t* val, const int64_t* seg_off, int64_t nseg,
                         int64_t total, int64_t max_len, Pool& pool, cudaStream_t s) {
   if (nseg <= 0 || total <= 1 || max_len <= 1) return SCAN_OK;
-  return sort_level(key, val, Segs{seg_off, seg_off + 1}, nseg, total, pool, s, 0);
+  return sort_level(key, val, nullptr, nullptr, Segs{seg_off, seg_off + 1}, nseg, total, false, pool,
+                    s, 0);
 }
 
 }  // namespace gscan
