@@ -173,28 +173,33 @@ k_co_scatter(const int32_t* __restrict__ perm, const int32_t* __restrict__ deg,
   const int64_t per = (total + gridDim.x - 1) / gridDim.x;
   const int64_t first = (int64_t)blockIdx.x * per, last = min(total, first + per);
   int64_t t = first < last ? last_le(rt_prefix, Tub, first) : 0;
+  // the 32 vertices of a q-tile are looked up once for all its rank tiles
+  int64_t cur_t = -1, q0 = 0, sbg = 0;
   for (int64_t tile = first; tile < last; ++tile) {
     while (rt_prefix[t + 1] <= tile) ++t;
     const int64_t r0 = (tile - rt_prefix[t]) * 32;
-    const int64_t g = m.G == 1 ? 0 : last_le(qtb, m.G, t);
-    const int64_t q0 = (t - qtb[g]) * 32;
-    const int64_t nq = cum(m, g, 1);
-    const int64_t vbg = m.vb[g];
-    const int64_t sbg = m.sb[g];
-    if (threadIdx.x < 32) {
-      const int64_t q = q0 + threadIdx.x;
-      if (q < nq) {
-        const int32_t v = perm[vbg + q];
-        tv[threadIdx.x] = (int32_t)(v - vbg);
-        td[threadIdx.x] = deg[v];
-        to[threadIdx.x] = off[v];
-      } else {
-        tv[threadIdx.x] = -1;
-        td[threadIdx.x] = 0;
-        to[threadIdx.x] = 0;
+    if (t != cur_t) {
+      cur_t = t;
+      const int64_t g = m.G == 1 ? 0 : last_le(qtb, m.G, t);
+      q0 = (t - qtb[g]) * 32;
+      sbg = m.sb[g];
+      const int64_t nq = cum(m, g, 1);
+      const int64_t vbg = m.vb[g];
+      if (threadIdx.x < 32) {
+        const int64_t q = q0 + threadIdx.x;
+        if (q < nq) {
+          const int32_t v = perm[vbg + q];
+          tv[threadIdx.x] = (int32_t)(v - vbg);
+          td[threadIdx.x] = deg[v];
+          to[threadIdx.x] = off[v];
+        } else {
+          tv[threadIdx.x] = -1;
+          td[threadIdx.x] = 0;
+          to[threadIdx.x] = 0;
+        }
       }
+      __syncthreads();
     }
-    __syncthreads();
     for (int row = ty; row < 32; row += 8) {
       const int64_t r = r0 + tx;
       if (r < td[row]) tk[row][tx] = no_key[to[row] + r];

@@ -198,10 +198,13 @@ __device__ __forceinline__ bool lower(int32_t du, int32_t u, int32_t dv, int32_t
 
 // Orientation in place: the out-arcs of v (neighbours of larger (degree, id))
 // are compacted, in id order, to the front of v's own CSR slot range, so
-// out(v) = oadj[off[v] .. off[v] + od[v]) needs no separate offsets; opos
-// holds each out-arc's position in the row. One warp per row; rows longer
-// than LONG_ROW are listed in long_rows for k_orient_long (a warp would walk
-// a hub's row of 10^5 entries alone).
+// out(v) = oadj[off[v] .. off[v] + od[v]) needs no separate offsets; the
+// in-arcs fill the row from its end; opos holds each arc's position in the
+// row. 32 rows per warp, as in k_degrees: lane j keeps row v0 + j's bounds
+// and its running out- and in-arc counts, the warp walks the group's arcs 32
+// positions at a time, and each lane finds its row by a five-step search and
+// its place by ballots masked to its row's lanes. Rows longer than LONG_ROW
+// are listed in long_rows for k_orient_long and jumped over.
 constexpr int LONG_ROW = 4096;
 constexpr int LONG_T = 1024;
 
@@ -211,41 +214,75 @@ __global__ void k_orient_inplace(const int64_t* __restrict__ off, const int32_t*
                                  int32_t* __restrict__ opos, int32_t* max_od,
                                  unsigned long long* sum_od, int32_t* __restrict__ long_rows,
                                  unsigned* __restrict__ n_long) {
+  constexpr unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;  // lanes below this one
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   unsigned long long local_sum = 0;
   int32_t local_max = 0;
-  for (int64_t v = warp; v < n; v += nwarps) {
-    const int64_t b = off[v], e = off[v + 1];
-    const int32_t dv = deg[v];
-    if (dv > LONG_ROW) {
-      if (lane == 0) long_rows[atomicAdd(n_long, 1u)] = (int32_t)v;
-      continue;
-    }
-    int64_t w = b, wi = 0;  // out-arcs placed from the front, in-arcs from the back
-    for (int64_t i0 = b; i0 < e; i0 += 32) {
+  for (int64_t v0 = warp * 32; v0 < n; v0 += nwarps * 32) {
+    const int cnt = (int)min((int64_t)32, n - v0);  // rows in this group
+    const int64_t v = v0 + lane;
+    int64_t b = 0, e = 0;
+    int32_t d = 0;
+    if (lane < cnt) { b = off[v]; e = off[v + 1]; d = deg[v]; }
+    const bool is_long = d > LONG_ROW;
+    if (is_long) long_rows[atomicAdd(n_long, 1u)] = (int32_t)v;
+    int32_t w = 0, wi = 0;  // this lane's row: out-arcs placed from the front, in-arcs from the back
+    const int64_t gb = __shfl_sync(FULL, b, 0), ge = __shfl_sync(FULL, e, cnt - 1);
+    for (int64_t i0 = gb; i0 < ge;) {
       const int64_t i = i0 + lane;
-      bool up = false;
-      int32_t x = 0;
-      if (i < e) { x = adj[i]; up = lower(dv, (int32_t)v, deg[x], x); }
-      const unsigned m = __ballot_sync(0xffffffffu, up);
-      const int before = __popc(m & ((1u << lane) - 1u));
-      if (up) {
-        const int64_t dst = w + before;
-        oadj[dst] = x;
-        opos[dst] = (int32_t)(i - b);
-      } else if (i < e) {
-        const int64_t dst = e - 1 - (wi + (lane - before));
-        oadj[dst] = x;
-        opos[dst] = (int32_t)(i - b);
+      int j = 0;  // row of position i: the last row of the group starting at or before it
+#pragma unroll
+      for (int step = 16; step; step >>= 1) {
+        const int64_t bs = __shfl_sync(FULL, b, (j + step) & 31);
+        if (j + step < cnt && bs <= i) j += step;
       }
-      w += __popc(m);
-      wi += min((int64_t)32, e - i0) - __popc(m);
+      const bool row_long = __shfl_sync(FULL, is_long, j);
+      const int j0 = __shfl_sync(FULL, j, 0);
+      if (__shfl_sync(FULL, row_long, 0)) {  // the chunk starts inside a long row: skip it
+        i0 = __shfl_sync(FULL, e, j0);
+        continue;
+      }
+      const int64_t bj = __shfl_sync(FULL, b, j), ej = __shfl_sync(FULL, e, j);
+      const int32_t dj = __shfl_sync(FULL, d, j);
+      const int32_t wj = __shfl_sync(FULL, w, j), wij = __shfl_sync(FULL, wi, j);
+      const bool act = i < ge && !row_long;
+      int32_t x = 0;
+      bool up = false;
+      if (act) { x = adj[i]; up = lower(dj, (int32_t)(v0 + j), deg[x], x); }
+      const unsigned m = __ballot_sync(FULL, up), am = __ballot_sync(FULL, act);
+      // lanes of row j in this chunk: [bj - i0, ej - i0) clipped to [0, 32)
+      const int lo = (int)max((int64_t)0, bj - i0), hi = (int)min((int64_t)32, ej - i0);
+      const unsigned rowm = (hi >= 32 ? FULL : ((1u << hi) - 1u)) & ~((1u << lo) - 1u);
+      if (up) {
+        const int64_t dst = bj + wj + __popc(m & rowm & lt);
+        oadj[dst] = x;
+        opos[dst] = (int32_t)(i - bj);
+      } else if (act) {
+        const int64_t dst = ej - 1 - (wij + __popc(~m & am & rowm & lt));
+        oadj[dst] = x;
+        opos[dst] = (int32_t)(i - bj);
+      }
+      // each row's owner lane adds its row's counts of this chunk
+      const int mlo = (int)max((int64_t)0, b - i0), mhi = (int)min((int64_t)32, e - i0);
+      if (lane < cnt && mlo < mhi) {
+        const unsigned own = (mhi >= 32 ? FULL : ((1u << mhi) - 1u)) & ~((1u << mlo) - 1u);
+        w += __popc(m & own);
+        wi += __popc(~m & am & own);
+      }
+      i0 += 32;
     }
-    if (lane == 0) od[v] = (int32_t)(w - b);
-    local_sum += (unsigned long long)(w - b);
-    local_max = max(local_max, (int32_t)(w - b));
+    if (lane < cnt && !is_long) {
+      od[v] = w;
+      local_sum += (unsigned long long)w;
+      local_max = max(local_max, w);
+    }
+  }
+  for (int o = 16; o; o >>= 1) {
+    local_sum += __shfl_xor_sync(FULL, local_sum, o);
+    local_max = max(local_max, __shfl_xor_sync(FULL, local_max, o));
   }
   if (lane == 0) {
     if (local_sum) atomicAdd(sum_od, local_sum);
@@ -362,7 +399,7 @@ int launch_orient(const int64_t* off, const int32_t* adj, const int32_t* deg, in
   if (!od || !oadj || !opos || !long_rows || !n_long) return SCAN_ENOMEM;
   if (n > 0) {
     GS_CUDA(cudaMemsetAsync(n_long, 0, sizeof(unsigned), s));
-    k_orient_inplace<<<grid_for(n, 8), 256, 0, s>>>(off, adj, deg, n, od, oadj, opos, max_od_dev,
+    k_orient_inplace<<<grid_for(n, 256), 256, 0, s>>>(off, adj, deg, n, od, oadj, opos, max_od_dev,
                                                     sum_od_dev, long_rows, n_long);
     GS_LAUNCH();
     k_orient_long<<<(unsigned)std::min<int64_t>(max_long, sm_count() * 2), LONG_T, 0, s>>>(
