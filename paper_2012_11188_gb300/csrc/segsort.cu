@@ -592,7 +592,7 @@ k_merge_pass(uint64_t* __restrict__ key, int32_t* __restrict__ val, uint64_t* __
 // single-element stores would be bound by L2 write transactions): a segment
 // of up to BKT_FAN * BKT_TARGET elements gets buckets of about BKT_TARGET
 // elements at once, a longer one buckets of BKT_TARGET * BKT_FAN^k first.
-constexpr int BKT_TARGET = 640;   // expected final bucket length (the 1024-element class)
+constexpr int BKT_TARGET = 896;   // expected final bucket length (swept on R-MAT s24: 448 to 2816)
 constexpr int BKT_FAN = 1024;     // buckets per segment and level
 constexpr int BKT_OS = 32;        // samples per bucket
 constexpr int BKT_CH = 4096;      // elements of one segment per chunk (sorted by bucket as one)
