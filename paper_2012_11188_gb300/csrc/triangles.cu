@@ -631,21 +631,31 @@ k_tri_small(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
     if (lane == 0) base = atomicAdd(work, 32ull);
     base = __shfl_sync(FULL, base, 0);
     if ((int64_t)base >= n) break;
-    const int64_t vend = min(n, (int64_t)base + 32);
-    for (int64_t vv = (int64_t)base; vv < vend; ++vv) {
-      const int32_t dv = deg[vv];
-      if (dv == 0) continue;
-      const int32_t od = odeg[vv];
-      if (!warp_vertex(dv, od, warp_deg) || dv - od == 0) continue;  // CTA kernel, or no in-neighbours
-      const int64_t ob = off[vv];
-      OutTable tab{nullptr, 0, 27, 0u, 0u, okey + odp[vv], deg, od, true};
+    // the lanes read the 32 vertices' degrees at once; the warp then visits
+    // only its vertices with in-neighbours (most have none: their
+    // neighbours all rank above them)
+    const int64_t vl = (int64_t)base + lane;
+    const int32_t dl = vl < n ? deg[vl] : 0;
+    const int32_t ol = vl < n ? odeg[vl] : 0;
+    const bool mine = dl > 0 && warp_vertex(dl, ol, warp_deg) && dl - ol > 0;
+    const int64_t offl = mine ? off[vl] : 0, odpl = mine ? odp[vl] : 0;
+    unsigned todo = __ballot_sync(FULL, mine);
+    while (todo) {
+      const int k = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const int64_t vv = (int64_t)base + k;
+      const int32_t dv = __shfl_sync(FULL, dl, k);
+      const int32_t od = __shfl_sync(FULL, ol, k);
+      const int64_t ob = __shfl_sync(FULL, offl, k);
+      const uint64_t* okv = okey + __shfl_sync(FULL, odpl, k);
+      OutTable tab{nullptr, 0, 27, 0u, 0u, okv, deg, od, true};
       if (od > 0) {
-        tab = table_build(s_tab[wid], SW_SLOTS, vcnt, oadj + ob, okey + odp[vv], deg, od, lane, 32,
+        tab = table_build(s_tab[wid], SW_SLOTS, vcnt, oadj + ob, okv, deg, od, lane, 32,
                           [] { __syncwarp(); },
                           [](bool b) { __syncwarp(); return __any_sync(0xffffffffu, b) != 0; });
       }
       const bool use_table = !tab.bsearch;
-      const int64_t rb = off[vv] + od;  // vv's in-arcs
+      const int64_t rb = ob + od;  // vv's in-arcs
       for (int64_t pos0 = 0; pos0 < dv - od; pos0 += 32) {
         if (use_table)
           process_slice<false, IT, WT, R>(pos0, dv - od, rb, (int32_t)vv, dv, od, ob, long_list, opos, adj,
