@@ -13,8 +13,12 @@
  *    with query batches; a build is admitted only when its estimated device
  *    footprint fits the memory budget next to the indexes already built;
  *  - every request gets a ticket; scan_serve_wait blocks (with a time limit)
- *    until it completes. Results are identical to the same request made alone
- *    (exact mode is deterministic bit for bit).
+ *    until it completes. Results are identical to the same request made alone:
+ *    the server's builds are unweighted (exact mode is deterministic bit for
+ *    bit), and a query's labels depend only on its index, so queries on a
+ *    weighted index (built outside the server, whose similarities may differ
+ *    in the last bits from one build to the next) are identical alone and in
+ *    the mix as well.
  *
  * Ownership: the CSR arrays of a build request and the label buffer of a query
  * must stay valid until the ticket completes. Indexes built by the server

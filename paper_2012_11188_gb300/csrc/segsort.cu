@@ -26,11 +26,6 @@ constexpr int TILE = 8192;   // tiles of long segments (one CTA of 1024 threads 
 constexpr int NCLASS = 7;    // <=32, <=256, <=512, <=1024, <=2048, <=4096, >4096
 constexpr int LONGC = NCLASS - 1;  // the long class
 
-struct KV {
-  uint64_t k;
-  int32_t v;
-};
-
 // Segments as begin/end arrays: segment i is [b[i], e[i]). A contiguous
 // segmentation by offsets is {off, off + 1}; the buckets of long segments
 // are listed on their own, without the short segments between them.

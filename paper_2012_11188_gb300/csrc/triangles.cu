@@ -706,6 +706,38 @@ __device__ __forceinline__ int64_t row_of(const int64_t* __restrict__ odp, int64
   return lo;
 }
 
+// Every out-arc in compact order (k = odp[a] + i, i < od[a], at CSR
+// position j = off[a] + i), 32 rows per warp: lane l holds row v0 + l's odp
+// and off, the warp walks the group's out-arcs [odp[v0], odp[v0 + 32]) --
+// contiguous -- 32 at a time, and each lane finds its row by a five-step
+// search over the lanes' odp values (no dependent global loads, unlike a
+// binary search of odp). f(k, a, j) runs for every out-arc.
+template <class F>
+__device__ __forceinline__ void walk_out_arcs(const int64_t* __restrict__ off,
+                                              const int64_t* __restrict__ odp, int64_t n, F f) {
+  constexpr unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v0 = warp * 32; v0 < n; v0 += nwarps * 32) {
+    const int cnt = (int)min((int64_t)32, n - v0);
+    int64_t kb = 0, rb = 0;
+    if (lane < cnt) { kb = odp[v0 + lane]; rb = off[v0 + lane]; }
+    const int64_t g0 = __shfl_sync(FULL, kb, 0), g1 = odp[v0 + cnt];
+    for (int64_t k0 = g0; k0 < g1; k0 += 32) {
+      const int64_t k = k0 + lane;
+      int r = 0;
+#pragma unroll
+      for (int step = 16; step; step >>= 1) {
+        const int64_t bs = __shfl_sync(FULL, kb, (r + step) & 31);
+        if (r + step < cnt && bs <= k) r += step;
+      }
+      const int64_t kbr = __shfl_sync(FULL, kb, r), rbr = __shfl_sync(FULL, rb, r);
+      if (k < g1) f(k, v0 + r, rbr + (k - kbr));
+    }
+  }
+}
+
 __global__ void __launch_bounds__(EXPAND_T)
 k_expand(int kind, const int64_t* __restrict__ off, const int32_t* __restrict__ deg,
          const int64_t* __restrict__ odp, const int32_t* __restrict__ oadj,
@@ -759,47 +791,21 @@ k_rank_keys(const int64_t* __restrict__ off, const int32_t* __restrict__ deg,
             const int64_t* __restrict__ odp, const int32_t* __restrict__ oadj,
             const int32_t* __restrict__ opos, int64_t n, uint64_t* __restrict__ okey,
             int32_t* __restrict__ oval) {
-  __shared__ int64_t s_bracket[2];
-  const int64_t m = odp[n];
-  constexpr int64_t CH = (int64_t)EXPAND_T * EXPAND_ITEMS;
-  for (int64_t k0 = (int64_t)blockIdx.x * CH; k0 < m; k0 += (int64_t)gridDim.x * CH) {
-    const int64_t k1 = min(m, k0 + CH);
-    if (threadIdx.x == 0) s_bracket[0] = row_of(odp, 0, n + 1, k0);
-    if (threadIdx.x == 1) s_bracket[1] = row_of(odp, 0, n + 1, k1 - 1) + 1;
-    __syncthreads();
-    const int64_t lo = s_bracket[0], hi = s_bracket[1];
-    for (int64_t k = k0 + threadIdx.x; k < k1; k += EXPAND_T) {
-      const int64_t a = row_of(odp, lo, hi, k);
-      const int64_t j = off[a] + (k - odp[a]);
-      const int32_t x = oadj[j];
-      okey[k] = rank_key(deg[x], x);
-      oval[k] = opos[j];
-    }
-    __syncthreads();
-  }
+  walk_out_arcs(off, odp, n, [&](int64_t k, int64_t, int64_t j) {
+    const int32_t x = oadj[j];
+    okey[k] = rank_key(deg[x], x);
+    oval[k] = opos[j];
+  });
 }
 
 __global__ void __launch_bounds__(EXPAND_T)
 k_rank_scatter(const int64_t* __restrict__ off, const int64_t* __restrict__ odp, int64_t n,
                const uint64_t* __restrict__ okey, const int32_t* __restrict__ oval,
                int32_t* __restrict__ oadj, int32_t* __restrict__ opos) {
-  __shared__ int64_t s_bracket[2];
-  const int64_t m = odp[n];
-  constexpr int64_t CH = (int64_t)EXPAND_T * EXPAND_ITEMS;
-  for (int64_t k0 = (int64_t)blockIdx.x * CH; k0 < m; k0 += (int64_t)gridDim.x * CH) {
-    const int64_t k1 = min(m, k0 + CH);
-    if (threadIdx.x == 0) s_bracket[0] = row_of(odp, 0, n + 1, k0);
-    if (threadIdx.x == 1) s_bracket[1] = row_of(odp, 0, n + 1, k1 - 1) + 1;
-    __syncthreads();
-    const int64_t lo = s_bracket[0], hi = s_bracket[1];
-    for (int64_t k = k0 + threadIdx.x; k < k1; k += EXPAND_T) {
-      const int64_t a = row_of(odp, lo, hi, k);
-      const int64_t j = off[a] + (k - odp[a]);
-      oadj[j] = (int32_t)(uint32_t)~okey[k];
-      opos[j] = oval[k];
-    }
-    __syncthreads();
-  }
+  walk_out_arcs(off, odp, n, [&](int64_t k, int64_t, int64_t j) {
+    oadj[j] = (int32_t)(uint32_t)~okey[k];
+    opos[j] = oval[k];
+  });
 }
 
 // Weighted mode: ow[j] = weight of out-arc j (read at its row position);
@@ -808,28 +814,15 @@ __global__ void __launch_bounds__(EXPAND_T)
 k_out_weights(const int64_t* __restrict__ off, const int64_t* __restrict__ odp, int64_t n,
               const int32_t* __restrict__ opos, const double* __restrict__ wcsr,
               double* __restrict__ ow, unsigned* status) {
-  __shared__ int64_t s_bracket[2];
-  const int64_t m = odp[n];
-  constexpr int64_t CH = (int64_t)EXPAND_T * EXPAND_ITEMS;
   bool bad = false;
-  for (int64_t k0 = (int64_t)blockIdx.x * CH; k0 < m; k0 += (int64_t)gridDim.x * CH) {
-    const int64_t k1 = min(m, k0 + CH);
-    if (threadIdx.x == 0) s_bracket[0] = row_of(odp, 0, n + 1, k0);
-    if (threadIdx.x == 1) s_bracket[1] = row_of(odp, 0, n + 1, k1 - 1) + 1;
-    __syncthreads();
-    const int64_t lo = s_bracket[0], hi = s_bracket[1];
-    for (int64_t k = k0 + threadIdx.x; k < k1; k += EXPAND_T) {
-      const int64_t a = row_of(odp, lo, hi, k);
-      const int64_t j = off[a] + (k - odp[a]);
-      const double w = wcsr[off[a] + opos[j]];
-      // integer tests (off the FP64 pipe): negative non-zero, or inf / NaN
-      const long long bits = __double_as_longlong(w);
-      if ((bits < 0 && bits != (long long)0x8000000000000000ull) || ((bits >> 52) & 0x7ff) == 0x7ff)
-        bad = true;
-      ow[j] = w;
-    }
-    __syncthreads();
-  }
+  walk_out_arcs(off, odp, n, [&](int64_t, int64_t a, int64_t j) {
+    const double w = wcsr[off[a] + opos[j]];
+    // integer tests (off the FP64 pipe): negative non-zero, or inf / NaN
+    const long long bits = __double_as_longlong(w);
+    if ((bits < 0 && bits != (long long)0x8000000000000000ull) || ((bits >> 52) & 0x7ff) == 0x7ff)
+      bad = true;
+    ow[j] = w;
+  });
   if (bad) atomicOr(status, (unsigned)DEV_BADWEIGHT);
 }
 
@@ -1072,6 +1065,11 @@ int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* a
     GS_CUDA(cudaEventCreate(&k1));
   }
   GS_CUDA(cudaEventRecord(e0, s));
+  // the rank and weight passes walk 32 rows per warp (EXPAND_T / 32 warps a
+  // CTA); the similarity pass takes EXPAND_T * EXPAND_ITEMS edges per CTA
+  const unsigned wgrid =
+      (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + EXPAND_T - 1) / EXPAND_T,
+                                                       sm_count() * 32));
   const int64_t ch = (int64_t)EXPAND_T * EXPAND_ITEMS;
   const unsigned egrid =
       (unsigned)std::max<int64_t>(1, std::min<int64_t>((edges + ch - 1) / ch, sm_count() * 32));
@@ -1079,13 +1077,13 @@ int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* a
     // out-lists in ascending degree order, with their rank keys kept for the
     // searches of the counting kernels
     GS_TRY(exclusive_scan_i32_to_i64(odeg, odp, n, pool, s));
-    k_rank_keys<<<egrid, EXPAND_T, 0, s>>>(off, deg, odp, oadj, opos, n, okey, oval);
+    k_rank_keys<<<wgrid, EXPAND_T, 0, s>>>(off, deg, odp, oadj, opos, n, okey, oval);
     GS_LAUNCH();
     GS_TRY(segmented_sort_desc(okey, oval, odp, n, edges, max_od, pool, s));
-    k_rank_scatter<<<egrid, EXPAND_T, 0, s>>>(off, odp, n, okey, oval, oadj, opos);
+    k_rank_scatter<<<wgrid, EXPAND_T, 0, s>>>(off, odp, n, okey, oval, oadj, opos);
     GS_LAUNCH();
     if (weighted) {
-      k_out_weights<<<egrid, EXPAND_T, 0, s>>>(off, odp, n, opos, wcsr, ow, status);
+      k_out_weights<<<wgrid, EXPAND_T, 0, s>>>(off, odp, n, opos, wcsr, ow, status);
       GS_LAUNCH();
       if (narrow) {
         GS_TRY((launch_counting_cfg<int32_t, true>(off, adj, deg, odeg, oadj, opos, okey, odp, n, item_off,
