@@ -333,6 +333,21 @@ int scan_tuning_save(const char* path);
 int scan_tuning_load(const char* path);
 int scan_tuning_clear(void);
 
+/* The counting step of a sharded build (Section 3.1, closed counts; Section
+ * 6.1, the degree orientation): every triangle u < v < w of the orientation
+ * (order by degree, then id) has one middle vertex v, and this call counts
+ * only the triangles whose middle vertex lies in [v_begin, v_end). For every
+ * arc (x, y), counts[arc] receives the number of such triangles through the
+ * edge {x, y} (both arcs of an edge get the same value). Ranks whose ranges
+ * partition [0, n) and add their counts (one sum all-reduce) obtain
+ * t(x, y) = |N(x) ∩ N(y)| for every arc; the closed count is t + 2.
+ * csr: as for scan_index_build (host or device, checked the same way:
+ * SCAN_EBADGRAPH). counts: num_arcs uint32 in CSR order, host or device,
+ * written whole. 0 <= v_begin <= v_end <= n, else SCAN_EINVAL. Synchronises
+ * `stream`. */
+int scan_closed_counts_range(const scan_csr* csr, int64_t v_begin, int64_t v_end,
+                             uint32_t* counts, uintptr_t stream);
+
 /* The segmented sort of the neighbour and core orders (Algorithm 2), for
  * callers that assemble orders themselves, such as the sharded build, whose
  * ranks sort their runs of CO[mu] and merge the runs they receive. Every

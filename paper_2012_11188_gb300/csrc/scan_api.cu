@@ -1046,6 +1046,80 @@ int scan_tuning_load(const char* path) {
   return SCAN_OK;
 }
 
+int scan_closed_counts_range(const scan_csr* csr, int64_t v_begin, int64_t v_end,
+                             uint32_t* counts, uintptr_t stream) {
+  if (!csr) return SCAN_EINVAL;
+  GS_TRY(gscan::check_csr_args(csr));
+  const int64_t n = csr->n, arcs = csr->num_arcs;
+  if (v_begin < 0 || v_end < v_begin || v_end > n) return SCAN_EINVAL;
+  if (arcs > 0 && !counts) return SCAN_EINVAL;
+  if (arcs == 0) return SCAN_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  gscan::Pool pool(s);
+  int64_t* off = pool.get<int64_t>(n + 1);
+  int32_t* adj = pool.get<int32_t>(arcs);
+  int32_t* deg = pool.get<int32_t>(n > 0 ? n : 1);
+  unsigned* scalars = pool.get<unsigned>(8);  // [0] status, [1] maxdeg, [2] max out-degree, [4..5] sum od
+  const bool out_dev = gscan::is_device_ptr(counts);
+  uint32_t* out = out_dev ? counts : pool.get<uint32_t>(arcs);
+  if (!off || !adj || !deg || !scalars || !out) return SCAN_ENOMEM;
+  GS_CUDA(cudaMemsetAsync(scalars, 0, 8 * sizeof(unsigned), s));
+  GS_CUDA(cudaMemsetAsync(out, 0, arcs * sizeof(uint32_t), s));
+  // the CSR into device arrays with int64 offsets
+  const bool dev_in = csr->on_device != 0;
+  const cudaMemcpyKind k_in = dev_in ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  std::vector<int64_t> off_host;
+  if (csr->offsets_64) {
+    GS_CUDA(cudaMemcpyAsync(off, csr->offsets, (n + 1) * sizeof(int64_t), k_in, s));
+  } else if (dev_in) {
+    gscan::k_off32_to_64<<<(unsigned)std::min<int64_t>((n + 256) / 256, 4096), 256, 0, s>>>(
+        (const int32_t*)csr->offsets, n + 1, off);
+    GS_LAUNCH();
+  } else {
+    off_host.resize(n + 1);
+    const int32_t* o32 = (const int32_t*)csr->offsets;
+    for (int64_t i = 0; i <= n; ++i) off_host[i] = o32[i];
+    GS_CUDA(cudaMemcpyAsync(off, off_host.data(), (n + 1) * sizeof(int64_t),
+                            cudaMemcpyHostToDevice, s));
+  }
+  GS_CUDA(cudaMemcpyAsync(adj, csr->adj, arcs * sizeof(int32_t), k_in, s));
+  int64_t ends[2] = {0, 0};
+  GS_CUDA(cudaMemcpyAsync(&ends[0], off, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  GS_CUDA(cudaMemcpyAsync(&ends[1], off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  GS_CUDA(cudaStreamSynchronize(s));
+  if (ends[0] != 0 || ends[1] != arcs) return SCAN_EBADGRAPH;
+  // degrees and CSR checks, orientation (Section 6.1)
+  GS_TRY(gscan::launch_degrees(off, adj, n, arcs, deg, (int32_t*)scalars + 1, scalars, pool, s));
+  unsigned hs[4];
+  GS_CUDA(cudaMemcpyAsync(hs, scalars, sizeof(hs), cudaMemcpyDeviceToHost, s));
+  GS_CUDA(cudaStreamSynchronize(s));
+  if (hs[0] & gscan::DEV_BADGRAPH) return SCAN_EBADGRAPH;
+  const int32_t maxdeg = (int32_t)hs[1];
+  int32_t *od = nullptr, *oadj = nullptr, *opos = nullptr;
+  unsigned long long* sum_od = (unsigned long long*)(scalars + 4);
+  GS_TRY(gscan::launch_orient(off, adj, deg, n, arcs, pool, &od, &oadj, &opos,
+                              (int32_t*)scalars + 2, sum_od, s));
+  unsigned long long hsum = 0;
+  GS_CUDA(cudaMemcpyAsync(hs, scalars, sizeof(hs), cudaMemcpyDeviceToHost, s));
+  GS_CUDA(cudaMemcpyAsync(&hsum, sum_od, sizeof(hsum), cudaMemcpyDeviceToHost, s));
+  GS_CUDA(cudaStreamSynchronize(s));
+  if ((int64_t)hsum != arcs / 2) return SCAN_EBADGRAPH;
+  // the counts of the middle vertices in [v_begin, v_end) (Section 3.1)
+  const gscan::CountCfg cfg = gscan::count_config_for(n, n, arcs);
+  GS_TRY(gscan::launch_closed_counts_and_sims(SCAN_COSINE, off, adj, deg, n, arcs, od, oadj, opos,
+                                              maxdeg, (int32_t)hs[2], -1, nullptr, nullptr,
+                                              scalars, pool, s, nullptr, cfg, v_begin, v_end,
+                                              out));
+  GS_CUDA(cudaMemcpyAsync(hs, scalars, sizeof(hs), cudaMemcpyDeviceToHost, s));
+  GS_CUDA(cudaStreamSynchronize(s));
+  if (hs[0] & gscan::DEV_BADGRAPH) return SCAN_EBADGRAPH;
+  if (!out_dev) {
+    GS_CUDA(cudaMemcpyAsync(counts, out, arcs * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    GS_CUDA(cudaStreamSynchronize(s));
+  }
+  return SCAN_OK;
+}
+
 int scan_sort_segments_desc(double* keys, int32_t* ids, const int64_t* seg_off, int64_t nseg,
                             int64_t total, int64_t max_len, uintptr_t stream) {
   if (nseg < 0 || total < 0 || max_len < 0) return SCAN_EINVAL;

@@ -152,13 +152,17 @@ CountCfg count_config_for(int64_t n_max, int64_t n_total, int64_t arcs);
 // Closed counts of every edge by oriented triangle enumeration, then the
 // similarity of every CSR arc written to sim_csr (the unsorted NO). With
 // lsh_T >= 0, edges whose endpoints both have degree > lsh_T are left for the
-// LSH estimate (their sim_csr entries are overwritten later).
+// LSH estimate (their sim_csr entries are overwritten later). Only the
+// triangles whose middle vertex lies in [v0, v1) are counted (v1 < 0: n);
+// with counts_out, the triangle count of every arc is written there (CSR
+// order, zeroed by the caller) instead of the similarities.
 int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* adj,
                                   const int32_t* deg, int64_t n, int64_t arcs, const int32_t* od,
                                   int32_t* oadj, int32_t* opos, int32_t maxdeg,
                                   int32_t max_od, int lsh_T, const double* wcsr, double* sim_csr,
                                   unsigned* status, Pool& pool, cudaStream_t s, float* count_ms,
-                                  const CountCfg& cfg);
+                                  const CountCfg& cfg, int64_t v0 = 0, int64_t v1 = -1,
+                                  uint32_t* counts_out = nullptr);
 
 // Sort every segment [seg_off[i], seg_off[i+1]) of (key, val) pairs by key
 // descending, then val ascending. Keys are non-negative doubles viewed as

@@ -65,14 +65,18 @@ constexpr int SW_WARPS = 4;
 // the position of its source in N(v), even when out(v) is empty and no
 // triangle has v in the middle). items[v] -> prefix -> item index maps to
 // (v, chunk).
+// (v0, v1): only middle vertices in [v0, v1) get items (a rank's share of a
+// sharded count; the whole graph otherwise).
 __global__ void k_item_counts(const int32_t* __restrict__ odeg, const int32_t* __restrict__ deg,
-                              int64_t n, int warp_deg, int chunk, int32_t* __restrict__ items) {
+                              int64_t n, int warp_deg, int chunk, int64_t v0, int64_t v1,
+                              int32_t* __restrict__ items) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
        v += (int64_t)gridDim.x * blockDim.x) {
     const int64_t od = odeg[v];
     const int32_t d = deg[v];
     int c = 0;
-    if (!warp_vertex(d, od, warp_deg) && d - od > 0) c = (int)((d - od + chunk - 1) / chunk);
+    if (v >= v0 && v < v1 && !warp_vertex(d, od, warp_deg) && d - od > 0)
+      c = (int)((d - od + chunk - 1) / chunk);
     items[v] = c;
   }
 }
@@ -808,6 +812,29 @@ k_rank_scatter(const int64_t* __restrict__ off, const int64_t* __restrict__ odp,
   });
 }
 
+// Count mode (a rank's share of a sharded count): the triangle count of every
+// oriented edge, written to both of its arcs in CSR order; the second arc is
+// found by a binary search of the tail in the head's id-sorted row.
+__global__ void __launch_bounds__(EXPAND_T)
+k_counts_out(const int64_t* __restrict__ off, const int32_t* __restrict__ adj,
+             const int64_t* __restrict__ odp, const int32_t* __restrict__ oadj,
+             const int32_t* __restrict__ opos, const uint32_t* __restrict__ tcnt,
+             const uint32_t* __restrict__ tc16, int64_t n, uint32_t* __restrict__ out) {
+  walk_out_arcs(off, odp, n, [&](int64_t, int64_t a, int64_t j) {
+    const int32_t b = oadj[j];
+    uint32_t t = tcnt[j];
+    if (tc16) t += (tc16[j >> 1] >> ((j & 1) << 4)) & 0xffffu;
+    out[off[a] + opos[j]] = t;
+    int64_t lo = off[b], hi = off[b + 1];
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (adj[mid] < a) lo = mid + 1;
+      else hi = mid;
+    }
+    if (lo < off[b + 1] && adj[lo] == (int32_t)a) out[lo] = t;
+  });
+}
+
 // Weighted mode: ow[j] = weight of out-arc j (read at its row position);
 // a weight that is negative or not finite marks the build DEV_BADWEIGHT.
 __global__ void __launch_bounds__(EXPAND_T)
@@ -939,7 +966,7 @@ int launch_counting(const int64_t* off, const int32_t* adj, const int32_t* deg, 
                     unsigned long long* work, int lsh_T, int32_t max_od, int64_t* deferred,
                     unsigned long long* n_deferred, uint32_t* tcnt, uint32_t* tc16, int32_t* twin,
                     unsigned* status, const double* ow, double* tsum, const CountCfg& cfg,
-                    cudaStream_t s, cudaEvent_t k0 = nullptr, cudaEvent_t k1 = nullptr) {
+                    cudaStream_t s, cudaEvent_t k0, cudaEvent_t k1, int64_t small_end) {
   int od_cap = 16;
   while (od_cap < max_od && od_cap < SMEM_OD_MAX) od_cap <<= 1;
   // the table (12 bytes per slot, 2 * od_cap slots) and the counters (4 bytes)
@@ -963,8 +990,10 @@ int launch_counting(const int64_t* off, const int32_t* adj, const int32_t* deg, 
   GS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&small_per_sm, k_tri_small<IT, WT, R>,
                                                         SW_WARPS * 32, 0));
   if (small_per_sm < 1) small_per_sm = 1;
+  // the warp kernel takes its vertices from work[2] (set to the range's
+  // first vertex) up to small_end
   k_tri_small<IT, WT, R><<<sms * small_per_sm, SW_WARPS * 32, 0, s>>>(
-      off, adj, deg, odeg, oadj, opos, okey, odp, n, work + 2, lsh_T, cfg.warp_deg, cfg.long_list,
+      off, adj, deg, odeg, oadj, opos, okey, odp, small_end, work + 2, lsh_T, cfg.warp_deg, cfg.long_list,
       tcnt,
       tc16, twin, status, ow, tsum);
   GS_LAUNCH();
@@ -989,14 +1018,14 @@ int launch_counting_cfg(const int64_t* off, const int32_t* adj, const int32_t* d
                         int64_t* deferred, unsigned long long* n_deferred, uint32_t* tcnt,
                         uint32_t* tc16, int32_t* twin, unsigned* status, const double* ow,
                         double* tsum, const CountCfg& cfg, cudaStream_t s, cudaEvent_t k0,
-                        cudaEvent_t k1) {
+                        cudaEvent_t k1, int64_t small_end) {
   if (!WT && cfg.rounds == 8)
     return launch_counting<IT, WT, 8>(off, adj, deg, odeg, oadj, opos, okey, odp, n, item_off, order,
                                       work, lsh_T, max_od, deferred, n_deferred, tcnt, tc16, twin,
-                                      status, ow, tsum, cfg, s, k0, k1);
+                                      status, ow, tsum, cfg, s, k0, k1, small_end);
   return launch_counting<IT, WT, 4>(off, adj, deg, odeg, oadj, opos, okey, odp, n, item_off, order,
                                     work, lsh_T, max_od, deferred, n_deferred, tcnt, tc16, twin,
-                                    status, ow, tsum, cfg, s, k0, k1);
+                                    status, ow, tsum, cfg, s, k0, k1, small_end);
 }
 
 int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* adj,
@@ -1004,7 +1033,9 @@ int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* a
                                   int32_t* oadj, int32_t* opos, int32_t maxdeg,
                                   int32_t max_od, int lsh_T, const double* wcsr, double* sim_csr,
                                   unsigned* status, Pool& pool, cudaStream_t s, float* count_ms,
-                                  const CountCfg& cfg) {
+                                  const CountCfg& cfg, int64_t v0, int64_t v1,
+                                  uint32_t* counts_out) {
+  if (v1 < 0) v1 = n;
   const bool weighted = wcsr != nullptr;
   const int64_t m = arcs;  // out-lists live in CSR slots: counts and twins are indexed by arc
   const int64_t edges = m / 2;  // oriented edges (the orientation checked sum od = arcs / 2)
@@ -1039,6 +1070,11 @@ int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* a
   GS_CUDA(cudaMemsetAsync(tcnt, 0, m * sizeof(uint32_t), s));
   if (narrow) GS_CUDA(cudaMemsetAsync(tc16, 0, (m / 2 + 1) * sizeof(uint32_t), s));
   GS_CUDA(cudaMemsetAsync(work, 0, 4 * sizeof(unsigned long long), s));
+  if (v0 > 0) {  // the warp kernel's first vertex
+    const unsigned long long first = (unsigned long long)v0;
+    GS_CUDA(cudaMemcpyAsync(work + 2, &first, sizeof(first), cudaMemcpyHostToDevice, s));
+    GS_CUDA(cudaStreamSynchronize(s));  // `first` lives on this stack frame
+  }
   GS_CUDA(cudaMemsetAsync(hist, 0, 2 * nbins * sizeof(unsigned long long), s));
   if (m > 0) {
     k_fill_i32<<<1024, 256, 0, s>>>(twin, m, -1);
@@ -1046,7 +1082,7 @@ int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* a
   }
   if (n > 0) {
     const unsigned g = (unsigned)std::min<int64_t>((n + 255) / 256, sm_count() * 64);
-    k_item_counts<<<g, 256, 0, s>>>(odeg, deg, n, cfg.warp_deg, cfg.cta_chunk, items);
+    k_item_counts<<<g, 256, 0, s>>>(odeg, deg, n, cfg.warp_deg, cfg.cta_chunk, v0, v1, items);
     GS_LAUNCH();
     k_item_hist<<<g, 256, 0, s>>>(items, deg, n, maxdeg, hist);
     GS_LAUNCH();
@@ -1088,24 +1124,27 @@ int launch_closed_counts_and_sims(int kind, const int64_t* off, const int32_t* a
       if (narrow) {
         GS_TRY((launch_counting_cfg<int32_t, true>(off, adj, deg, odeg, oadj, opos, okey, odp, n, item_off,
                                                order, work, lsh_T, max_od, deferred, work + 3,
-                                               tcnt, tc16, twin, status, ow, tsum, cfg, s, k0, k1)));
+                                               tcnt, tc16, twin, status, ow, tsum, cfg, s, k0, k1, v1)));
       } else {
         GS_TRY((launch_counting_cfg<int64_t, true>(off, adj, deg, odeg, oadj, opos, okey, odp, n, item_off,
                                                order, work, lsh_T, max_od, deferred, work + 3,
-                                               tcnt, nullptr, twin, status, ow, tsum, cfg, s, k0, k1)));
+                                               tcnt, nullptr, twin, status, ow, tsum, cfg, s, k0, k1, v1)));
       }
     } else if (narrow) {
       GS_TRY((launch_counting_cfg<int32_t, false>(off, adj, deg, odeg, oadj, opos, okey, odp, n, item_off,
                                               order, work, lsh_T, max_od, deferred, work + 3, tcnt,
-                                              tc16, twin, status, nullptr, nullptr, cfg, s, k0, k1)));
+                                              tc16, twin, status, nullptr, nullptr, cfg, s, k0, k1, v1)));
     } else {
       GS_TRY((launch_counting_cfg<int64_t, false>(off, adj, deg, odeg, oadj, opos, okey, odp, n, item_off,
                                               order, work, lsh_T, max_od, deferred, work + 3, tcnt,
-                                              nullptr, twin, status, nullptr, nullptr, cfg, s, k0, k1)));
+                                              nullptr, twin, status, nullptr, nullptr, cfg, s, k0, k1, v1)));
     }
   }
   GS_CUDA(cudaEventRecord(e1, s));
-  if (n > 0 && m > 0) {
+  if (n > 0 && m > 0 && counts_out) {
+    k_counts_out<<<wgrid, EXPAND_T, 0, s>>>(off, adj, odp, oadj, opos, tcnt, tc16, n, counts_out);
+    GS_LAUNCH();
+  } else if (n > 0 && m > 0) {
     if (weighted) {
       k_wnorm<<<(unsigned)std::min<int64_t>((n + 255) / 256, sm_count() * 16), 256, 0, s>>>(off, wcsr, n,
                                                                                       norm);

@@ -92,6 +92,7 @@ def load():
         "scan_tuning_load": (i32, [ctypes.c_char_p]),
         "scan_tuning_clear": (i32, []),
         "scan_sort_segments_desc": (i32, [P, P, P, i64, i64, i64, ctypes.c_size_t]),
+        "scan_closed_counts_range": (i32, [P, i64, i64, P, ctypes.c_size_t]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -162,6 +163,22 @@ def sort_segments_desc(keys, ids, seg_off, max_len: int = 0, stream=None):
     _check(load().scan_sort_segments_desc(_ptr(keys), _ptr(ids), _ptr(seg_off), nseg, total,
                                           int(max_len), _stream_handle(stream)),
            "scan_sort_segments_desc")
+
+
+def closed_counts_range(g, v_begin: int, v_end: int, out=None, stream=None):
+    """Triangle counts per arc from the triangles whose middle vertex (degree
+    order) lies in [v_begin, v_end): a rank's share of a sharded count (the
+    shares of a partition of [0, n) sum to |N(u) ∩ N(v)|). g as for
+    ScanIndex.build; out: None (a new uint32 numpy array) or a uint32 array
+    or CUDA tensor of num_arcs entries."""
+    c, keep = _csr_struct(g, device=False)
+    if out is None:
+        out = np.zeros(c.num_arcs, dtype=np.uint32)
+    _check(load().scan_closed_counts_range(ctypes.byref(c), int(v_begin), int(v_end), _ptr(out),
+                                           _stream_handle(stream)),
+           "scan_closed_counts_range")
+    del keep
+    return out
 
 
 def paper_sigma():

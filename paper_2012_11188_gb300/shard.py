@@ -26,9 +26,11 @@ One process per GPU. The CSR is replicated on every rank (R-MAT scale 24 is
 
 Exchanges run over ``torch.distributed`` (NCCL on GPUs, gloo on the CPU):
 an all-reduce of 4 bytes per arc and all-to-alls of 12 bytes per CO entry.
-The sorting and merging of runs are device work; the functions here take
-them as callables (``device_sort`` is the library's segmented sort).
-Not measured on hardware: every run of this project has one GPU.
+The counting, sorting and merging are device work: ``device_counts`` is the
+library's counting restricted to a range of middle vertices, and the
+functions that sort take the sort as a callable (``device_sort`` is the
+library's segmented sort). Not measured on more than one GPU: every run of
+this project has one.
 """
 from __future__ import annotations
 
@@ -174,6 +176,13 @@ def device_sort(keys, ids, seg_off):
     sort_segments_desc(k, v, o)
     keys[:] = k.cpu().numpy()
     ids[:] = v.cpu().numpy()
+
+
+def device_counts(g, v0: int, v1: int, out=None):
+    """Step 2 on this rank's GPU: per-arc triangle counts of the triangles
+    whose middle vertex lies in [v0, v1) (scan_closed_counts_range)."""
+    from .scan import closed_counts_range
+    return closed_counts_range(g, v0, v1, out=out)
 
 
 def allreduce_counts(dist, counts, group=None):

@@ -54,6 +54,20 @@ def test_strerror_and_argument_checks_without_gpu():
     assert lib.scan_set_allocator(None, None, None) == 0
 
 
+def test_range_count_argument_checks_without_gpu():
+    lib = gs.load()
+    import graphgen
+    from paper_2012_11188_gb300.scan import _csr_struct
+    g = graphgen.from_edges(4, [(0, 1), (1, 2), (2, 0), (2, 3)])
+    c, keep = _csr_struct(g, device=False)
+    out = (ctypes.c_uint32 * g.arcs)()
+    assert lib.scan_closed_counts_range(None, 0, 4, out, 0) == -1
+    for v0, v1 in [(-1, 2), (3, 2), (0, 5)]:  # outside [0, n] or reversed
+        assert lib.scan_closed_counts_range(ctypes.byref(c), v0, v1, out, 0) == -1
+    assert lib.scan_closed_counts_range(ctypes.byref(c), 0, 4, None, 0) == -1
+    del keep
+
+
 def test_build_script_targets_sm103a():
     from paper_2012_11188_gb300 import _build
     assert "arch=compute_103a,code=sm_103a" in " ".join(_build.NVCC_FLAGS)

@@ -1,6 +1,7 @@
-"""Device steps of the sharded build: the library's segmented sort sorts and
-merges CO runs exactly like a plain lexicographic sort, and the per-rank runs
-of a one-rank plan on the GPU give the oracle's core order."""
+"""Device steps of the sharded build: the counting restricted to each rank's
+middle vertices adds up to the oracle's counts, the library's segmented sort
+sorts and merges CO runs exactly like a plain lexicographic sort, and the
+per-rank runs of a one-rank plan on the GPU give the oracle's core order."""
 import numpy as np
 import pytest
 
@@ -43,3 +44,35 @@ def test_one_rank_plan_with_device_sorts_is_the_oracle_core_order():
     seg_off, mid, mthr = shard.merge_runs(ids, thr, run_len, shard.device_sort)
     assert np.array_equal(mid, ox.co_id) and np.array_equal(mthr, ox.co_thr)
     assert np.array_equal(seg_off, ox.co_off)
+
+
+@pytest.mark.parametrize("world", [1, 3, 5])
+def test_range_counts_of_a_partition_add_up_to_the_oracle(world):
+    # R-MAT rows longer than 512 (the CTA kernel's items) and short rows (the
+    # warp kernel) fall on both sides of the range bounds
+    g = graphgen.rmat(15, 16, seed=3)
+    want = oracle.closed_counts(g).astype(np.int64) - 2
+    bounds = shard.partition_by_arcs(g.off, world)
+    total = np.zeros(g.arcs, dtype=np.int64)
+    for r in range(world):
+        part = shard.device_counts(g, int(bounds[r]), int(bounds[r + 1]))
+        assert part.dtype == np.uint32 and part.shape == (g.arcs,)
+        total += part
+    assert np.array_equal(total, want)
+
+
+def test_range_counts_device_output_and_empty_range():
+    import torch
+    g = graphgen.sbm(600, 3, 0.2, 0.02, seed=2)
+    host = gs.closed_counts_range(g, 100, 400)
+    dev = torch.zeros(g.arcs, dtype=torch.int32, device="cuda")
+    gs.closed_counts_range(g, 100, 400, out=dev)
+    assert np.array_equal(dev.cpu().numpy().view(np.uint32), host)
+    assert not gs.closed_counts_range(g, 250, 250).any()
+    # both arcs of an edge carry the same count
+    off, adj = g.off, g.adj
+    for u in (0, 150, 599):
+        for i in range(off[u], off[u + 1]):
+            v = adj[i]
+            j = off[v] + np.searchsorted(adj[off[v]:off[v + 1]], u)
+            assert host[i] == host[j]
