@@ -120,8 +120,9 @@ bool is_device_ptr(const void* p) {
 
 size_t build_footprint(int64_t n, int64_t arcs) {
   // index 28 B/arc + 12 B/vertex; build temporaries: oriented lists, counts,
-  // twins (16 B/edge), sort scratch (12 B/arc), item and scan arrays (~24 B/vertex)
-  return (size_t)arcs * 28 + (size_t)n * 12 + (size_t)(arcs / 2) * 16 + (size_t)arcs * 12 +
+  // twins (16 B/edge), sort scratch (a second key/val pair, bucket ids,
+  // samples and group counts: 15 B/arc), item and scan arrays (~24 B/vertex)
+  return (size_t)arcs * 28 + (size_t)n * 12 + (size_t)(arcs / 2) * 16 + (size_t)arcs * 15 +
          (size_t)n * 24 + (1u << 20);
 }
 
