@@ -365,7 +365,7 @@ def lsh_quality(gs, off_d, adj_d, g, stream, timed: bool):
     """LSH index mode on one graph under the paper's protocol (Section 7.3.4,
     Fig. 9): the (mu, eps) of Sigma whose exact clustering has the highest
     modularity is found by the sweep on the exact index, and the LSH index
-    is judged there by the adjusted Rand index of its clustering against the
+    is measured there by the adjusted Rand index of its clustering against the
     exact one and by the fraction of edges whose side of eps changes.
     SimHash 64/256 bits for cosine and k-partition MinHash 64 for Jaccard, at
     the degree threshold T = 128 and at the paper's rule (T = k for cosine,
