@@ -76,3 +76,36 @@ def test_range_counts_device_output_and_empty_range():
             v = adj[i]
             j = off[v] + np.searchsorted(adj[off[v]:off[v + 1]], u)
             assert host[i] == host[j]
+
+
+def middle_vertex_counts(g, v0, v1):
+    """Plain restatement: every triangle, ordered by (degree, id), adds one to
+    both arcs of its three edges when its middle vertex lies in [v0, v1)."""
+    off, adj = g.off, g.adj
+    deg = np.diff(off)
+    pos = {}
+    for u in range(g.n):
+        for i in range(off[u], off[u + 1]):
+            pos[(u, int(adj[i]))] = i
+    nbr = [set(int(x) for x in adj[off[u]:off[u + 1]]) for u in range(g.n)]
+    cnt = np.zeros(g.arcs, dtype=np.int64)
+    for a in range(g.n):
+        for b in nbr[a]:
+            if b <= a:
+                continue
+            for c in nbr[a] & nbr[b]:
+                if c <= b:
+                    continue
+                mid = sorted((a, b, c), key=lambda x: (deg[x], x))[1]
+                if v0 <= mid < v1:
+                    for x, y in ((a, b), (b, c), (a, c)):
+                        cnt[pos[(x, y)]] += 1
+                        cnt[pos[(y, x)]] += 1
+    return cnt
+
+
+def test_range_counts_equal_the_middle_vertex_definition():
+    g = graphgen.sbm(300, 3, 0.25, 0.03, seed=7)
+    for v0, v1 in ((0, 300), (0, 1), (37, 180), (180, 300), (299, 300)):
+        assert np.array_equal(gs.closed_counts_range(g, v0, v1).astype(np.int64),
+                              middle_vertex_counts(g, v0, v1)), (v0, v1)
