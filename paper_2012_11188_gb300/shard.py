@@ -191,6 +191,19 @@ def allreduce_counts(dist, counts, group=None):
     return counts
 
 
+def sharded_counts(dist, g, rank: int, world: int, count_fn=device_counts, group=None):
+    """Steps 1 and 2 on one rank: this rank's vertex range by arcs, its partial
+    counts (count_fn(g, v0, v1): the device counting by default), and the sum
+    over all ranks. Returns (bounds, t) with t[arc] = |N(u) ∩ N(v)| (int64
+    tensor) on every rank."""
+    import torch
+    bounds = partition_by_arcs(g.off, world)
+    part = np.asarray(count_fn(g, int(bounds[rank]), int(bounds[rank + 1])))
+    t = torch.from_numpy(part.astype(np.int64))
+    allreduce_counts(dist, t, group=group)
+    return bounds, t
+
+
 def allgather_v(dist, local, world: int, group=None):
     """Concatenation over ranks of arrays of different lengths (replicas)."""
     import torch

@@ -58,11 +58,9 @@ def run_rank(rank, world, port, q):
         g = graphgen.sbm(400, 4, 0.2, 0.02, seed=1)  # replicated input
         ox = oracle.Index(g)
         deg = np.diff(g.off)
-        bounds = shard.partition_by_arcs(g.off, world)
+        # counts: partial per rank (the device step emulated), one all-reduce
+        bounds, cnt = shard.sharded_counts(dist, g, rank, world, count_fn=owned_triangle_counts)
         v0, v1 = int(bounds[rank]), int(bounds[rank + 1])
-        # counts: partial per rank, one all-reduce
-        cnt = torch.from_numpy(owned_triangle_counts(g, v0, v1))
-        shard.allreduce_counts(dist, cnt)
         counts_ok = bool(np.array_equal(cnt.numpy() + 2, oracle.closed_counts(g)))
         # core order: local runs, one exchange, merge per mu
         mu_b = shard.mu_ranges(deg, world)
