@@ -185,6 +185,19 @@ def device_counts(g, v0: int, v1: int, out=None):
     return closed_counts_range(g, v0, v1, out=out)
 
 
+def sharded_core_order(dist, no_off, no_sim, deg, v0: int, v1: int, rank: int, world: int,
+                       sort_fn=device_sort, group=None):
+    """Step 4 on one rank: the runs of its vertices [v0, v1) (no_off / no_sim:
+    its NO rows, as for local_runs), one exchange by mu range, and the merge
+    of the runs of every mu of its range. Returns (mu_bounds, co_off_local,
+    ids, thr): CO[mu] for mu_bounds[rank] <= mu < mu_bounds[rank + 1]."""
+    mu_b = mu_ranges(deg, world)
+    ids, thr, dest, per_mu = local_runs(no_off, no_sim, deg, v0, v1, mu_b, sort_fn)
+    rid, rthr, run_len = exchange_runs(dist, ids, thr, dest, per_mu, mu_b, rank, world, group=group)
+    seg_off, mid, mthr = merge_runs(rid, rthr, run_len, sort_fn)
+    return mu_b, seg_off, mid, mthr
+
+
 def allreduce_counts(dist, counts, group=None):
     """Sum the per-arc partial counts of all ranks, in place (step 2)."""
     dist.all_reduce(counts, group=group)

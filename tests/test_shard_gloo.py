@@ -62,13 +62,11 @@ def run_rank(rank, world, port, q):
         bounds, cnt = shard.sharded_counts(dist, g, rank, world, count_fn=owned_triangle_counts)
         v0, v1 = int(bounds[rank]), int(bounds[rank + 1])
         counts_ok = bool(np.array_equal(cnt.numpy() + 2, oracle.closed_counts(g)))
-        # core order: local runs, one exchange, merge per mu
-        mu_b = shard.mu_ranges(deg, world)
+        # core order: local runs, one exchange, merge per mu (the device sort
+        # emulated)
         no_off = g.off[v0:v1 + 1].astype(np.int64)
-        ids, thr, dest, per_mu = shard.local_runs(no_off, ox.no_sim, deg, v0, v1, mu_b,
-                                                  sort_segments)
-        rid, rthr, run_len = shard.exchange_runs(dist, ids, thr, dest, per_mu, mu_b, rank, world)
-        seg_off, mid, mthr = shard.merge_runs(rid, rthr, run_len, sort_segments)
+        mu_b, seg_off, mid, mthr = shard.sharded_core_order(dist, no_off, ox.no_sim, deg, v0, v1,
+                                                            rank, world, sort_fn=sort_segments)
         lo, hi = int(mu_b[rank]), int(mu_b[rank + 1])
         a, b = int(ox.co_off[lo - 2]), int(ox.co_off[hi - 2])
         co_ok = bool(np.array_equal(mid, ox.co_id[a:b]) and np.array_equal(mthr, ox.co_thr[a:b])
