@@ -85,7 +85,7 @@ def free_port():
         return s.getsockname()[1]
 
 
-@pytest.mark.parametrize("world", [2, 3])
+@pytest.mark.parametrize("world", [1, 2, 3])
 def test_sharded_core_order_and_counts_equal_single_process(world):
     import torch.multiprocessing as mp
     ctx = mp.get_context("spawn")
